@@ -1,0 +1,196 @@
+"""Pins of the oracle's solves, w, roots, multi-boson action and log-det factors.
+
+* Eq. (detD): ln|det D| = ln|det W_1| + ln|det D_Lambda1|
+  + sum_a [ln|det D_Omega0^a| - ln|det D_Phi1^a|], every factor a dense LU of
+  an independently assembled matrix, on 4^4 and 6x4^3 (Sec. 3).
+* Green's-function identity: for eta on dPi and psi = D^{-1} eta (one global
+  direct solve), W_1 psi|dPi equals the block / frame solves of eta.
+* w as a vector operation equals w as an assembled dense matrix.
+* kappa = 0 gives w = 0 and S = sum_k |u_k|^2 |chi_k|^2.
+* Block locality of S^a and of S^r (Sec. 4, Eqs. localMB, globalMB).
+* Gauge invariance of S.
+* Roots: the polynomial identity z c_N prod (z - z_k) = 1 - R_{N+1}(z) with
+  Chebyshev R evaluated by numpy's Chebyshev module; c = 0 gives roots of unity.
+* The oracle's iterative solver agrees with a sparse direct LU.
+"""
+
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as C
+
+from paper_2211_06902_gb300 import synth
+from oracle.dd import Oracle, bicgstab, field_roots, roots
+from oracle.geometry import Decomposition, uniform_cores
+from oracle.lattice import dirac_matrix, gauge_transform_links
+
+L44 = (4, 4, 4, 4)
+L6444 = (6, 4, 4, 4)
+CORES6444 = [[(0, 1), (3, 4)]] + [[(0, 0), (2, 2)]] * 3
+
+
+def _slog_sum(pairs, signs=(1,)):
+    return sum(p[1] for p in pairs)
+
+
+@pytest.mark.parametrize("L,cores", [(L44, uniform_cores(L44, 1, 1)), (L6444, CORES6444)])
+def test_det_factorization_identity(L, cores):
+    U = synth.gauge_field(L, 0.3, 1)
+    o = Oracle(U, 0.13, Decomposition(L, cores))
+    f = o.logdet_factors()
+    rhs = f["W1"][1] + f["Lambda1"][1] + sum(x[1] for x in f["Omega"]) - sum(x[1] for x in f["Phi"])
+    assert abs(f["D"][1] - rhs) < 1e-10
+    sign = f["W1"][0] * f["Lambda1"][0] * np.prod([x[0] for x in f["Omega"]]) \
+        / np.prod([x[0] for x in f["Phi"]])
+    assert abs(sign - f["D"][0]) < 1e-10
+    assert abs(f["D"][0].imag) < 1e-12                  # det D real (gamma_5-hermiticity)
+
+
+def test_det_identity_fails_for_a_wrong_w():
+    """A plausible mistake (dropping the frame solve) breaks Eq. (detD)."""
+    U = synth.gauge_field(L44, 0.3, 1)
+    g = Decomposition(L44, uniform_cores(L44, 1, 1))
+    o = Oracle(U, 0.13, g)
+    w = o.w_matrix()
+    dpi = g.sites(g.dPi)
+    isC = np.repeat(g.C.ravel()[dpi], 12)
+    w_bad = w.copy()
+    w_bad[np.ix_(isC, ~isC)] = 0
+    f = o.logdet_factors()
+    rhs_bad = np.linalg.slogdet(np.eye(len(w)) - w_bad)[1] + f["Lambda1"][1] \
+        + sum(x[1] for x in f["Omega"]) - sum(x[1] for x in f["Phi"])
+    assert abs(f["D"][1] - rhs_bad) > 1e-3
+
+
+def test_w_vector_equals_w_matrix():
+    U = synth.gauge_field(L44, 0.4, 2)
+    g = Decomposition(L44, uniform_cores(L44, 1, 1))
+    o = Oracle(U, 0.13, g)
+    chi = synth.complex_gaussian(2, synth.TAG_CHI, L44 + (4, 3)) * g.dPi[..., None, None]
+    dpi = g.sites(g.dPi)
+    wv = o.apply_w(chi).reshape(-1, 12)[dpi].ravel()
+    wm = o.w_matrix() @ chi.reshape(-1, 12)[dpi].ravel()
+    assert np.linalg.norm(wv - wm) / np.linalg.norm(wm) < 1e-11
+    out = o.apply_w(chi)
+    assert np.all(out[~g.dPi] == 0)
+
+
+def test_greens_function_identity():
+    L, cores = L6444, CORES6444
+    U = synth.gauge_field(L, 0.3, 3)
+    g = Decomposition(L, cores)
+    o = Oracle(U, 0.13, g)
+    V = int(np.prod(L))
+    eta = synth.complex_gaussian(3, synth.TAG_RHS, L + (4, 3)) * g.dPi[..., None, None]
+    from scipy.sparse.linalg import splu
+    lu = splu(dirac_matrix(U, 0.13, np.arange(V)).tocsc())
+    psi = lu.solve(eta.reshape(-1)).reshape(eta.shape) * g.dPi[..., None, None]
+    lhs = o.apply_W1(psi)
+    for a in range(g.nblocks):
+        rhs = o.omega_solver(a).solve_field(eta * g.omega_mask[a][..., None, None])
+        bm = g.B_mask[a]
+        assert np.linalg.norm(lhs[bm] - rhs[bm]) < 1e-11 * np.linalg.norm(rhs[bm])
+    rhs = o.frame_solver().solve_field(eta * g.Lambda1[..., None, None])
+    assert np.linalg.norm(lhs[g.C] - rhs[g.C]) < 1e-11 * np.linalg.norm(rhs[g.C])
+
+
+def test_kappa_zero_action():
+    U = synth.gauge_field(L44, 0.3, 1)
+    g = Decomposition(L44, uniform_cores(L44, 1, 1))
+    o = Oracle(U, 0.0, g)
+    u = field_roots(4, 0.5)
+    chis = [synth.complex_gaussian(1, 10 + k, L44 + (4, 3)) * g.dPi[..., None, None]
+            for k in range(2)]
+    S, sa, sr = o.multiboson_action(u, chis)
+    expect = sum(abs(uk) ** 2 * np.sum(np.abs(c) ** 2) for uk, c in zip(u, chis))
+    assert abs(S - expect) < 1e-12 * expect
+    assert abs(S - (sum(sa) + sr)) < 1e-12 * S
+
+
+def test_block_locality_of_the_action():
+    """A link inside Lambda0^a changes only S^a; a link inside the frame changes
+    S^r and only the S^b whose framed block touches it (Sec. 4)."""
+    L = (8,) * 4
+    g = Decomposition(L, uniform_cores(L, 3, 1))
+    U = synth.gauge_field(L, 0.3, 1)
+    u = field_roots(4, 0.5)[:1]
+    chi = [synth.complex_gaussian(1, synth.TAG_CHI, L + (4, 3)) * g.dPi[..., None, None]]
+    S0, sa0, sr0 = Oracle(U, 0.13, g).multiboson_action(u, chi)
+    assert abs(S0 - (sum(sa0) + sr0)) < 1e-12 * S0
+    # link U_1(x) with x and x+1^ in the core of block 5
+    a = 5
+    x = tuple(b[0] for b in g.blocks[a].core)
+    U1 = U.copy()
+    U1[x + (1,)] = synth.gauge_field((1, 1, 1, 1), 0.9, 77)[0, 0, 0, 0, 0]
+    S1, sa1, sr1 = Oracle(U1, 0.13, g).multiboson_action(u, chi)
+    assert sa1[a] != sa0[a]
+    assert all(sa1[b] == sa0[b] for b in range(g.nblocks) if b != a)
+    assert sr1 == sr0
+    # link U_2(y) with y and y+2^ in the frame Lambda1
+    ys = np.argwhere(g.Lambda1 & np.roll(g.Lambda1, -1, axis=2))
+    y = tuple(int(v) for v in ys[0])
+    U2 = U.copy()
+    U2[y + (2,)] = synth.gauge_field((1, 1, 1, 1), 0.9, 78)[0, 0, 0, 0, 0]
+    S2, sa2, sr2 = Oracle(U2, 0.13, g).multiboson_action(u, chi)
+    assert sr2 != sr0
+    yp = list(y)
+    yp[2] = (yp[2] + 1) % L[2]
+    for b in range(g.nblocks):
+        touches = g.omega_mask[b][y] or g.omega_mask[b][tuple(yp)]
+        if not touches:
+            assert sa2[b] == sa0[b]
+
+
+def test_gauge_invariance_of_the_action():
+    L = L6444
+    g = Decomposition(L, CORES6444)
+    U = synth.gauge_field(L, 0.3, 2)
+    gx = synth.gauge_transform(9, L)
+    u = field_roots(4, 0.5)
+    chis = [synth.complex_gaussian(2, 20 + k, L + (4, 3)) * g.dPi[..., None, None] for k in range(2)]
+    S, sa, sr = Oracle(U, 0.13, g).multiboson_action(u, chis)
+    gchis = [np.einsum("...ab,...sb->...sa", gx, c) for c in chis]
+    Sg, sag, srg = Oracle(gauge_transform_links(U, gx), 0.13, g).multiboson_action(u, gchis)
+    assert abs(S - Sg) < 1e-11 * S
+    assert np.allclose(sa, sag, rtol=1e-10)
+
+
+@pytest.mark.parametrize("N,c", [(4, 0.5), (12, 0.3), (24, 0.7), (6, 0.0)])
+def test_roots_polynomial_identity(N, c):
+    u = roots(N, c)
+    z_k = 1 - u
+    rng = np.random.default_rng(N)
+    for z in rng.normal(size=4) + 1j * rng.normal(size=4):
+        if c == 0:
+            rhs = 1 - (1 - z) ** (N + 1)                    # limit c -> 0
+            lead = -(-1.0) ** (N + 1)
+        else:
+            coef = np.zeros(N + 2)
+            coef[N + 1] = 1
+            rhs = 1 - C.chebval((1 - z) / c, coef) / C.chebval(1 / c, coef)
+            lead = -(2.0 ** N) * (-1.0 / c) ** (N + 1) / C.chebval(1 / c, coef)
+        lhs = z * lead * np.prod(z - z_k)
+        assert abs(lhs - rhs) < 1e-10 * max(1, abs(rhs))
+
+
+def test_roots_special_cases():
+    u = roots(6, 0.0)
+    assert np.allclose(u, np.exp(2j * np.pi * np.arange(1, 7) / 7))
+    u = roots(8, 0.4)
+    assert np.allclose(u[::-1], np.conj(u))                 # u_{N+1-k} = conj(u_k)
+    assert len(field_roots(8, 0.4)) == 4
+    with pytest.raises(ValueError):
+        field_roots(5, 0.4)
+
+
+def test_iterative_solver_matches_direct_lu():
+    L = (4, 4, 4, 4)
+    U = synth.gauge_field(L, 0.5, 6)
+    V = int(np.prod(L))
+    sites = np.arange(0, V, 2)
+    M = dirac_matrix(U, 0.13, sites)
+    b = synth.complex_gaussian(6, synth.TAG_RHS, (M.shape[0],))
+    from scipy.sparse.linalg import splu
+    xd = splu(M.tocsc()).solve(b)
+    xi, rel = bicgstab(lambda v: M @ v, b, 1e-13)
+    assert rel < 1e-12
+    assert np.linalg.norm(xi - xd) < 1e-11 * np.linalg.norm(xd)
