@@ -1,0 +1,206 @@
+/*
+ * dd4d.h - C ABI of libdd4d.so, the GB300 (sm_103a) implementation of the
+ * data-parallel hot path of the four-dimensional overlapping domain
+ * decomposition of the lattice Wilson-Dirac operator and of the factorization
+ * of det D (Saccardi & Giusti, "Four-dimensional domain decomposition for the
+ * factorization of the fermion determinant", Lattice 2022).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * - Every call returns a dd_status; DD_OK is 0.  dd_strerror() names a code,
+ *   dd_last_error() gives the message of the last failure on a context.  No
+ *   C++ exception crosses this interface.
+ * - Lattice: extents L[4], x0 is time.  Global site index is lexicographic
+ *   with x3 fastest: ((x0*L1 + x1)*L2 + x2)*L3 + x3.  Boundary conditions:
+ *   periodic in x1..x3; the hop across x0 = L0-1 <-> 0 is multiplied by
+ *   time_bc (+1 periodic, -1 antiperiodic).
+ * - Spinor fields are complex128 (interleaved re, im doubles) with 12
+ *   components per site, spin-major: component = 3*spin + colour, in the
+ *   chiral basis gamma_0 = [[0,-1],[-1,0]], gamma_k = [[0,-i s_k],[i s_k,0]],
+ *   gamma_5 = diag(1,1,-1,-1).
+ * - Dirac operator (paper Sec. 1 and 3; Wilson, kappa normalisation, r = 1):
+ *   (D psi)(x) = psi(x) - kappa sum_mu [(1-gamma_mu) U_mu(x) psi(x+mu)
+ *                                     + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu)].
+ *   Restriction to a site set X: D_X = P_X D P_X (hops leaving X dropped,
+ *   Dirichlet boundary).
+ * - Pointers to fields may be device pointers or host pointers (pageable or
+ *   pinned); the library detects which.  With host pointers the call copies
+ *   in and out itself and returns after the result is on the host.  With
+ *   device pointers the call is asynchronous on `stream` unless stated.
+ *   Callers keep ownership of every buffer they pass; the context owns the
+ *   gauge field, the geometry tables and its work space.
+ * - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef DD4D_H
+#define DD4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DD_OK = 0,
+  DD_EINVAL = 1,    /* invalid argument (size, id, layout, state) */
+  DD_ENOMEM = 2,    /* device or host allocation failed */
+  DD_ENOCONV = 3,   /* a Krylov solve stopped before reaching its tolerance */
+  DD_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  DD_ENAN = 5,      /* NaN or Inf in an input or a residual */
+  DD_ECUDA = 6      /* a CUDA runtime call failed */
+} dd_status;
+
+typedef enum { DD_F64 = 0, DD_F32 = 1, DD_BF16 = 2 } dd_prec;
+
+/* Site sets on which D can be restricted (paper Sec. 2). */
+typedef enum {
+  DD_DOMAIN_FULL = 0,    /* the whole lattice                                   */
+  DD_DOMAIN_OMEGA = 1,   /* framed block Omega0^a = Lambda0^a u Phi1^a          */
+  DD_DOMAIN_PHI = 2,     /* its frame piece Phi1^a = Omega0^a \ Lambda0^a       */
+  DD_DOMAIN_LAMBDA1 = 3  /* the inactive connected frame Lambda1                */
+} dd_domain;
+
+/* Site sets that can be listed with dd_geom_sites(). */
+typedef enum {
+  DD_SET_DPI = 0,        /* dPi: union of the block-boundary hyperplanes        */
+  DD_SET_B = 1,          /* dLambda0^a of one block (block id required)          */
+  DD_SET_C = 2,          /* dPi1 = dPi \ dLambda0                               */
+  DD_SET_OMEGA = 3,      /* Omega0^a of one block, in the block's field order    */
+  DD_SET_PHI = 4,        /* Phi1^a of one block, in its field order              */
+  DD_SET_LAMBDA1 = 5     /* Lambda1 in its field order                           */
+} dd_set;
+
+typedef struct dd_ctx dd_ctx;
+
+typedef struct {
+  int nblocks;
+  int n_dpi;        /* |dPi|        */
+  int n_B;          /* |dLambda0|   */
+  int n_C;          /* |dPi1|       */
+  int n_E;          /* |Lambda1 \ dPi1| */
+  int n_A;          /* |Lambda0 \ dLambda0| (bulk of the blocks) */
+  int n_lambda1;    /* |Lambda1|    */
+  int max_omega;    /* largest |Omega0^a| */
+  int max_phi;      /* largest |Phi1^a|   */
+} dd_geom_info;
+
+typedef struct {
+  double tol;          /* stop when |b - D x| <= tol |b| per system (e.g. 1e-10) */
+  int maxiter;         /* Krylov iterations cap per system (inner ones for mixed) */
+  dd_prec inner_prec;  /* DD_F64: plain FP64 BiCGstab; DD_F32 / DD_BF16: inner
+                          solve at that precision with FP64 defect correction */
+  double inner_tol;    /* relative reduction per inner solve (mixed only), e.g. 1e-5 */
+  int max_outer;       /* defect-correction cycles cap (mixed only) */
+  int check_every;     /* iterations between host convergence checks (>= 1) */
+} dd_solve_params;
+
+typedef struct {
+  int systems;         /* number of (block, rhs) systems solved */
+  int converged;       /* how many reached tol */
+  int max_iters;       /* largest Krylov iteration count over systems (all cycles) */
+  int outer_cycles;    /* defect-correction cycles run (1 for plain FP64) */
+  double max_relres;   /* largest final |b - D x|/|b|, FP64, over systems */
+  double seconds;      /* device time of the call (CUDA events) */
+} dd_solve_stats;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Creates a context for a lattice of extents L (each even, >= 2), time
+ * boundary sign time_bc (+1 or -1) and hopping parameter kappa.  Uses the
+ * current CUDA device. DD_EINVAL on bad sizes. */
+dd_status dd_create(dd_ctx** ctx, const int L[4], int time_bc, double kappa);
+dd_status dd_destroy(dd_ctx* ctx);
+const char* dd_strerror(dd_status s);
+const char* dd_last_error(const dd_ctx* ctx);
+dd_status dd_set_kappa(dd_ctx* ctx, double kappa);
+
+/* Gauge links U_mu(x) in SU(3) (paper Sec. 1).  Host buffer, layout
+ * [site (global index)][mu 0..3][3][3] complex128 (row-major 3x3).  The
+ * stored links are not modified; the time boundary sign is applied by the
+ * operator.  Rebuilds every gathered per-domain copy.  Synchronous. */
+dd_status dd_gauge_upload(dd_ctx* ctx, const double* U_host);
+
+/* ---- geometry (paper Sec. 2) ------------------------------------------
+ * Per direction mu a sorted list of core intervals [lo, hi] (inclusive,
+ * 0 <= lo <= hi < L_mu) separated by at least one frame site (periodic);
+ * at least two per direction.  ncores[mu] entries for direction mu are
+ * taken in turn from core_lo / core_hi (direction 0 first).  Blocks
+ * Lambda0^a are the products of one interval per direction, numbered
+ * lexicographically in the interval indices with direction 3 fastest.
+ * Omega0^a spans the sites strictly between the neighbouring intervals'
+ * hyperplanes; its field order is local lexicographic (x3 fastest) starting
+ * at the site after the previous interval.  DD_EINVAL on an invalid list. */
+dd_status dd_set_geometry(dd_ctx* ctx, const int ncores[4], const int* core_lo,
+                          const int* core_hi, dd_geom_info* info);
+
+/* Global site indices of a set, in the order the library uses for fields on
+ * it.  `block` selects the block for per-block sets (ignored otherwise).
+ * `out` is a host array of at least *count entries; pass out = NULL to get
+ * only *count.  dPi, dPi1 and Lambda1 are in increasing global order. */
+dd_status dd_geom_sites(dd_ctx* ctx, dd_set set, int block, int* out, int* count);
+
+/* Block descriptor: origin (first site of Omega0^a per direction), the side
+ * of Omega0^a and the core interval, all per direction. */
+dd_status dd_geom_block(dd_ctx* ctx, int block, int origin[4], int side[4],
+                        int core_lo[4], int core_hi[4]);
+
+/* ---- restricted Wilson stencil (paper Sec. 3, D_X) -----------------------
+ * out = D_X in for nblk domains of kind `kind` (block ids `ids`, host array;
+ * ignored for FULL and LAMBDA1, which take nblk = 1) and nrhs fields each.
+ * in/out layout: [blk][rhs][site in the domain's field order][12] complex128.
+ * prec selects the storage/arithmetic of the stencil (FP64, or FP32 / BF16
+ * storage with FP32 arithmetic). */
+dd_status dd_apply_D_block(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
+                           int nrhs, const double* in, double* out, dd_prec prec,
+                           void* stream);
+
+/* ---- batched block solves (paper Sec. 3, D_Omega^-1, D_Phi^-1, D_Lambda1^-1)
+ * x = D_X^{-1} b for every (block, rhs) pair, with even-odd (site parity)
+ * preconditioning and BiCGstab; plain FP64, or an FP32/BF16 inner solve with
+ * FP64 defect correction (FP64 residuals, norms and updates).  Layout as for
+ * dd_apply_D_block.  Synchronises `stream` (the host polls convergence).
+ * Returns DD_ENOCONV (with stats filled) if some system missed params->tol. */
+dd_status dd_solve_blocks(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
+                          int nrhs, const double* b, double* x,
+                          const dd_solve_params* params, dd_solve_stats* stats,
+                          void* stream);
+
+/* ---- the operator w (paper Sec. 3, Eqs. Wz and offdiagW1) ----------------
+ * For n_f fields chi on dPi (layout [f][dPi site in dd_geom_sites order][12]):
+ *   (w chi)_{dLambda0^a} = -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi
+ *   (w chi)_{dPi1}       = -P_{dPi1} D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi
+ * i.e. W_1 = 1 - w, W_u = u - w.  Solves to params->tol.  Synchronises. */
+dd_status dd_apply_w(dd_ctx* ctx, int n_f, const double* chi, double* w_chi,
+                     const dd_solve_params* params, void* stream);
+
+/* ---- multi-boson action (paper Sec. 4, Eqs. MBaction, localMB, globalMB)
+ * S = sum_k |(u_k - w) chi_k|^2 = sum_a S^a + S^r with
+ * S^a = sum_k |P_{dLambda0^a}(u_k - w)chi_k|^2, S^r = sum_k |P_{dPi1}(...)|^2.
+ * u: 2*n_f doubles (re, im); chi as for dd_apply_w.  S, S_r: host doubles;
+ * S_block: host array of nblocks doubles or NULL.  FP64 reductions in a fixed
+ * order (deterministic).  Synchronises. */
+dd_status dd_multiboson_action(dd_ctx* ctx, int n_f, const double* u, const double* chi,
+                               double* S, double* S_block, double* S_r,
+                               const dd_solve_params* params, void* stream);
+
+/* ---- roots (paper Sec. 4) --------------------------------------------------
+ * u_k = 1 - z_k = cos(2 pi k/(N+1)) + i sqrt(1-c^2) sin(2 pi k/(N+1)),
+ * k = 1..N/2: the roots that carry the N/2 multi-boson fields (conjugates
+ * u_{N+1-k} pair with them).  N even >= 2, 0 <= c < 1.  u: host, N doubles. */
+dd_status dd_roots(int N, double c, double* u);
+
+/* ---- kernel timing -----------------------------------------------------
+ * With timing on, the library brackets every launch of its stencil kernels
+ * with CUDA events on the launching stream.  dd_timing_get returns, for
+ * kernel class `which` (0: FP64 hop, 1: FP32 hop, 2: BF16 hop), the summed
+ * device time in ms, the number of launches and the summed algorithmic
+ * bytes, then clears the record.  Synchronises. */
+dd_status dd_timing_enable(dd_ctx* ctx, int on);
+dd_status dd_timing_get(dd_ctx* ctx, int which, double* ms, long long* launches,
+                        double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD4D_H */

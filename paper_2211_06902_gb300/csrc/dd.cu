@@ -1,0 +1,401 @@
+// The operator w (paper Sec. 3, Eqs. Wz and offdiagW1) and the multi-boson
+// action (paper Sec. 4, Eqs. MBaction, localMB, globalMB).
+//
+//   (w chi)_{dLambda0^a} = -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi
+//   (w chi)_{dPi1}       = -P_{dPi1} D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi
+//   S = sum_k |(u_k - w) chi_k|^2 = sum_a S^a + S^r
+//
+// Boundary injection (D_{X, ext} chi: the hops from the sites just outside X
+// into X) is a gather from chi on dPi with the global FP64 links; the block
+// and frame solves go through the batched solver; extraction and the FP64
+// reductions follow in fixed order (deterministic).
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "spinor.cuh"
+
+namespace dd {
+
+namespace {
+
+struct InjectArgs {
+  const double2* U;        // global links [V][4][9], time sign folded
+  const double2* chi;      // [f][n_dpi][12]
+  const int* dpi_pos;      // [V] -> dPi index or -1
+  double2* src;            // caller-layout sources of the batch
+  int L[4];
+  int n_dpi, n_f;
+  double kappa;
+};
+
+__device__ __forceinline__ void site_coords(long long s, const int* dims, int* x) {
+  x[3] = (int)(s % dims[3]);
+  x[2] = (int)((s / dims[3]) % dims[2]);
+  x[1] = (int)((s / ((long long)dims[3] * dims[2])) % dims[1]);
+  x[0] = (int)(s / ((long long)dims[3] * dims[2] * dims[1]));
+}
+
+__device__ __forceinline__ int glob_index(const int* x, const int* L) {
+  return ((x[0] * L[1] + x[1]) * L[2] + x[2]) * L[3] + x[3];
+}
+
+// Adds the hop from global site y (direction dir seen from x) into acc.
+__device__ void add_exterior_hop(double2 (&acc)[12], int dir, int gx, int gy, const InjectArgs& a,
+                                 int f) {
+  const int mu = dir & 3;
+  const bool fwd = dir < 4;
+  const int q = a.dpi_pos[gy];
+  if (q < 0) return;     // cannot happen for a valid geometry (exterior sites lie on dPi)
+  double2 psi[12];
+  const double2* c = a.chi + ((long long)f * a.n_dpi + q) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) psi[k] = c[k];
+  double2 U[9];
+  const double2* l = a.U + (long long)(fwd ? gx : gy) * 36 + mu * 9;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) U[k] = l[k];
+  switch (dir) {
+    case 0: hop_dir<0, true>(acc, psi, U); break;
+    case 1: hop_dir<1, true>(acc, psi, U); break;
+    case 2: hop_dir<2, true>(acc, psi, U); break;
+    case 3: hop_dir<3, true>(acc, psi, U); break;
+    case 4: hop_dir<0, false>(acc, psi, U); break;
+    case 5: hop_dir<1, false>(acc, psi, U); break;
+    case 6: hop_dir<2, false>(acc, psi, U); break;
+    default: hop_dir<3, false>(acc, psi, U); break;
+  }
+}
+
+// Sources for the Omega blocks: s(x) = D_{Omega, ext} chi, x in the box.
+// grid: (ceil(max_sites/128), nblk * n_f)
+__global__ void k_inject_omega(BatchDev bd, InjectArgs a) {
+  const int sys = blockIdx.y;
+  const int j = sys / a.n_f, f = sys % a.n_f;
+  const DomInst* d = bd.inst_tab + bd.inst[j];
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= d->nsites) return;
+  int dims[4] = {d->dims[0], d->dims[1], d->dims[2], d->dims[3]};
+  int x[4];
+  site_coords(l, dims, x);
+  int g[4];
+  for (int m = 0; m < 4; ++m) g[m] = (d->origin[m] + x[m]) % a.L[m];
+  const int gx = glob_index(g, a.L);
+  double2 acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = make_double2(0.0, 0.0);
+  for (int dir = 0; dir < 8; ++dir) {
+    const int mu = dir & 3, step = dir < 4 ? 1 : -1;
+    const int y = x[mu] + step;
+    if (y >= 0 && y < dims[mu]) continue;           // hop stays inside the box
+    int gy[4] = {g[0], g[1], g[2], g[3]};
+    gy[mu] = (g[mu] + step + a.L[mu]) % a.L[mu];
+    add_exterior_hop(acc, dir, gx, glob_index(gy, a.L), a, f);
+  }
+  double2* out = a.src + bd.uoff[sys] + 12 * l;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[k] = make_double2(-a.kappa * acc[k].x, -a.kappa * acc[k].y);
+}
+
+// Sources for the frame: t(x) = D_{Lambda1, dLambda0} chi, x in Lambda1 (field order).
+__global__ void k_inject_frame(const int* __restrict__ l1_glob, int n_l1,
+                               const unsigned char* __restrict__ in_l1, InjectArgs a) {
+  const int f = blockIdx.y;
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_l1) return;
+  const int gx = l1_glob[k];
+  int g[4];
+  site_coords(gx, a.L, g);
+  double2 acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = make_double2(0.0, 0.0);
+  for (int dir = 0; dir < 8; ++dir) {
+    const int mu = dir & 3, step = dir < 4 ? 1 : -1;
+    int gy[4] = {g[0], g[1], g[2], g[3]};
+    gy[mu] = (g[mu] + step + a.L[mu]) % a.L[mu];
+    const int y = glob_index(gy, a.L);
+    if (in_l1[y]) continue;                           // neighbour inside the frame
+    add_exterior_hop(acc, dir, gx, y, a, f);
+  }
+  double2* out = a.src + ((long long)f * n_l1 + k) * 12;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) out[c] = make_double2(-a.kappa * acc[c].x, -a.kappa * acc[c].y);
+}
+
+// (w chi) on dLambda0: -x at the block-boundary sites; on dPi1: -y.  For
+// every listed site: its system (block, or 0 for the frame), its offset
+// inside the system's caller-layout solution and its dPi index.
+__global__ void k_extract(const int* __restrict__ sys_blk, const long long* __restrict__ loc,
+                          const int* __restrict__ dpi_idx, int n, int n_f, int n_dpi,
+                          const long long* __restrict__ uoff, const double2* __restrict__ sol,
+                          double2* __restrict__ w) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (k >= n) return;
+  const int blk = sys_blk ? sys_blk[k] : 0;
+  const double2* s = sol + uoff[(long long)blk * n_f + f] + loc[k];
+  double2* o = w + ((long long)f * n_dpi + dpi_idx[k]) * 12;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) o[c] = make_double2(-s[c].x, -s[c].y);
+}
+
+// S^a (one CTA per block) and partial S^r over the dPi1 sites.
+__global__ void k_action_blocks(const int* __restrict__ grp_begin, const int* __restrict__ dpi_idx,
+                                int n_f, int n_dpi, const double2* __restrict__ u,
+                                const double2* __restrict__ chi, const double2* __restrict__ w,
+                                double* out) {
+  __shared__ double red[32];
+  const int a = blockIdx.x;
+  double acc[1] = {0.0};
+  for (int f = 0; f < n_f; ++f) {
+    const double2 uk = u[f];
+    for (int k = grp_begin[a] + threadIdx.x; k < grp_begin[a + 1]; k += blockDim.x) {
+      const long long base = ((long long)f * n_dpi + dpi_idx[k]) * 12;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const double2 x = chi[base + c], y = w[base + c];
+        const double re = uk.x * x.x - uk.y * x.y - y.x;
+        const double im = uk.x * x.y + uk.y * x.x - y.y;
+        acc[0] += re * re + im * im;
+      }
+    }
+  }
+  block_reduce<1>(acc, red);
+  if (threadIdx.x == 0) out[a] = acc[0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+struct WPlan {           // host-built gather lists, one per context
+  int n_l1 = 0;
+  int* d_l1_glob = nullptr;          // [n_l1] global site of Lambda1 field index
+  unsigned char* d_in_l1 = nullptr;  // [V]
+  int* d_b_blk = nullptr;            // [n_B] block of the B site (grouped by block)
+  long long* d_b_loc = nullptr;      // [n_B] 12 * field position inside Omega0^b
+  int* d_b_dpi = nullptr;            // [n_B] dPi index
+  int* d_b_grp = nullptr;            // [nblocks + 1] group boundaries
+  long long* d_c_loc = nullptr;      // [n_C] 12 * field position inside Lambda1
+  int* d_c_dpi = nullptr;            // [n_C]
+  int* d_c_grp = nullptr;            // C sites split into chunks for the S^r partials
+  int n_cgrp = 0;
+};
+
+void free_plan(dd_ctx* c) {
+  WPlan* P = (WPlan*)c->wplan;
+  if (!P) return;
+  dfree(P->d_l1_glob); dfree(P->d_in_l1); dfree(P->d_b_blk); dfree(P->d_b_loc);
+  dfree(P->d_b_dpi); dfree(P->d_b_grp); dfree(P->d_c_loc); dfree(P->d_c_dpi); dfree(P->d_c_grp);
+  delete P;
+  c->wplan = nullptr;
+}
+
+static dd_status build_plan(dd_ctx* c, WPlan** out) {
+  if (c->wplan) {
+    *out = (WPlan*)c->wplan;
+    return DD_OK;
+  }
+  WPlan* P = new WPlan();
+  c->wplan = P;
+  const int V = c->V, nb = (int)c->blocks.size();
+  dd_status e;
+  const Instance& l1 = c->inst[c->lambda1];
+  std::vector<int> l1_glob(l1.d.nsites);
+  for (int k = 0; k < l1.d.nsites; ++k) l1_glob[l1.h_fmap[k]] = l1.h_glob[k];
+  std::vector<unsigned char> in_l1(V, 0);
+  std::vector<int> l1_pos(V, -1);
+  for (int k = 0; k < (int)l1_glob.size(); ++k) {
+    in_l1[l1_glob[k]] = 1;
+    l1_pos[l1_glob[k]] = k;
+  }
+  std::vector<int> b_blk, b_dpi, b_grp(1, 0);
+  std::vector<long long> b_loc;
+  std::vector<int> fpos(V, -1);
+  for (int b = 0; b < nb; ++b) {
+    const Instance& om = c->inst[c->omega0 + b];
+    for (int k = 0; k < om.d.nsites; ++k) fpos[om.h_glob[k]] = om.h_fmap[k];
+    for (int s : c->B_of_block[b]) {
+      b_blk.push_back(b);
+      b_loc.push_back(12LL * fpos[s]);
+      b_dpi.push_back(c->dpi_pos[s]);
+    }
+    for (int k = 0; k < om.d.nsites; ++k) fpos[om.h_glob[k]] = -1;
+    b_grp.push_back((int)b_loc.size());
+  }
+  std::vector<long long> c_loc;
+  std::vector<int> c_dpi, c_grp(1, 0);
+  for (int s : c->C_sites) {
+    c_loc.push_back(12LL * l1_pos[s]);
+    c_dpi.push_back(c->dpi_pos[s]);
+  }
+  const int CG = 4096;
+  for (int k = CG; k < (int)c_loc.size(); k += CG) c_grp.push_back(k);
+  c_grp.push_back((int)c_loc.size());
+  auto up = [&](auto& vec, auto** dst) -> dd_status {
+    size_t bytes = sizeof(vec[0]) * std::max<size_t>(1, vec.size());
+    dd_status st = dalloc(c, (void**)dst, bytes);
+    if (st != DD_OK) return st;
+    if (!vec.empty())
+      cudaMemcpy(*dst, vec.data(), sizeof(vec[0]) * vec.size(), cudaMemcpyHostToDevice);
+    return DD_OK;
+  };
+  if ((e = up(l1_glob, &P->d_l1_glob)) || (e = up(in_l1, &P->d_in_l1)) ||
+      (e = up(b_blk, &P->d_b_blk)) || (e = up(b_loc, &P->d_b_loc)) || (e = up(b_dpi, &P->d_b_dpi)) ||
+      (e = up(b_grp, &P->d_b_grp)) || (e = up(c_loc, &P->d_c_loc)) || (e = up(c_dpi, &P->d_c_dpi)) ||
+      (e = up(c_grp, &P->d_c_grp))) {
+    free_plan(c);
+    return e;
+  }
+  P->n_l1 = (int)l1_glob.size();
+  P->n_cgrp = (int)c_grp.size() - 1;
+  *out = P;
+  return DD_OK;
+}
+
+// w chi for n_f fields (device pointers, caller layout on dPi).
+static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi,
+                             const dd_solve_params* prm, cudaStream_t s) {
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  const int nb = (int)c->blocks.size();
+  std::vector<int> ids(nb);
+  for (int b = 0; b < nb; ++b) ids[b] = b;
+  Batch *ob, *fb;
+  dd_status e;
+  if ((e = get_batch(c, DD_DOMAIN_OMEGA, ids.data(), nb, n_f, &ob)) != DD_OK) return e;
+  if ((e = get_batch(c, DD_DOMAIN_LAMBDA1, nullptr, 1, n_f, &fb)) != DD_OK) return e;
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  void *src_o, *sol_o, *src_f, *sol_f;
+  if ((e = workspace(c, 40, 16ULL * ob->user_tot, &src_o)) ||
+      (e = workspace(c, 41, 16ULL * ob->user_tot, &sol_o)) ||
+      (e = workspace(c, 42, 16ULL * fb->user_tot, &src_f)) ||
+      (e = workspace(c, 43, 16ULL * fb->user_tot, &sol_f)))
+    return e;
+  InjectArgs a;
+  a.U = c->d_U;
+  a.chi = (const double2*)chi;
+  a.dpi_pos = c->d_dpi_pos;
+  for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
+  a.n_dpi = c->info.n_dpi;
+  a.n_f = n_f;
+  a.kappa = c->kappa;
+  // Omega sources and solves
+  a.src = (double2*)src_o;
+  BatchDev bd = batch_view(c, *ob);
+  dim3 g1((c->info.max_omega + 127) / 128, nb * n_f);
+  k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
+  DD_CUDA(c, cudaGetLastError());
+  dd_solve_stats st1{};
+  dd_status r1 = solve_batch(c, *ob, (const double*)src_o, (double*)sol_o, prm, &st1, s, true);
+  if (r1 != DD_OK && r1 != DD_ENOCONV) return r1;
+  // frame source and solve
+  a.src = (double2*)src_f;
+  dim3 g2((P.n_l1 + 127) / 128, n_f);
+  k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
+  DD_CUDA(c, cudaGetLastError());
+  dd_solve_stats st2{};
+  dd_status r2 = solve_batch(c, *fb, (const double*)src_f, (double*)sol_f, prm, &st2, s, true);
+  if (r2 != DD_OK && r2 != DD_ENOCONV) return r2;
+  // extraction into w chi (zero outside dPi by construction: dPi = B u C)
+  const int nB = c->info.n_B, nC = c->info.n_C;
+  if (nB) {
+    dim3 g((nB + 127) / 128, n_f);
+    k_extract<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
+                                ob->d_uoff, (const double2*)sol_o, (double2*)wchi);
+  }
+  if (nC) {
+    dim3 g((nC + 127) / 128, n_f);
+    k_extract<<<g, 128, 0, s>>>(nullptr, P.d_c_loc, P.d_c_dpi, nC, n_f, c->info.n_dpi,
+                                fb->d_uoff, (const double2*)sol_f, (double2*)wchi);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  if (r1 == DD_ENOCONV || r2 == DD_ENOCONV)
+    return fail(c, DD_ENOCONV, "a block or frame solve missed its tolerance");
+  return DD_OK;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_apply_w(dd_ctx* c, int n_f, const double* chi, double* w_chi,
+                     const dd_solve_params* prm, void* stream) {
+  if (!c || !chi || !w_chi || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
+  const double* din = chi;
+  double* dout = w_chi;
+  bool hin = !is_device_ptr(chi), hout = !is_device_ptr(w_chi);
+  dd_status e;
+  if (hin) {
+    void* p;
+    if ((e = workspace(c, 44, bytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, chi, bytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  if (hout) {
+    void* p;
+    if ((e = workspace(c, 45, bytes, &p)) != DD_OK) return e;
+    dout = (double*)p;
+  }
+  dd_status r = apply_w_dev(c, n_f, din, dout, prm, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  if (hout) DD_CUDA(c, cudaMemcpyAsync(w_chi, dout, bytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  return r;
+}
+
+dd_status dd_multiboson_action(dd_ctx* c, int n_f, const double* u, const double* chi, double* S,
+                               double* S_block, double* S_r, const dd_solve_params* prm,
+                               void* stream) {
+  if (!c || !u || !chi || !S || !S_r || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)c->blocks.size();
+  size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
+  const double* din = chi;
+  dd_status e;
+  if (!is_device_ptr(chi)) {
+    void* p;
+    if ((e = workspace(c, 44, bytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, chi, bytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  void *wv, *du, *dS;
+  if ((e = workspace(c, 46, bytes, &wv)) || (e = workspace(c, 47, 16ULL * n_f, &du)) ||
+      (e = workspace(c, 48, sizeof(double) * (nb + 1 + 4096), &dS)))
+    return e;
+  dd_status r = apply_w_dev(c, n_f, din, (double*)wv, prm, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  DD_CUDA(c, cudaMemcpyAsync(du, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
+  WPlan& P = *(WPlan*)c->wplan;
+  k_action_blocks<<<nb, 256, 0, s>>>(P.d_b_grp, P.d_b_dpi, n_f, c->info.n_dpi,
+                                     (const double2*)du, (const double2*)din,
+                                     (const double2*)wv, (double*)dS);
+  if (P.n_cgrp > 0)
+    k_action_blocks<<<P.n_cgrp, 256, 0, s>>>(P.d_c_grp, P.d_c_dpi, n_f, c->info.n_dpi,
+                                             (const double2*)du, (const double2*)din,
+                                             (const double2*)wv, (double*)dS + nb);
+  DD_CUDA(c, cudaGetLastError());
+  std::vector<double> h(nb + P.n_cgrp);
+  DD_CUDA(c, cudaMemcpyAsync(h.data(), dS, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  double sb = 0.0, sr = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    sb += h[b];
+    if (S_block) S_block[b] = h[b];
+  }
+  for (int k = 0; k < P.n_cgrp; ++k) sr += h[nb + k];
+  *S_r = sr;
+  *S = sb + sr;
+  return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal data model of libdd4d (not part of the C ABI).
+//
+// Every site set on which D is restricted (the full lattice, the frame
+// Lambda1, each framed block Omega0^a and its frame piece Phi1^a) is a
+// "domain instance".  Its sites are split by parity; within a parity they are
+// numbered in increasing field order.  Per instance the library keeps
+//   nbr  [p][8][n_p]  neighbour (index in the other parity) in directions
+//                     +0,+1,+2,+3,-0,-1,-2,-3, or -1 when the hop leaves the set;
+//   fmap [p][n_p]     position of the site in the caller's field order;
+//   glob [p][n_p]     global lexicographic site index;
+//   lex  [p][n_p]     local lexicographic index inside the box (boxes only);
+//   links [p][mu][9][n_p]  forward links U_mu(x) of the instance's sites, with
+//                     the time-boundary sign folded into U_0 at x0 = L0-1,
+//                     stored complex (SoA, site fastest) in FP64, FP32, BF16.
+// Boxes of the same shape share nbr/fmap/lex.  Spinor work vectors use the
+// same SoA order: for one (instance, rhs) system and one parity,
+// 12 components x n_p sites, component-major, component = 3*spin + colour.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dd4d.h"
+
+namespace dd {
+
+struct DomInst {            // device-visible descriptor (plain data)
+  int n[2];                 // sites per parity
+  int dims[4];              // box extents (lattice extents for FULL / LAMBDA1)
+  int origin[4];            // global coordinates of local site 0 (boxes)
+  int kind;                 // dd_domain
+  int nsites;               // n[0] + n[1]
+  const int* nbr;           // [p][8][n_p], parity-1 table at 8*n[0]
+  const int* fmap;          // [p][n_p]
+  const int* glob;          // [p][n_p]
+  const int* lex;           // [p][n_p] (boxes), nullptr otherwise
+  const double2* link64;    // [p][4][9][n_p]
+  const float2* link32;
+  const __nv_bfloat162* link16;
+};
+
+// Owning host record of an instance.
+struct Instance {
+  DomInst d{};
+  int block = -1;
+  std::shared_ptr<void> nbr_buf, fmap_buf, lex_buf;   // shared between same-shape boxes
+  void* glob_buf = nullptr;
+  void* link64_buf = nullptr;
+  void* link32_buf = nullptr;
+  void* link16_buf = nullptr;
+  std::vector<int> h_glob;      // host copy [p][n_p]
+  std::vector<int> h_fmap;      // host copy [p][n_p]
+  bool links_ready = false;
+};
+
+struct BlockDesc {
+  int core_lo[4], core_hi[4];
+  int origin[4], side[4];
+};
+
+// A batch of systems: instances x nrhs, with per-parity work items.
+struct Batch {
+  int nb = 0, nrhs = 0;
+  std::vector<int> inst;                    // instance index per batch position
+  long long tot[2] = {0, 0};                // complex elements per parity (all systems)
+  long long user_tot = 0;                   // complex elements in caller layout
+  // device arrays
+  int* d_inst = nullptr;
+  long long* d_off[2] = {nullptr, nullptr}; // [nb*nrhs] offsets (complex elements)
+  long long* d_uoff = nullptr;              // [nb*nrhs] caller-layout offsets
+  int4* d_items[2] = {nullptr, nullptr};    // {j, start, count, 0}
+  int nitems[2] = {0, 0};
+  int* d_item_begin[2] = {nullptr, nullptr}; // [nb+1] first item of instance j
+  std::vector<int> item_begin[2];
+  int maxn[2] = {0, 0};
+  ~Batch();
+};
+
+struct BatchDev {           // device-visible view of a Batch
+  const DomInst* inst_tab;  // all instances
+  const int* inst;          // [nb]
+  const long long* off[2];
+  const long long* uoff;
+  const int4* items[2];
+  const int* item_begin[2];
+  int nitems[2];
+  int nb, nrhs;
+};
+
+struct TimingRec {
+  cudaEvent_t a, b;
+  int which;
+  double bytes;
+};
+
+}  // namespace dd
+
+struct dd_ctx {
+  int L[4];
+  int V;
+  int time_bc;
+  double kappa;
+  int device = 0;
+  std::string err;
+  // gauge field, FP64, [V][4][9] complex (time sign folded in)
+  double2* d_U = nullptr;
+  bool gauge_ready = false;
+  // geometry
+  bool geom_ready = false;
+  std::vector<std::vector<int>> cores_lo, cores_hi;   // per direction
+  std::vector<dd::BlockDesc> blocks;
+  std::vector<int> dpi_sites, B_sites, C_sites;       // increasing global order
+  std::vector<std::vector<int>> B_of_block;           // per block, increasing global order
+  std::vector<int> dpi_pos;                            // [V] -> index in dPi or -1
+  std::vector<int> block_of_B;                         // [n_B in dPi order?] unused
+  dd_geom_info info{};
+  // instances: 0 = FULL, 1 = LAMBDA1, then OMEGA blocks, then PHI blocks (lazy)
+  std::vector<dd::Instance> inst;
+  int omega0 = -1, phi0 = -1, lambda1 = -1;
+  dd::DomInst* d_inst = nullptr;
+  int d_inst_cap = 0;
+  bool inst_dirty = true;
+  std::map<std::string, std::shared_ptr<void>> shape_cache;
+  // device copies of the dPi bookkeeping
+  int* d_dpi_pos = nullptr;      // [V]
+  int* d_dpi_kind = nullptr;     // [n_dpi] 0..nblocks-1: block of a B site; -1: C site
+  // timing
+  bool timing = false;
+  std::vector<dd::TimingRec> trec;
+  double t_ms[3] = {0, 0, 0};
+  long long t_n[3] = {0, 0, 0};
+  double t_bytes[3] = {0, 0, 0};
+  // work space (krylov.cu) and cached batches
+  void* scratch = nullptr;
+  std::map<std::string, std::unique_ptr<dd::Batch>> batches;
+  void* wplan = nullptr;     // gather lists of apply_w (dd.cu)
+};
+
+// ---- helpers shared by the translation units --------------------------------
+namespace dd {
+
+dd_status fail(dd_ctx* c, dd_status s, const std::string& msg);
+dd_status cuda_fail(dd_ctx* c, cudaError_t e, const char* where);
+#define DD_CUDA(ctx, call)                                         \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return dd::cuda_fail(ctx, e_, #call);   \
+  } while (0)
+
+dd_status sync_instances(dd_ctx* c);              // upload DomInst table if dirty
+dd_status ensure_links(dd_ctx* c, int i, dd_prec prec);
+dd_status ensure_phi(dd_ctx* c);
+dd_status instance_of(dd_ctx* c, dd_domain kind, int id, int* out);
+dd_status make_batch(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch& b);
+BatchDev batch_view(dd_ctx* c, const Batch& b);
+
+// Device memory: plain cudaMalloc wrappers that record failures.
+dd_status dalloc(dd_ctx* c, void** p, size_t bytes);
+void dfree(void* p);
+
+// Host-or-device pointer helper: returns true when p is device-accessible memory.
+bool is_device_ptr(const void* p);
+
+// stencil launches (stencil.cu)
+struct HopArgs {
+  int p_out;                // output parity
+  const void* in;           // parity 1-p_out vector base
+  void* out;                // parity p_out vector base
+  const void* s1;           // optional self term (parity p_out)
+  const void* s2;           // optional second self term
+  double a1, a2, b;         // out = a1*s1 + a2*s2 + b*H in
+  const void* dotq;         // optional: partial (dotq, out)  [complex]
+  const void* dots;         // optional: partials (out, dots) and (out, out)
+  double* partial;          // [k][nitems*nrhs] complex (2 doubles)
+  const int* active;        // optional per-system flags, active[sys * active_stride]
+  int active_stride;
+};
+dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s);
+
+// layout conversions (stencil.cu)
+dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
+                      dd_prec prec, cudaStream_t s);
+dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* vo, double* user,
+                        dd_prec prec, cudaStream_t s);
+
+// solver (krylov.cu)
+dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x_user,
+                      const dd_solve_params* prm, dd_solve_stats* st, cudaStream_t s,
+                      bool user_layout);
+
+size_t prec_bytes(dd_prec p);
+
+// growable per-context device work buffers (krylov.cu); slots are reused by
+// every call on the context, so calls on one context must not overlap
+dd_status workspace(dd_ctx* c, int slot, size_t bytes, void** out);
+void free_workspace(dd_ctx* c);
+void free_plan(dd_ctx* c);
+dd_status get_batch(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs, Batch** out);   // bytes per complex number at a storage precision
+
+}  // namespace dd

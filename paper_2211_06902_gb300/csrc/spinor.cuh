@@ -1,0 +1,144 @@
+// Device arithmetic of the Wilson hop term on SoA even-odd spinor fields.
+//
+// Hop term (paper Sec. 1/3, Wilson operator, kappa normalisation):
+//   (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                       + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu) ],   D = 1 - kappa H.
+// In the chiral basis gamma_0 = [[0,-1],[-1,0]], gamma_k = [[0,-i s_k],[i s_k,0]]
+// the projector (1 -/+ gamma_mu) has rank 2: the two upper spin components of
+// the projected spinor (h) determine the lower two, so only h (2 spins x 3
+// colours) is multiplied by the link and the lower half is rebuilt.
+#pragma once
+#include <cuda_bf16.h>
+
+namespace dd {
+
+// ---- storage <-> compute conversions -----------------------------------------
+template <class S> struct StoreTraits;
+template <> struct StoreTraits<double2> { typedef double T; typedef double2 C; };
+template <> struct StoreTraits<float2> { typedef float T; typedef float2 C; };
+template <> struct StoreTraits<__nv_bfloat162> { typedef float T; typedef float2 C; };
+
+__device__ __forceinline__ double2 ldc(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldc(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) {
+  return __bfloat1622float2(*p);
+}
+__device__ __forceinline__ void stc(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
+// ---- complex helpers ------------------------------------------------------------
+template <class C> __device__ __forceinline__ C cmk(double re, double im);
+template <> __device__ __forceinline__ double2 cmk<double2>(double re, double im) {
+  return make_double2(re, im);
+}
+template <> __device__ __forceinline__ float2 cmk<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+// a + i*b and a - i*b
+template <class C> __device__ __forceinline__ C caddi(C a, C b) { a.x -= b.y; a.y += b.x; return a; }
+template <class C> __device__ __forceinline__ C csubi(C a, C b) { a.x += b.y; a.y -= b.x; return a; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+// acc += a * b and acc += conj(a) * b
+template <class C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+template <class C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+template <class C, class T> __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+// i*a, -i*a
+template <class C> __device__ __forceinline__ C cmuli(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
+template <class C> __device__ __forceinline__ C cmulmi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+
+// ---- one hop direction ------------------------------------------------------------
+// psi: the neighbour's 12 components; U: 9 link entries (row-major a*3+b);
+// FWD: (1 - gamma_mu) U psi; otherwise (1 + gamma_mu) U^+ psi; accumulated into acc.
+template <int MU, bool FWD, class C>
+__device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const C (&U)[9]) {
+  C h[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const C p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
+    if (MU == 0) {
+      h[0][c] = FWD ? cadd(p0, p2) : csub(p0, p2);
+      h[1][c] = FWD ? cadd(p1, p3) : csub(p1, p3);
+    } else if (MU == 1) {
+      h[0][c] = FWD ? caddi(p0, p3) : csubi(p0, p3);
+      h[1][c] = FWD ? caddi(p1, p2) : csubi(p1, p2);
+    } else if (MU == 2) {
+      h[0][c] = FWD ? cadd(p0, p3) : csub(p0, p3);
+      h[1][c] = FWD ? csub(p1, p2) : cadd(p1, p2);
+    } else {
+      h[0][c] = FWD ? caddi(p0, p2) : csubi(p0, p2);
+      h[1][c] = FWD ? csubi(p1, p3) : caddi(p1, p3);
+    }
+  }
+  C uh[2][3];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      C v = cmk<C>(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (FWD) cfma(v, U[a * 3 + b], h[s][b]);
+        else cfmac(v, U[b * 3 + a], h[s][b]);
+      }
+      uh[s][a] = v;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc[a] = cadd(acc[a], uh[0][a]);
+    acc[3 + a] = cadd(acc[3 + a], uh[1][a]);
+    if (MU == 0) {
+      acc[6 + a] = FWD ? cadd(acc[6 + a], uh[0][a]) : csub(acc[6 + a], uh[0][a]);
+      acc[9 + a] = FWD ? cadd(acc[9 + a], uh[1][a]) : csub(acc[9 + a], uh[1][a]);
+    } else if (MU == 1) {
+      acc[6 + a] = FWD ? csubi(acc[6 + a], uh[1][a]) : caddi(acc[6 + a], uh[1][a]);
+      acc[9 + a] = FWD ? csubi(acc[9 + a], uh[0][a]) : caddi(acc[9 + a], uh[0][a]);
+    } else if (MU == 2) {
+      acc[6 + a] = FWD ? csub(acc[6 + a], uh[1][a]) : cadd(acc[6 + a], uh[1][a]);
+      acc[9 + a] = FWD ? cadd(acc[9 + a], uh[0][a]) : csub(acc[9 + a], uh[0][a]);
+    } else {
+      acc[6 + a] = FWD ? csubi(acc[6 + a], uh[0][a]) : caddi(acc[6 + a], uh[0][a]);
+      acc[9 + a] = FWD ? caddi(acc[9 + a], uh[1][a]) : csubi(acc[9 + a], uh[1][a]);
+    }
+  }
+}
+
+// Warp + block reduction of NV doubles (sum); result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double* sh /* >= 32*NV */) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[warp * NV + k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = lane < nw ? sh[lane * NV + k] : 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+}
+
+}  // namespace dd

@@ -1,0 +1,270 @@
+// Restricted Wilson stencil on batches of domain instances (paper Sec. 3, D_X).
+//
+// The even-odd split of a domain X gives D_X = [[1, -k H_eo], [-k H_oe, 1]];
+// k_hop computes, for one output parity p and every (instance, rhs) system of
+// a batch,
+//     out_p = a1 * s1_p + a2 * s2_p + b * (H_{p,1-p} in_{1-p})
+// where hops that leave X are dropped (Dirichlet boundary), and can fuse the
+// per-system inner products the Krylov solver needs into its epilogue.
+#include <algorithm>
+#include <cstdio>
+
+#include "internal.h"
+#include "spinor.cuh"
+
+namespace dd {
+
+constexpr int HOP_THREADS = 128;
+
+template <class S>
+__device__ __forceinline__ const S* links_of(const DomInst& d);
+template <>
+__device__ __forceinline__ const double2* links_of<double2>(const DomInst& d) { return d.link64; }
+template <>
+__device__ __forceinline__ const float2* links_of<float2>(const DomInst& d) { return d.link32; }
+template <>
+__device__ __forceinline__ const __nv_bfloat162* links_of<__nv_bfloat162>(const DomInst& d) {
+  return d.link16;
+}
+
+template <int DIR, class S, class C>
+__device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int n_out,
+                                        int n_in, const int* __restrict__ nbr,
+                                        const S* __restrict__ in_sys, const S* __restrict__ lk) {
+  constexpr int MU = DIR & 3;
+  constexpr bool FWD = DIR < 4;
+  const int j = nbr[DIR * n_out + i];
+  if (j < 0) return;
+  C psi[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) psi[k] = ldc(in_sys + (long long)k * n_in + j);
+  C U[9];
+  if (FWD) {
+    const S* l = lk + (p ? 36LL * n0 : 0) + (long long)MU * 9 * n_out + i;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) U[c] = ldc(l + (long long)c * n_out);
+  } else {
+    const int q = 1 - p;
+    const S* l = lk + (q ? 36LL * n0 : 0) + (long long)MU * 9 * n_in + j;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) U[c] = ldc(l + (long long)c * n_in);
+  }
+  hop_dir<MU, FWD>(acc, psi, U);
+}
+
+// grid: (nitems[p], nrhs); block: HOP_THREADS threads, one output site each.
+template <class S>
+__global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
+  typedef typename StoreTraits<S>::C C;
+  typedef typename StoreTraits<S>::T T;
+  __shared__ double red[32 * 4];
+  const int p = a.p_out;
+  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+  const int r = blockIdx.y;
+  const int sys = it.x * bd.nrhs + r;
+  if (a.active && !a.active[(long long)sys * a.active_stride]) return;
+  const DomInst* dp = bd.inst_tab + bd.inst[it.x];
+  const int n0 = dp->n[0];
+  const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
+  const int i = it.y + threadIdx.x;
+  const bool live = threadIdx.x < it.z;
+  const S* in_sys = (const S*)a.in + (p ? bd.off[0] : bd.off[1])[sys];
+  S* out_sys = (S*)a.out + (p ? bd.off[1] : bd.off[0])[sys];
+  C out[12];
+  if (live) {
+    C acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = cmk<C>(0.0, 0.0);
+    const int* nbr = dp->nbr + (p ? 8LL * n0 : 0);
+    const S* lk = links_of<S>(*dp);
+    hop_one<0, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<1, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<2, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<3, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<4, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<5, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<6, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    hop_one<7, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    const T b = (T)a.b;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = cscale(acc[k], b);
+    if (a.s1) {
+      const S* s1 = (const S*)a.s1 + (p ? bd.off[1] : bd.off[0])[sys];
+      const T a1 = (T)a.a1;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        C v = ldc(s1 + (long long)k * n_out + i);
+        out[k].x = fma(a1, v.x, out[k].x);
+        out[k].y = fma(a1, v.y, out[k].y);
+      }
+    }
+    if (a.s2) {
+      const S* s2 = (const S*)a.s2 + (p ? bd.off[1] : bd.off[0])[sys];
+      const T a2 = (T)a.a2;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        C v = ldc(s2 + (long long)k * n_out + i);
+        out[k].x = fma(a2, v.x, out[k].x);
+        out[k].y = fma(a2, v.y, out[k].y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) stc(out_sys + (long long)k * n_out + i, out[k]);
+  }
+  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
+  const long long my = (long long)blockIdx.x * bd.nrhs + r;
+  if (a.dotq) {
+    double v[2] = {0.0, 0.0};
+    if (live) {
+      const S* q = (const S*)a.dotq + (p ? bd.off[1] : bd.off[0])[sys];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        C w = ldc(q + (long long)k * n_out + i);
+        v[0] += (double)w.x * out[k].x + (double)w.y * out[k].y;
+        v[1] += (double)w.x * out[k].y - (double)w.y * out[k].x;
+      }
+    }
+    block_reduce<2>(v, red);
+    if (threadIdx.x == 0) {
+      a.partial[2 * my] = v[0];
+      a.partial[2 * my + 1] = v[1];
+    }
+  }
+  if (a.dots) {
+    double v[3] = {0.0, 0.0, 0.0};
+    if (live) {
+      const S* q = (const S*)a.dots + (p ? bd.off[1] : bd.off[0])[sys];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        C w = ldc(q + (long long)k * n_out + i);
+        // (out, s) = sum conj(out) s ; (out, out)
+        v[0] += (double)out[k].x * w.x + (double)out[k].y * w.y;
+        v[1] += (double)out[k].x * w.y - (double)out[k].y * w.x;
+        v[2] += (double)out[k].x * out[k].x + (double)out[k].y * out[k].y;
+      }
+    }
+    block_reduce<3>(v, red);
+    if (threadIdx.x == 0) {
+      double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
+      P[2 * my] = v[0];
+      P[2 * my + 1] = v[1];
+      P[2 * (slot_stride + my)] = v[2];
+      P[2 * (slot_stride + my) + 1] = 0.0;
+    }
+  }
+}
+
+// Algorithmic bytes of one hop launch per output site and rhs (see DESIGN):
+// neighbour input read once, output written once, self terms read once,
+// each of the 8 links read once per output site (shared by the nrhs systems).
+static double hop_bytes(const Batch& b, int p, size_t cb, int nself) {
+  const double site_rhs = (double)b.tot[p] / 12.0;   // output (site, rhs) pairs
+  const double spinors = 12.0 * cb * (2 + nself);     // input, output, self terms
+  const double links = 8.0 * 9.0 * cb / b.nrhs;       // 8 links per site, shared by rhs
+  return site_rhs * (spinors + links);
+}
+
+dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s) {
+  dd_status st = sync_instances(c);
+  if (st != DD_OK) return st;
+  BatchDev bd = batch_view(c, b);
+  int p = a.p_out;
+  if (b.nitems[p] == 0) return DD_OK;
+  dim3 grid(b.nitems[p], b.nrhs);
+  dd::TimingRec rec;
+  bool tm = c->timing;
+  if (tm) {
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    rec.which = prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2);
+    rec.bytes = hop_bytes(b, p, prec_bytes(prec), (a.s1 ? 1 : 0) + (a.s2 ? 1 : 0));
+    cudaEventRecord(rec.a, s);
+  }
+  if (prec == DD_F64) k_hop<double2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  else if (prec == DD_F32) k_hop<float2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  else k_hop<__nv_bfloat162><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  if (tm) {
+    cudaEventRecord(rec.b, s);
+    c->trec.push_back(rec);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  return DD_OK;
+}
+
+// ---- caller layout <-> internal SoA --------------------------------------------
+// caller: [j][r][field-order site][12] complex128; internal: per parity, per
+// system 12 x n_p complex at the storage precision.  grid: (nitems[p], nrhs).
+template <class S>
+__global__ void k_pack(BatchDev bd, int p, const double2* __restrict__ user, S* __restrict__ v) {
+  typedef typename StoreTraits<S>::C C;
+  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+  const int r = blockIdx.y;
+  if (threadIdx.x >= it.z) return;
+  const int sys = it.x * bd.nrhs + r;
+  const DomInst d = bd.inst_tab[bd.inst[it.x]];
+  const int i = it.y + threadIdx.x;
+  const int np = p ? d.n[1] : d.n[0];
+  const int f = d.fmap[(p ? d.n[0] : 0) + i];
+  const double2* src = user + bd.uoff[sys] + 12LL * f;
+  S* dst = v + (p ? bd.off[1] : bd.off[0])[sys] + i;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 x = src[k];
+    stc(dst + (long long)k * np, cmk<C>(x.x, x.y));
+  }
+}
+
+template <class S>
+__global__ void k_unpack(BatchDev bd, int p, const S* __restrict__ v, double2* __restrict__ user) {
+  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+  const int r = blockIdx.y;
+  if (threadIdx.x >= it.z) return;
+  const int sys = it.x * bd.nrhs + r;
+  const DomInst d = bd.inst_tab[bd.inst[it.x]];
+  const int i = it.y + threadIdx.x;
+  const int np = p ? d.n[1] : d.n[0];
+  const int f = d.fmap[(p ? d.n[0] : 0) + i];
+  double2* dst = user + bd.uoff[sys] + 12LL * f;
+  const S* src = v + (p ? bd.off[1] : bd.off[0])[sys] + i;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    auto x = ldc(src + (long long)k * np);
+    dst[k] = make_double2((double)x.x, (double)x.y);
+  }
+}
+
+dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
+                      dd_prec prec, cudaStream_t s) {
+  dd_status st = sync_instances(c);
+  if (st != DD_OK) return st;
+  BatchDev bd = batch_view(c, b);
+  for (int p = 0; p < 2; ++p) {
+    if (b.nitems[p] == 0) continue;
+    dim3 grid(b.nitems[p], b.nrhs);
+    void* v = p ? vo : ve;
+    if (prec == DD_F64) k_pack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (double2*)v);
+    else if (prec == DD_F32) k_pack<float2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (float2*)v);
+    else k_pack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (__nv_bfloat162*)v);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  return DD_OK;
+}
+
+dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* vo, double* user,
+                        dd_prec prec, cudaStream_t s) {
+  dd_status st = sync_instances(c);
+  if (st != DD_OK) return st;
+  BatchDev bd = batch_view(c, b);
+  for (int p = 0; p < 2; ++p) {
+    if (b.nitems[p] == 0) continue;
+    dim3 grid(b.nitems[p], b.nrhs);
+    const void* v = p ? vo : ve;
+    if (prec == DD_F64) k_unpack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)v, (double2*)user);
+    else if (prec == DD_F32) k_unpack<float2><<<grid, 128, 0, s>>>(bd, p, (const float2*)v, (double2*)user);
+    else k_unpack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const __nv_bfloat162*)v, (double2*)user);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  return DD_OK;
+}
+
+}  // namespace dd

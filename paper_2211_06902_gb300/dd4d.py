@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libdd4d.so (C ABI in include/dd4d.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Fields may be numpy arrays (host; the library copies them in and
+out) or CUDA torch tensors (device; used in place on the current stream).
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdd4d.so")
+
+DD_OK, DD_EINVAL, DD_ENOMEM, DD_ENOCONV, DD_ETIMEOUT, DD_ENAN, DD_ECUDA = range(7)
+F64, F32, BF16 = 0, 1, 2
+FULL, OMEGA, PHI, LAMBDA1 = 0, 1, 2, 3
+SET_DPI, SET_B, SET_C, SET_OMEGA, SET_PHI, SET_LAMBDA1 = range(6)
+PREC = {"f64": F64, "f32": F32, "bf16": BF16}
+DOMAIN = {"full": FULL, "omega": OMEGA, "phi": PHI, "lambda1": LAMBDA1}
+
+
+class GeomInfo(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("nblocks", "n_dpi", "n_B", "n_C", "n_E", "n_A",
+                                        "n_lambda1", "max_omega", "max_phi")]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("inner_prec", C.c_int),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("systems", C.c_int), ("converged", C.c_int), ("max_iters", C.c_int),
+                ("outer_cycles", C.c_int), ("max_relres", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dd4d status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdd4d.so is not built (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+        sig = {
+            "dd_create": [C.POINTER(vp), ip, C.c_int, C.c_double],
+            "dd_destroy": [vp],
+            "dd_strerror": [C.c_int],
+            "dd_last_error": [vp],
+            "dd_set_kappa": [vp, C.c_double],
+            "dd_gauge_upload": [vp, vp],
+            "dd_set_geometry": [vp, ip, ip, ip, C.POINTER(GeomInfo)],
+            "dd_geom_sites": [vp, C.c_int, C.c_int, ip, ip],
+            "dd_geom_block": [vp, C.c_int, ip, ip, ip, ip],
+            "dd_apply_D_block": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, C.c_int, vp],
+            "dd_solve_blocks": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp,
+                                C.POINTER(SolveParams), C.POINTER(SolveStats), vp],
+            "dd_apply_w": [vp, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
+            "dd_multiboson_action": [vp, C.c_int, dp, vp, dp, dp, dp, C.POINTER(SolveParams), vp],
+            "dd_roots": [C.c_int, C.c_double, dp],
+            "dd_timing_enable": [vp, C.c_int],
+            "dd_timing_get": [vp, C.c_int, dp, C.POINTER(C.c_longlong), dp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name in ("dd_strerror", "dd_last_error") else C.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C ABI entry points the binding expects."""
+    return ["dd_create", "dd_destroy", "dd_strerror", "dd_last_error", "dd_set_kappa",
+            "dd_gauge_upload", "dd_set_geometry", "dd_geom_sites", "dd_geom_block",
+            "dd_apply_D_block", "dd_solve_blocks", "dd_apply_w", "dd_multiboson_action",
+            "dd_roots", "dd_timing_enable", "dd_timing_get"]
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(x.ctypes.data)
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(0)
+
+
+def params(tol=1e-10, maxiter=2000, inner_prec="f64", inner_tol=1e-5, max_outer=None,
+           check_every=8):
+    ip = PREC[inner_prec] if isinstance(inner_prec, str) else inner_prec
+    if max_outer is None:
+        max_outer = 4 if ip == F64 else 30
+    return SolveParams(tol, maxiter, ip, inner_tol, max_outer, check_every)
+
+
+def roots(N, c):
+    """u_k, k = 1..N/2 (complex numpy array)."""
+    out = np.zeros(N, dtype=np.float64)
+    st = lib().dd_roots(N, c, out.ctypes.data_as(C.POINTER(C.c_double)))
+    if st:
+        raise DDError(st, lib().dd_strerror(st).decode())
+    return out[0::2] + 1j * out[1::2]
+
+
+class Context:
+    """A lattice, its gauge field and its domain decomposition on the GPU."""
+
+    def __init__(self, L, kappa, time_bc=-1):
+        self.L = tuple(int(v) for v in L)
+        self._h = C.c_void_p()
+        Larr = (C.c_int * 4)(*self.L)
+        st = lib().dd_create(C.byref(self._h), Larr, int(time_bc), float(kappa))
+        if st:
+            raise DDError(st, lib().dd_strerror(st).decode())
+        self.info = None
+
+    def close(self):
+        if self._h:
+            lib().dd_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st and st != DD_ENOCONV:
+            raise DDError(st, lib().dd_last_error(self._h).decode())
+        return st
+
+    def set_kappa(self, kappa):
+        self._check(lib().dd_set_kappa(self._h, float(kappa)))
+
+    def gauge_upload(self, U):
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        if U.shape != self.L + (4, 3, 3):
+            raise ValueError("gauge field shape must be L + (4, 3, 3)")
+        self._check(lib().dd_gauge_upload(self._h, C.c_void_p(U.ctypes.data)))
+
+    def set_geometry(self, cores):
+        nc = (C.c_int * 4)(*[len(c) for c in cores])
+        lo = [iv[0] for c in cores for iv in c]
+        hi = [iv[1] for c in cores for iv in c]
+        info = GeomInfo()
+        self._check(lib().dd_set_geometry(self._h, nc, (C.c_int * len(lo))(*lo),
+                                          (C.c_int * len(hi))(*hi), C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in info._fields_}
+        return self.info
+
+    def geom_sites(self, which, block=0):
+        n = C.c_int(0)
+        self._check(lib().dd_geom_sites(self._h, which, block, None, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.int32)
+        self._check(lib().dd_geom_sites(self._h, which, block,
+                                        out.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n)))
+        return out
+
+    def geom_block(self, b):
+        arrs = [(C.c_int * 4)() for _ in range(4)]
+        self._check(lib().dd_geom_block(self._h, b, *arrs))
+        return dict(zip(("origin", "side", "core_lo", "core_hi"), [list(a) for a in arrs]))
+
+    def apply_D_block(self, kind, ids, nrhs, inp, out, prec="f64", stream=None):
+        kind = DOMAIN[kind] if isinstance(kind, str) else kind
+        ids = list(ids) if ids is not None else [0]
+        idarr = (C.c_int * len(ids))(*ids)
+        p = PREC[prec] if isinstance(prec, str) else prec
+        self._check(lib().dd_apply_D_block(self._h, kind, idarr, len(ids), nrhs, _ptr(inp),
+                                           _ptr(out), p, _stream(stream)))
+
+    def solve_blocks(self, kind, ids, nrhs, b, x, prm=None, stream=None):
+        kind = DOMAIN[kind] if isinstance(kind, str) else kind
+        ids = list(ids) if ids is not None else [0]
+        idarr = (C.c_int * len(ids))(*ids)
+        prm = prm or params()
+        stats = SolveStats()
+        st = self._check(lib().dd_solve_blocks(self._h, kind, idarr, len(ids), nrhs, _ptr(b),
+                                               _ptr(x), C.byref(prm), C.byref(stats),
+                                               _stream(stream)))
+        d = stats.as_dict()
+        d["status"] = st
+        return d
+
+    def apply_w(self, n_f, chi, w_chi, prm=None, stream=None):
+        prm = prm or params()
+        st = self._check(lib().dd_apply_w(self._h, n_f, _ptr(chi), _ptr(w_chi), C.byref(prm),
+                                          _stream(stream)))
+        return st
+
+    def multiboson_action(self, u, chi, prm=None, stream=None):
+        u = np.asarray(u, dtype=np.complex128)
+        n_f = len(u)
+        uu = np.empty(2 * n_f)
+        uu[0::2], uu[1::2] = u.real, u.imag
+        S = C.c_double(0)
+        Sr = C.c_double(0)
+        nb = self.info["nblocks"]
+        Sb = np.zeros(nb)
+        prm = prm or params()
+        st = self._check(lib().dd_multiboson_action(
+            self._h, n_f, uu.ctypes.data_as(C.POINTER(C.c_double)), _ptr(chi), C.byref(S),
+            Sb.ctypes.data_as(C.POINTER(C.c_double)), C.byref(Sr), C.byref(prm),
+            _stream(stream)))
+        return S.value, Sb, Sr.value, st
+
+    def timing_enable(self, on=True):
+        self._check(lib().dd_timing_enable(self._h, 1 if on else 0))
+
+    def timing_get(self, which):
+        ms = C.c_double(0)
+        n = C.c_longlong(0)
+        by = C.c_double(0)
+        self._check(lib().dd_timing_get(self._h, which, C.byref(ms), C.byref(n), C.byref(by)))
+        return ms.value, n.value, by.value

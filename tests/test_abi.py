@@ -1,0 +1,45 @@
+"""The C-ABI library loads and exports every entry point include/dd4d.h declares.
+
+CPU only: no compute call is made (there may be no GPU here).
+"""
+
+import os
+import re
+
+import pytest
+
+from paper_2211_06902_gb300 import dd4d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "dd4d.h")).read()
+    return sorted(set(re.findall(r"\b(dd_[a-z_0-9A-Z]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(dd4d.LIB_PATH):
+        from paper_2211_06902_gb300 import build
+        build.build()
+    return dd4d.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "dd_solve_blocks" in names and "dd_multiboson_action" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(dd4d.exported_symbols()) == names
+
+
+def test_strerror_and_roots_without_gpu(lib):
+    assert lib.dd_strerror(0) == b"ok"
+    assert lib.dd_strerror(3) == b"solver did not converge"
+    u = dd4d.roots(8, 0.5)
+    import numpy as np
+    k = np.arange(1, 5)
+    assert np.allclose(u, np.cos(2 * np.pi * k / 9) + 1j * np.sqrt(0.75) * np.sin(2 * np.pi * k / 9))
+    with pytest.raises(dd4d.DDError):
+        dd4d.roots(5, 0.5)
