@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the batched block solves of the 4D domain decomposition.
+
+Workload (one step): x = D_{Omega0^a}^{-1} b for every framed block Omega0^a
+of a 32^4 lattice (256 blocks of 9^4 sites: 7^4 cores and a one-site frame)
+and 12 Gaussian right-hand sides per block (3072 systems, 20.15 M site-rhs),
+kappa = 0.135, links exp(i 0.5 H) with seed 2, every system solved to
+|b - D x| <= 1e-10 |b| with the FP32 inner BiCGstab and FP64 defect
+correction of libdd4d.  Inputs are resident on the GPU when the timed region
+starts and are larger than L2.  The line also reports the plain FP64 solve
+of the same batch, the stencil's roofline, the multi-boson action rate on the
+8^4 lattice, an end-to-end number through the C ABI with host buffers, and
+the FP64 CPU oracle on a bounded sample (the reference arm).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank solves its own batch (weak scaling, no collective on
+the data path); rank 0 prints the JSON line.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LATTICE = (32, 32, 32, 32)
+KAPPA, EPS, SEED = 0.135, 0.5, 2
+CORE, FRAME, NRHS = 7, 1, 12
+TOL = 1e-10
+WORKLOAD = ("32^4 Wilson-Dirac (kappa 0.135, links exp(i 0.5 H), seed 2): 256 framed blocks "
+            "Omega0^a of 9^4 sites (7^4 cores, frame 1) x 12 Gaussian rhs = 3072 block "
+            "systems solved to 1e-10")
+METRIC = "block-solve sites/s to 1e-10"
+UNIT = "site-rhs/s"
+
+
+def cores_uniform(L, core, frame):
+    out = []
+    for mu in range(4):
+        period = core + frame
+        out.append([(i * period, i * period + core - 1) for i in range(L[mu] // period)])
+    return out
+
+
+def site_rhs():
+    nb = 1
+    for mu in range(4):
+        nb *= LATTICE[mu] // (CORE + FRAME)
+    return nb * (CORE + 2 * FRAME) ** 4 * NRHS
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 7:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev] if vis else dev
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """ncu DRAM bytes per launch of the FP32 hop kernel (profiles/), or None."""
+    path = os.path.join(ROOT, "profiles", "hop_f32_traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(U, reps=1):
+    """The FP64 oracle on a bounded sample: one framed block, 2 rhs (CPU)."""
+    from oracle.dd import DomainSolver
+    from oracle.geometry import Decomposition
+    from paper_2211_06902_gb300 import synth
+
+    geo = Decomposition(LATTICE, cores_uniform(LATTICE, CORE, FRAME))
+    nr = 2
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sol = DomainSolver(U, KAPPA, geo.omega_mask[0])
+        n = len(sol.sites)
+        b = synth.complex_gaussian(SEED, synth.TAG_RHS, (nr, 12 * n))
+        for r in range(nr):
+            sol.solve_vec(b[r])
+        times.append(time.perf_counter() - t0)
+    return nr * n, times
+
+
+def cpu_baseline_entry(U):
+    units, times = oracle_sample(U, 1)
+    return {"value": units / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one 9^4 framed block x 2 rhs of the same workload (oracle BiCGstab "
+                      "to 1e-13 on the assembled sparse D_Omega, assembly included), %.1f s"
+                      % times[0]}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2211_06902_gb300 import synth
+    U = synth.gauge_field(LATTICE, EPS, SEED)
+    for _ in range(args.warmup):
+        oracle_sample(U, 1)
+    units, times = oracle_sample(U, args.steps)
+    t = sum(times) / len(times)
+    value = units / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "one framed block x 2 rhs per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one 9^4 framed block x 2 rhs per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2211_06902_gb300 import dd4d, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    if not os.path.exists(dd4d.LIB_PATH):
+        from paper_2211_06902_gb300 import build
+        build.build()
+
+    U = synth.gauge_field(LATTICE, EPS, SEED)
+    ctx = dd4d.Context(LATTICE, KAPPA)
+    ctx.gauge_upload(U)
+    info = ctx.set_geometry(cores_uniform(LATTICE, CORE, FRAME))
+    ids = list(range(info["nblocks"]))
+    n_om = info["max_omega"]
+    b_h = synth.complex_gaussian(SEED + 1000 * rank, synth.TAG_RHS, (len(ids), NRHS, n_om, 12))
+    b = torch.from_numpy(b_h.view(np.float64)).to(dev)
+    x = torch.zeros_like(b)
+    units = site_rhs()
+    assert units == len(ids) * NRHS * n_om
+    mixed = dd4d.params(TOL, inner_prec="f32", inner_tol=args.inner_tol, check_every=8)
+    plain = dd4d.params(TOL, inner_prec="f64", check_every=8)
+
+    def step(prm):
+        st = ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
+        if st["status"] != 0 or st["max_relres"] > TOL:
+            raise RuntimeError("solve missed tolerance: %s" % st)
+        return st
+
+    for _ in range(args.warmup):
+        step(mixed)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(gpu_smi_id(torch, local))
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ctx.timing_enable(True)
+    ctx.timing_get(0)
+    ctx.timing_get(1)
+    launches0 = dd4d.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = None
+    for _ in range(args.steps):
+        stats = step(mixed)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = dd4d.launch_count() - launches0
+    hop32_ms, hop32_n, hop32_bytes = ctx.timing_get(1)
+    hop64_ms, hop64_n, hop64_bytes = ctx.timing_get(0)
+    ctx.timing_enable(False)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units / (ms * 1e-3)
+
+    # plain FP64 form of the same batch (the reference form of the ratio)
+    step(plain)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    pst = step(plain)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+
+    # end to end through the C ABI with pinned host buffers
+    bh = torch.from_numpy(b_h.view(np.float64)).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    ctx.solve_blocks("omega", ids, NRHS, bh, xh, mixed)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = ctx.solve_blocks("omega", ids, NRHS, bh, xh, mixed)
+        if st["status"] != 0:
+            raise RuntimeError("e2e solve failed: %s" % st)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": world * units / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(bh.numel() * 8), "d2h_bytes_per_step": int(xh.numel() * 8)}
+    del bh, xh
+
+    # multi-boson action on the 8^4 lattice (16 blocks of 5^4, N = 4, 2 fields)
+    action = None
+    if rank == 0:
+        action = action_rate(dd4d, synth, torch)
+
+    peak, peak_kind = measured_peaks()
+    achieved = hop32_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
+    tr = traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": tr.get("bytes_per_launch") if tr else None,
+                "kernel": "k_hop<float2> (FP32 even-odd hop inside the inner BiCGstab)",
+                "peak_kind": peak_kind, "launches": hop32_n,
+                "avg_launch_ms": hop32_ms / hop32_n if hop32_n else None,
+                "algorithmic_bytes_per_launch": hop32_bytes / hop32_n if hop32_n else None}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(LATTICE), "blocks": len(ids),
+                   "omega_sites": n_om, "rhs_per_block": NRHS, "systems": len(ids) * NRHS,
+                   "site_rhs_per_step": units, "inner": "f32", "inner_tol": args.inner_tol,
+                   "tol": TOL, "l2": "inputs larger than L2 (3.9 GB rhs, ~15 GB working set)"},
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "solver": {"max_relres": stats["max_relres"], "max_iters": stats["max_iters"],
+                   "outer_cycles": stats["outer_cycles"]},
+        "plain_f64": {"value": world * units / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                      "max_iters": pst["max_iters"], "speedup_of_mixed": plain_ms / ms,
+                      "fp64_hop_ms_in_mixed_step": hop64_ms / args.steps},
+        "action": action,
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline_entry(U) if world == 1 else None
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def action_rate(dd4d, synth, torch, evals=5):
+    L = (8, 8, 8, 8)
+    U = synth.gauge_field(L, 0.3, 1)
+    c = dd4d.Context(L, 0.13)
+    c.gauge_upload(U)
+    c.set_geometry(cores_uniform(L, 3, 1))
+    dpi = c.geom_sites(dd4d.SET_DPI)
+    u = dd4d.roots(4, 0.5)
+    chi = synth.complex_gaussian(1, synth.TAG_CHI, (2, len(dpi), 12))
+    d = torch.from_numpy(chi.view(np.float64)).cuda()
+    prm = dd4d.params(TOL, inner_prec="f64")
+    for _ in range(2):
+        c.multiboson_action(u, d, prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        S, Sb, Sr, st = c.multiboson_action(u, d, prm)
+    dt = (time.perf_counter() - t0) / evals
+    c.close()
+    return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s",
+            "workload": "8^4, kappa 0.13, eps 0.3, 16 blocks of 5^4, N = 4 (2 fields), "
+                        "FP64 solves to 1e-10", "S": S}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

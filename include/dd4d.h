@@ -200,6 +200,10 @@ dd_status dd_timing_enable(dd_ctx* ctx, int on);
 dd_status dd_timing_get(dd_ctx* ctx, int which, double* ms, long long* launches,
                         double* bytes);
 
+/* Number of CUDA kernel launches the library has issued in this process
+ * (all contexts), for launch accounting by callers.  Host-only, no sync. */
+dd_status dd_launch_count(long long* n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,8 @@
 
 namespace dd {
 
+std::atomic<long long> g_launches{0};
+
 dd_status fail(dd_ctx* c, dd_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
@@ -305,11 +307,11 @@ dd_status ensure_links(dd_ctx* c, int i, dd_prec prec) {
   int th = 256;
   long long nb = (tot + th - 1) / th;
   if (prec == DD_F64)
-    k_gather_links<double2><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (double2*)*buf);
+    DD_COUNT_LAUNCH(), k_gather_links<double2><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (double2*)*buf);
   else if (prec == DD_F32)
-    k_gather_links<float2><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (float2*)*buf);
+    DD_COUNT_LAUNCH(), k_gather_links<float2><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (float2*)*buf);
   else
-    k_gather_links<__nv_bfloat162><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U,
+    DD_COUNT_LAUNCH(), k_gather_links<__nv_bfloat162><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U,
                                                (__nv_bfloat162*)*buf);
   DD_CUDA(c, cudaGetLastError());
   in.d.link64 = (const double2*)in.link64_buf;
@@ -533,7 +535,7 @@ dd_status dd_gauge_upload(dd_ctx* c, const double* U) {
   int spatial = c->V / c->L[0];
   if (c->time_bc != 1) {
     long long n = 9LL * spatial;
-    k_fold_time_sign<<<(n + 255) / 256, 256>>>(c->d_U, c->V, c->L[0], spatial, c->time_bc);
+    DD_COUNT_LAUNCH(), k_fold_time_sign<<<(n + 255) / 256, 256>>>(c->d_U, c->V, c->L[0], spatial, c->time_bc);
     DD_CUDA(c, cudaGetLastError());
   }
   DD_CUDA(c, cudaDeviceSynchronize());
@@ -749,6 +751,12 @@ dd_status dd_roots(int N, double c, double* u) {
     u[2 * (k - 1)] = cos(ph);
     u[2 * (k - 1) + 1] = s * sin(ph);
   }
+  return DD_OK;
+}
+
+dd_status dd_launch_count(long long* n) {
+  if (!n) return DD_EINVAL;
+  *n = dd::g_launches.load();
   return DD_OK;
 }
 

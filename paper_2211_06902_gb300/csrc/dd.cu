@@ -287,7 +287,7 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
   a.src = (double2*)src_o;
   BatchDev bd = batch_view(c, *ob);
   dim3 g1((c->info.max_omega + 127) / 128, nb * n_f);
-  k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
+  DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
   DD_CUDA(c, cudaGetLastError());
   dd_solve_stats st1{};
   dd_status r1 = solve_batch(c, *ob, (const double*)src_o, (double*)sol_o, prm, &st1, s, true);
@@ -295,7 +295,7 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
   // frame source and solve
   a.src = (double2*)src_f;
   dim3 g2((P.n_l1 + 127) / 128, n_f);
-  k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
+  DD_COUNT_LAUNCH(), k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
   DD_CUDA(c, cudaGetLastError());
   dd_solve_stats st2{};
   dd_status r2 = solve_batch(c, *fb, (const double*)src_f, (double*)sol_f, prm, &st2, s, true);
@@ -304,12 +304,12 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
   const int nB = c->info.n_B, nC = c->info.n_C;
   if (nB) {
     dim3 g((nB + 127) / 128, n_f);
-    k_extract<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
+    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
                                 ob->d_uoff, (const double2*)sol_o, (double2*)wchi);
   }
   if (nC) {
     dim3 g((nC + 127) / 128, n_f);
-    k_extract<<<g, 128, 0, s>>>(nullptr, P.d_c_loc, P.d_c_dpi, nC, n_f, c->info.n_dpi,
+    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(nullptr, P.d_c_loc, P.d_c_dpi, nC, n_f, c->info.n_dpi,
                                 fb->d_uoff, (const double2*)sol_f, (double2*)wchi);
   }
   DD_CUDA(c, cudaGetLastError());
@@ -376,11 +376,11 @@ dd_status dd_multiboson_action(dd_ctx* c, int n_f, const double* u, const double
   if (r != DD_OK && r != DD_ENOCONV) return r;
   DD_CUDA(c, cudaMemcpyAsync(du, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
   WPlan& P = *(WPlan*)c->wplan;
-  k_action_blocks<<<nb, 256, 0, s>>>(P.d_b_grp, P.d_b_dpi, n_f, c->info.n_dpi,
+  DD_COUNT_LAUNCH(), k_action_blocks<<<nb, 256, 0, s>>>(P.d_b_grp, P.d_b_dpi, n_f, c->info.n_dpi,
                                      (const double2*)du, (const double2*)din,
                                      (const double2*)wv, (double*)dS);
   if (P.n_cgrp > 0)
-    k_action_blocks<<<P.n_cgrp, 256, 0, s>>>(P.d_c_grp, P.d_c_dpi, n_f, c->info.n_dpi,
+    DD_COUNT_LAUNCH(), k_action_blocks<<<P.n_cgrp, 256, 0, s>>>(P.d_c_grp, P.d_c_dpi, n_f, c->info.n_dpi,
                                              (const double2*)du, (const double2*)din,
                                              (const double2*)wv, (double*)dS + nb);
   DD_CUDA(c, cudaGetLastError());

@@ -18,6 +18,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -142,6 +143,10 @@ struct dd_ctx {
 
 // ---- helpers shared by the translation units --------------------------------
 namespace dd {
+
+// process-wide count of kernel launches issued by the library
+extern std::atomic<long long> g_launches;
+#define DD_COUNT_LAUNCH() (dd::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 dd_status fail(dd_ctx* c, dd_status s, const std::string& msg);
 dd_status cuda_fail(dd_ctx* c, cudaError_t e, const char* where);

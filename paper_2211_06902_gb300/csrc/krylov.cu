@@ -70,9 +70,11 @@ __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restric
   typedef typename StoreTraits<S>::C C;
   __shared__ double red[64];
   ELEM_PROLOGUE
+  typedef typename StoreTraits<S>::T T;
   double acc[1] = {0.0};
   if (live) {
     const C z = cmk<C>(0.0, 0.0);
+    T t = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       long long q = o + (long long)k * n;
@@ -82,8 +84,9 @@ __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restric
       stc(p + q, z);
       stc(v + q, z);
       stc(x + q, z);
-      acc[0] += (double)b.x * b.x + (double)b.y * b.y;
+      t = fma(b.x, b.x, fma(b.y, b.y, t));
     }
+    acc[0] = t;
   }
   block_reduce<1>(acc, red);
   if (threadIdx.x == 0) {
@@ -140,10 +143,12 @@ __global__ void k_xr_update(BatchDev bd, const SysState* st, S* x, S* r, const S
   __shared__ double red[96];
   ELEM_PROLOGUE
   if (!st[sys].active) return;
+  typedef typename StoreTraits<S>::T T;
   double acc[3] = {0.0, 0.0, 0.0};
   if (live) {
     const C al = cmk<C>(st[sys].alpha.x, st[sys].alpha.y);
     const C om = cmk<C>(st[sys].omega.x, st[sys].omega.y);
+    T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       long long q = o + (long long)k * n;
@@ -153,10 +158,13 @@ __global__ void k_xr_update(BatchDev bd, const SysState* st, S* x, S* r, const S
       C rr = csub(ss, cmul(om, ldc(t + q)));
       stc(r + q, rr);
       C rh = ldc(rhat + q);
-      acc[0] += (double)rh.x * rr.x + (double)rh.y * rr.y;
-      acc[1] += (double)rh.x * rr.y - (double)rh.y * rr.x;
-      acc[2] += (double)rr.x * rr.x + (double)rr.y * rr.y;
+      a0 = fma(rh.x, rr.x, fma(rh.y, rr.y, a0));
+      a1 = fma(rh.x, rr.y, fma(-rh.y, rr.x, a1));
+      a2 = fma(rr.x, rr.x, fma(rr.y, rr.y, a2));
     }
+    acc[0] = a0;
+    acc[1] = a1;
+    acc[2] = a2;
   }
   block_reduce<3>(acc, red);
   if (threadIdx.x == 0) {
@@ -198,14 +206,22 @@ __global__ void k_norm2(BatchDev bd, int p, const S* __restrict__ v, double* par
   }
 }
 
-// y (type D) = x (type S), even parity, every system
+#define ELEM_PROLOGUE_P                                              \
+  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];        \
+  const int rh = blockIdx.y;                                          \
+  const int sys = it.x * bd.nrhs + rh;                                \
+  const DomInst* dp_ = bd.inst_tab + bd.inst[it.x];                   \
+  const int n = p ? dp_->n[1] : dp_->n[0];                            \
+  const int i = it.y + threadIdx.x;                                   \
+  const bool live = threadIdx.x < it.z;                               \
+  const long long o = (p ? bd.off[1] : bd.off[0])[sys] + i;
+
+// y (type SD) = x (type SS) on parity p, for systems still in the outer loop
 template <class SD, class SS>
-__global__ void k_convert(BatchDev bd, SD* y, const SS* __restrict__ x, const SysState* st,
-                          int only_outer_active) {
+__global__ void k_convert(BatchDev bd, int p, SD* y, const SS* __restrict__ x, const SysState* st) {
   typedef typename StoreTraits<SD>::C CD;
-  ELEM_PROLOGUE
-  if (!live) return;
-  if (only_outer_active && !st[sys].outer_active) return;
+  ELEM_PROLOGUE_P
+  if (!live || !st[sys].outer_active) return;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     long long q = o + (long long)k * n;
@@ -214,17 +230,18 @@ __global__ void k_convert(BatchDev bd, SD* y, const SS* __restrict__ x, const Sy
   }
 }
 
-// x64 += e (type S) for systems still in the outer loop
+// x64 += sign * e (type S) on parity p, for systems still in the outer loop
 template <class S>
-__global__ void k_accumulate(BatchDev bd, double2* x, const S* __restrict__ e, const SysState* st) {
-  ELEM_PROLOGUE
+__global__ void k_axpy64(BatchDev bd, int p, double2* x, const S* __restrict__ e, double sign,
+                         const SysState* st) {
+  ELEM_PROLOGUE_P
   if (!live || !st[sys].outer_active) return;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     long long q = o + (long long)k * n;
     auto v = ldc(e + q);
     double2 a = x[q];
-    x[q] = make_double2(a.x + (double)v.x, a.y + (double)v.y);
+    x[q] = make_double2(fma(sign, (double)v.x, a.x), fma(sign, (double)v.y, a.y));
   }
 }
 
@@ -256,17 +273,25 @@ __global__ void k_sc_bnorm(ScalarArgs a, const double* partial_o, const int* ib_
   s.outer_active = 1;
 }
 
-// outer residual |r|^2 (slot 0) -> outer_active
-__global__ void k_sc_outer(ScalarArgs a, int* count) {
+// outer residual |r|^2 over both parities -> outer_active, relres, count,
+// largest relative residual (as ordered bits of a non-negative double)
+__global__ void k_sc_outer(ScalarArgs a, const double* partial_o, const int* ib_o,
+                           long long stride_o, double margin2, int* count,
+                           unsigned long long* maxrel, double* relres) {
   int sys = blockIdx.x * blockDim.x + threadIdx.x;
   if (sys >= a.nsys) return;
   int j = sys / a.nrhs, r = sys % a.nrhs;
   SysState& s = a.st[sys];
-  double rr = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
+  double re = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
+  double ro = sum_slot(partial_o, 0, stride_o, ib_o[j], ib_o[j + 1], a.nrhs, r).x;
+  double rr = re + ro;
   s.rr = rr;
-  s.outer_active = (rr > s.outer2) && !(rr != rr) ? 1 : 0;
   if (rr != rr) s.status = 3;
+  s.outer_active = (rr > margin2 * s.outer2) && (rr == rr) ? 1 : 0;
+  double rel = s.bnorm2 > 0 ? sqrt(rr / s.bnorm2) : sqrt(rr);
+  relres[sys] = rel;
   if (s.outer_active) atomicAdd(count, 1);
+  atomicMax(maxrel, (unsigned long long)__double_as_longlong(rel == rel ? rel : 1e300));
 }
 
 // inner init: rho = |r|^2, alpha = omega = 1, threshold, active
@@ -332,17 +357,6 @@ __global__ void k_sc_omega(ScalarArgs a) {
   double2 ts = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r);
   double tt = sum_slot(a.partial, 1, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
   s.omega = tt > 0.0 ? make_double2(ts.x / tt, ts.y / tt) : make_double2(0.0, 0.0);
-}
-
-__global__ void k_sc_residual(ScalarArgs a, const double* partial_o, const int* ib_o,
-                              long long stride_o, double* relres) {
-  int sys = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sys >= a.nsys) return;
-  int j = sys / a.nrhs, r = sys % a.nrhs;
-  double re = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
-  double ro = sum_slot(partial_o, 0, stride_o, ib_o[j], ib_o[j + 1], a.nrhs, r).x;
-  double b2 = a.st[sys].bnorm2;
-  relres[sys] = b2 > 0 ? sqrt((re + ro) / b2) : sqrt(re + ro);
 }
 
 }  // namespace
@@ -411,16 +425,16 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
   const int sth = 128, sbl = (nsys + sth - 1) / sth;
   dim3 eg(b.nitems[0], b.nrhs);
   const double k2 = c->kappa * c->kappa;
-  k_inner_init<S><<<eg, 128, 0, s>>>(bd, st, (const S*)rhs, (S*)w.r, (S*)w.rhat, (S*)w.p, (S*)w.v,
+  DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, st, (const S*)rhs, (S*)w.r, (S*)w.rhat, (S*)w.p, (S*)w.v,
                                      (S*)w.x, partial);
-  k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
+  DD_COUNT_LAUNCH(), k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
   DD_CUDA(c, cudaGetLastError());
   int it = 0;
   for (; it < maxiter; ++it) {
     bool check = ((it + 1) % check_every) == 0;
     if (check) DD_CUDA(c, cudaMemsetAsync(d_count, 0, sizeof(int), s));
-    k_sc_beta<<<sbl, sth, 0, s>>>(sa, check ? d_count : nullptr);
-    k_p_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (S*)w.p, (const S*)w.v);
+    DD_COUNT_LAUNCH(), k_sc_beta<<<sbl, sth, 0, s>>>(sa, check ? d_count : nullptr);
+    DD_COUNT_LAUNCH(), k_p_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (S*)w.p, (const S*)w.v);
     // v = M p = p - k^2 H_eo H_oe p ; partial (rhat, v)
     HopArgs h1{};
     h1.p_out = 1; h1.in = w.p; h1.out = w.tmp; h1.b = 1.0;
@@ -433,8 +447,8 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     h2.dotq = w.rhat; h2.partial = partial;
     h2.active = h1.active; h2.active_stride = h1.active_stride;
     if ((e = launch_hop(c, b, prec, h2, s)) != DD_OK) return e;
-    k_sc_alpha<<<sbl, sth, 0, s>>>(sa);
-    k_s_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (const S*)w.v, (S*)w.s);
+    DD_COUNT_LAUNCH(), k_sc_alpha<<<sbl, sth, 0, s>>>(sa);
+    DD_COUNT_LAUNCH(), k_s_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (const S*)w.v, (S*)w.s);
     HopArgs h3{};
     h3.p_out = 1; h3.in = w.s; h3.out = w.tmp; h3.b = 1.0;
     h3.active = h1.active; h3.active_stride = h1.active_stride;
@@ -444,8 +458,8 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     h4.dots = w.s; h4.partial = partial;
     h4.active = h1.active; h4.active_stride = h1.active_stride;
     if ((e = launch_hop(c, b, prec, h4, s)) != DD_OK) return e;
-    k_sc_omega<<<sbl, sth, 0, s>>>(sa);
-    k_xr_update<S><<<eg, 128, 0, s>>>(bd, st, (S*)w.x, (S*)w.r, (const S*)w.p, (const S*)w.s,
+    DD_COUNT_LAUNCH(), k_sc_omega<<<sbl, sth, 0, s>>>(sa);
+    DD_COUNT_LAUNCH(), k_xr_update<S><<<eg, 128, 0, s>>>(bd, st, (S*)w.x, (S*)w.r, (const S*)w.p, (const S*)w.s,
                                       (const S*)w.t, (const S*)w.rhat, partial);
     DD_CUDA(c, cudaGetLastError());
     if (check) {
@@ -458,7 +472,7 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     }
   }
   // final beta pass marks converged systems (updates rr) without a p update
-  k_sc_beta<<<sbl, sth, 0, s>>>(sa, nullptr);
+  DD_COUNT_LAUNCH(), k_sc_beta<<<sbl, sth, 0, s>>>(sa, nullptr);
   *iters_run = it;
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
@@ -474,18 +488,21 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const dd_prec ip = prm->inner_prec;
   const size_t c64 = 16, cin = prec_bytes(ip);
   const long long ne = b.tot[0], no = b.tot[1];
-  // workspace slots: 0..6 FP64 outer, 7..14 inner, 15 partial, 16 states, 17 counters, 18 relres, 19 partial_o
-  void *be, *bo, *bh, *xe, *xo, *r64, *t64;
+  // FP64 outer vectors: b, x, r (both parities)
+  void *be, *bo, *xe, *xo, *re, *ro;
   if ((e = ws_get(c, 0, ne * c64, &be)) || (e = ws_get(c, 1, no * c64, &bo)) ||
-      (e = ws_get(c, 2, ne * c64, &bh)) || (e = ws_get(c, 3, ne * c64, &xe)) ||
-      (e = ws_get(c, 4, no * c64, &xo)) || (e = ws_get(c, 5, ne * c64, &r64)) ||
-      (e = ws_get(c, 6, no * c64, &t64)))
+      (e = ws_get(c, 2, ne * c64, &xe)) || (e = ws_get(c, 3, no * c64, &xo)) ||
+      (e = ws_get(c, 4, ne * c64, &re)) || (e = ws_get(c, 5, no * c64, &ro)))
     return e;
+  // inner vectors at the inner precision
   InnerVecs w;
+  void *rso, *rhs, *eo;
   if ((e = ws_get(c, 7, ne * cin, &w.r)) || (e = ws_get(c, 8, ne * cin, &w.rhat)) ||
       (e = ws_get(c, 9, ne * cin, &w.p)) || (e = ws_get(c, 10, ne * cin, &w.v)) ||
       (e = ws_get(c, 11, ne * cin, &w.s)) || (e = ws_get(c, 12, ne * cin, &w.t)) ||
-      (e = ws_get(c, 13, ne * cin, &w.x)) || (e = ws_get(c, 14, no * cin, &w.tmp)))
+      (e = ws_get(c, 13, ne * cin, &w.x)) || (e = ws_get(c, 14, no * cin, &w.tmp)) ||
+      (e = ws_get(c, 24, no * cin, &rso)) || (e = ws_get(c, 25, ne * cin, &rhs)) ||
+      (e = ws_get(c, 26, no * cin, &eo)))
     return e;
   void *vpart, *vst, *vcnt, *vrel, *vpart_o;
   const long long stride = (long long)b.nitems[0] * b.nrhs;
@@ -499,7 +516,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   double* partial_o = (double*)vpart_o;
   SysState* st = (SysState*)vst;
   int* d_count = (int*)vcnt;
-  int h_count = 0;
+  unsigned long long* d_maxrel = (unsigned long long*)((char*)vcnt + 16);
   for (int j = 0; j < b.nb; ++j) {
     if ((e = ensure_links(c, b.inst[j], DD_F64)) != DD_OK) return e;
     if (ip != DD_F64 && (e = ensure_links(c, b.inst[j], ip)) != DD_OK) return e;
@@ -509,7 +526,8 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   ScalarArgs sa{st, partial, b.d_item_begin[0], stride, nsys, b.nrhs};
   const int sth = 128, sbl = (nsys + sth - 1) / sth;
   dim3 eg(b.nitems[0], b.nrhs), og(b.nitems[1], b.nrhs);
-  const double kap = c->kappa, k2 = kap * kap;
+  const double kap = c->kappa;
+  const bool has_odd = b.nitems[1] > 0;
 
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
@@ -517,42 +535,63 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   cudaEventRecord(ev0, s);
 
   if ((e = launch_pack(c, b, b_user, be, bo, DD_F64, s)) != DD_OK) return e;
-  // |b|^2 over both parities
-  k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)be, partial, 0);
-  if (b.nitems[1]) k_norm2<double2><<<og, 128, 0, s>>>(bd, 1, (const double2*)bo, partial_o, 0);
-  k_sc_bnorm<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o, prm->tol * prm->tol);
-  // b^_e = b_e + k H_eo b_o
-  {
-    HopArgs h{};
-    h.p_out = 0; h.in = bo; h.out = bh; h.s1 = be; h.a1 = 1.0; h.b = kap;
-    if ((e = launch_hop(c, b, DD_F64, h, s)) != DD_OK) return e;
-  }
-  k_zero64<<<(ne + 255) / 256, 256, 0, s>>>((double2*)xe, ne);
-  DD_CUDA(c, cudaMemcpyAsync(r64, bh, ne * c64, cudaMemcpyDeviceToDevice, s));
+  DD_COUNT_LAUNCH(), k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)be, partial, 0);
+  if (has_odd) DD_COUNT_LAUNCH(), k_norm2<double2><<<og, 128, 0, s>>>(bd, 1, (const double2*)bo, partial_o, 0);
+  DD_COUNT_LAUNCH(), k_sc_bnorm<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o, prm->tol * prm->tol);
+  // x = 0, r = b
+  DD_COUNT_LAUNCH(), k_zero64<<<(ne + 255) / 256, 256, 0, s>>>((double2*)xe, ne);
+  if (no) DD_COUNT_LAUNCH(), k_zero64<<<(no + 255) / 256, 256, 0, s>>>((double2*)xo, no);
+  DD_CUDA(c, cudaMemcpyAsync(re, be, ne * c64, cudaMemcpyDeviceToDevice, s));
+  if (no) DD_CUDA(c, cudaMemcpyAsync(ro, bo, no * c64, cudaMemcpyDeviceToDevice, s));
   DD_CUDA(c, cudaGetLastError());
 
   const int check_every = std::max(1, prm->check_every);
-  const int max_outer = ip == DD_F64 ? std::max(1, prm->max_outer) : std::max(1, prm->max_outer);
+  const int max_outer = std::max(1, prm->max_outer);
   const double inner_tol2 = ip == DD_F64 ? 0.0 : prm->inner_tol * prm->inner_tol;
   const double floor_frac = ip == DD_F64 ? 0.25 : 0.0;
-  int cycles = 0, total_iters = 0;
-  for (int cyc = 0; cyc < max_outer; ++cyc) {
-    // outer residual norm and convergence
-    k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)r64, partial, 0);
-    DD_CUDA(c, cudaMemsetAsync(d_count, 0, sizeof(int), s));
-    k_sc_outer<<<sbl, sth, 0, s>>>(sa, d_count);
+  // The residual after a correction is recomputed in FP64 (r = b - D x) until
+  // it is below theta |b|; from there on it is updated as r -= D e with D e at
+  // the inner precision, whose rounding error (~ u32 cond(D) |r|) stays far
+  // below tol |b|.  Systems then stop at tol / 2 to keep a margin.
+  const double theta = prm->tol * 1e4;
+  int cycles = 0;
+  bool last_true = true;
+  double maxrel = 1.0;
+  for (int cyc = 0;; ++cyc) {
+    // |r|^2 of both parities -> convergence
+    DD_COUNT_LAUNCH(), k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)re, partial, 0);
+    if (has_odd) DD_COUNT_LAUNCH(), k_norm2<double2><<<og, 128, 0, s>>>(bd, 1, (const double2*)ro, partial_o, 0);
+    DD_CUDA(c, cudaMemsetAsync(vcnt, 0, 64, s));
+    DD_COUNT_LAUNCH(), k_sc_outer<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o,
+                                                     last_true ? 1.0 : 0.25, d_count, d_maxrel,
+                                                     (double*)vrel);
+    int h_count = 0;
+    unsigned long long h_max = 0;
     DD_CUDA(c, cudaMemcpyAsync(&h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(c, cudaMemcpyAsync(&h_max, d_maxrel, sizeof(h_max), cudaMemcpyDeviceToHost, s));
     DD_CUDA(c, cudaStreamSynchronize(s));
-    if (h_count == 0) break;
+    memcpy(&maxrel, &h_max, sizeof(double));
+    if (h_count == 0 || cyc == max_outer) break;
     ++cycles;
-    const void* rhs = r64;
+    const bool true_residual = (ip == DD_F64) || cyc == 0 || maxrel > theta;
+    // residual at the inner precision
+    const void *rin_e = re, *rin_o = ro;
     if (ip != DD_F64) {
-      if (ip == DD_F32)
-        k_convert<float2, double2><<<eg, 128, 0, s>>>(bd, (float2*)w.s, (const double2*)r64, st, 0);
-      else
-        k_convert<__nv_bfloat162, double2><<<eg, 128, 0, s>>>(bd, (__nv_bfloat162*)w.s,
-                                                              (const double2*)r64, st, 0);
-      rhs = w.s;   // k_inner_init copies rhs into r and rhat before s is reused
+      if (ip == DD_F32) {
+        DD_COUNT_LAUNCH(), k_convert<float2, double2><<<eg, 128, 0, s>>>(bd, 0, (float2*)w.s, (const double2*)re, st);
+        if (has_odd) DD_COUNT_LAUNCH(), k_convert<float2, double2><<<og, 128, 0, s>>>(bd, 1, (float2*)rso, (const double2*)ro, st);
+      } else {
+        DD_COUNT_LAUNCH(), k_convert<__nv_bfloat162, double2><<<eg, 128, 0, s>>>(bd, 0, (__nv_bfloat162*)w.s, (const double2*)re, st);
+        if (has_odd) DD_COUNT_LAUNCH(), k_convert<__nv_bfloat162, double2><<<og, 128, 0, s>>>(bd, 1, (__nv_bfloat162*)rso, (const double2*)ro, st);
+      }
+      rin_e = w.s;
+      rin_o = rso;
+    }
+    // Schur right-hand side r^_e = r_e + k H_eo r_o
+    {
+      HopArgs h{};
+      h.p_out = 0; h.in = rin_o; h.out = rhs; h.s1 = rin_e; h.a1 = 1.0; h.b = kap;
+      if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
     }
     int its = 0;
     if (ip == DD_F64)
@@ -565,36 +604,49 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       e = run_bicgstab<__nv_bfloat162>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
                                        floor_frac, prm->maxiter, check_every, s, &its);
     if (e != DD_OK) return e;
-    total_iters += its;
-    // x_e += e ; r = b^_e - M x_e (FP64)
-    if (ip == DD_F64) k_accumulate<double2><<<eg, 128, 0, s>>>(bd, (double2*)xe, (const double2*)w.x, st);
-    else if (ip == DD_F32) k_accumulate<float2><<<eg, 128, 0, s>>>(bd, (double2*)xe, (const float2*)w.x, st);
-    else k_accumulate<__nv_bfloat162><<<eg, 128, 0, s>>>(bd, (double2*)xe, (const __nv_bfloat162*)w.x, st);
-    HopArgs h1{};
-    h1.p_out = 1; h1.in = xe; h1.out = t64; h1.b = 1.0;
-    if ((e = launch_hop(c, b, DD_F64, h1, s)) != DD_OK) return e;
-    HopArgs h2{};
-    h2.p_out = 0; h2.in = t64; h2.out = r64; h2.s1 = bh; h2.a1 = 1.0; h2.s2 = xe; h2.a2 = -1.0;
-    h2.b = k2;
-    if ((e = launch_hop(c, b, DD_F64, h2, s)) != DD_OK) return e;
-  }
-  // x_o = b_o + k H_oe x_e
-  {
-    HopArgs h{};
-    h.p_out = 1; h.in = xe; h.out = xo; h.s1 = bo; h.a1 = 1.0; h.b = kap;
-    if ((e = launch_hop(c, b, DD_F64, h, s)) != DD_OK) return e;
-  }
-  // true residual of the full system: res = b - D x, both parities (FP64)
-  {
-    HopArgs h{};
-    h.p_out = 0; h.in = xo; h.out = r64; h.s1 = be; h.a1 = 1.0; h.s2 = xe; h.a2 = -1.0; h.b = kap;
-    if ((e = launch_hop(c, b, DD_F64, h, s)) != DD_OK) return e;
-    HopArgs g{};
-    g.p_out = 1; g.in = xe; g.out = t64; g.s1 = bo; g.a1 = 1.0; g.s2 = xo; g.a2 = -1.0; g.b = kap;
-    if ((e = launch_hop(c, b, DD_F64, g, s)) != DD_OK) return e;
-    k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)r64, partial, 0);
-    if (b.nitems[1]) k_norm2<double2><<<og, 128, 0, s>>>(bd, 1, (const double2*)t64, partial_o, 0);
-    k_sc_residual<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o, (double*)vrel);
+    // e_o = r_o + k H_oe e_e
+    {
+      HopArgs h{};
+      h.p_out = 1; h.in = w.x; h.out = eo; h.s1 = rin_o; h.a1 = 1.0; h.b = kap;
+      if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
+    }
+    // x += e (FP64)
+    if (ip == DD_F64) {
+      DD_COUNT_LAUNCH(), k_axpy64<double2><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const double2*)w.x, 1.0, st);
+      if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<double2><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const double2*)eo, 1.0, st);
+    } else if (ip == DD_F32) {
+      DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const float2*)w.x, 1.0, st);
+      if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const float2*)eo, 1.0, st);
+    } else {
+      DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const __nv_bfloat162*)w.x, 1.0, st);
+      if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const __nv_bfloat162*)eo, 1.0, st);
+    }
+    if (true_residual) {
+      // r = b - D x in FP64
+      HopArgs h{};
+      h.p_out = 0; h.in = xo; h.out = re; h.s1 = be; h.a1 = 1.0; h.s2 = xe; h.a2 = -1.0; h.b = kap;
+      if ((e = launch_hop(c, b, DD_F64, h, s)) != DD_OK) return e;
+      HopArgs g{};
+      g.p_out = 1; g.in = xe; g.out = ro; g.s1 = bo; g.a1 = 1.0; g.s2 = xo; g.a2 = -1.0; g.b = kap;
+      if ((e = launch_hop(c, b, DD_F64, g, s)) != DD_OK) return e;
+    } else {
+      // r -= D e with D e at the inner precision
+      HopArgs h{};
+      h.p_out = 0; h.in = eo; h.out = w.t; h.s1 = w.x; h.a1 = 1.0; h.b = -kap;
+      if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
+      HopArgs g{};
+      g.p_out = 1; g.in = w.x; g.out = w.tmp; g.s1 = eo; g.a1 = 1.0; g.b = -kap;
+      if ((e = launch_hop(c, b, ip, g, s)) != DD_OK) return e;
+      if (ip == DD_F32) {
+        DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)re, (const float2*)w.t, -1.0, st);
+        if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)ro, (const float2*)w.tmp, -1.0, st);
+      } else {
+        DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<eg, 128, 0, s>>>(bd, 0, (double2*)re, (const __nv_bfloat162*)w.t, -1.0, st);
+        if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<og, 128, 0, s>>>(bd, 1, (double2*)ro, (const __nv_bfloat162*)w.tmp, -1.0, st);
+      }
+    }
+    last_true = true_residual;
+    DD_CUDA(c, cudaGetLastError());
   }
   if ((e = launch_unpack(c, b, xe, xo, x_user, DD_F64, s)) != DD_OK) return e;
   cudaEventRecord(ev1, s);
@@ -619,7 +671,6 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     out.max_iters = std::max(out.max_iters, hst[k].iters);
     if (rel[k] <= prm->tol) out.converged++;
   }
-  (void)total_iters;
   if (stats) *stats = out;
   if (nan) return fail(c, DD_ENAN, "NaN in a solve residual");
   if (out.converged < nsys) {

@@ -52,15 +52,17 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
   hop_dir<MU, FWD>(acc, psi, U);
 }
 
-// grid: (nitems[p], nrhs); block: HOP_THREADS threads, one output site each.
+// grid: nitems[p] * nrhs CTAs, rhs fastest (the CTAs that share a site chunk,
+// and so its links, run together and hit L2); one output site per thread.
 template <class S>
 __global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<S>::T T;
   __shared__ double red[32 * 4];
   const int p = a.p_out;
-  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
-  const int r = blockIdx.y;
+  const int item = blockIdx.x / bd.nrhs;
+  const int r = blockIdx.x - item * bd.nrhs;
+  const int4 it = (p ? bd.items[1] : bd.items[0])[item];
   const int sys = it.x * bd.nrhs + r;
   if (a.active && !a.active[(long long)sys * a.active_stride]) return;
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
@@ -112,17 +114,21 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
     for (int k = 0; k < 12; ++k) stc(out_sys + (long long)k * n_out + i, out[k]);
   }
   const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
-  const long long my = (long long)blockIdx.x * bd.nrhs + r;
+  const long long my = (long long)item * bd.nrhs + r;
+  // per-thread sums in the storage's compute type (12 terms), FP64 across threads
   if (a.dotq) {
     double v[2] = {0.0, 0.0};
     if (live) {
       const S* q = (const S*)a.dotq + (p ? bd.off[1] : bd.off[0])[sys];
+      T t0 = 0, t1 = 0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         C w = ldc(q + (long long)k * n_out + i);
-        v[0] += (double)w.x * out[k].x + (double)w.y * out[k].y;
-        v[1] += (double)w.x * out[k].y - (double)w.y * out[k].x;
+        t0 = fma(w.x, out[k].x, fma(w.y, out[k].y, t0));
+        t1 = fma(w.x, out[k].y, fma(-w.y, out[k].x, t1));
       }
+      v[0] = t0;
+      v[1] = t1;
     }
     block_reduce<2>(v, red);
     if (threadIdx.x == 0) {
@@ -134,14 +140,18 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
     double v[3] = {0.0, 0.0, 0.0};
     if (live) {
       const S* q = (const S*)a.dots + (p ? bd.off[1] : bd.off[0])[sys];
+      T t0 = 0, t1 = 0, t2 = 0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         C w = ldc(q + (long long)k * n_out + i);
         // (out, s) = sum conj(out) s ; (out, out)
-        v[0] += (double)out[k].x * w.x + (double)out[k].y * w.y;
-        v[1] += (double)out[k].x * w.y - (double)out[k].y * w.x;
-        v[2] += (double)out[k].x * out[k].x + (double)out[k].y * out[k].y;
+        t0 = fma(out[k].x, w.x, fma(out[k].y, w.y, t0));
+        t1 = fma(out[k].x, w.y, fma(-out[k].y, w.x, t1));
+        t2 = fma(out[k].x, out[k].x, fma(out[k].y, out[k].y, t2));
       }
+      v[0] = t0;
+      v[1] = t1;
+      v[2] = t2;
     }
     block_reduce<3>(v, red);
     if (threadIdx.x == 0) {
@@ -170,7 +180,9 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, 
   BatchDev bd = batch_view(c, b);
   int p = a.p_out;
   if (b.nitems[p] == 0) return DD_OK;
-  dim3 grid(b.nitems[p], b.nrhs);
+  const long long nblk = (long long)b.nitems[p] * b.nrhs;
+  if (nblk > 0x7fffffffLL) return fail(c, DD_EINVAL, "batch too large for one launch");
+  dim3 grid((unsigned)nblk);
   dd::TimingRec rec;
   bool tm = c->timing;
   if (tm) {
@@ -180,9 +192,9 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, 
     rec.bytes = hop_bytes(b, p, prec_bytes(prec), (a.s1 ? 1 : 0) + (a.s2 ? 1 : 0));
     cudaEventRecord(rec.a, s);
   }
-  if (prec == DD_F64) k_hop<double2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
-  else if (prec == DD_F32) k_hop<float2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
-  else k_hop<__nv_bfloat162><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  if (prec == DD_F64) DD_COUNT_LAUNCH(), k_hop<double2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_hop<float2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  else DD_COUNT_LAUNCH(), k_hop<__nv_bfloat162><<<grid, HOP_THREADS, 0, s>>>(bd, a);
   if (tm) {
     cudaEventRecord(rec.b, s);
     c->trec.push_back(rec);
@@ -242,9 +254,9 @@ dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, v
     if (b.nitems[p] == 0) continue;
     dim3 grid(b.nitems[p], b.nrhs);
     void* v = p ? vo : ve;
-    if (prec == DD_F64) k_pack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (double2*)v);
-    else if (prec == DD_F32) k_pack<float2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (float2*)v);
-    else k_pack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (__nv_bfloat162*)v);
+    if (prec == DD_F64) DD_COUNT_LAUNCH(), k_pack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (double2*)v);
+    else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_pack<float2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (float2*)v);
+    else DD_COUNT_LAUNCH(), k_pack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (__nv_bfloat162*)v);
   }
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
@@ -259,9 +271,9 @@ dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* v
     if (b.nitems[p] == 0) continue;
     dim3 grid(b.nitems[p], b.nrhs);
     const void* v = p ? vo : ve;
-    if (prec == DD_F64) k_unpack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)v, (double2*)user);
-    else if (prec == DD_F32) k_unpack<float2><<<grid, 128, 0, s>>>(bd, p, (const float2*)v, (double2*)user);
-    else k_unpack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const __nv_bfloat162*)v, (double2*)user);
+    if (prec == DD_F64) DD_COUNT_LAUNCH(), k_unpack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)v, (double2*)user);
+    else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_unpack<float2><<<grid, 128, 0, s>>>(bd, p, (const float2*)v, (double2*)user);
+    else DD_COUNT_LAUNCH(), k_unpack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const __nv_bfloat162*)v, (double2*)user);
   }
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;

@@ -76,6 +76,7 @@ def lib():
             "dd_roots": [C.c_int, C.c_double, dp],
             "dd_timing_enable": [vp, C.c_int],
             "dd_timing_get": [vp, C.c_int, dp, C.POINTER(C.c_longlong), dp],
+            "dd_launch_count": [C.POINTER(C.c_longlong)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -90,7 +91,7 @@ def exported_symbols():
     return ["dd_create", "dd_destroy", "dd_strerror", "dd_last_error", "dd_set_kappa",
             "dd_gauge_upload", "dd_set_geometry", "dd_geom_sites", "dd_geom_block",
             "dd_apply_D_block", "dd_solve_blocks", "dd_apply_w", "dd_multiboson_action",
-            "dd_roots", "dd_timing_enable", "dd_timing_get"]
+            "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count"]
 
 
 def _ptr(x):
@@ -131,6 +132,13 @@ def roots(N, c):
     if st:
         raise DDError(st, lib().dd_strerror(st).decode())
     return out[0::2] + 1j * out[1::2]
+
+
+def launch_count():
+    """Kernel launches issued by the library so far in this process."""
+    n = C.c_longlong(0)
+    lib().dd_launch_count(C.byref(n))
+    return n.value
 
 
 class Context:
