@@ -550,9 +550,11 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const double inner_tol2 = ip == DD_F64 ? 0.0 : prm->inner_tol * prm->inner_tol;
   const double floor_frac = ip == DD_F64 ? 0.25 : 0.0;
   // The residual after a correction is recomputed in FP64 (r = b - D x) until
-  // it is below theta |b|; from there on it is updated as r -= D e with D e at
-  // the inner precision, whose rounding error (~ u32 cond(D) |r|) stays far
-  // below tol |b|.  Systems then stop at tol / 2 to keep a margin.
+  // it is below theta |b|; from there on, with an FP32 inner solve, it is
+  // updated as r -= D e with D e in FP32, whose rounding error
+  // (~ u32 cond(D) |r|) stays far below tol |b|.  Systems then stop at tol / 2
+  // to keep a margin.  BF16 links round at 2^-9, so BF16 inner solves always
+  // recompute the residual in FP64.
   const double theta = prm->tol * 1e4;
   int cycles = 0;
   bool last_true = true;
@@ -573,7 +575,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     memcpy(&maxrel, &h_max, sizeof(double));
     if (h_count == 0 || cyc == max_outer) break;
     ++cycles;
-    const bool true_residual = (ip == DD_F64) || cyc == 0 || maxrel > theta;
+    const bool true_residual = (ip != DD_F32) || cyc == 0 || maxrel > theta;
     // residual at the inner precision
     const void *rin_e = re, *rin_o = ro;
     if (ip != DD_F64) {
