@@ -141,4 +141,30 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* sh /* >= 3
   }
 }
 
+// Block reduction of per-thread values held in the compute type T: the warp
+// stage runs in T (FP32 for the FP32 / BF16 kernels, whose FP64 pipe is
+// narrow on this GPU), the cross-warp stage in FP64.  Result in thread 0.
+template <class T, int NV>
+__device__ __forceinline__ void block_reduce_t(T (&t)[NV], double (&v)[NV], double* sh) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[warp * NV + k] = (double)t[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < nw; ++w) a += sh[w * NV + k];
+      v[k] = a;
+    }
+  }
+}
+
 }  // namespace dd

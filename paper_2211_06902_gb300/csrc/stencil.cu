@@ -29,11 +29,10 @@ __device__ __forceinline__ const __nv_bfloat162* links_of<__nv_bfloat162>(const 
 
 template <int DIR, class S, class C>
 __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int n_out,
-                                        int n_in, const int* __restrict__ nbr,
-                                        const S* __restrict__ in_sys, const S* __restrict__ lk) {
+                                        int n_in, int j, const S* __restrict__ in_sys,
+                                        const S* __restrict__ lk) {
   constexpr int MU = DIR & 3;
   constexpr bool FWD = DIR < 4;
-  const int j = nbr[DIR * n_out + i];
   if (j < 0) return;
   C psi[12];
 #pragma unroll
@@ -54,8 +53,13 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
 
 // grid: nitems[p] * nrhs CTAs, rhs fastest (the CTAs that share a site chunk,
 // and so its links, run together and hit L2); one output site per thread.
+// resident CTAs per SM asked of the register allocator, per storage type
+template <class S> struct HopOccupancy { static constexpr int value = 6; };
+template <> struct HopOccupancy<double2> { static constexpr int value = 3; };
+template <> struct HopOccupancy<__nv_bfloat162> { static constexpr int value = 5; };
+
 template <class S>
-__global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
+__global__ void __launch_bounds__(HOP_THREADS, HopOccupancy<S>::value) k_hop(BatchDev bd, HopArgs a) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<S>::T T;
   __shared__ double red[32 * 4];
@@ -79,14 +83,17 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
     for (int k = 0; k < 12; ++k) acc[k] = cmk<C>(0.0, 0.0);
     const int* nbr = dp->nbr + (p ? 8LL * n0 : 0);
     const S* lk = links_of<S>(*dp);
-    hop_one<0, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<1, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<2, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<3, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<4, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<5, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<6, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
-    hop_one<7, S>(acc, n0, p, i, n_out, n_in, nbr, in_sys, lk);
+    int jn[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) jn[d] = __ldg(nbr + d * n_out + i);
+    hop_one<0, S>(acc, n0, p, i, n_out, n_in, jn[0], in_sys, lk);
+    hop_one<1, S>(acc, n0, p, i, n_out, n_in, jn[1], in_sys, lk);
+    hop_one<2, S>(acc, n0, p, i, n_out, n_in, jn[2], in_sys, lk);
+    hop_one<3, S>(acc, n0, p, i, n_out, n_in, jn[3], in_sys, lk);
+    hop_one<4, S>(acc, n0, p, i, n_out, n_in, jn[4], in_sys, lk);
+    hop_one<5, S>(acc, n0, p, i, n_out, n_in, jn[5], in_sys, lk);
+    hop_one<6, S>(acc, n0, p, i, n_out, n_in, jn[6], in_sys, lk);
+    hop_one<7, S>(acc, n0, p, i, n_out, n_in, jn[7], in_sys, lk);
     const T b = (T)a.b;
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = cscale(acc[k], b);
@@ -118,19 +125,17 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
   // per-thread sums in the storage's compute type (12 terms), FP64 across threads
   if (a.dotq) {
     double v[2] = {0.0, 0.0};
+    T t[2] = {0, 0};
     if (live) {
       const S* q = (const S*)a.dotq + (p ? bd.off[1] : bd.off[0])[sys];
-      T t0 = 0, t1 = 0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         C w = ldc(q + (long long)k * n_out + i);
-        t0 = fma(w.x, out[k].x, fma(w.y, out[k].y, t0));
-        t1 = fma(w.x, out[k].y, fma(-w.y, out[k].x, t1));
+        t[0] = fma(w.x, out[k].x, fma(w.y, out[k].y, t[0]));
+        t[1] = fma(w.x, out[k].y, fma(-w.y, out[k].x, t[1]));
       }
-      v[0] = t0;
-      v[1] = t1;
     }
-    block_reduce<2>(v, red);
+    block_reduce_t<T, 2>(t, v, red);
     if (threadIdx.x == 0) {
       a.partial[2 * my] = v[0];
       a.partial[2 * my + 1] = v[1];
@@ -138,22 +143,19 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop(BatchDev bd, HopArgs a) {
   }
   if (a.dots) {
     double v[3] = {0.0, 0.0, 0.0};
+    T t[3] = {0, 0, 0};
     if (live) {
       const S* q = (const S*)a.dots + (p ? bd.off[1] : bd.off[0])[sys];
-      T t0 = 0, t1 = 0, t2 = 0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         C w = ldc(q + (long long)k * n_out + i);
         // (out, s) = sum conj(out) s ; (out, out)
-        t0 = fma(out[k].x, w.x, fma(out[k].y, w.y, t0));
-        t1 = fma(out[k].x, w.y, fma(-out[k].y, w.x, t1));
-        t2 = fma(out[k].x, out[k].x, fma(out[k].y, out[k].y, t2));
+        t[0] = fma(out[k].x, w.x, fma(out[k].y, w.y, t[0]));
+        t[1] = fma(out[k].x, w.y, fma(-out[k].y, w.x, t[1]));
+        t[2] = fma(out[k].x, out[k].x, fma(out[k].y, out[k].y, t[2]));
       }
-      v[0] = t0;
-      v[1] = t1;
-      v[2] = t2;
     }
-    block_reduce<3>(v, red);
+    block_reduce_t<T, 3>(t, v, red);
     if (threadIdx.x == 0) {
       double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
       P[2 * my] = v[0];
