@@ -544,7 +544,9 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const int check_every = std::max(1, prm->check_every);
   const int max_outer = std::max(1, prm->max_outer);
   const double inner_tol2 = ip == DD_F64 ? 0.0 : prm->inner_tol * prm->inner_tol;
-  const double floor_frac = ip == DD_F64 ? 0.25 : 0.0;
+  // inner solves stop at inner_tol |r| but never below (tol/2)^2 |b|^2 (plain
+  // FP64) or (tol/4)^2 |b|^2 (mixed, whose last cycle must clear tol/2)
+  const double floor_frac = ip == DD_F64 ? 0.25 : 0.0625;
   // The residual after a correction is recomputed in FP64 (r = b - D x) until
   // it is below theta |b|; from there on, with an FP32 inner solve, it is
   // updated as r -= D e with D e in FP32, whose rounding error
