@@ -200,6 +200,28 @@ dd_status dd_timing_enable(dd_ctx* ctx, int on);
 dd_status dd_timing_get(dd_ctx* ctx, int which, double* ms, long long* launches,
                         double* bytes);
 
+/* ---- stencil without device allocation -------------------------------------
+ * The paper has no counterpart: this entry point is for callers that must not
+ * allocate GPU memory during a call (a host that budgets all device memory up
+ * front, an external caching allocator that must own every allocation, or
+ * code that cannot take the implicit synchronisation of cudaMalloc/cudaFree).
+ * It computes the same FP64 result as dd_apply_D_block(..., DD_F64, ...) with
+ * the same caller layout, but takes its scratch (packed copies and launch
+ * descriptors) from one static device array of DD_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library keeps until the process exits, and reads the
+ * links from the context's global FP64 gauge copy.  in/out must be device
+ * pointers.  Requests whose scratch exceeds the array (about 64 MiB / 384 B
+ * per (site, rhs) pair) return DD_EINVAL with the size in dd_last_error.
+ * Phi1 domains must have been built by an earlier dd_apply_D_block or
+ * dd_solve_blocks call on them.  Every call shares the array: calls whose GPU
+ * work overlaps (other streams or threads) race, so serialise them.  The first
+ * call on each device resolves the array's address (cudaGetSymbolAddress);
+ * make it before any stream capture.  Asynchronous on `stream`; calls no
+ * allocating routine. */
+#define DD_NOALLOC_SCRATCH_BYTES (64u << 20)
+dd_status dd_apply_D_block_noalloc(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
+                                   int nrhs, const double* in, double* out, void* stream);
+
 /* Number of CUDA kernel launches the library has issued in this process
  * (all contexts), for launch accounting by callers.  Host-only, no sync. */
 dd_status dd_launch_count(long long* n);

@@ -77,6 +77,7 @@ def lib():
             "dd_timing_enable": [vp, C.c_int],
             "dd_timing_get": [vp, C.c_int, dp, C.POINTER(C.c_longlong), dp],
             "dd_launch_count": [C.POINTER(C.c_longlong)],
+            "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -91,7 +92,8 @@ def exported_symbols():
     return ["dd_create", "dd_destroy", "dd_strerror", "dd_last_error", "dd_set_kappa",
             "dd_gauge_upload", "dd_set_geometry", "dd_geom_sites", "dd_geom_block",
             "dd_apply_D_block", "dd_solve_blocks", "dd_apply_w", "dd_multiboson_action",
-            "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count"]
+            "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count",
+            "dd_apply_D_block_noalloc"]
 
 
 def _ptr(x):
@@ -208,6 +210,14 @@ class Context:
         p = PREC[prec] if isinstance(prec, str) else prec
         self._check(lib().dd_apply_D_block(self._h, kind, idarr, len(ids), nrhs, _ptr(inp),
                                            _ptr(out), p, _stream(stream)))
+
+    def apply_D_block_noalloc(self, kind, ids, nrhs, inp, out, stream=None):
+        """FP64 D_X without device allocation (device tensors only)."""
+        kind = DOMAIN[kind] if isinstance(kind, str) else kind
+        ids = list(ids) if ids is not None else [0]
+        idarr = (C.c_int * len(ids))(*ids)
+        self._check(lib().dd_apply_D_block_noalloc(self._h, kind, idarr, len(ids), nrhs,
+                                                   _ptr(inp), _ptr(out), _stream(stream)))
 
     def solve_blocks(self, kind, ids, nrhs, b, x, prm=None, stream=None):
         kind = DOMAIN[kind] if isinstance(kind, str) else kind
