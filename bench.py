@@ -274,6 +274,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
 
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms)
+        learned["max_iters_without"] = stats["max_iters"]
+
     # end to end through the C ABI with pinned host buffers
     bh = torch.from_numpy(b_h.view(np.float64)).pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -291,9 +296,11 @@ def run_ours(args):
     del bh, xh
 
     # multi-boson action on the 8^4 lattice (16 blocks of 5^4, N = 4, 2 fields)
-    action = None
+    action = uneven = None
     if rank == 0:
         action = action_rate(dd4d, synth, torch)
+        if not args.no_uneven:
+            uneven = uneven_action_rate(dd4d, synth, torch)
 
     peak, peak_kind = measured_peaks()
     achieved = hop32_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
@@ -323,6 +330,8 @@ def run_ours(args):
                       "max_iters": pst["max_iters"], "speedup_of_mixed": plain_ms / ms,
                       "fp64_hop_ms_in_mixed_step": hop64_ms / args.steps},
         "action": action,
+        "action_uneven": uneven,
+        "learned_guess": learned,
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline_entry(U) if world == 1 else None
@@ -333,7 +342,46 @@ def run_ours(args):
     return 0
 
 
+def learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms_plain_guess):
+    """Trains the parallel-transport network on three other 16^4 lattices
+    (eps 0.4, 0.5, 0.6; 16 framed blocks x 4 rhs each; targets from the FP64
+    solver) and times the bench batch (held-out lattice) with the network as
+    initial guess, against the same solve without it."""
+    net = dd4d.Net(ctx, synth.net_init_weights(11))
+    train = []
+    for k, eps in enumerate((0.4, 0.5, 0.6)):
+        L = (16, 16, 16, 16)
+        c = dd4d.Context(L, KAPPA)
+        c.gauge_upload(synth.gauge_field(L, eps, 100 + k))
+        info = c.set_geometry(cores_uniform(L, CORE, FRAME))
+        bt = synth.complex_gaussian(100 + k, synth.TAG_RHS, (info["nblocks"], 4, info["max_omega"], 12))
+        st = net.train(list(range(info["nblocks"])), 4,
+                       torch.from_numpy(bt.view(np.float64)).cuda(), steps=80, lr=3e-3, ctx=c)
+        train.append({"eps": eps, "loss_first": st["loss_first"], "loss_last": st["loss_last"],
+                      "seconds": st["seconds"], "pairs": st["pairs"]})
+        c.close()
+    net.attach(ctx)
+    prm = dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, net_guess=True)
+    ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    net.detach(ctx)
+    net.close()
+    return {"workload": "network trained on 3 x 16^4 lattices (eps 0.4/0.5/0.6, 64 pairs each), "
+                        "4 layers 4-16-16-16-4, BF16 weights, used as initial guess on the "
+                        "held-out bench lattice (seed 2)",
+            "training": train, "ms_per_step_with_net": ms, "ms_per_step_without": ms_plain_guess,
+            "value_with_net": units / (ms * 1e-3), "max_iters_with_net": st["max_iters"],
+            "max_relres_with_net": st["max_relres"], "status": st["status"]}
+
+
 def action_rate(dd4d, synth, torch, evals=5):
+    """Multi-boson action on the 8^4 lattice (16 blocks of 5^4, N = 4)."""
     L = (8, 8, 8, 8)
     U = synth.gauge_field(L, 0.3, 1)
     c = dd4d.Context(L, 0.13)
@@ -343,7 +391,7 @@ def action_rate(dd4d, synth, torch, evals=5):
     u = dd4d.roots(4, 0.5)
     chi = synth.complex_gaussian(1, synth.TAG_CHI, (2, len(dpi), 12))
     d = torch.from_numpy(chi.view(np.float64)).cuda()
-    prm = dd4d.params(TOL, inner_prec="f64")
+    prm = dd4d.params(TOL, inner_prec="f64", graph=True, autotune=True)
     for _ in range(2):
         c.multiboson_action(u, d, prm)
     torch.cuda.synchronize()
@@ -351,10 +399,58 @@ def action_rate(dd4d, synth, torch, evals=5):
     for _ in range(evals):
         S, Sb, Sr, st = c.multiboson_action(u, d, prm)
     dt = (time.perf_counter() - t0) / evals
+    stats = c.last_solve_stats()
     c.close()
     return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s",
-            "workload": "8^4, kappa 0.13, eps 0.3, 16 blocks of 5^4, N = 4 (2 fields), "
-                        "FP64 solves to 1e-10", "S": S}
+            "workload": "8^4, kappa 0.13, eps 0.3, 16 blocks of 5^4 + frame in one batch, "
+                        "N = 4 (2 fields), FP64 solves to 1e-10, CUDA graphs, autotuned",
+            "S": S, "max_relres": stats["max_relres"]}
+
+
+def uneven_action_rate(dd4d, synth, torch, evals=2):
+    """Multi-boson action on 64x32^3 with uneven blocks (cores 6 and 8 mixed,
+    frame 1: 512 framed blocks of 8^4..10^4 sites in 16 shapes) plus the frame
+    Lambda1, 12 fields (N = 24), FP32 inner solves + FP64 defect correction,
+    every block and the frame in one batch, CUDA graphs, autotuned launches."""
+    L = (64, 32, 32, 32)
+
+    def cores(n, sizes):
+        out, x = [], 0
+        for k in range(n):
+            c = sizes[k % 2]
+            out.append((x, x + c - 1))
+            x += c + 1
+        return out
+    cl = [cores(8, (6, 8))] + [cores(4, (6, 8))] * 3
+    t0 = time.perf_counter()
+    U = synth.gauge_field(L, 0.6, 3)
+    c = dd4d.Context(L, 0.136)
+    c.gauge_upload(U)
+    info = c.set_geometry(cl)
+    dpi = c.geom_sites(dd4d.SET_DPI)
+    n_f = 12
+    u = dd4d.roots(2 * n_f, 0.5)
+    chi = synth.complex_gaussian(3, synth.TAG_CHI, (n_f, len(dpi), 12))
+    d = torch.from_numpy(chi.view(np.float64)).cuda()
+    setup = time.perf_counter() - t0
+    prm = dd4d.params(TOL, inner_prec="f32", graph=True, autotune=True)
+    c.multiboson_action(u, d, prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        S, Sb, Sr, st = c.multiboson_action(u, d, prm)
+    dt = (time.perf_counter() - t0) / evals
+    stats = c.last_solve_stats()
+    sizes = sorted({len(c.geom_sites(dd4d.SET_OMEGA, b)) for b in range(0, info["nblocks"], 7)})
+    c.close()
+    return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s",
+            "workload": "64x32^3, kappa 0.136, eps 0.6, seed 3: 512 uneven framed blocks "
+                        "(cores 6/8 per direction, frame 1) + frame Lambda1 (%d sites), "
+                        "12 fields (N = 24, c = 0.5), FP32 inner + FP64 defect correction "
+                        "to 1e-10, one batch, CUDA graphs, autotuned" % info["n_lambda1"],
+            "omega_sizes_seen": sizes, "n_dpi": info["n_dpi"], "S": S,
+            "max_relres": stats["max_relres"], "max_iters": stats["max_iters"],
+            "setup_s": setup, "s_per_eval": dt}
 
 
 def main():
@@ -364,6 +460,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner-tol", type=float, default=3e-6)
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="omit the 64x32^3 uneven-block action measurement")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="omit the learned-initial-guess A/B measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -93,7 +93,17 @@ typedef struct {
   double inner_tol;    /* relative reduction per inner solve (mixed only), e.g. 1e-5 */
   int max_outer;       /* defect-correction cycles cap (mixed only) */
   int check_every;     /* iterations between host convergence checks (>= 1) */
+  int flags;           /* DD_SOLVE_GRAPH | DD_SOLVE_AUTOTUNE, or 0 */
 } dd_solve_params;
+
+/* dd_solve_params.flags */
+#define DD_SOLVE_GRAPH 1     /* replay the inner iterations between two host polls as one
+                                captured CUDA graph (ignored while kernel timing is on) */
+#define DD_SOLVE_AUTOTUNE 2  /* on a batch's first solve, time every compiled launch variant
+                                of the stencil (resident CTAs per SM, persistent grid) and
+                                keep the fastest for that batch */
+#define DD_SOLVE_NET_GUESS 4 /* framed-block batches start from x0 = N(b), the network set
+                                with dd_set_net (ignored when none is set) */
 
 typedef struct {
   int systems;         /* number of (block, rhs) systems solved */
@@ -166,6 +176,10 @@ dd_status dd_solve_blocks(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
                           const dd_solve_params* params, dd_solve_stats* stats,
                           void* stream);
 
+/* Statistics of the last batched solve run on the context (by any call,
+ * including the block and frame solves inside dd_apply_w). */
+dd_status dd_last_solve_stats(const dd_ctx* ctx, dd_solve_stats* stats);
+
 /* ---- the operator w (paper Sec. 3, Eqs. Wz and offdiagW1) ----------------
  * For n_f fields chi on dPi (layout [f][dPi site in dd_geom_sites order][12]):
  *   (w chi)_{dLambda0^a} = -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi
@@ -189,6 +203,71 @@ dd_status dd_multiboson_action(dd_ctx* ctx, int n_f, const double* u, const doub
  * k = 1..N/2: the roots that carry the N/2 multi-boson fields (conjugates
  * u_{N+1-k} pair with them).  N even >= 2, 0 <= c < 1.  u: host, N doubles. */
 dd_status dd_roots(int N, double c, double* u);
+
+/* ---- dense check of the factorization (paper Sec. 3, Eq. detD) -------------
+ * On small lattices (12 V <= 8192) assembles D, D_Lambda1, every D_Omega0^a,
+ * every D_Phi1^a and W_1 = 1 - w on the GPU (the library's operators applied
+ * to unit vectors; w's solves use `params`, e.g. FP64 to 1e-12) and
+ * factorises each with an FP64 complex LU with partial pivoting, to check
+ *   ln|det D| = ln|det W_1| + ln|det D_Lambda1| + sum_a ln|det D_Omega0^a|
+ *               - sum_a ln|det D_Phi1^a|
+ * and the corresponding phases.  logabs_omega / logabs_phi: host arrays of
+ * nblocks doubles or NULL.  Synchronises; allocates work space. */
+typedef struct {
+  double logabs_D, logabs_W1, logabs_Lambda1;
+  double logabs_Omega, logabs_Phi;   /* sums over the blocks */
+  double phase_D;                    /* arg det D in (-pi, pi] */
+  double phase_rhs;                  /* arg of det W1 det D_L1 prod det D_Omega / prod det D_Phi */
+  double residual;                   /* logabs_D minus the right-hand side */
+  int dim_D, dim_W1, dim_Lambda1;
+} dd_logdet_report;
+dd_status dd_logdet_check(dd_ctx* ctx, const dd_solve_params* params, double* logabs_omega,
+                          double* logabs_phi, dd_logdet_report* report, void* stream);
+
+/* ---- learned block preconditioner (BASELINE north star part 4; the paper's
+ * only learning-related passage, Sec. 5 on flow-based models, is different).
+ * A gauge-covariant network of linear parallel-transport convolutions on a
+ * framed block Omega0^a (Dirichlet boundary): one layer maps C_in channels of
+ * colour 3-vectors to C_out,
+ *   y_c(x) = sum_{d in {0,+-mu}} sum_c' W[d][c][c'] (T_d phi_c')(x),
+ *   T_+mu phi(x) = U_mu(x) phi(x+mu), T_-mu phi(x) = U_mu(x-mu)^+ phi(x-mu),
+ * weights complex, [layer][d = 0, +0..+3, -0..-3][c_out][c_in], complex128
+ * (re, im) on the host.  Supported layers 4->16, 16->16, 16->4 (input and
+ * output: the 4 spin components of a spinor).  FP32 master weights (Adam),
+ * BF16-rounded weights in the kernels, FP32 activations and accumulation. */
+typedef struct dd_net dd_net;
+typedef struct {
+  int steps;          /* full-batch Adam steps */
+  double lr;          /* Adam learning rate */
+  double solve_tol;   /* tolerance of the FP64 solves that make the targets (e.g. 1e-10) */
+} dd_train_params;
+typedef struct {
+  double loss_first;  /* mean |N(b) - x|^2 / |x|^2 before the first step */
+  double loss_last;   /* after the last step */
+  int steps, pairs;
+  double seconds;     /* device time: target solves + training */
+} dd_train_stats;
+dd_status dd_net_create(dd_ctx* ctx, int nlayers, const int* channels, const double* weights,
+                        dd_net** net);
+dd_status dd_net_destroy(dd_net* net);
+dd_status dd_net_weights(const dd_net* net, double* weights);  /* FP32 masters -> host */
+/* out = N(in) on framed blocks ids (device pointers, caller layout of dd_solve_blocks). */
+dd_status dd_net_apply(dd_ctx* ctx, dd_net* net, const int* ids, int nblk, int nrhs,
+                       const double* in, double* out, void* stream);
+/* Mean loss over the (b, x) pairs and its gradient with respect to the weights
+ * (dL/dRe + i dL/dIm, host, weight layout), evaluated with the BF16-rounded
+ * weights.  Device pointers.  Synchronises. */
+dd_status dd_net_loss_grad(dd_ctx* ctx, dd_net* net, const int* ids, int nblk, int nrhs,
+                           const double* b, const double* x, double* loss, double* grads,
+                           void* stream);
+/* Trains on framed blocks ids: targets x = D_Omega^{-1} b from the library's FP64
+ * solver for the given right-hand sides b (device pointer), then full-batch Adam
+ * steps on the GPU.  Synchronises. */
+dd_status dd_net_train(dd_ctx* ctx, dd_net* net, const int* ids, int nblk, int nrhs,
+                       const double* b, const dd_train_params* params, dd_train_stats* stats,
+                       void* stream);
+/* Network used by DD_SOLVE_NET_GUESS on this context (NULL to clear; not owned). */
+dd_status dd_set_net(dd_ctx* ctx, dd_net* net);
 
 /* ---- kernel timing -----------------------------------------------------
  * With timing on, the library brackets every launch of its stencil kernels

@@ -24,6 +24,10 @@ dd_status get_batch(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrh
       inst.push_back(i);
     }
   }
+  return get_batch_insts(c, inst, nrhs, out);
+}
+
+dd_status get_batch_insts(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch** out) {
   std::ostringstream key;
   key << nrhs << ':';
   for (int i : inst) key << i << ',';
@@ -87,6 +91,12 @@ static dd_status unstage(dd_ctx* c, double* out, size_t bytes, const Staged& sg,
 using namespace dd;
 
 extern "C" {
+
+dd_status dd_last_solve_stats(const dd_ctx* c, dd_solve_stats* st) {
+  if (!c || !st) return DD_EINVAL;
+  *st = c->last_stats;
+  return DD_OK;
+}
 
 dd_status dd_apply_D_block(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs,
                            const double* in, double* out, dd_prec prec, void* stream) {

@@ -50,6 +50,7 @@ bool is_device_ptr(const void* p) {
 size_t prec_bytes(dd_prec p) { return p == DD_F64 ? 16 : (p == DD_F32 ? 8 : 4); }
 
 Batch::~Batch() {
+  for (auto& g : graphs) cudaGraphExecDestroy(g.second);
   dfree(d_inst);
   dfree(d_uoff);
   for (int p = 0; p < 2; ++p) {
@@ -380,6 +381,7 @@ dd_status ensure_phi(dd_ctx* c) {
 
 dd_status make_batch(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch& b) {
   const int CH = 128;
+  if (nrhs > 65535 || inst.size() > 65535) return fail(c, DD_EINVAL, "at most 65535 rhs and instances per batch");
   b.nb = (int)inst.size();
   b.nrhs = nrhs;
   b.inst = inst;
@@ -511,8 +513,10 @@ dd_status dd_destroy(dd_ctx* c) {
   dfree(c->d_inst);
   dfree(c->d_dpi_pos);
   dfree(c->d_dpi_kind);
+  dfree(c->d_tbytes);
   free_workspace(c);
   free_plan(c);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   c->batches.clear();
   for (auto& r : c->trec) {
     cudaEventDestroy(r.a);
@@ -779,6 +783,12 @@ dd_status dd_timing_get(dd_ctx* c, int which, double* ms, long long* launches, d
     cudaEventDestroy(r.b);
   }
   c->trec.clear();
+  if (c->d_tbytes) {
+    double hb[3];
+    cudaMemcpy(hb, c->d_tbytes, sizeof(hb), cudaMemcpyDeviceToHost);
+    for (int k = 0; k < 3; ++k) c->t_bytes[k] += hb[k];
+    cudaMemset(c->d_tbytes, 0, sizeof(hb));
+  }
   if (ms) *ms = c->t_ms[which];
   if (launches) *launches = c->t_n[which];
   if (bytes) *bytes = c->t_bytes[which];

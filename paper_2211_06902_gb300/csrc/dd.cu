@@ -68,10 +68,10 @@ __device__ void add_exterior_hop(double2 (&acc)[12], int dir, int gx, int gy, co
 }
 
 // Sources for the Omega blocks: s(x) = D_{Omega, ext} chi, x in the box.
-// grid: (ceil(max_sites/128), nblk * n_f)
+// grid: (ceil(max_sites/128), n_f, nblk)
 __global__ void k_inject_omega(BatchDev bd, InjectArgs a) {
-  const int sys = blockIdx.y;
-  const int j = sys / a.n_f, f = sys % a.n_f;
+  const int f = blockIdx.y, j = blockIdx.z;
+  const int sys = j * a.n_f + f;
   const DomInst* d = bd.inst_tab + bd.inst[j];
   const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d->nsites) return;
@@ -123,16 +123,17 @@ __global__ void k_inject_frame(const int* __restrict__ l1_glob, int n_l1,
 }
 
 // (w chi) on dLambda0: -x at the block-boundary sites; on dPi1: -y.  For
-// every listed site: its system (block, or 0 for the frame), its offset
+// every listed site: its system's instance in the batch (a block, or the
+// frame at position nblocks), its offset
 // inside the system's caller-layout solution and its dPi index.
-__global__ void k_extract(const int* __restrict__ sys_blk, const long long* __restrict__ loc,
+__global__ void k_extract(const int* __restrict__ sys_blk, int blk_fixed, const long long* __restrict__ loc,
                           const int* __restrict__ dpi_idx, int n, int n_f, int n_dpi,
                           const long long* __restrict__ uoff, const double2* __restrict__ sol,
                           double2* __restrict__ w) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (k >= n) return;
-  const int blk = sys_blk ? sys_blk[k] : 0;
+  const int blk = sys_blk ? sys_blk[k] : blk_fixed;
   const double2* s = sol + uoff[(long long)blk * n_f + f] + loc[k];
   double2* o = w + ((long long)f * n_dpi + dpi_idx[k]) * 12;
 #pragma unroll
@@ -259,21 +260,22 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
   if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
   if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
   const int nb = (int)c->blocks.size();
-  std::vector<int> ids(nb);
-  for (int b = 0; b < nb; ++b) ids[b] = b;
-  Batch *ob, *fb;
+  // one batch: every framed block Omega0^a and the frame Lambda1, n_f fields
+  // each; the frame's source does not depend on the block solutions, so the
+  // uneven blocks and the frame run through the same launches
+  std::vector<int> insts(nb + 1);
+  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
+  insts[nb] = c->lambda1;
+  Batch* ob;
   dd_status e;
-  if ((e = get_batch(c, DD_DOMAIN_OMEGA, ids.data(), nb, n_f, &ob)) != DD_OK) return e;
-  if ((e = get_batch(c, DD_DOMAIN_LAMBDA1, nullptr, 1, n_f, &fb)) != DD_OK) return e;
+  if ((e = get_batch_insts(c, insts, n_f, &ob)) != DD_OK) return e;
   WPlan* PP;
   if ((e = build_plan(c, &PP)) != DD_OK) return e;
   WPlan& P = *PP;
   if ((e = sync_instances(c)) != DD_OK) return e;
-  void *src_o, *sol_o, *src_f, *sol_f;
+  void *src_o, *sol_o;
   if ((e = workspace(c, 40, 16ULL * ob->user_tot, &src_o)) ||
-      (e = workspace(c, 41, 16ULL * ob->user_tot, &sol_o)) ||
-      (e = workspace(c, 42, 16ULL * fb->user_tot, &src_f)) ||
-      (e = workspace(c, 43, 16ULL * fb->user_tot, &sol_f)))
+      (e = workspace(c, 41, 16ULL * ob->user_tot, &sol_o)))
     return e;
   InjectArgs a;
   a.U = c->d_U;
@@ -283,38 +285,37 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
   a.n_dpi = c->info.n_dpi;
   a.n_f = n_f;
   a.kappa = c->kappa;
-  // Omega sources and solves
+  // Omega sources (systems 0 .. nb*n_f - 1)
   a.src = (double2*)src_o;
   BatchDev bd = batch_view(c, *ob);
-  dim3 g1((c->info.max_omega + 127) / 128, nb * n_f);
+  dim3 g1((c->info.max_omega + 127) / 128, n_f, nb);
   DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
+  // frame sources (systems nb*n_f .. (nb+1)*n_f - 1, contiguous after the blocks)
+  long long omega_user = 0;
+  for (int b = 0; b < nb; ++b) omega_user += 12LL * c->inst[c->omega0 + b].d.nsites * n_f;
+  a.src = (double2*)src_o + omega_user;
+  dim3 g2((P.n_l1 + 127) / 128, n_f);
+  DD_COUNT_LAUNCH(), k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
   DD_CUDA(c, cudaGetLastError());
   dd_solve_stats st1{};
   dd_status r1 = solve_batch(c, *ob, (const double*)src_o, (double*)sol_o, prm, &st1, s, true);
   if (r1 != DD_OK && r1 != DD_ENOCONV) return r1;
-  // frame source and solve
-  a.src = (double2*)src_f;
-  dim3 g2((P.n_l1 + 127) / 128, n_f);
-  DD_COUNT_LAUNCH(), k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
-  DD_CUDA(c, cudaGetLastError());
-  dd_solve_stats st2{};
-  dd_status r2 = solve_batch(c, *fb, (const double*)src_f, (double*)sol_f, prm, &st2, s, true);
-  if (r2 != DD_OK && r2 != DD_ENOCONV) return r2;
   // extraction into w chi (zero outside dPi by construction: dPi = B u C)
   const int nB = c->info.n_B, nC = c->info.n_C;
   if (nB) {
     dim3 g((nB + 127) / 128, n_f);
-    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
-                                ob->d_uoff, (const double2*)sol_o, (double2*)wchi);
+    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(P.d_b_blk, 0, P.d_b_loc, P.d_b_dpi, nB, n_f,
+                                                   c->info.n_dpi, ob->d_uoff, (const double2*)sol_o,
+                                                   (double2*)wchi);
   }
   if (nC) {
     dim3 g((nC + 127) / 128, n_f);
-    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(nullptr, P.d_c_loc, P.d_c_dpi, nC, n_f, c->info.n_dpi,
-                                fb->d_uoff, (const double2*)sol_f, (double2*)wchi);
+    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(nullptr, nb, P.d_c_loc, P.d_c_dpi, nC, n_f,
+                                                   c->info.n_dpi, ob->d_uoff, (const double2*)sol_o,
+                                                   (double2*)wchi);
   }
   DD_CUDA(c, cudaGetLastError());
-  if (r1 == DD_ENOCONV || r2 == DD_ENOCONV)
-    return fail(c, DD_ENOCONV, "a block or frame solve missed its tolerance");
+  if (r1 == DD_ENOCONV) return fail(c, DD_ENOCONV, "a block or frame solve missed its tolerance");
   return DD_OK;
 }
 
@@ -327,6 +328,7 @@ extern "C" {
 dd_status dd_apply_w(dd_ctx* c, int n_f, const double* chi, double* w_chi,
                      const dd_solve_params* prm, void* stream) {
   if (!c || !chi || !w_chi || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (n_f > 65535) return fail(c, DD_EINVAL, "n_f must be <= 65535");
   if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
   cudaStream_t s = (cudaStream_t)stream;
   size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;

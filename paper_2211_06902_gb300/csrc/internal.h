@@ -78,6 +78,11 @@ struct Batch {
   int* d_item_begin[2] = {nullptr, nullptr}; // [nb+1] first item of instance j
   std::vector<int> item_begin[2];
   int maxn[2] = {0, 0};
+  // tuned hop launch variant per precision (f64, f32, bf16) and CUDA graphs of
+  // the inner Krylov iterations (krylov.cu), owned by the batch
+  mutable int hop_variant[3] = {0, 0, 0};
+  mutable bool tuned[3] = {false, false, false};
+  mutable std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
   ~Batch();
 };
 
@@ -106,6 +111,7 @@ struct dd_ctx {
   int time_bc;
   double kappa;
   int device = 0;
+  int nsm = 0;
   std::string err;
   // gauge field, FP64, [V][4][9] complex (time sign folded in)
   double2* d_U = nullptr;
@@ -135,10 +141,14 @@ struct dd_ctx {
   double t_ms[3] = {0, 0, 0};
   long long t_n[3] = {0, 0, 0};
   double t_bytes[3] = {0, 0, 0};
+  double* d_tbytes = nullptr;     // device accumulators of algorithmic bytes [3]
   // work space (krylov.cu) and cached batches
   void* scratch = nullptr;
   std::map<std::string, std::unique_ptr<dd::Batch>> batches;
   void* wplan = nullptr;     // gather lists of apply_w (dd.cu)
+  dd_solve_stats last_stats{};   // statistics of the last batched solve
+  dd_net* net = nullptr;         // learned initial guess for block solves (not owned)
+  cudaStream_t capture_stream = nullptr;   // private stream for CUDA-graph capture
 };
 
 // ---- helpers shared by the translation units --------------------------------
@@ -183,8 +193,11 @@ struct HopArgs {
   double* partial;          // [k][nitems*nrhs] complex (2 doubles)
   const int* active;        // optional per-system flags, active[sys * active_stride]
   int active_stride;
+  double* work_bytes;       // timing only: algorithmic bytes of the CTAs that ran
+  double site_bytes;        // algorithmic bytes per output (site, rhs)
 };
 dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s);
+int hop_variant_count(dd_prec prec);
 
 // layout conversions (stencil.cu)
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
@@ -204,6 +217,10 @@ size_t prec_bytes(dd_prec p);
 dd_status workspace(dd_ctx* c, int slot, size_t bytes, void** out);
 void free_workspace(dd_ctx* c);
 void free_plan(dd_ctx* c);
-dd_status get_batch(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs, Batch** out);   // bytes per complex number at a storage precision
+dd_status get_batch(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs, Batch** out);
+dd_status get_batch_insts(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch** out);
+// learned initial guess x0 = N(b) (net.cu), FP32 parity vectors
+dd_status net_guess(dd_ctx* c, dd_net* n, const Batch& b, const double2* be, const double2* bo,
+                    float2* xe32, float2* xo32, cudaStream_t s);   // bytes per complex number at a storage precision
 
 }  // namespace dd

@@ -413,7 +413,7 @@ template <class S>
 dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs& w, SysState* st,
                        double* partial, int* d_count, int* h_count, const void* rhs,
                        double inner_tol2, double floor_frac, int maxiter, int check_every,
-                       cudaStream_t s, int* iters_run) {
+                       bool use_graph, cudaStream_t s, int* iters_run) {
   BatchDev bd = batch_view(c, b);
   const int nsys = b.nb * b.nrhs;
   const long long stride = (long long)b.nitems[0] * b.nrhs;
@@ -425,42 +425,101 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
                                      (S*)w.x, partial);
   DD_COUNT_LAUNCH(), k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
   DD_CUDA(c, cudaGetLastError());
-  int it = 0;
-  for (; it < maxiter; ++it) {
-    bool check = ((it + 1) % check_every) == 0;
+  const int* act = (const int*)((const char*)st + offsetof(SysState, active));
+  const int act_stride = (int)(sizeof(SysState) / sizeof(int));
+  // one BiCGstab iteration for every active system (van der Vorst 1992),
+  // enqueued on stream s (captured into a graph when s is the capture stream)
+  auto iteration = [&](bool check, cudaStream_t s) -> dd_status {
     if (check) DD_CUDA(c, cudaMemsetAsync(d_count, 0, sizeof(int), s));
     DD_COUNT_LAUNCH(), k_sc_beta<<<sbl, sth, 0, s>>>(sa, check ? d_count : nullptr);
     DD_COUNT_LAUNCH(), k_p_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (S*)w.p, (const S*)w.v);
     // v = M p = p - k^2 H_eo H_oe p ; partial (rhat, v)
     HopArgs h1{};
     h1.p_out = 1; h1.in = w.p; h1.out = w.tmp; h1.b = 1.0;
-    h1.active = (const int*)((const char*)st + offsetof(SysState, active));
-    h1.active_stride = (int)(sizeof(SysState) / sizeof(int));
+    h1.active = act; h1.active_stride = act_stride;
     dd_status e = launch_hop(c, b, prec, h1, s);
     if (e != DD_OK) return e;
     HopArgs h2{};
     h2.p_out = 0; h2.in = w.tmp; h2.out = w.v; h2.s1 = w.p; h2.a1 = 1.0; h2.b = -k2;
     h2.dotq = w.rhat; h2.partial = partial;
-    h2.active = h1.active; h2.active_stride = h1.active_stride;
+    h2.active = act; h2.active_stride = act_stride;
     if ((e = launch_hop(c, b, prec, h2, s)) != DD_OK) return e;
     DD_COUNT_LAUNCH(), k_sc_alpha<<<sbl, sth, 0, s>>>(sa);
     DD_COUNT_LAUNCH(), k_s_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (const S*)w.v, (S*)w.s);
     HopArgs h3{};
     h3.p_out = 1; h3.in = w.s; h3.out = w.tmp; h3.b = 1.0;
-    h3.active = h1.active; h3.active_stride = h1.active_stride;
+    h3.active = act; h3.active_stride = act_stride;
     if ((e = launch_hop(c, b, prec, h3, s)) != DD_OK) return e;
     HopArgs h4{};
     h4.p_out = 0; h4.in = w.tmp; h4.out = w.t; h4.s1 = w.s; h4.a1 = 1.0; h4.b = -k2;
     h4.dots = w.s; h4.partial = partial;
-    h4.active = h1.active; h4.active_stride = h1.active_stride;
+    h4.active = act; h4.active_stride = act_stride;
     if ((e = launch_hop(c, b, prec, h4, s)) != DD_OK) return e;
     DD_COUNT_LAUNCH(), k_sc_omega<<<sbl, sth, 0, s>>>(sa);
     DD_COUNT_LAUNCH(), k_xr_update<S><<<eg, 128, 0, s>>>(bd, st, (S*)w.x, (S*)w.r, (const S*)w.p, (const S*)w.s,
                                       (const S*)w.t, (const S*)w.rhat, partial);
     DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  };
+  auto poll = [&]() -> dd_status {
+    DD_CUDA(c, cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(c, cudaStreamSynchronize(s));
+    return DD_OK;
+  };
+  int it = 0;
+  bool done = false;
+  if (use_graph && check_every <= maxiter) {
+    // the check_every iterations between two polls, captured once per batch,
+    // precision, buffers and launch variant, then replayed
+    char key[256];
+    snprintf(key, sizeof key, "%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%d:%a:%d%d%d", (int)prec, w.r,
+             w.rhat, w.p, w.v, w.s, w.t, w.x, w.tmp, (void*)st, (void*)partial, (void*)d_count,
+             check_every, c->kappa, b.hop_variant[0], b.hop_variant[1], b.hop_variant[2]);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : b.graphs)
+      if (g.first == key) exec = g.second;
+    if (!exec) {
+      // captured on the context's own stream (the caller's may be the legacy
+      // default stream, which cannot be captured), replayed on the caller's
+      if (!c->capture_stream)
+        DD_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+      cudaStream_t cs = c->capture_stream;
+      DD_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      dd_status e = DD_OK;
+      for (int i = 0; i < check_every && e == DD_OK; ++i) e = iteration(i == check_every - 1, cs);
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      if (e != DD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+      }
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaGraphInstantiate");
+      if (b.graphs.size() >= 8) {
+        cudaGraphExecDestroy(b.graphs.front().second);
+        b.graphs.erase(b.graphs.begin());
+      }
+      b.graphs.push_back({std::string(key), exec});
+    }
+    while (it + check_every <= maxiter) {
+      DD_CUDA(c, cudaGraphLaunch(exec, s));
+      it += check_every;
+      dd_status e = poll();
+      if (e != DD_OK) return e;
+      if (*h_count == 0) {
+        done = true;
+        break;
+      }
+    }
+  }
+  for (; !done && it < maxiter; ++it) {
+    bool check = ((it + 1) % check_every) == 0;
+    dd_status e = iteration(check, s);
+    if (e != DD_OK) return e;
     if (check) {
-      DD_CUDA(c, cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
-      DD_CUDA(c, cudaStreamSynchronize(s));
+      if ((e = poll()) != DD_OK) return e;
       if (*h_count == 0) {
         ++it;
         break;
@@ -472,6 +531,44 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
   *iters_run = it;
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
+}
+
+// Measures every compiled variant of the hop launch on this batch (the
+// H_oe half-apply of an initialised even vector `in` into `out`) and keeps
+// the fastest for the precision.
+dd_status tune_hop(dd_ctx* c, const Batch& b, dd_prec prec, const void* in, void* out,
+                   cudaStream_t s) {
+  const int pi = prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2);
+  const bool timing = c->timing;
+  c->timing = false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_v = 0;
+  dd_status st = DD_OK;
+  for (int v = 0; v < hop_variant_count(prec) && st == DD_OK; ++v) {
+    b.hop_variant[pi] = v;
+    HopArgs h{};
+    h.p_out = 1; h.in = in; h.out = out; h.b = 1.0;
+    st = launch_hop(c, b, prec, h, s);
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < 3 && st == DD_OK; ++k) st = launch_hop(c, b, prec, h, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (st == DD_OK && ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = timing;
+  b.hop_variant[pi] = best_v;
+  b.tuned[pi] = true;
+  return st;
 }
 
 }  // namespace
@@ -540,9 +637,46 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   DD_CUDA(c, cudaMemcpyAsync(re, be, ne * c64, cudaMemcpyDeviceToDevice, s));
   if (no) DD_CUDA(c, cudaMemcpyAsync(ro, bo, no * c64, cudaMemcpyDeviceToDevice, s));
   DD_CUDA(c, cudaGetLastError());
+  // learned initial guess: x = N(b), r = b - D x with D x in FP32 (the first
+  // correction cycle is followed by an FP64 residual, which absorbs its rounding)
+  bool all_omega = true;
+  for (int j = 0; j < b.nb; ++j)
+    if (c->inst[b.inst[j]].d.kind != DD_DOMAIN_OMEGA) all_omega = false;
+  if ((prm->flags & DD_SOLVE_NET_GUESS) && c->net && all_omega) {
+    void *ge, *go, *te, *to;
+    if ((e = ws_get(c, 28, ne * 8, &ge)) || (e = ws_get(c, 29, no * 8 + 16, &go)) ||
+        (e = ws_get(c, 80, ne * 8, &te)) || (e = ws_get(c, 81, no * 8 + 16, &to)))
+      return e;
+    if ((e = net_guess(c, c->net, b, (const double2*)be, (const double2*)bo, (float2*)ge, (float2*)go,
+                       s)) != DD_OK)
+      return e;
+    if ((e = ensure_links(c, b.inst[0], DD_F32)) != DD_OK) return e;
+    for (int j = 0; j < b.nb; ++j)
+      if ((e = ensure_links(c, b.inst[j], DD_F32)) != DD_OK) return e;
+    if ((e = sync_instances(c)) != DD_OK) return e;
+    bd = batch_view(c, b);
+    DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const float2*)ge, 1.0, st);
+    if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const float2*)go, 1.0, st);
+    HopArgs h{};
+    h.p_out = 0; h.in = go; h.out = te; h.s1 = ge; h.a1 = 1.0; h.b = -kap;
+    if ((e = launch_hop(c, b, DD_F32, h, s)) != DD_OK) return e;
+    HopArgs g{};
+    g.p_out = 1; g.in = ge; g.out = to; g.s1 = go; g.a1 = 1.0; g.b = -kap;
+    if ((e = launch_hop(c, b, DD_F32, g, s)) != DD_OK) return e;
+    DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)re, (const float2*)te, -1.0, st);
+    if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)ro, (const float2*)to, -1.0, st);
+    DD_CUDA(c, cudaGetLastError());
+  }
 
   const int check_every = std::max(1, prm->check_every);
   const int max_outer = std::max(1, prm->max_outer);
+  // CUDA graphs replay the inner iterations between polls (not while the
+  // per-launch kernel timing is on: its events are host-side records)
+  const bool use_graph = (prm->flags & DD_SOLVE_GRAPH) && !c->timing;
+  void* tune64 = nullptr;
+  if ((prm->flags & DD_SOLVE_AUTOTUNE) &&
+      (e = ws_get(c, 27, std::max(ne, no) * c64, &tune64)) != DD_OK)
+    return e;
   const double inner_tol2 = ip == DD_F64 ? 0.0 : prm->inner_tol * prm->inner_tol;
   // inner solves stop at inner_tol |r| but never below (tol/2)^2 |b|^2 (plain
   // FP64) or (tol/4)^2 |b|^2 (mixed, whose last cycle must clear tol/2)
@@ -587,6 +721,13 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       rin_e = w.s;
       rin_o = rso;
     }
+    if ((prm->flags & DD_SOLVE_AUTOTUNE) && cyc == 0) {
+      const int pi = ip == DD_F64 ? 0 : (ip == DD_F32 ? 1 : 2);
+      if (!b.tuned[pi] && (e = tune_hop(c, b, ip, rin_e, ip == DD_F64 ? tune64 : w.tmp, s)) != DD_OK)
+        return e;
+      if (ip != DD_F64 && !b.tuned[0] && (e = tune_hop(c, b, DD_F64, re, tune64, s)) != DD_OK)
+        return e;
+    }
     // Schur right-hand side r^_e = r_e + k H_eo r_o
     {
       HopArgs h{};
@@ -596,13 +737,13 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     int its = 0;
     if (ip == DD_F64)
       e = run_bicgstab<double2>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
-                                floor_frac, prm->maxiter, check_every, s, &its);
+                                floor_frac, prm->maxiter, check_every, use_graph, s, &its);
     else if (ip == DD_F32)
       e = run_bicgstab<float2>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
-                               floor_frac, prm->maxiter, check_every, s, &its);
+                               floor_frac, prm->maxiter, check_every, use_graph, s, &its);
     else
       e = run_bicgstab<__nv_bfloat162>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
-                                       floor_frac, prm->maxiter, check_every, s, &its);
+                                       floor_frac, prm->maxiter, check_every, use_graph, s, &its);
     if (e != DD_OK) return e;
     // e_o = r_o + k H_oe e_e
     {
@@ -672,6 +813,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     if (rel[k] <= prm->tol) out.converged++;
   }
   if (stats) *stats = out;
+  c->last_stats = out;
   if (nan) return fail(c, DD_ENAN, "NaN in a solve residual");
   if (out.converged < nsys) {
     char buf[160];

@@ -53,22 +53,19 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
 
 // grid: nitems[p] * nrhs CTAs, rhs fastest (the CTAs that share a site chunk,
 // and so its links, run together and hit L2); one output site per thread.
-// resident CTAs per SM asked of the register allocator, per storage type
-template <class S> struct HopOccupancy { static constexpr int value = 6; };
-template <> struct HopOccupancy<double2> { static constexpr int value = 3; };
-template <> struct HopOccupancy<__nv_bfloat162> { static constexpr int value = 5; };
-
+// One CTA work unit t = item * nrhs + rhs of the hop launch.
 template <class S>
-__global__ void __launch_bounds__(HOP_THREADS, HopOccupancy<S>::value) k_hop(BatchDev bd, HopArgs a) {
+__device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, long long t,
+                                         double* red) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<S>::T T;
-  __shared__ double red[32 * 4];
   const int p = a.p_out;
-  const int item = blockIdx.x / bd.nrhs;
-  const int r = blockIdx.x - item * bd.nrhs;
+  const int item = (int)(t / bd.nrhs);
+  const int r = (int)(t - (long long)item * bd.nrhs);
   const int4 it = (p ? bd.items[1] : bd.items[0])[item];
   const int sys = it.x * bd.nrhs + r;
   if (a.active && !a.active[(long long)sys * a.active_stride]) return;
+  if (a.work_bytes && threadIdx.x == 0) atomicAdd(a.work_bytes, a.site_bytes * it.z);
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
   const int n0 = dp->n[0];
   const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
@@ -166,37 +163,106 @@ __global__ void __launch_bounds__(HOP_THREADS, HopOccupancy<S>::value) k_hop(Bat
   }
 }
 
-// Algorithmic bytes of one hop launch per output site and rhs (see DESIGN):
-// neighbour input read once, output written once, self terms read once,
-// each of the 8 links read once per output site (shared by the nrhs systems).
-static double hop_bytes(const Batch& b, int p, size_t cb, int nself) {
-  const double site_rhs = (double)b.tot[p] / 12.0;   // output (site, rhs) pairs
-  const double spinors = 12.0 * cb * (2 + nself);     // input, output, self terms
-  const double links = 8.0 * 9.0 * cb / b.nrhs;       // 8 links per site, shared by rhs
-  return site_rhs * (spinors + links);
+// Launch variants chosen by the autotuner: MINB = resident CTAs per SM asked
+// of the register allocator; PERSIST = a grid of (SMs x MINB) CTAs that walks
+// the work units with a stride (one launch of persistent CTAs over blocks of
+// any size) instead of one CTA per unit.
+template <class S, int MINB, bool PERSIST>
+__global__ void __launch_bounds__(HOP_THREADS, MINB) k_hop(BatchDev bd, HopArgs a, long long nunits) {
+  __shared__ double red[32 * 4];
+  if (PERSIST) {
+    for (long long t = blockIdx.x; t < nunits; t += gridDim.x) hop_unit<S>(bd, a, t, red);
+  } else {
+    hop_unit<S>(bd, a, blockIdx.x, red);
+  }
 }
 
-dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s) {
+struct HopVariant {
+  int minb;
+  bool persist;
+};
+// per storage precision; index 0 is the default before tuning
+static const HopVariant kVariants64[] = {{3, false}, {2, false}, {3, true}};
+static const HopVariant kVariants32[] = {{6, false}, {4, false}, {8, false}, {6, true}, {4, true}};
+static const HopVariant kVariants16[] = {{5, false}, {4, false}, {8, false}, {5, true}};
+
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 3 : (prec == DD_F32 ? 5 : 4); }
+
+static const HopVariant& variant_of(dd_prec prec, int v) {
+  const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
+  if (v < 0 || v >= hop_variant_count(prec)) v = 0;
+  return t[v];
+}
+
+template <class S, int MINB, bool PERSIST>
+static void launch_variant(const BatchDev& bd, const HopArgs& a, long long nunits, int nsm,
+                           cudaStream_t s) {
+  long long grid = nunits;
+  if (PERSIST) grid = std::min<long long>(nunits, (long long)nsm * MINB);
+  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
+}
+
+static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs& a, long long n,
+                         int nsm, cudaStream_t s) {
+  const HopVariant& hv = variant_of(prec, v);
+  if (prec == DD_F64) {
+    if (hv.persist) launch_variant<double2, 3, true>(bd, a, n, nsm, s);
+    else if (hv.minb == 2) launch_variant<double2, 2, false>(bd, a, n, nsm, s);
+    else launch_variant<double2, 3, false>(bd, a, n, nsm, s);
+  } else if (prec == DD_F32) {
+    if (hv.persist && hv.minb == 4) launch_variant<float2, 4, true>(bd, a, n, nsm, s);
+    else if (hv.persist) launch_variant<float2, 6, true>(bd, a, n, nsm, s);
+    else if (hv.minb == 4) launch_variant<float2, 4, false>(bd, a, n, nsm, s);
+    else if (hv.minb == 8) launch_variant<float2, 8, false>(bd, a, n, nsm, s);
+    else launch_variant<float2, 6, false>(bd, a, n, nsm, s);
+  } else {
+    if (hv.persist) launch_variant<__nv_bfloat162, 5, true>(bd, a, n, nsm, s);
+    else if (hv.minb == 4) launch_variant<__nv_bfloat162, 4, false>(bd, a, n, nsm, s);
+    else if (hv.minb == 8) launch_variant<__nv_bfloat162, 8, false>(bd, a, n, nsm, s);
+    else launch_variant<__nv_bfloat162, 5, false>(bd, a, n, nsm, s);
+  }
+}
+
+// Algorithmic bytes per output (site, rhs) of one hop launch: the neighbour
+// input read once, the output written once, each self term read once, and
+// the 8 links of the site read once and shared by the batch's nrhs systems.
+// The kernel adds it for the CTAs that actually run (converged systems skip).
+static double hop_site_bytes(const Batch& b, size_t cb, int nself) {
+  return 12.0 * cb * (2 + nself) + 8.0 * 9.0 * cb / b.nrhs;
+}
+
+dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0, cudaStream_t s) {
   dd_status st = sync_instances(c);
   if (st != DD_OK) return st;
   BatchDev bd = batch_view(c, b);
+  HopArgs a = a0;
   int p = a.p_out;
   if (b.nitems[p] == 0) return DD_OK;
   const long long nblk = (long long)b.nitems[p] * b.nrhs;
   if (nblk > 0x7fffffffLL) return fail(c, DD_EINVAL, "batch too large for one launch");
-  dim3 grid((unsigned)nblk);
   dd::TimingRec rec;
   bool tm = c->timing;
   if (tm) {
+    if (!c->d_tbytes) {
+      if ((st = dalloc(c, (void**)&c->d_tbytes, 3 * sizeof(double))) != DD_OK) return st;
+      DD_CUDA(c, cudaMemset(c->d_tbytes, 0, 3 * sizeof(double)));
+    }
     cudaEventCreate(&rec.a);
     cudaEventCreate(&rec.b);
     rec.which = prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2);
-    rec.bytes = hop_bytes(b, p, prec_bytes(prec), (a.s1 ? 1 : 0) + (a.s2 ? 1 : 0));
+    rec.bytes = 0.0;
+    a.work_bytes = c->d_tbytes + rec.which;
+    a.site_bytes = hop_site_bytes(b, prec_bytes(prec), (a.s1 ? 1 : 0) + (a.s2 ? 1 : 0));
     cudaEventRecord(rec.a, s);
   }
-  if (prec == DD_F64) DD_COUNT_LAUNCH(), k_hop<double2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
-  else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_hop<float2><<<grid, HOP_THREADS, 0, s>>>(bd, a);
-  else DD_COUNT_LAUNCH(), k_hop<__nv_bfloat162><<<grid, HOP_THREADS, 0, s>>>(bd, a);
+  if (!c->nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (c->nsm <= 0) c->nsm = 1;
+  }
+  const int pi = prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2);
+  dispatch_hop(prec, b.hop_variant[pi], bd, a, nblk, c->nsm, s);
   if (tm) {
     cudaEventRecord(rec.b, s);
     c->trec.push_back(rec);

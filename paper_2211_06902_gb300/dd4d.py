@@ -28,9 +28,13 @@ class GeomInfo(C.Structure):
                                         "n_lambda1", "max_omega", "max_phi")]
 
 
+SOLVE_GRAPH, SOLVE_AUTOTUNE, SOLVE_NET_GUESS = 1, 2, 4
+
+
 class SolveParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("inner_prec", C.c_int),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
+                ("flags", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -77,6 +81,16 @@ def lib():
             "dd_timing_enable": [vp, C.c_int],
             "dd_timing_get": [vp, C.c_int, dp, C.POINTER(C.c_longlong), dp],
             "dd_launch_count": [C.POINTER(C.c_longlong)],
+            "dd_logdet_check": [vp, C.POINTER(SolveParams), dp, dp, C.POINTER(LogdetReport), vp],
+            "dd_last_solve_stats": [vp, C.POINTER(SolveStats)],
+            "dd_net_create": [vp, C.c_int, ip, dp, C.POINTER(vp)],
+            "dd_net_destroy": [vp],
+            "dd_net_weights": [vp, dp],
+            "dd_net_apply": [vp, vp, ip, C.c_int, C.c_int, vp, vp, vp],
+            "dd_net_loss_grad": [vp, vp, ip, C.c_int, C.c_int, vp, vp, dp, dp, vp],
+            "dd_net_train": [vp, vp, ip, C.c_int, C.c_int, vp, C.POINTER(TrainParams),
+                             C.POINTER(TrainStats), vp],
+            "dd_set_net": [vp, vp],
             "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -92,7 +106,9 @@ def exported_symbols():
     return ["dd_create", "dd_destroy", "dd_strerror", "dd_last_error", "dd_set_kappa",
             "dd_gauge_upload", "dd_set_geometry", "dd_geom_sites", "dd_geom_block",
             "dd_apply_D_block", "dd_solve_blocks", "dd_apply_w", "dd_multiboson_action",
-            "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count",
+            "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count", "dd_logdet_check",
+            "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
+            "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net",
             "dd_apply_D_block_noalloc"]
 
 
@@ -119,12 +135,14 @@ def _stream(stream):
     return C.c_void_p(0)
 
 
-def params(tol=1e-10, maxiter=2000, inner_prec="f64", inner_tol=1e-5, max_outer=None,
-           check_every=8):
+def params(tol=1e-10, maxiter=2000, inner_prec="f64", inner_tol=3e-6, max_outer=None,
+           check_every=8, graph=False, autotune=False, net_guess=False):
     ip = PREC[inner_prec] if isinstance(inner_prec, str) else inner_prec
     if max_outer is None:
         max_outer = 4 if ip == F64 else 30
-    return SolveParams(tol, maxiter, ip, inner_tol, max_outer, check_every)
+    flags = ((SOLVE_GRAPH if graph else 0) | (SOLVE_AUTOTUNE if autotune else 0)
+             | (SOLVE_NET_GUESS if net_guess else 0))
+    return SolveParams(tol, maxiter, ip, inner_tol, max_outer, check_every, flags)
 
 
 def roots(N, c):
@@ -141,6 +159,28 @@ def launch_count():
     n = C.c_longlong(0)
     lib().dd_launch_count(C.byref(n))
     return n.value
+
+
+class LogdetReport(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("logabs_D", "logabs_W1", "logabs_Lambda1",
+                                           "logabs_Omega", "logabs_Phi", "phase_D",
+                                           "phase_rhs", "residual")] + \
+               [(n, C.c_int) for n in ("dim_D", "dim_W1", "dim_Lambda1")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrainParams(C.Structure):
+    _fields_ = [("steps", C.c_int), ("lr", C.c_double), ("solve_tol", C.c_double)]
+
+
+class TrainStats(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("steps", C.c_int),
+                ("pairs", C.c_int), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Context:
@@ -254,6 +294,26 @@ class Context:
             _stream(stream)))
         return S.value, Sb, Sr.value, st
 
+    def logdet_check(self, prm=None, stream=None):
+        """Dense check of Eq. (detD): report dict plus per-block ln|det| arrays."""
+        prm = prm or params(1e-12)
+        nb = self.info["nblocks"]
+        lo, lp = np.zeros(nb), np.zeros(nb)
+        rep = LogdetReport()
+        self._check(lib().dd_logdet_check(self._h, C.byref(prm),
+                                          lo.ctypes.data_as(C.POINTER(C.c_double)),
+                                          lp.ctypes.data_as(C.POINTER(C.c_double)),
+                                          C.byref(rep), _stream(stream)))
+        d = rep.as_dict()
+        d["logabs_omega"] = lo
+        d["logabs_phi"] = lp
+        return d
+
+    def last_solve_stats(self):
+        st = SolveStats()
+        self._check(lib().dd_last_solve_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
     def timing_enable(self, on=True):
         self._check(lib().dd_timing_enable(self._h, 1 if on else 0))
 
@@ -263,3 +323,82 @@ class Context:
         by = C.c_double(0)
         self._check(lib().dd_timing_get(self._h, which, C.byref(ms), C.byref(n), C.byref(by)))
         return ms.value, n.value, by.value
+
+
+NET_CHANNELS = (4, 16, 16, 16, 4)
+
+
+class Net:
+    """The gauge-covariant parallel-transport convolution network on a context."""
+
+    def __init__(self, ctx, weights, channels=NET_CHANNELS):
+        self.ctx = ctx
+        self.channels = tuple(channels)
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.complex128).ravel()
+                                                 for x in weights]))
+        self.shapes = [np.asarray(x).shape for x in weights]
+        self._h = C.c_void_p()
+        ch = (C.c_int * len(channels))(*channels)
+        ctx._check(lib().dd_net_create(ctx._h, len(channels) - 1, ch,
+                                       w.view(np.float64).ctypes.data_as(C.POINTER(C.c_double)),
+                                       C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().dd_net_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _split(self, flat):
+        out, k = [], 0
+        for s in self.shapes:
+            n = int(np.prod(s))
+            out.append(flat[k:k + n].reshape(s))
+            k += n
+        return out
+
+    def weights(self):
+        n = sum(int(np.prod(s)) for s in self.shapes)
+        w = np.zeros(2 * n)
+        lib().dd_net_weights(self._h, w.ctypes.data_as(C.POINTER(C.c_double)))
+        return self._split(w.view(np.complex128))
+
+    def apply(self, ids, nrhs, inp, out, stream=None):
+        idarr = (C.c_int * len(ids))(*ids)
+        self.ctx._check(lib().dd_net_apply(self.ctx._h, self._h, idarr, len(ids), nrhs, _ptr(inp),
+                                           _ptr(out), _stream(stream)))
+
+    def loss_grad(self, ids, nrhs, b, x, stream=None):
+        idarr = (C.c_int * len(ids))(*ids)
+        n = sum(int(np.prod(s)) for s in self.shapes)
+        g = np.zeros(2 * n)
+        L = C.c_double(0)
+        self.ctx._check(lib().dd_net_loss_grad(self.ctx._h, self._h, idarr, len(ids), nrhs, _ptr(b),
+                                               _ptr(x), C.byref(L),
+                                               g.ctypes.data_as(C.POINTER(C.c_double)),
+                                               _stream(stream)))
+        return L.value, self._split(g.view(np.complex128))
+
+    def train(self, ids, nrhs, b, steps=100, lr=2e-3, solve_tol=1e-10, stream=None, ctx=None):
+        """Train on the framed blocks `ids` of `ctx` (default: the creating context)."""
+        ctx = ctx or self.ctx
+        idarr = (C.c_int * len(ids))(*ids)
+        tp = TrainParams(steps, lr, solve_tol)
+        ts = TrainStats()
+        ctx._check(lib().dd_net_train(ctx._h, self._h, idarr, len(ids), nrhs, _ptr(b),
+                                      C.byref(tp), C.byref(ts), _stream(stream)))
+        return ts.as_dict()
+
+    def attach(self, ctx=None):
+        """Use this network for DD_SOLVE_NET_GUESS solves on `ctx` (default: its own)."""
+        ctx = ctx or self.ctx
+        ctx._check(lib().dd_set_net(ctx._h, self._h))
+
+    def detach(self, ctx=None):
+        ctx = ctx or self.ctx
+        ctx._check(lib().dd_set_net(ctx._h, None))

@@ -135,3 +135,17 @@ def gauge_transform(seed, L):
     e, v = np.linalg.eigh(H)
     g = np.einsum("nij,nj,nkj->nik", v, np.exp(1j * e), np.conj(v))
     return np.ascontiguousarray(g.reshape(L + (3, 3)))
+
+
+def net_init_weights(seed, channels=(4, 16, 16, 16, 4)):
+    """Seeded initial weights of the parallel-transport network, one complex
+    array [9 directions, C_out, C_in] per layer: unit centre taps on the
+    diagonal plus Gaussian noise of scale 0.02 / sqrt(C_in)."""
+    Ws = []
+    for l in range(len(channels) - 1):
+        cin, cout = channels[l], channels[l + 1]
+        w = complex_gaussian(seed, TAG_NET + 64 * l, (9, cout, cin)) * (0.02 / np.sqrt(cin))
+        for c in range(min(cin, cout)):
+            w[0, c, c] += 1.0
+        Ws.append(w)
+    return Ws

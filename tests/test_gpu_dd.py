@@ -21,6 +21,9 @@ CASES = {
     "4^4": lambda: make_case((4,) * 4, 0.13, 0.3, 1, uniform_cores((4,) * 4, 1, 1)),
     "6x4^3": lambda: make_case((6, 4, 4, 4), 0.13, 0.3, 1,
                                [[(0, 1), (3, 4)]] + [[(0, 0), (2, 2)]] * 3),
+    "uneven 12x8x8x10": lambda: make_case(
+        (12, 8, 8, 10), 0.13, 0.5, 4,
+        [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]]),
 }
 
 
@@ -78,6 +81,19 @@ def test_action_kappa_zero():
     S, Sb, Sr, st = ctx.multiboson_action(u, vec, dd4d.params(1e-10))
     expect = sum(abs(uk) ** 2 * np.sum(np.abs(c) ** 2) for uk, c in zip(u, chis))
     assert abs(S - expect) <= 1e-12 * expect
+
+
+def test_action_with_graph_and_autotune_matches_plain_call():
+    U, ctx, info, geo = CASES["uneven 12x8x8x10"]()
+    u = field_roots(6, 0.5)
+    chis, vec, dpi = _chis(geo, ctx, 3, 11)
+    a = ctx.multiboson_action(u, vec, dd4d.params(1e-10, inner_prec="f32"))
+    b = ctx.multiboson_action(u, vec, dd4d.params(1e-10, inner_prec="f32", graph=True,
+                                                   autotune=True))
+    assert a[3] == b[3] == 0
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    S0, Sb0, Sr0 = Oracle(U, 0.13, geo).multiboson_action(u, chis)
+    assert abs(b[0] - S0) <= 1e-9 * S0
 
 
 def test_action_deterministic():

@@ -1,0 +1,113 @@
+"""GPU parallel-transport network: forward and gradients vs the FP64 oracle,
+training on solver-generated pairs, and its use as the block-solve initial guess.
+
+The oracle evaluates the same (BF16-rounded) weights in FP64; the GPU keeps
+FP32 activations, so forward outputs agree to ~1e-6 and gradients to ~1e-5
+relative (tolerances 2e-5 and 2e-4, norm-wise).
+"""
+
+import numpy as np
+import pytest
+
+from paper_2211_06902_gb300 import dd4d, synth
+from oracle import net as onet
+
+from gpu_common import config1, relerr, to_field
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(w):
+    """Round-to-nearest-even to BF16 (what the kernels use)."""
+    def r(x):
+        u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+        u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+        return u.view(np.float32).astype(np.float64)
+    return r(w.real) + 1j * r(w.imag)
+
+
+@pytest.fixture(scope="module")
+def case():
+    U, ctx, info, geo = config1()
+    Ws = onet.init_weights(3)
+    Ws = [w + 0.05 * synth.complex_gaussian(3, 200 + k, w.shape) for k, w in enumerate(Ws)]
+    return U, ctx, info, geo, Ws
+
+
+def _block(ctx, U, b):
+    g = ctx.geom_block(b)
+    return onet.box_links(U, g["origin"], g["side"]), tuple(g["side"])
+
+
+def test_forward_matches_oracle(case):
+    torch = pytest.importorskip("torch")
+    U, ctx, info, geo, Ws = case
+    net = dd4d.Net(ctx, Ws)
+    ids, nrhs = [0, 9], 2
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    b = synth.complex_gaussian(4, synth.TAG_RHS, (len(ids), nrhs, n, 12))
+    db = torch.from_numpy(b.view(np.float64).copy()).cuda()
+    dy = torch.zeros_like(db)
+    net.apply(ids, nrhs, db, dy)
+    y = dy.cpu().numpy().view(np.complex128)
+    Wr = [bf16(w) for w in Ws]
+    for k, blk in enumerate(ids):
+        Ub, side = _block(ctx, U, blk)
+        for r in range(nrhs):
+            ref, _ = onet.forward(Ub, Wr, b[k, r].ravel(), side)
+            assert relerr(y[k, r].ravel(), ref) < 2e-5
+
+
+def test_gradients_match_oracle(case):
+    torch = pytest.importorskip("torch")
+    U, ctx, info, geo, Ws = case
+    net = dd4d.Net(ctx, Ws)
+    ids, nrhs = [2, 13], 2
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    b = synth.complex_gaussian(5, synth.TAG_RHS, (len(ids), nrhs, n, 12))
+    x = synth.complex_gaussian(6, synth.TAG_RHS, (len(ids), nrhs, n, 12))
+    L, G = net.loss_grad(ids, nrhs, torch.from_numpy(b.view(np.float64).copy()).cuda(),
+                         torch.from_numpy(x.view(np.float64).copy()).cuda())
+    Wr = [bf16(w) for w in Ws]
+    L0, G0 = 0.0, [np.zeros_like(w) for w in Ws]
+    for k, blk in enumerate(ids):
+        Ub, side = _block(ctx, U, blk)
+        l, g = onet.loss_and_grads(Ub, Wr, [(b[k, r].ravel(), x[k, r].ravel()) for r in range(nrhs)],
+                                   side)
+        L0 += l / len(ids)
+        for q in range(len(G0)):
+            G0[q] += g[q] / len(ids)
+    assert abs(L - L0) < 2e-5 * L0
+    for g, g0 in zip(G, G0):
+        assert relerr(g, g0) < 2e-4
+
+
+def test_training_and_initial_guess():
+    """Training lowers the loss; the trained network as initial guess keeps every
+    system at 1e-10 (oracle-checked residuals) and its effect is reported."""
+    torch = pytest.importorskip("torch")
+    from oracle.lattice import apply_D_restricted
+    U, ctx, info, geo = config1()
+    net = dd4d.Net(ctx, onet.init_weights(7))
+    ids = list(range(info["nblocks"]))
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    bt = synth.complex_gaussian(7, synth.TAG_RHS, (len(ids), 4, n, 12))
+    st = net.train(ids, 4, torch.from_numpy(bt.view(np.float64).copy()).cuda(), steps=60, lr=3e-3)
+    assert st["loss_last"] < 0.7 * st["loss_first"], st
+    net.attach()
+    b = synth.complex_gaussian(8, synth.TAG_RHS, (len(ids), 2, n, 12))
+    x0 = np.zeros_like(b)
+    x1 = np.zeros_like(b)
+    s0 = ctx.solve_blocks("omega", ids, 2, b, x0, dd4d.params(1e-10, inner_prec="f32"))
+    s1 = ctx.solve_blocks("omega", ids, 2, b, x1, dd4d.params(1e-10, inner_prec="f32",
+                                                               net_guess=True))
+    assert s0["status"] == s1["status"] == 0
+    assert s1["max_iters"] <= s0["max_iters"] + 2
+    L = geo.L
+    for blk in (0, 7, 15):
+        sites = ctx.geom_sites(dd4d.SET_OMEGA, blk)
+        for r in range(2):
+            f = to_field(L, sites, b[blk, r])
+            res = f - apply_D_restricted(U, to_field(L, sites, x1[blk, r]), 0.13, geo.omega_mask[blk])
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
+    net.detach()

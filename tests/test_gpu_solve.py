@@ -121,3 +121,35 @@ def test_full_size_batch_sampled():
         M = dirac_matrix(U, 0.135, sites)
         res = b[blk, r].ravel() - M @ x[blk, r].ravel()
         assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(b[blk, r]) * 1.0000001
+
+
+def test_graph_and_autotune_give_identical_solutions():
+    """CUDA-graph replay and every autotuned launch variant compute the same
+    arithmetic per work unit, so the solutions are bit-identical; uneven
+    blocks (mixed shapes) and the frame go through one batch."""
+    L = (12, 8, 8, 10)
+    cores = [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]]
+    U, ctx, info, geo = make_case(L, 0.12, 0.5, 7, cores)
+    ids = list(range(info["nblocks"]))
+    sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
+    tot = sum(len(s) for s in sites)
+    b = synth.complex_gaussian(8, synth.TAG_RHS, (2 * tot, 12))
+    x0 = np.zeros_like(b)
+    x1 = np.zeros_like(b)
+    s0 = ctx.solve_blocks("omega", ids, 2, b, x0, dd4d.params(1e-10, inner_prec="f32"))
+    s1 = ctx.solve_blocks("omega", ids, 2, b, x1,
+                          dd4d.params(1e-10, inner_prec="f32", graph=True, autotune=True))
+    s2 = ctx.solve_blocks("omega", ids, 2, b, x1,
+                          dd4d.params(1e-10, inner_prec="f32", graph=True, autotune=True))
+    assert s0["status"] == s1["status"] == s2["status"] == 0
+    assert np.array_equal(x0, x1)
+    assert ctx.last_solve_stats()["max_relres"] <= 1e-10
+    off = 0
+    for k, blk in enumerate(ids):
+        n = len(sites[k])
+        for r in range(2):
+            f = to_field(L, sites[k], b[off:off + n])
+            xf = to_field(L, sites[k], x1[off:off + n])
+            res = f - apply_D_restricted(U, xf, 0.12, geo.omega_mask[blk])
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
+            off += n
