@@ -193,11 +193,9 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2211_06902_gb300 import dd4d, synth
+    from paper_2211_06902_gb300 import dd4d, ranks, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = ranks.rank_info()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -205,8 +203,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        ranks.barrier(world)
         torch.cuda.synchronize()
 
     if not os.path.exists(dd4d.LIB_PATH):
@@ -219,12 +216,13 @@ def run_ours(args):
     info = ctx.set_geometry(cores_uniform(LATTICE, CORE, FRAME))
     ids = list(range(info["nblocks"]))
     n_om = info["max_omega"]
-    b_h = synth.complex_gaussian(SEED + 1000 * rank, synth.TAG_RHS, (len(ids), NRHS, n_om, 12))
+    b_h = synth.complex_gaussian(ranks.batch_seed(SEED, rank), synth.TAG_RHS, (len(ids), NRHS, n_om, 12))
     b = torch.from_numpy(b_h.view(np.float64)).to(dev)
     x = torch.zeros_like(b)
     units = site_rhs()
     assert units == len(ids) * NRHS * n_om
-    mixed = dd4d.params(TOL, inner_prec="f32", inner_tol=args.inner_tol, check_every=8)
+    mixed = dd4d.params(TOL, inner_prec="f32", inner_tol=args.inner_tol, check_every=8,
+                        autotune=True)
     plain = dd4d.params(TOL, inner_prec="f64", check_every=8)
 
     def step(prm):
@@ -258,11 +256,8 @@ def run_ours(args):
     hop64_ms, hop64_n, hop64_bytes = ctx.timing_get(0)
     ctx.timing_enable(False)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms * 1e-3)
+    ms = ranks.max_over_ranks(ms, world, dev)
+    value = ranks.aggregate_rate(units, world, ms * 1e-3)
 
     # plain FP64 form of the same batch (the reference form of the ratio)
     step(plain)
@@ -315,20 +310,21 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(LATTICE), "blocks": len(ids),
                    "omega_sites": n_om, "rhs_per_block": NRHS, "systems": len(ids) * NRHS,
-                   "site_rhs_per_step": units, "inner": "f32", "inner_tol": args.inner_tol,
+                   "site_rhs_per_step": units, "inner": "f32",
+                   "residual": "double-float (f32 pairs)", "inner_tol": args.inner_tol,
                    "tol": TOL, "l2": "inputs larger than L2 (3.9 GB rhs, ~15 GB working set)"},
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,
         "solver": {"max_relres": stats["max_relres"], "max_iters": stats["max_iters"],
-                   "outer_cycles": stats["outer_cycles"]},
+                   "outer_cycles": stats["outer_cycles"], "hop_variant": stats["hop_variant"]},
         "plain_f64": {"value": world * units / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                       "max_iters": pst["max_iters"], "speedup_of_mixed": plain_ms / ms,
-                      "fp64_hop_ms_in_mixed_step": hop64_ms / args.steps},
+                      "residual_hop_ms_in_mixed_step": hop64_ms / args.steps},
         "action": action,
         "action_uneven": uneven,
         "learned_guess": learned,
@@ -361,7 +357,7 @@ def learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms_plain_guess):
                       "seconds": st["seconds"], "pairs": st["pairs"]})
         c.close()
     net.attach(ctx)
-    prm = dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, net_guess=True)
+    prm = dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, net_guess=True, autotune=True)
     ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)

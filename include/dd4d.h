@@ -112,6 +112,7 @@ typedef struct {
   int outer_cycles;    /* defect-correction cycles run (1 for plain FP64) */
   double max_relres;   /* largest final |b - D x|/|b|, FP64, over systems */
   double seconds;      /* device time of the call (CUDA events) */
+  int hop_variant;     /* stencil launch variant used at the inner precision (autotuner) */
 } dd_solve_stats;
 
 /* ---- context --------------------------------------------------------- */
@@ -175,6 +176,13 @@ dd_status dd_solve_blocks(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
                           int nrhs, const double* b, double* x,
                           const dd_solve_params* params, dd_solve_stats* stats,
                           void* stream);
+
+/* Manual choice of the stencil launch variant (0 .. dd_hop_variants(prec)-1)
+ * for every batch used afterwards on the context, overriding the autotuner;
+ * v = -1 returns to the defaults.  Variants differ only in launch shape
+ * (resident CTAs per SM, persistent grid, rhs per thread), not in arithmetic. */
+dd_status dd_set_hop_variant(dd_ctx* ctx, dd_prec prec, int v);
+int dd_hop_variants(dd_prec prec);
 
 /* Statistics of the last batched solve run on the context (by any call,
  * including the block and frame solves inside dd_apply_w). */

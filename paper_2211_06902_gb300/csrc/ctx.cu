@@ -5,6 +5,7 @@
 #include <sstream>
 
 #include "internal.h"
+#include "spinor.cuh"
 
 namespace dd {
 
@@ -47,7 +48,7 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-size_t prec_bytes(dd_prec p) { return p == DD_F64 ? 16 : (p == DD_F32 ? 8 : 4); }
+size_t prec_bytes(dd_prec p) { return (p == DD_F64 || p == DD_DF64) ? 16 : (p == DD_F32 ? 8 : 4); }
 
 Batch::~Batch() {
   for (auto& g : graphs) cudaGraphExecDestroy(g.second);
@@ -144,7 +145,8 @@ void free_instance(Instance& in) {
   dfree(in.link64_buf);
   dfree(in.link32_buf);
   dfree(in.link16_buf);
-  in.glob_buf = in.link64_buf = in.link32_buf = in.link16_buf = nullptr;
+  dfree(in.linkdf_buf);
+  in.glob_buf = in.link64_buf = in.link32_buf = in.link16_buf = in.linkdf_buf = nullptr;
   in.nbr_buf.reset();
   in.fmap_buf.reset();
   in.lex_buf.reset();
@@ -262,7 +264,16 @@ template <>
 __device__ __forceinline__ __nv_bfloat162 to_store<__nv_bfloat162>(double2 v) {
   return __floats2bfloat162_rn((float)v.x, (float)v.y);
 }
+template <>
+__device__ __forceinline__ df2s to_store<df2s>(double2 v) {
+  const float2 r = split_d(v.x), i = split_d(v.y);
+  df2s o;
+  o.v = make_float4(r.x, i.x, r.y, i.y);
+  return o;
+}
 
+// per-instance link copy in the pair layout [p][mu][10 entries][n_p] (entry
+// 9 of each link is padding, zeroed by the caller)
 template <class S>
 __global__ void k_gather_links(const int* __restrict__ glob, int n0, int n1,
                                const double2* __restrict__ U, S* __restrict__ out) {
@@ -271,12 +282,12 @@ __global__ void k_gather_links(const int* __restrict__ glob, int n0, int n1,
   if (k >= ns * 36) return;
   int site = (int)(k % ns);
   int comp = (int)(k / ns);          // mu*9 + c
+  int mu = comp / 9, c = comp % 9;
   int p = site < n0 ? 0 : 1;
   int i = p ? site - n0 : site;
   int np = p ? n1 : n0;
-  long long base = p ? 36LL * n0 : 0;
   int g = glob[site];
-  out[base + (long long)comp * np + i] = to_store<S>(U[(long long)g * 36 + comp]);
+  out[link_block(p, mu, n0, np) + cidx(c, np, i)] = to_store<S>(U[(long long)g * 36 + comp]);
 }
 
 __global__ void k_fold_time_sign(double2* U, int V, int L0, int spatial, int sign) {
@@ -291,33 +302,44 @@ __global__ void k_fold_time_sign(double2* U, int V, int L0, int spatial, int sig
 dd_status ensure_links(dd_ctx* c, int i, dd_prec prec) {
   if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
   Instance& in = c->inst[i];
-  void** buf = prec == DD_F64 ? &in.link64_buf : (prec == DD_F32 ? &in.link32_buf : &in.link16_buf);
+  void** buf = prec == DD_F64 ? &in.link64_buf
+               : prec == DD_F32 ? &in.link32_buf
+               : prec == DD_BF16 ? &in.link16_buf : &in.linkdf_buf;
   if (*buf && in.links_ready) return DD_OK;
   if (!in.links_ready) {
     // gauge changed: drop stale copies
     dfree(in.link64_buf);
     dfree(in.link32_buf);
     dfree(in.link16_buf);
-    in.link64_buf = in.link32_buf = in.link16_buf = nullptr;
+    dfree(in.linkdf_buf);
+    in.link64_buf = in.link32_buf = in.link16_buf = in.linkdf_buf = nullptr;
+    in.d.link64 = nullptr;
+    in.d.link32 = nullptr;
+    in.d.link16 = nullptr;
+    in.d.linkdf = nullptr;
     in.links_ready = true;
   }
-  size_t n = 36ULL * in.d.nsites;
+  size_t n = 40ULL * in.d.nsites;
   dd_status st = dalloc(c, buf, n * prec_bytes(prec));
   if (st != DD_OK) return st;
-  long long tot = (long long)n;
+  DD_CUDA(c, cudaMemset(*buf, 0, n * prec_bytes(prec)));
+  long long tot = 36LL * in.d.nsites;
   int th = 256;
   long long nb = (tot + th - 1) / th;
   if (prec == DD_F64)
     DD_COUNT_LAUNCH(), k_gather_links<double2><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (double2*)*buf);
   else if (prec == DD_F32)
     DD_COUNT_LAUNCH(), k_gather_links<float2><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (float2*)*buf);
-  else
+  else if (prec == DD_BF16)
     DD_COUNT_LAUNCH(), k_gather_links<__nv_bfloat162><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U,
                                                (__nv_bfloat162*)*buf);
+  else
+    DD_COUNT_LAUNCH(), k_gather_links<df2s><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (df2s*)*buf);
   DD_CUDA(c, cudaGetLastError());
   in.d.link64 = (const double2*)in.link64_buf;
   in.d.link32 = (const float2*)in.link32_buf;
   in.d.link16 = (const __nv_bfloat162*)in.link16_buf;
+  in.d.linkdf = (const df2s*)in.linkdf_buf;
   c->inst_dirty = true;
   return DD_OK;
 }

@@ -1,0 +1,128 @@
+// Double-float (two FP32 numbers, value = h + l) arithmetic for the residual of
+// the mixed-precision defect correction.  GB300 executes FP64 at a small
+// fraction of its FP32 rate, so the FP64-accurate residual r = b - D x is
+// computed with error-free FP32 transformations instead: TwoSum (Knuth) for
+// sums and FMA-based TwoProduct for products (Dekker 1971; the double-double
+// algorithms of Hida, Li & Bailey 2001).  Relative accuracy about 2^-44, far
+// below the 1e-10 residuals the solver needs.
+#pragma once
+
+namespace dd {
+
+struct dfc {            // complex double-float
+  float2 h, l;          // (re, im) high and low parts
+};
+struct df2s {           // its storage: (re_h, im_h, re_l, im_l), 16 bytes like a double2
+  float4 v;
+};
+template <> struct StoreTraits<df2s> { typedef float T; typedef dfc C; };
+
+// ---- real double-float primitives ---------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// (h, l) += a * b for double-float a, b
+__device__ __forceinline__ void df_fma(float& h, float& l, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  float s, t;
+  two_sum(h, p, s, t);
+  t += l + e;
+  quick_two_sum(s, t, h, l);
+}
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  float s, t;
+  two_sum(h, bh, s, t);
+  t += l + bl;
+  quick_two_sum(s, t, h, l);
+}
+
+// ---- complex helpers used by the generic stencil code -------------------------------
+__device__ __forceinline__ dfc ldc(const df2s* p) {
+  const float4 v = __ldg(&p->v);
+  return dfc{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void stc(df2s* p, dfc v) { p->v = make_float4(v.h.x, v.h.y, v.l.x, v.l.y); }
+__device__ __forceinline__ void ld_pair(const df2s* p, dfc& a, dfc& b) {
+  a = ldc(p);
+  b = ldc(p + 1);
+}
+__device__ __forceinline__ void ld_pair(df2s* p, dfc& a, dfc& b) {
+  const float4 x = p[0].v, y = p[1].v;
+  a = dfc{make_float2(x.x, x.y), make_float2(x.z, x.w)};
+  b = dfc{make_float2(y.x, y.y), make_float2(y.z, y.w)};
+}
+__device__ __forceinline__ void st_pair(df2s* p, dfc a, dfc b) {
+  stc(p, a);
+  stc(p + 1, b);
+}
+__device__ __forceinline__ float2 split_d(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+template <> __device__ __forceinline__ dfc cmk<dfc>(double re, double im) {
+  const float2 r = split_d(re), i = split_d(im);
+  return dfc{make_float2(r.x, i.x), make_float2(r.y, i.y)};
+}
+__device__ __forceinline__ double2 to_d2(dfc a) {
+  return make_double2((double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
+}
+__device__ __forceinline__ dfc cadd(dfc a, dfc b) {
+  df_add(a.h.x, a.l.x, b.h.x, b.l.x);
+  df_add(a.h.y, a.l.y, b.h.y, b.l.y);
+  return a;
+}
+__device__ __forceinline__ dfc csub(dfc a, dfc b) {
+  df_add(a.h.x, a.l.x, -b.h.x, -b.l.x);
+  df_add(a.h.y, a.l.y, -b.h.y, -b.l.y);
+  return a;
+}
+// a + i b and a - i b
+__device__ __forceinline__ dfc caddi(dfc a, dfc b) {
+  df_add(a.h.x, a.l.x, -b.h.y, -b.l.y);
+  df_add(a.h.y, a.l.y, b.h.x, b.l.x);
+  return a;
+}
+__device__ __forceinline__ dfc csubi(dfc a, dfc b) {
+  df_add(a.h.x, a.l.x, b.h.y, b.l.y);
+  df_add(a.h.y, a.l.y, -b.h.x, -b.l.x);
+  return a;
+}
+// acc += a b and acc += conj(a) b
+__device__ __forceinline__ void cfma(dfc& acc, dfc a, dfc b) {
+  df_fma(acc.h.x, acc.l.x, a.h.x, a.l.x, b.h.x, b.l.x);
+  df_fma(acc.h.x, acc.l.x, -a.h.y, -a.l.y, b.h.y, b.l.y);
+  df_fma(acc.h.y, acc.l.y, a.h.x, a.l.x, b.h.y, b.l.y);
+  df_fma(acc.h.y, acc.l.y, a.h.y, a.l.y, b.h.x, b.l.x);
+}
+__device__ __forceinline__ void cfmac(dfc& acc, dfc a, dfc b) {
+  df_fma(acc.h.x, acc.l.x, a.h.x, a.l.x, b.h.x, b.l.x);
+  df_fma(acc.h.x, acc.l.x, a.h.y, a.l.y, b.h.y, b.l.y);
+  df_fma(acc.h.y, acc.l.y, a.h.x, a.l.x, b.h.y, b.l.y);
+  df_fma(acc.h.y, acc.l.y, -a.h.y, -a.l.y, b.h.x, b.l.x);
+}
+
+template <> struct ScalOf<dfc> { typedef float2 type; };
+template <> __device__ __forceinline__ float2 mkscal<dfc>(double x) { return split_d(x); }
+// a * s for a double-float real s
+__device__ __forceinline__ dfc scale(dfc a, float2 s) {
+  dfc r{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  df_fma(r.h.x, r.l.x, a.h.x, a.l.x, s.x, s.y);
+  df_fma(r.h.y, r.l.y, a.h.y, a.l.y, s.x, s.y);
+  return r;
+}
+__device__ __forceinline__ void axpy(dfc& o, float2 s, dfc v) {
+  df_fma(o.h.x, o.l.x, v.h.x, v.l.x, s.x, s.y);
+  df_fma(o.h.y, o.l.y, v.h.y, v.l.y, s.x, s.y);
+}
+__device__ __forceinline__ float nrm2f(dfc a) { return fmaf(a.h.x, a.h.x, a.h.y * a.h.y); }
+
+}  // namespace dd

@@ -29,6 +29,10 @@
 
 namespace dd {
 
+// internal storage precision (not in the C ABI): double-float pairs of FP32
+constexpr dd_prec DD_DF64 = (dd_prec)3;
+struct df2s;
+
 struct DomInst {            // device-visible descriptor (plain data)
   int n[2];                 // sites per parity
   int dims[4];              // box extents (lattice extents for FULL / LAMBDA1)
@@ -42,6 +46,7 @@ struct DomInst {            // device-visible descriptor (plain data)
   const double2* link64;    // [p][4][9][n_p]
   const float2* link32;
   const __nv_bfloat162* link16;
+  const df2s* linkdf;       // double-float copy (residual of the mixed solver)
 };
 
 // Owning host record of an instance.
@@ -53,6 +58,7 @@ struct Instance {
   void* link64_buf = nullptr;
   void* link32_buf = nullptr;
   void* link16_buf = nullptr;
+  void* linkdf_buf = nullptr;
   std::vector<int> h_glob;      // host copy [p][n_p]
   std::vector<int> h_fmap;      // host copy [p][n_p]
   bool links_ready = false;
@@ -149,6 +155,7 @@ struct dd_ctx {
   dd_solve_stats last_stats{};   // statistics of the last batched solve
   dd_net* net = nullptr;         // learned initial guess for block solves (not owned)
   cudaStream_t capture_stream = nullptr;   // private stream for CUDA-graph capture
+  int forced_variant[3] = {-1, -1, -1};    // manual stencil launch variant per precision
 };
 
 // ---- helpers shared by the translation units --------------------------------
@@ -219,8 +226,9 @@ void free_workspace(dd_ctx* c);
 void free_plan(dd_ctx* c);
 dd_status get_batch(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs, Batch** out);
 dd_status get_batch_insts(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch** out);
-// learned initial guess x0 = N(b) (net.cu), FP32 parity vectors
-dd_status net_guess(dd_ctx* c, dd_net* n, const Batch& b, const double2* be, const double2* bo,
-                    float2* xe32, float2* xo32, cudaStream_t s);   // bytes per complex number at a storage precision
+// learned initial guess x0 = N(b) (net.cu) from FP64 or double-float (df)
+// parity vectors, written as FP32 parity vectors
+dd_status net_guess(dd_ctx* c, dd_net* n, const Batch& b, const void* be, const void* bo, bool df,
+                    float2* xe32, float2* xo32, cudaStream_t s);
 
 }  // namespace dd

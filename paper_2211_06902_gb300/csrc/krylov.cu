@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "spinor.cuh"
@@ -62,7 +63,10 @@ __device__ __forceinline__ double2 sum_slot(const double* partial, int slot, lon
   const int n = d.n[0];                                          \
   const int i = it.y + threadIdx.x;                              \
   const bool live = threadIdx.x < it.z;                          \
-  const long long o = bd.off[0][sys] + i;
+  const long long o = bd.off[0][sys];
+
+// (the elementwise kernels touch the 12 components of site i of every vector
+// at the same pair-layout positions o + cidx(k, n, i))
 
 template <class S>
 __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restrict__ rhs, S* r,
@@ -74,18 +78,18 @@ __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restric
   double acc[1] = {0.0};
   T t[1] = {0};
   if (live) {
-    const C z = cmk<C>(0.0, 0.0);
+    C b[12], z[12];
+    ld_site<12>(rhs + o, n, i, b);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      long long q = o + (long long)k * n;
-      C b = ldc(rhs + q);
-      stc(r + q, b);
-      stc(rhat + q, b);
-      stc(p + q, z);
-      stc(v + q, z);
-      stc(x + q, z);
-      t[0] = fma(b.x, b.x, fma(b.y, b.y, t[0]));
+      z[k] = cmk<C>(0.0, 0.0);
+      t[0] = fma(b[k].x, b[k].x, fma(b[k].y, b[k].y, t[0]));
     }
+    st_site<12>(r + o, n, i, b);
+    st_site<12>(rhat + o, n, i, b);
+    st_site<12>(p + o, n, i, z);
+    st_site<12>(v + o, n, i, z);
+    st_site<12>(x + o, n, i, z);
   }
   block_reduce_t<T, 1>(t, acc, red);
   if (threadIdx.x == 0) {
@@ -103,20 +107,17 @@ template <class S>
 __global__ void k_p_update(BatchDev bd, const SysState* st, const S* __restrict__ r, S* p,
                            const S* __restrict__ v) {
   typedef typename StoreTraits<S>::C C;
-  typedef typename StoreTraits<S>::T T;
   ELEM_PROLOGUE
   if (!live || !st[sys].active) return;
   const C beta = cmk<C>(st[sys].beta.x, st[sys].beta.y);
   const C om = cmk<C>(st[sys].omega.x, st[sys].omega.y);
+  C pp[12], vv[12], rr[12];
+  ld_site<12>(p + o, n, i, pp);
+  ld_site<12>(v + o, n, i, vv);
+  ld_site<12>(r + o, n, i, rr);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    long long q = o + (long long)k * n;
-    C pp = ldc(p + q), vv = ldc(v + q), rr = ldc(r + q);
-    C t = csub(pp, cmul(om, vv));
-    C res = cadd(rr, cmul(beta, t));
-    stc(p + q, res);
-  }
-  (void)sizeof(T);
+  for (int k = 0; k < 12; ++k) pp[k] = cadd(rr[k], cmul(beta, csub(pp[k], cmul(om, vv[k]))));
+  st_site<12>(p + o, n, i, pp);
 }
 
 template <class S>
@@ -126,11 +127,12 @@ __global__ void k_s_update(BatchDev bd, const SysState* st, const S* __restrict_
   ELEM_PROLOGUE
   if (!live || !st[sys].active) return;
   const C al = cmk<C>(st[sys].alpha.x, st[sys].alpha.y);
+  C rr[12], vv[12];
+  ld_site<12>(r + o, n, i, rr);
+  ld_site<12>(v + o, n, i, vv);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    long long q = o + (long long)k * n;
-    stc(s + q, csub(ldc(r + q), cmul(al, ldc(v + q))));
-  }
+  for (int k = 0; k < 12; ++k) rr[k] = csub(rr[k], cmul(al, vv[k]));
+  st_site<12>(s + o, n, i, rr);
 }
 
 // x += alpha p + omega s ; r = s - omega t ; partials (rhat, r) and |r|^2
@@ -148,19 +150,25 @@ __global__ void k_xr_update(BatchDev bd, const SysState* st, S* x, S* r, const S
   if (live) {
     const C al = cmk<C>(st[sys].alpha.x, st[sys].alpha.y);
     const C om = cmk<C>(st[sys].omega.x, st[sys].omega.y);
+    C xx[12], pv[12], ss[12];
+    ld_site<12>(x + o, n, i, xx);
+    ld_site<12>(p + o, n, i, pv);
+    ld_site<12>(s + o, n, i, ss);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) xx[k] = cadd(xx[k], cadd(cmul(al, pv[k]), cmul(om, ss[k])));
+    st_site<12>(x + o, n, i, xx);
+    C tv[12], rh[12];
+    ld_site<12>(t + o, n, i, tv);
+    ld_site<12>(rhat + o, n, i, rh);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      long long q = o + (long long)k * n;
-      C ss = ldc(s + q);
-      C xx = cadd(ldc(x + q), cadd(cmul(al, ldc(p + q)), cmul(om, ss)));
-      stc(x + q, xx);
-      C rr = csub(ss, cmul(om, ldc(t + q)));
-      stc(r + q, rr);
-      C rh = ldc(rhat + q);
-      tt[0] = fma(rh.x, rr.x, fma(rh.y, rr.y, tt[0]));
-      tt[1] = fma(rh.x, rr.y, fma(-rh.y, rr.x, tt[1]));
+      const C rr = csub(ss[k], cmul(om, tv[k]));
+      ss[k] = rr;
+      tt[0] = fma(rh[k].x, rr.x, fma(rh[k].y, rr.y, tt[0]));
+      tt[1] = fma(rh[k].x, rr.y, fma(-rh[k].y, rr.x, tt[1]));
       tt[2] = fma(rr.x, rr.x, fma(rr.y, rr.y, tt[2]));
     }
+    st_site<12>(r + o, n, i, ss);
   }
   block_reduce_t<T, 3>(tt, acc, red);
   if (threadIdx.x == 0) {
@@ -186,11 +194,16 @@ __global__ void k_norm2(BatchDev bd, int p, const S* __restrict__ v, double* par
   const int i = it.y + threadIdx.x;
   double acc[1] = {0.0};
   if (threadIdx.x < it.z) {
-    const long long o = (p ? bd.off[1] : bd.off[0])[sys] + i;
+    C w[12];
+    ld_site<12>(v + (p ? bd.off[1] : bd.off[0])[sys], n, i, w);
+    if constexpr (std::is_same<C, dfc>::value) {
+      float t = 0.f;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      C w = ldc(v + o + (long long)k * n);
-      acc[0] += (double)w.x * w.x + (double)w.y * w.y;
+      for (int k = 0; k < 12; ++k) t += nrm2f(w[k]);
+      acc[0] = t;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[0] += (double)w[k].x * w[k].x + (double)w[k].y * w[k].y;
     }
   }
   block_reduce<1>(acc, red);
@@ -210,35 +223,49 @@ __global__ void k_norm2(BatchDev bd, int p, const S* __restrict__ v, double* par
   const int n = p ? dp_->n[1] : dp_->n[0];                            \
   const int i = it.y + threadIdx.x;                                   \
   const bool live = threadIdx.x < it.z;                               \
-  const long long o = (p ? bd.off[1] : bd.off[0])[sys] + i;
+  const long long o = (p ? bd.off[1] : bd.off[0])[sys];
 
 // y (type SD) = x (type SS) on parity p, for systems still in the outer loop
 template <class SD, class SS>
 __global__ void k_convert(BatchDev bd, int p, SD* y, const SS* __restrict__ x, const SysState* st) {
   typedef typename StoreTraits<SD>::C CD;
+  typedef typename StoreTraits<SS>::C CS;
   ELEM_PROLOGUE_P
   if (!live || !st[sys].outer_active) return;
+  CS v[12];
+  CD w[12];
+  ld_site<12>(x + o, n, i, v);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    long long q = o + (long long)k * n;
-    auto v = ldc(x + q);
-    stc(y + q, cmk<CD>((double)v.x, (double)v.y));
+    if constexpr (std::is_same<CS, dfc>::value) w[k] = v[k].h;      // nearest FP32 value
+    else w[k] = cmk<CD>((double)v[k].x, (double)v[k].y);
   }
+  st_site<12>(y + o, n, i, w);
 }
 
-// x64 += sign * e (type S) on parity p, for systems still in the outer loop
-template <class S>
-__global__ void k_axpy64(BatchDev bd, int p, double2* x, const S* __restrict__ e, double sign,
+// outer x += sign * e (e of type S) on parity p, for systems still in the
+// outer loop; the outer vector is FP64 (double2) or double-float (df2s)
+template <class O, class S>
+__global__ void k_axpy64(BatchDev bd, int p, O* x, const S* __restrict__ e, double sign,
                          const SysState* st) {
+  typedef typename StoreTraits<S>::C C;
+  typedef typename StoreTraits<O>::C CO;
   ELEM_PROLOGUE_P
   if (!live || !st[sys].outer_active) return;
+  C v[12];
+  CO a[12];
+  ld_site<12>(e + o, n, i, v);
+  ld_site<12>(x + o, n, i, a);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    long long q = o + (long long)k * n;
-    auto v = ldc(e + q);
-    double2 a = x[q];
-    x[q] = make_double2(fma(sign, (double)v.x, a.x), fma(sign, (double)v.y, a.y));
+    if constexpr (std::is_same<CO, dfc>::value) {
+      df_add(a[k].h.x, a[k].l.x, (float)sign * (float)v[k].x, 0.f);
+      df_add(a[k].h.y, a[k].l.y, (float)sign * (float)v[k].y, 0.f);
+    } else {
+      a[k] = make_double2(fma(sign, (double)v[k].x, a[k].x), fma(sign, (double)v[k].y, a[k].y));
+    }
   }
+  st_site<12>(x + o, n, i, a);
 }
 
 __global__ void k_zero64(double2* x, long long n) {
@@ -571,6 +598,40 @@ dd_status tune_hop(dd_ctx* c, const Batch& b, dd_prec prec, const void* in, void
   return st;
 }
 
+// outer-vector launches: the outer vectors are FP64 (plain FP64 solve) or
+// double-float (mixed solve); `sp` is the precision of the added vector
+template <class O>
+void axpy_outer_t(const BatchDev& bd, dim3 g, int p, void* x, const void* v, dd_prec sp, double sign,
+                  const SysState* st, cudaStream_t s) {
+  if (sp == DD_F64)
+    DD_COUNT_LAUNCH(), k_axpy64<O, double2><<<g, 128, 0, s>>>(bd, p, (O*)x, (const double2*)v, sign, st);
+  else if (sp == DD_F32)
+    DD_COUNT_LAUNCH(), k_axpy64<O, float2><<<g, 128, 0, s>>>(bd, p, (O*)x, (const float2*)v, sign, st);
+  else
+    DD_COUNT_LAUNCH(), k_axpy64<O, __nv_bfloat162><<<g, 128, 0, s>>>(bd, p, (O*)x, (const __nv_bfloat162*)v, sign, st);
+}
+void axpy_outer(bool dfo, const BatchDev& bd, dim3 g, int p, void* x, const void* v, dd_prec sp,
+                double sign, const SysState* st, cudaStream_t s) {
+  if (dfo) axpy_outer_t<df2s>(bd, g, p, x, v, sp, sign, st, s);
+  else axpy_outer_t<double2>(bd, g, p, x, v, sp, sign, st, s);
+}
+void norm2_outer(bool dfo, const BatchDev& bd, dim3 g, int p, const void* v, double* partial,
+                 cudaStream_t s) {
+  if (dfo) DD_COUNT_LAUNCH(), k_norm2<df2s><<<g, 128, 0, s>>>(bd, p, (const df2s*)v, partial, 0);
+  else DD_COUNT_LAUNCH(), k_norm2<double2><<<g, 128, 0, s>>>(bd, p, (const double2*)v, partial, 0);
+}
+// outer residual -> inner precision ip (F32 or BF16)
+void convert_outer(bool dfo, dd_prec ip, const BatchDev& bd, dim3 g, int p, void* y, const void* x,
+                   const SysState* st, cudaStream_t s) {
+  if (ip == DD_F32) {
+    if (dfo) DD_COUNT_LAUNCH(), k_convert<float2, df2s><<<g, 128, 0, s>>>(bd, p, (float2*)y, (const df2s*)x, st);
+    else DD_COUNT_LAUNCH(), k_convert<float2, double2><<<g, 128, 0, s>>>(bd, p, (float2*)y, (const double2*)x, st);
+  } else {
+    if (dfo) DD_COUNT_LAUNCH(), k_convert<__nv_bfloat162, df2s><<<g, 128, 0, s>>>(bd, p, (__nv_bfloat162*)y, (const df2s*)x, st);
+    else DD_COUNT_LAUNCH(), k_convert<__nv_bfloat162, double2><<<g, 128, 0, s>>>(bd, p, (__nv_bfloat162*)y, (const double2*)x, st);
+  }
+}
+
 }  // namespace
 
 dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x_user,
@@ -581,7 +642,12 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const dd_prec ip = prm->inner_prec;
   const size_t c64 = 16, cin = prec_bytes(ip);
   const long long ne = b.tot[0], no = b.tot[1];
-  // FP64 outer vectors: b, x, r (both parities)
+  // Outer vectors b, x, r (both parities), 16 bytes per complex number: FP64
+  // for the plain FP64 solve; double-float for the mixed solves, whose true
+  // residual r = b - D x then runs on the FP32 pipes (GB300 issues FP64 at a
+  // small fraction of its FP32 rate) with about 44 significant bits.
+  const bool dfo = ip != DD_F64;
+  const dd_prec op = dfo ? DD_DF64 : DD_F64;
   void *be, *bo, *xe, *xo, *re, *ro;
   if ((e = ws_get(c, 0, ne * c64, &be)) || (e = ws_get(c, 1, no * c64, &bo)) ||
       (e = ws_get(c, 2, ne * c64, &xe)) || (e = ws_get(c, 3, no * c64, &xo)) ||
@@ -611,7 +677,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   int* d_count = (int*)vcnt;
   unsigned long long* d_maxrel = (unsigned long long*)((char*)vcnt + 16);
   for (int j = 0; j < b.nb; ++j) {
-    if ((e = ensure_links(c, b.inst[j], DD_F64)) != DD_OK) return e;
+    if ((e = ensure_links(c, b.inst[j], op)) != DD_OK) return e;
     if (ip != DD_F64 && (e = ensure_links(c, b.inst[j], ip)) != DD_OK) return e;
   }
   if ((e = sync_instances(c)) != DD_OK) return e;
@@ -627,11 +693,11 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   cudaEventCreate(&ev1);
   cudaEventRecord(ev0, s);
 
-  if ((e = launch_pack(c, b, b_user, be, bo, DD_F64, s)) != DD_OK) return e;
-  DD_COUNT_LAUNCH(), k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)be, partial, 0);
-  if (has_odd) DD_COUNT_LAUNCH(), k_norm2<double2><<<og, 128, 0, s>>>(bd, 1, (const double2*)bo, partial_o, 0);
+  if ((e = launch_pack(c, b, b_user, be, bo, op, s)) != DD_OK) return e;
+  norm2_outer(dfo, bd, eg, 0, be, partial, s);
+  if (has_odd) norm2_outer(dfo, bd, og, 1, bo, partial_o, s);
   DD_COUNT_LAUNCH(), k_sc_bnorm<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o, prm->tol * prm->tol);
-  // x = 0, r = b
+  // x = 0 (all-zero bytes in both storages), r = b
   DD_COUNT_LAUNCH(), k_zero64<<<(ne + 255) / 256, 256, 0, s>>>((double2*)xe, ne);
   if (no) DD_COUNT_LAUNCH(), k_zero64<<<(no + 255) / 256, 256, 0, s>>>((double2*)xo, no);
   DD_CUDA(c, cudaMemcpyAsync(re, be, ne * c64, cudaMemcpyDeviceToDevice, s));
@@ -647,24 +713,22 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     if ((e = ws_get(c, 28, ne * 8, &ge)) || (e = ws_get(c, 29, no * 8 + 16, &go)) ||
         (e = ws_get(c, 80, ne * 8, &te)) || (e = ws_get(c, 81, no * 8 + 16, &to)))
       return e;
-    if ((e = net_guess(c, c->net, b, (const double2*)be, (const double2*)bo, (float2*)ge, (float2*)go,
-                       s)) != DD_OK)
-      return e;
+    if ((e = net_guess(c, c->net, b, be, bo, dfo, (float2*)ge, (float2*)go, s)) != DD_OK) return e;
     if ((e = ensure_links(c, b.inst[0], DD_F32)) != DD_OK) return e;
     for (int j = 0; j < b.nb; ++j)
       if ((e = ensure_links(c, b.inst[j], DD_F32)) != DD_OK) return e;
     if ((e = sync_instances(c)) != DD_OK) return e;
     bd = batch_view(c, b);
-    DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const float2*)ge, 1.0, st);
-    if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const float2*)go, 1.0, st);
+    axpy_outer(dfo, bd, eg, 0, xe, ge, DD_F32, 1.0, st, s);
+    if (has_odd) axpy_outer(dfo, bd, og, 1, xo, go, DD_F32, 1.0, st, s);
     HopArgs h{};
     h.p_out = 0; h.in = go; h.out = te; h.s1 = ge; h.a1 = 1.0; h.b = -kap;
     if ((e = launch_hop(c, b, DD_F32, h, s)) != DD_OK) return e;
     HopArgs g{};
     g.p_out = 1; g.in = ge; g.out = to; g.s1 = go; g.a1 = 1.0; g.b = -kap;
     if ((e = launch_hop(c, b, DD_F32, g, s)) != DD_OK) return e;
-    DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)re, (const float2*)te, -1.0, st);
-    if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)ro, (const float2*)to, -1.0, st);
+    axpy_outer(dfo, bd, eg, 0, re, te, DD_F32, -1.0, st, s);
+    if (has_odd) axpy_outer(dfo, bd, og, 1, ro, to, DD_F32, -1.0, st, s);
     DD_CUDA(c, cudaGetLastError());
   }
 
@@ -693,8 +757,8 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   double maxrel = 1.0;
   for (int cyc = 0;; ++cyc) {
     // |r|^2 of both parities -> convergence
-    DD_COUNT_LAUNCH(), k_norm2<double2><<<eg, 128, 0, s>>>(bd, 0, (const double2*)re, partial, 0);
-    if (has_odd) DD_COUNT_LAUNCH(), k_norm2<double2><<<og, 128, 0, s>>>(bd, 1, (const double2*)ro, partial_o, 0);
+    norm2_outer(dfo, bd, eg, 0, re, partial, s);
+    if (has_odd) norm2_outer(dfo, bd, og, 1, ro, partial_o, s);
     DD_CUDA(c, cudaMemsetAsync(vcnt, 0, 64, s));
     DD_COUNT_LAUNCH(), k_sc_outer<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o,
                                                      last_true ? 1.0 : 0.25, d_count, d_maxrel,
@@ -711,21 +775,14 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     // residual at the inner precision
     const void *rin_e = re, *rin_o = ro;
     if (ip != DD_F64) {
-      if (ip == DD_F32) {
-        DD_COUNT_LAUNCH(), k_convert<float2, double2><<<eg, 128, 0, s>>>(bd, 0, (float2*)w.s, (const double2*)re, st);
-        if (has_odd) DD_COUNT_LAUNCH(), k_convert<float2, double2><<<og, 128, 0, s>>>(bd, 1, (float2*)rso, (const double2*)ro, st);
-      } else {
-        DD_COUNT_LAUNCH(), k_convert<__nv_bfloat162, double2><<<eg, 128, 0, s>>>(bd, 0, (__nv_bfloat162*)w.s, (const double2*)re, st);
-        if (has_odd) DD_COUNT_LAUNCH(), k_convert<__nv_bfloat162, double2><<<og, 128, 0, s>>>(bd, 1, (__nv_bfloat162*)rso, (const double2*)ro, st);
-      }
+      convert_outer(dfo, ip, bd, eg, 0, w.s, re, st, s);
+      if (has_odd) convert_outer(dfo, ip, bd, og, 1, rso, ro, st, s);
       rin_e = w.s;
       rin_o = rso;
     }
     if ((prm->flags & DD_SOLVE_AUTOTUNE) && cyc == 0) {
       const int pi = ip == DD_F64 ? 0 : (ip == DD_F32 ? 1 : 2);
       if (!b.tuned[pi] && (e = tune_hop(c, b, ip, rin_e, ip == DD_F64 ? tune64 : w.tmp, s)) != DD_OK)
-        return e;
-      if (ip != DD_F64 && !b.tuned[0] && (e = tune_hop(c, b, DD_F64, re, tune64, s)) != DD_OK)
         return e;
     }
     // Schur right-hand side r^_e = r_e + k H_eo r_o
@@ -751,25 +808,17 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       h.p_out = 1; h.in = w.x; h.out = eo; h.s1 = rin_o; h.a1 = 1.0; h.b = kap;
       if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
     }
-    // x += e (FP64)
-    if (ip == DD_F64) {
-      DD_COUNT_LAUNCH(), k_axpy64<double2><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const double2*)w.x, 1.0, st);
-      if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<double2><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const double2*)eo, 1.0, st);
-    } else if (ip == DD_F32) {
-      DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const float2*)w.x, 1.0, st);
-      if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const float2*)eo, 1.0, st);
-    } else {
-      DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<eg, 128, 0, s>>>(bd, 0, (double2*)xe, (const __nv_bfloat162*)w.x, 1.0, st);
-      if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<og, 128, 0, s>>>(bd, 1, (double2*)xo, (const __nv_bfloat162*)eo, 1.0, st);
-    }
+    // x += e
+    axpy_outer(dfo, bd, eg, 0, xe, w.x, ip, 1.0, st, s);
+    if (has_odd) axpy_outer(dfo, bd, og, 1, xo, eo, ip, 1.0, st, s);
     if (true_residual) {
-      // r = b - D x in FP64
+      // r = b - D x at the outer precision
       HopArgs h{};
       h.p_out = 0; h.in = xo; h.out = re; h.s1 = be; h.a1 = 1.0; h.s2 = xe; h.a2 = -1.0; h.b = kap;
-      if ((e = launch_hop(c, b, DD_F64, h, s)) != DD_OK) return e;
+      if ((e = launch_hop(c, b, op, h, s)) != DD_OK) return e;
       HopArgs g{};
       g.p_out = 1; g.in = xe; g.out = ro; g.s1 = bo; g.a1 = 1.0; g.s2 = xo; g.a2 = -1.0; g.b = kap;
-      if ((e = launch_hop(c, b, DD_F64, g, s)) != DD_OK) return e;
+      if ((e = launch_hop(c, b, op, g, s)) != DD_OK) return e;
     } else {
       // r -= D e with D e at the inner precision
       HopArgs h{};
@@ -778,18 +827,13 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       HopArgs g{};
       g.p_out = 1; g.in = w.x; g.out = w.tmp; g.s1 = eo; g.a1 = 1.0; g.b = -kap;
       if ((e = launch_hop(c, b, ip, g, s)) != DD_OK) return e;
-      if (ip == DD_F32) {
-        DD_COUNT_LAUNCH(), k_axpy64<float2><<<eg, 128, 0, s>>>(bd, 0, (double2*)re, (const float2*)w.t, -1.0, st);
-        if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<float2><<<og, 128, 0, s>>>(bd, 1, (double2*)ro, (const float2*)w.tmp, -1.0, st);
-      } else {
-        DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<eg, 128, 0, s>>>(bd, 0, (double2*)re, (const __nv_bfloat162*)w.t, -1.0, st);
-        if (has_odd) DD_COUNT_LAUNCH(), k_axpy64<__nv_bfloat162><<<og, 128, 0, s>>>(bd, 1, (double2*)ro, (const __nv_bfloat162*)w.tmp, -1.0, st);
-      }
+      axpy_outer(dfo, bd, eg, 0, re, w.t, ip, -1.0, st, s);
+      if (has_odd) axpy_outer(dfo, bd, og, 1, ro, w.tmp, ip, -1.0, st, s);
     }
     last_true = true_residual;
     DD_CUDA(c, cudaGetLastError());
   }
-  if ((e = launch_unpack(c, b, xe, xo, x_user, DD_F64, s)) != DD_OK) return e;
+  if ((e = launch_unpack(c, b, xe, xo, x_user, op, s)) != DD_OK) return e;
   cudaEventRecord(ev1, s);
   DD_CUDA(c, cudaGetLastError());
   std::vector<double> rel(nsys);
@@ -805,6 +849,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   out.systems = nsys;
   out.outer_cycles = cycles;
   out.seconds = ms * 1e-3;
+  out.hop_variant = b.hop_variant[ip == DD_F64 ? 0 : (ip == DD_F32 ? 1 : 2)];
   bool nan = false;
   for (int k = 0; k < nsys; ++k) {
     if (!(rel[k] == rel[k])) nan = true;

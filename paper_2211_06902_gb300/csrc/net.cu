@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_ptconv(BatchDev bd, int p, const float2*
   for (int cp = 0; cp < CIN; ++cp) {
     float2 v[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) v[a] = inp[(long long)(cp * 3 + a) * n_out + i];
+    for (int a = 0; a < 3; ++a) v[a] = inp[cidx(cp * 3 + a, n_out, i)];
 #pragma unroll
     for (int c = 0; c < COUT; ++c) {
       const float2 wc = w[c * CIN + cp];
@@ -90,21 +90,14 @@ __global__ void __launch_bounds__(NT) k_ptconv(BatchDev bd, int p, const float2*
     const int mu = dir & 3;
     const bool fwd = dir < 4;
     float2 U[9];
-    if (fwd) {
-      const float2* l = lk + (p ? 36LL * n0 : 0) + (long long)mu * 9 * n_out + i;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) U[k] = l[(long long)k * n_out];
-    } else {
-      const float2* l = lk + (p ? 0 : 36LL * n0) + (long long)mu * 9 * n_in + j;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) U[k] = l[(long long)k * n_in];
-    }
+    if (fwd) ld_link(lk + link_block(p, mu, n0, n_out), n_out, i, U);
+    else ld_link(lk + link_block(1 - p, mu, n0, n_in), n_in, j, U);
     const float2* wd = w + (1 + dir) * COUT * CIN;
 #pragma unroll 1
     for (int cp = 0; cp < CIN; ++cp) {
       float2 v[3], tv[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) v[a] = inq[(long long)(cp * 3 + a) * n_in + j];
+      for (int a = 0; a < 3; ++a) v[a] = inq[cidx(cp * 3 + a, n_in, j)];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         tv[a] = make_float2(0.f, 0.f);
@@ -126,7 +119,7 @@ __global__ void __launch_bounds__(NT) k_ptconv(BatchDev bd, int p, const float2*
 #pragma unroll
   for (int c = 0; c < COUT; ++c)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) o[(long long)(c * 3 + a) * n_out + i] = acc[c][a];
+    for (int a = 0; a < 3; ++a) o[cidx(c * 3 + a, n_out, i)] = acc[c][a];
 }
 
 // weight gradient partials: one CTA per (item, rhs) work unit of parity p;
@@ -157,7 +150,7 @@ __global__ void __launch_bounds__(256) k_ptconv_wgrad(BatchDev bd, int p, const 
   if (s < NT)
     for (int c = 0; c < COUT; ++c)
       for (int a = 0; a < 3; ++a)
-        sg[(c * 3 + a) * NT + s] = live ? gp[(long long)(c * 3 + a) * n_out + i] : make_float2(0.f, 0.f);
+        sg[(c * 3 + a) * NT + s] = live ? gp[cidx(c * 3 + a, n_out, i)] : make_float2(0.f, 0.f);
   const int* nbr = dp->nbr + (p ? 8LL * n0 : 0);
   const float2* lk = dp->link32;
   for (int d = 0; d < 9; ++d) {
@@ -169,19 +162,19 @@ __global__ void __launch_bounds__(256) k_ptconv_wgrad(BatchDev bd, int p, const 
         float2 tv[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         if (j >= 0) {
           if (d == 0) {
-            for (int a = 0; a < 3; ++a) tv[a] = inp[(long long)(cp * 3 + a) * n_out + i];
+            for (int a = 0; a < 3; ++a) tv[a] = inp[cidx(cp * 3 + a, n_out, i)];
           } else {
             const int mu = (d - 1) & 3;
             const bool fwd = d <= 4;
             float2 v[3];
-            for (int a = 0; a < 3; ++a) v[a] = inq[(long long)(cp * 3 + a) * n_in + j];
+            for (int a = 0; a < 3; ++a) v[a] = inq[cidx(cp * 3 + a, n_in, j)];
             for (int a = 0; a < 3; ++a)
               for (int b2 = 0; b2 < 3; ++b2) {
                 if (fwd) {
-                  float2 u = lk[(p ? 36LL * n0 : 0) + (long long)(mu * 9 + a * 3 + b2) * n_out + i];
+                  float2 u = lk[link_block(p, mu, n0, n_out) + cidx(a * 3 + b2, n_out, i)];
                   cfma(tv[a], u, v[b2]);
                 } else {
-                  float2 u = lk[(p ? 0 : 36LL * n0) + (long long)(mu * 9 + b2 * 3 + a) * n_in + j];
+                  float2 u = lk[link_block(1 - p, mu, n0, n_in) + cidx(b2 * 3 + a, n_in, j)];
                   cfmac(tv[a], u, v[b2]);
                 }
               }
@@ -229,7 +222,7 @@ __global__ void k_loss_grad(BatchDev bd, int p, const float2* __restrict__ y, co
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
   const int n = p ? dp->n[1] : dp->n[0];
   const int i = it.y + threadIdx.x;
-  const long long o = (p ? bd.off[1] : bd.off[0])[sys] + i;
+  const long long o = (p ? bd.off[1] : bd.off[0])[sys];
   float t[1] = {0.f};
   double v[1] = {0.0};
   if ((int)threadIdx.x < it.z) {
@@ -237,10 +230,11 @@ __global__ void k_loss_grad(BatchDev bd, int p, const float2* __restrict__ y, co
     const float f = (float)(2.0 * sc * invS);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      float2 a = y[o + (long long)k * n], b = x[o + (long long)k * n];
+      const long long q = o + cidx(k, n, i);
+      float2 a = y[q], b = x[q];
       float2 d = make_float2(a.x - b.x, a.y - b.y);
       t[0] = fmaf(d.x, d.x, fmaf(d.y, d.y, t[0]));
-      if (g) g[o + (long long)k * n] = make_float2(f * d.x, f * d.y);
+      if (g) g[q] = make_float2(f * d.x, f * d.y);
     }
     t[0] = (float)(t[0] * sc * invS);
   }
@@ -260,10 +254,10 @@ __global__ void k_norm2_act(BatchDev bd, int p, const float2* __restrict__ x, do
   float t[1] = {0.f};
   double v[1] = {0.0};
   if ((int)threadIdx.x < it.z) {
-    const long long o = (p ? bd.off[1] : bd.off[0])[sys] + i;
+    const long long o = (p ? bd.off[1] : bd.off[0])[sys];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      float2 a = x[o + (long long)k * n];
+      float2 a = x[o + cidx(k, n, i)];
       t[0] = fmaf(a.x, a.x, fmaf(a.y, a.y, t[0]));
     }
   }
@@ -286,6 +280,14 @@ __global__ void k_sum_sys(const double* pe, const double* po, const int* ib0, co
 __global__ void k_f64_to_f32(const double2* a, float2* b, long long n) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k < n) b[k] = make_float2((float)a[k].x, (float)a[k].y);
+}
+// double-float (re_h, im_h, re_l, im_l) -> nearest FP32 (the high parts)
+__global__ void k_df_to_f32(const float4* a, float2* b, long long n) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < n) {
+    const float4 v = a[k];
+    b[k] = make_float2(v.x, v.y);
+  }
 }
 
 }  // namespace
@@ -478,17 +480,24 @@ static dd_status target_norms(dd_ctx* c, const Batch& b, const float2* const xt[
   return DD_OK;
 }
 
-// initial guess for the solver: x0 = N(b) from FP64 caller-layout b (parity
-// vectors be, bo), written as FP32 parity vectors xe32, xo32
-dd_status net_guess(dd_ctx* c, dd_net* n, const Batch& b, const double2* be, const double2* bo,
+// initial guess for the solver: x0 = N(b) from the solver's parity vectors
+// be, bo (FP64, or double-float when `df`), written as FP32 parity vectors
+// xe32, xo32
+dd_status net_guess(dd_ctx* c, dd_net* n, const Batch& b, const void* be, const void* bo, bool df,
                     float2* xe32, float2* xo32, cudaStream_t s) {
   dd_status e = check_net(c, n, b);
   if (e != DD_OK) return e;
   Acts A;
   if ((e = alloc_acts(c, b, n, 100, A)) != DD_OK) return e;
   // FP64 parity vectors -> FP32 activations of layer 0 (same SoA layout)
-  if (b.tot[0]) DD_COUNT_LAUNCH(), k_f64_to_f32<<<(unsigned)((b.tot[0] + 255) / 256), 256, 0, s>>>(be, A.a[0][0], b.tot[0]);
-  if (b.tot[1]) DD_COUNT_LAUNCH(), k_f64_to_f32<<<(unsigned)((b.tot[1] + 255) / 256), 256, 0, s>>>(bo, A.a[0][1], b.tot[1]);
+  for (int p = 0; p < 2; ++p) {
+    const long long m = b.tot[p];
+    if (!m) continue;
+    const unsigned g = (unsigned)((m + 255) / 256);
+    const void* v = p ? bo : be;
+    if (df) DD_COUNT_LAUNCH(), k_df_to_f32<<<g, 256, 0, s>>>((const float4*)v, A.a[0][p], m);
+    else DD_COUNT_LAUNCH(), k_f64_to_f32<<<g, 256, 0, s>>>((const double2*)v, A.a[0][p], m);
+  }
   DD_CUDA(c, cudaGetLastError());
   if ((e = net_forward(c, n, b, A, s)) != DD_OK) return e;
   DD_CUDA(c, cudaMemcpyAsync(xe32, A.a[n->nl][0], sizeof(float2) * b.tot[0], cudaMemcpyDeviceToDevice, s));

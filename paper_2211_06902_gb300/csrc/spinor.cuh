@@ -9,6 +9,7 @@
 // colours) is multiplied by the link and the lower half is rebuilt.
 #pragma once
 #include <cuda_bf16.h>
+#include <cstring>
 
 namespace dd {
 
@@ -26,6 +27,91 @@ __device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) {
 __device__ __forceinline__ void stc(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
+// ---- pair layout ---------------------------------------------------------------
+// Work vectors and per-site link copies store, for n sites of one system and
+// parity, component k of site i at complex index ((k / 2) * n + i) * 2 + k % 2:
+// components come in pairs per site, so one thread loads two components with
+// one 16-byte (FP32), 8-byte (BF16) or 2 x 16-byte (FP64) access.  A link
+// keeps its 9 entries in 5 pairs (the 10th entry is padding).
+__device__ __host__ __forceinline__ long long cidx(int k, long long n, long long i) {
+  return (((long long)(k >> 1)) * n + i) * 2 + (k & 1);
+}
+
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  a = __ldg(p);
+  b = __ldg(p + 1);
+}
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const __nv_bfloat162* p, float2& a, float2& b) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  __nv_bfloat162 x, y;
+  memcpy(&x, &v.x, 4);
+  memcpy(&y, &v.y, 4);
+  a = __bfloat1622float2(x);
+  b = __bfloat1622float2(y);
+}
+// plain (coherent) loads for vectors the same kernel also writes
+__device__ __forceinline__ void ld_pair(double2* p, double2& a, double2& b) {
+  a = p[0];
+  b = p[1];
+}
+__device__ __forceinline__ void ld_pair(float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(__nv_bfloat162* p, float2& a, float2& b) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  __nv_bfloat162 x, y;
+  memcpy(&x, &v.x, 4);
+  memcpy(&y, &v.y, 4);
+  a = __bfloat1622float2(x);
+  b = __bfloat1622float2(y);
+}
+
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat162* p, float2 a, float2 b) {
+  __nv_bfloat162 x = __float22bfloat162_rn(a), y = __float22bfloat162_rn(b);
+  uint2 v;
+  memcpy(&v.x, &x, 4);
+  memcpy(&v.y, &y, 4);
+  *reinterpret_cast<uint2*>(p) = v;
+}
+
+// 12 components of site i (NC = 12) or any even count NC
+template <int NC, class S, class C>
+__device__ __forceinline__ void ld_site(const S* base, long long n, long long i, C (&v)[NC]) {
+#pragma unroll
+  for (int q = 0; q < NC / 2; ++q) ld_pair(base + (q * n + i) * 2, v[2 * q], v[2 * q + 1]);
+}
+template <int NC, class S, class C>
+__device__ __forceinline__ void st_site(S* base, long long n, long long i, const C (&v)[NC]) {
+#pragma unroll
+  for (int q = 0; q < NC / 2; ++q) st_pair(base + (q * n + i) * 2, v[2 * q], v[2 * q + 1]);
+}
+
+// the 9 entries of a link stored at site i of a (parity, mu) block of n sites
+template <class S, class C>
+__device__ __forceinline__ void ld_link(const S* blk, long long n, long long i, C (&U)[9]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ld_pair(blk + (q * n + i) * 2, U[2 * q], U[2 * q + 1]);
+  U[8] = ldc(blk + (4 * n + i) * 2);
+}
+// offset of the (parity, mu) link block: [p][mu][10 entries][n_p]
+__device__ __host__ __forceinline__ long long link_block(int p, int mu, long long n0, long long np) {
+  return (p ? 40 * n0 : 0) + (long long)mu * 10 * np;
+}
 
 // ---- complex helpers ------------------------------------------------------------
 template <class C> __device__ __forceinline__ C cmk(double re, double im);
@@ -117,6 +203,29 @@ __device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const 
   }
 }
 
+// ---- scalar helpers of the stencil epilogue (overloaded for double-float) ---------
+template <class C> struct ScalOf;
+template <> struct ScalOf<float2> { typedef float type; };
+template <> struct ScalOf<double2> { typedef double type; };
+template <class C> __device__ __forceinline__ typename ScalOf<C>::type mkscal(double x);
+template <> __device__ __forceinline__ float mkscal<float2>(double x) { return (float)x; }
+template <> __device__ __forceinline__ double mkscal<double2>(double x) { return x; }
+__device__ __forceinline__ float2 scale(float2 a, float s) { return cscale(a, s); }
+__device__ __forceinline__ double2 scale(double2 a, double s) { return cscale(a, s); }
+__device__ __forceinline__ void axpy(float2& o, float s, float2 v) {
+  o.x = fma(s, v.x, o.x);
+  o.y = fma(s, v.y, o.y);
+}
+__device__ __forceinline__ void axpy(double2& o, double s, double2 v) {
+  o.x = fma(s, v.x, o.x);
+  o.y = fma(s, v.y, o.y);
+}
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+// |a|^2 of one component as float (norms for convergence tests)
+__device__ __forceinline__ float nrm2f(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ float nrm2f(double2 a) { return (float)(a.x * a.x + a.y * a.y); }
+
 // Warp + block reduction of NV doubles (sum); result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], double* sh /* >= 32*NV */) {
@@ -168,3 +277,5 @@ __device__ __forceinline__ void block_reduce_t(T (&t)[NV], double (&v)[NV], doub
 }
 
 }  // namespace dd
+
+#include "dfloat.cuh"

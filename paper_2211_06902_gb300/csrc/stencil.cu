@@ -8,6 +8,7 @@
 // per-system inner products the Krylov solver needs into its epilogue.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.h"
 #include "spinor.cuh"
@@ -26,6 +27,8 @@ template <>
 __device__ __forceinline__ const __nv_bfloat162* links_of<__nv_bfloat162>(const DomInst& d) {
   return d.link16;
 }
+template <>
+__device__ __forceinline__ const df2s* links_of<df2s>(const DomInst& d) { return d.linkdf; }
 
 template <int DIR, class S, class C>
 __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int n_out,
@@ -35,19 +38,10 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
   constexpr bool FWD = DIR < 4;
   if (j < 0) return;
   C psi[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) psi[k] = ldc(in_sys + (long long)k * n_in + j);
+  ld_site<12>(in_sys, n_in, j, psi);
   C U[9];
-  if (FWD) {
-    const S* l = lk + (p ? 36LL * n0 : 0) + (long long)MU * 9 * n_out + i;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) U[c] = ldc(l + (long long)c * n_out);
-  } else {
-    const int q = 1 - p;
-    const S* l = lk + (q ? 36LL * n0 : 0) + (long long)MU * 9 * n_in + j;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) U[c] = ldc(l + (long long)c * n_in);
-  }
+  if (FWD) ld_link(lk + link_block(p, MU, n0, n_out), n_out, i, U);
+  else ld_link(lk + link_block(1 - p, MU, n0, n_in), n_in, j, U);
   hop_dir<MU, FWD>(acc, psi, U);
 }
 
@@ -91,32 +85,30 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     hop_one<5, S>(acc, n0, p, i, n_out, n_in, jn[5], in_sys, lk);
     hop_one<6, S>(acc, n0, p, i, n_out, n_in, jn[6], in_sys, lk);
     hop_one<7, S>(acc, n0, p, i, n_out, n_in, jn[7], in_sys, lk);
-    const T b = (T)a.b;
+    const auto b = mkscal<C>(a.b);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = cscale(acc[k], b);
+    for (int k = 0; k < 12; ++k) out[k] = scale(acc[k], b);
     if (a.s1) {
       const S* s1 = (const S*)a.s1 + (p ? bd.off[1] : bd.off[0])[sys];
-      const T a1 = (T)a.a1;
+      const auto a1 = mkscal<C>(a.a1);
+      C v[12];
+      ld_site<12>(s1, n_out, i, v);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        C v = ldc(s1 + (long long)k * n_out + i);
-        out[k].x = fma(a1, v.x, out[k].x);
-        out[k].y = fma(a1, v.y, out[k].y);
-      }
+      for (int k = 0; k < 12; ++k) axpy(out[k], a1, v[k]);
     }
     if (a.s2) {
       const S* s2 = (const S*)a.s2 + (p ? bd.off[1] : bd.off[0])[sys];
-      const T a2 = (T)a.a2;
+      const auto a2 = mkscal<C>(a.a2);
+      C v[12];
+      ld_site<12>(s2, n_out, i, v);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        C v = ldc(s2 + (long long)k * n_out + i);
-        out[k].x = fma(a2, v.x, out[k].x);
-        out[k].y = fma(a2, v.y, out[k].y);
-      }
+      for (int k = 0; k < 12; ++k) axpy(out[k], a2, v[k]);
     }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) stc(out_sys + (long long)k * n_out + i, out[k]);
+    st_site<12>(out_sys, n_out, i, out);
   }
+  if constexpr (std::is_same<C, dfc>::value) {
+    return;      // the double-float residual kernel takes no fused inner products
+  } else {
   const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
   const long long my = (long long)item * bd.nrhs + r;
   // per-thread sums in the storage's compute type (12 terms), FP64 across threads
@@ -125,9 +117,11 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     T t[2] = {0, 0};
     if (live) {
       const S* q = (const S*)a.dotq + (p ? bd.off[1] : bd.off[0])[sys];
+      C wv[12];
+      ld_site<12>(q, n_out, i, wv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        C w = ldc(q + (long long)k * n_out + i);
+        const C w = wv[k];
         t[0] = fma(w.x, out[k].x, fma(w.y, out[k].y, t[0]));
         t[1] = fma(w.x, out[k].y, fma(-w.y, out[k].x, t[1]));
       }
@@ -143,9 +137,11 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     T t[3] = {0, 0, 0};
     if (live) {
       const S* q = (const S*)a.dots + (p ? bd.off[1] : bd.off[0])[sys];
+      C wv[12];
+      ld_site<12>(q, n_out, i, wv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        C w = ldc(q + (long long)k * n_out + i);
+        const C w = wv[k];
         // (out, s) = sum conj(out) s ; (out, out)
         t[0] = fma(out[k].x, w.x, fma(out[k].y, w.y, t[0]));
         t[1] = fma(out[k].x, w.y, fma(-out[k].y, w.x, t[1]));
@@ -161,32 +157,373 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
       P[2 * (slot_stride + my) + 1] = 0.0;
     }
   }
+  }
+}
+
+// Register-blocked variant: one thread computes R rhs of the same output site,
+// loading each link once for the R systems (work unit t = item * ceil(nrhs/R) + group).
+template <int DIR, class S, class C, int R>
+__device__ __forceinline__ void hop_one_r(C (&acc)[R][12], int n0, int p, int i, int n_out, int n_in,
+                                          int j, const S* const (&in_sys)[R], const bool (&act)[R],
+                                          const S* __restrict__ lk) {
+  constexpr int MU = DIR & 3;
+  constexpr bool FWD = DIR < 4;
+  if (j < 0) return;
+  C U[9];
+  if (FWD) ld_link(lk + link_block(p, MU, n0, n_out), n_out, i, U);
+  else ld_link(lk + link_block(1 - p, MU, n0, n_in), n_in, j, U);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    if (!act[q]) continue;
+    C psi[12];
+    ld_site<12>(in_sys[q], n_in, j, psi);
+    hop_dir<MU, FWD>(acc[q], psi, U);
+  }
+}
+
+template <class S, int R>
+__device__ __forceinline__ void hop_unit_r(const BatchDev& bd, const HopArgs& a, long long t,
+                                           double* red) {
+  typedef typename StoreTraits<S>::C C;
+  typedef typename StoreTraits<S>::T T;
+  const int p = a.p_out;
+  const int ng = (bd.nrhs + R - 1) / R;
+  const int item = (int)(t / ng);
+  const int g = (int)(t - (long long)item * ng);
+  const int4 it = (p ? bd.items[1] : bd.items[0])[item];
+  bool act[R];
+  int nact = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = g * R + q;
+    act[q] = r < bd.nrhs &&
+             (!a.active || a.active[(long long)(it.x * bd.nrhs + r) * a.active_stride]);
+    nact += act[q] ? 1 : 0;
+  }
+  if (nact == 0) return;
+  if (a.work_bytes && threadIdx.x == 0) atomicAdd(a.work_bytes, a.site_bytes * it.z * nact);
+  const DomInst* dp = bd.inst_tab + bd.inst[it.x];
+  const int n0 = dp->n[0];
+  const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
+  const int i = it.y + threadIdx.x;
+  const bool live = threadIdx.x < it.z;
+  const long long* off_in = p ? bd.off[0] : bd.off[1];
+  const long long* off_out = p ? bd.off[1] : bd.off[0];
+  const S* in_sys[R];
+  long long oo[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = min(g * R + q, bd.nrhs - 1);
+    const int sys = it.x * bd.nrhs + r;
+    in_sys[q] = (const S*)a.in + off_in[sys];
+    oo[q] = off_out[sys];
+  }
+  C out[R][12];
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) out[q][k] = cmk<C>(0.0, 0.0);
+    const int* nbr = dp->nbr + (p ? 8LL * n0 : 0);
+    const S* lk = links_of<S>(*dp);
+    int jn[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) jn[d] = __ldg(nbr + d * n_out + i);
+    hop_one_r<0, S, C, R>(out, n0, p, i, n_out, n_in, jn[0], in_sys, act, lk);
+    hop_one_r<1, S, C, R>(out, n0, p, i, n_out, n_in, jn[1], in_sys, act, lk);
+    hop_one_r<2, S, C, R>(out, n0, p, i, n_out, n_in, jn[2], in_sys, act, lk);
+    hop_one_r<3, S, C, R>(out, n0, p, i, n_out, n_in, jn[3], in_sys, act, lk);
+    hop_one_r<4, S, C, R>(out, n0, p, i, n_out, n_in, jn[4], in_sys, act, lk);
+    hop_one_r<5, S, C, R>(out, n0, p, i, n_out, n_in, jn[5], in_sys, act, lk);
+    hop_one_r<6, S, C, R>(out, n0, p, i, n_out, n_in, jn[6], in_sys, act, lk);
+    hop_one_r<7, S, C, R>(out, n0, p, i, n_out, n_in, jn[7], in_sys, act, lk);
+    const T b = (T)a.b, a1 = (T)a.a1, a2 = (T)a.a2;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (!act[q]) continue;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) out[q][k] = cscale(out[q][k], b);
+      if (a.s1) {
+        C v[12];
+        ld_site<12>((const S*)a.s1 + oo[q], n_out, i, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          out[q][k].x = fma(a1, v[k].x, out[q][k].x);
+          out[q][k].y = fma(a1, v[k].y, out[q][k].y);
+        }
+      }
+      if (a.s2) {
+        C v[12];
+        ld_site<12>((const S*)a.s2 + oo[q], n_out, i, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          out[q][k].x = fma(a2, v[k].x, out[q][k].x);
+          out[q][k].y = fma(a2, v[k].y, out[q][k].y);
+        }
+      }
+      st_site<12>((S*)a.out + oo[q], n_out, i, out[q]);
+    }
+  }
+  if (!a.dotq && !a.dots) return;
+  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    if (!act[q]) continue;                       // uniform over the CTA
+    const long long my = (long long)item * bd.nrhs + g * R + q;
+    if (a.dotq) {
+      double v[2] = {0.0, 0.0};
+      T tt[2] = {0, 0};
+      if (live) {
+        C wv[12];
+        ld_site<12>((const S*)a.dotq + oo[q], n_out, i, wv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const C w = wv[k];
+          tt[0] = fma(w.x, out[q][k].x, fma(w.y, out[q][k].y, tt[0]));
+          tt[1] = fma(w.x, out[q][k].y, fma(-w.y, out[q][k].x, tt[1]));
+        }
+      }
+      block_reduce_t<T, 2>(tt, v, red);
+      if (threadIdx.x == 0) {
+        a.partial[2 * my] = v[0];
+        a.partial[2 * my + 1] = v[1];
+      }
+    }
+    if (a.dots) {
+      double v[3] = {0.0, 0.0, 0.0};
+      T tt[3] = {0, 0, 0};
+      if (live) {
+        C wv[12];
+        ld_site<12>((const S*)a.dots + oo[q], n_out, i, wv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const C w = wv[k];
+          tt[0] = fma(out[q][k].x, w.x, fma(out[q][k].y, w.y, tt[0]));
+          tt[1] = fma(out[q][k].x, w.y, fma(-out[q][k].y, w.x, tt[1]));
+          tt[2] = fma(out[q][k].x, out[q][k].x, fma(out[q][k].y, out[q][k].y, tt[2]));
+        }
+      }
+      block_reduce_t<T, 3>(tt, v, red);
+      if (threadIdx.x == 0) {
+        double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
+        P[2 * my] = v[0];
+        P[2 * my + 1] = v[1];
+        P[2 * (slot_stride + my)] = v[2];
+        P[2 * (slot_stride + my) + 1] = 0.0;
+      }
+    }
+  }
+}
+
+// Direction-split variant: 256 threads per 128-site work item; thread t works
+// on site t % 128 and on the forward (t < 128) or backward hops, so the eight
+// dependent load-compute phases of a site run as two parallel chains of four.
+// The two halves are summed through shared memory and the epilogue (self
+// terms, store, inner products) is shared: each half writes 6 components.
+template <class S>
+__device__ __forceinline__ void hop_unit_split(const BatchDev& bd, const HopArgs& a, long long t,
+                                               double* red, typename StoreTraits<S>::T* xs) {
+  typedef typename StoreTraits<S>::C C;
+  typedef typename StoreTraits<S>::T T;
+  const int p = a.p_out;
+  const int item = (int)(t / bd.nrhs);
+  const int r = (int)(t - (long long)item * bd.nrhs);
+  const int4 it = (p ? bd.items[1] : bd.items[0])[item];
+  const int sys = it.x * bd.nrhs + r;
+  if (a.active && !a.active[(long long)sys * a.active_stride]) return;
+  if (a.work_bytes && threadIdx.x == 0) atomicAdd(a.work_bytes, a.site_bytes * it.z);
+  const DomInst* dp = bd.inst_tab + bd.inst[it.x];
+  const int n0 = dp->n[0];
+  const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
+  const int s = threadIdx.x & (HOP_THREADS - 1);
+  const int half = threadIdx.x >> 7;
+  const int i = it.y + s;
+  const bool live = s < it.z;
+  const S* in_sys = (const S*)a.in + (p ? bd.off[0] : bd.off[1])[sys];
+  S* out_sys = (S*)a.out + (p ? bd.off[1] : bd.off[0])[sys];
+  C acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = cmk<C>(0.0, 0.0);
+  if (live) {
+    const int* nbr = dp->nbr + (p ? 8LL * n0 : 0);
+    const S* lk = links_of<S>(*dp);
+    if (half == 0) {
+      int jn[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) jn[d] = __ldg(nbr + d * n_out + i);
+      hop_one<0, S>(acc, n0, p, i, n_out, n_in, jn[0], in_sys, lk);
+      hop_one<1, S>(acc, n0, p, i, n_out, n_in, jn[1], in_sys, lk);
+      hop_one<2, S>(acc, n0, p, i, n_out, n_in, jn[2], in_sys, lk);
+      hop_one<3, S>(acc, n0, p, i, n_out, n_in, jn[3], in_sys, lk);
+    } else {
+      int jn[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) jn[d] = __ldg(nbr + (4 + d) * n_out + i);
+      hop_one<4, S>(acc, n0, p, i, n_out, n_in, jn[0], in_sys, lk);
+      hop_one<5, S>(acc, n0, p, i, n_out, n_in, jn[1], in_sys, lk);
+      hop_one<6, S>(acc, n0, p, i, n_out, n_in, jn[2], in_sys, lk);
+      hop_one<7, S>(acc, n0, p, i, n_out, n_in, jn[3], in_sys, lk);
+    }
+  }
+  // exchange: half h keeps components 6h..6h+5 and receives them from the other half
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int kk = half ? k : 6 + k;           // components the other half keeps
+    xs[(k * 2 + 0) * 2 * HOP_THREADS + half * HOP_THREADS + s] = acc[kk].x;
+    xs[(k * 2 + 1) * 2 * HOP_THREADS + half * HOP_THREADS + s] = acc[kk].y;
+  }
+  __syncthreads();
+  C out[6];
+  const int other = 1 - half;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int kk = half ? 6 + k : k;
+    C o = acc[kk];
+    o.x += xs[(k * 2 + 0) * 2 * HOP_THREADS + other * HOP_THREADS + s];
+    o.y += xs[(k * 2 + 1) * 2 * HOP_THREADS + other * HOP_THREADS + s];
+    out[k] = o;
+  }
+  const int q0 = 3 * half;                     // first pair of this half's components
+  if (live) {
+    const T b = (T)a.b;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k] = cscale(out[k], b);
+    if (a.s1) {
+      const S* s1 = (const S*)a.s1 + (p ? bd.off[1] : bd.off[0])[sys];
+      const T a1 = (T)a.a1;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        C v0, v1;
+        ld_pair(s1 + ((long long)(q0 + q) * n_out + i) * 2, v0, v1);
+        out[2 * q].x = fma(a1, v0.x, out[2 * q].x);
+        out[2 * q].y = fma(a1, v0.y, out[2 * q].y);
+        out[2 * q + 1].x = fma(a1, v1.x, out[2 * q + 1].x);
+        out[2 * q + 1].y = fma(a1, v1.y, out[2 * q + 1].y);
+      }
+    }
+    if (a.s2) {
+      const S* s2 = (const S*)a.s2 + (p ? bd.off[1] : bd.off[0])[sys];
+      const T a2 = (T)a.a2;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        C v0, v1;
+        ld_pair(s2 + ((long long)(q0 + q) * n_out + i) * 2, v0, v1);
+        out[2 * q].x = fma(a2, v0.x, out[2 * q].x);
+        out[2 * q].y = fma(a2, v0.y, out[2 * q].y);
+        out[2 * q + 1].x = fma(a2, v1.x, out[2 * q + 1].x);
+        out[2 * q + 1].y = fma(a2, v1.y, out[2 * q + 1].y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      st_pair(out_sys + ((long long)(q0 + q) * n_out + i) * 2, out[2 * q], out[2 * q + 1]);
+  }
+  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
+  const long long my = (long long)item * bd.nrhs + r;
+  if (a.dotq) {
+    double v[2] = {0.0, 0.0};
+    T tt[2] = {0, 0};
+    if (live) {
+      const S* qv = (const S*)a.dotq + (p ? bd.off[1] : bd.off[0])[sys];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        C w0, w1;
+        ld_pair(qv + ((long long)(q0 + q) * n_out + i) * 2, w0, w1);
+        const C w[2] = {w0, w1};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const C o = out[2 * q + e];
+          tt[0] = fma(w[e].x, o.x, fma(w[e].y, o.y, tt[0]));
+          tt[1] = fma(w[e].x, o.y, fma(-w[e].y, o.x, tt[1]));
+        }
+      }
+    }
+    block_reduce_t<T, 2>(tt, v, red);
+    if (threadIdx.x == 0) {
+      a.partial[2 * my] = v[0];
+      a.partial[2 * my + 1] = v[1];
+    }
+  }
+  if (a.dots) {
+    double v[3] = {0.0, 0.0, 0.0};
+    T tt[3] = {0, 0, 0};
+    if (live) {
+      const S* qv = (const S*)a.dots + (p ? bd.off[1] : bd.off[0])[sys];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        C w0, w1;
+        ld_pair(qv + ((long long)(q0 + q) * n_out + i) * 2, w0, w1);
+        const C w[2] = {w0, w1};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const C o = out[2 * q + e];
+          tt[0] = fma(o.x, w[e].x, fma(o.y, w[e].y, tt[0]));
+          tt[1] = fma(o.x, w[e].y, fma(-o.y, w[e].x, tt[1]));
+          tt[2] = fma(o.x, o.x, fma(o.y, o.y, tt[2]));
+        }
+      }
+    }
+    block_reduce_t<T, 3>(tt, v, red);
+    if (threadIdx.x == 0) {
+      double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
+      P[2 * my] = v[0];
+      P[2 * my + 1] = v[1];
+      P[2 * (slot_stride + my)] = v[2];
+      P[2 * (slot_stride + my) + 1] = 0.0;
+    }
+  }
+}
+
+template <class S, int MINB, bool PERSIST>
+__global__ void __launch_bounds__(2 * HOP_THREADS, MINB) k_hop_split(BatchDev bd, HopArgs a,
+                                                                      long long nunits) {
+  __shared__ double red[32 * 4];
+  __shared__ typename StoreTraits<S>::T xs[12 * 2 * HOP_THREADS];
+  if (PERSIST) {
+    for (long long t = blockIdx.x; t < nunits; t += gridDim.x) {
+      hop_unit_split<S>(bd, a, t, red, xs);
+      __syncthreads();
+    }
+  } else {
+    hop_unit_split<S>(bd, a, blockIdx.x, red, xs);
+  }
 }
 
 // Launch variants chosen by the autotuner: MINB = resident CTAs per SM asked
 // of the register allocator; PERSIST = a grid of (SMs x MINB) CTAs that walks
 // the work units with a stride (one launch of persistent CTAs over blocks of
 // any size) instead of one CTA per unit.
-template <class S, int MINB, bool PERSIST>
+template <class S, int MINB, bool PERSIST, int R>
 __global__ void __launch_bounds__(HOP_THREADS, MINB) k_hop(BatchDev bd, HopArgs a, long long nunits) {
   __shared__ double red[32 * 4];
   if (PERSIST) {
-    for (long long t = blockIdx.x; t < nunits; t += gridDim.x) hop_unit<S>(bd, a, t, red);
+    for (long long t = blockIdx.x; t < nunits; t += gridDim.x) {
+      if constexpr (R == 1) hop_unit<S>(bd, a, t, red);
+      else hop_unit_r<S, R>(bd, a, t, red);
+    }
   } else {
-    hop_unit<S>(bd, a, blockIdx.x, red);
+    if constexpr (R == 1) hop_unit<S>(bd, a, blockIdx.x, red);
+    else hop_unit_r<S, R>(bd, a, blockIdx.x, red);
   }
 }
 
 struct HopVariant {
   int minb;
   bool persist;
+  int r;          // rhs per thread (0: direction-split, 256 threads per item)
 };
 // per storage precision; index 0 is the default before tuning
-static const HopVariant kVariants64[] = {{3, false}, {2, false}, {3, true}};
-static const HopVariant kVariants32[] = {{6, false}, {4, false}, {8, false}, {6, true}, {4, true}};
-static const HopVariant kVariants16[] = {{5, false}, {4, false}, {8, false}, {5, true}};
+static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
+                                         {2, false, 0}};
+static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false, 1}, {6, true, 1},
+                                         {4, true, 1}, {4, false, 2}, {5, false, 2}, {4, true, 2},
+                                         {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
+                                         {3, true, 0}};
+static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
+                                         {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 3 : (prec == DD_F32 ? 5 : 4); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 13 : 8); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -194,32 +531,63 @@ static const HopVariant& variant_of(dd_prec prec, int v) {
   return t[v];
 }
 
-template <class S, int MINB, bool PERSIST>
-static void launch_variant(const BatchDev& bd, const HopArgs& a, long long nunits, int nsm,
+template <class S, int MINB, bool PERSIST, int R>
+static void launch_variant(const BatchDev& bd, const HopArgs& a, long long nitems_p, int nsm,
                            cudaStream_t s) {
+  const long long nunits = nitems_p * ((bd.nrhs + R - 1) / R);
   long long grid = nunits;
   if (PERSIST) grid = std::min<long long>(nunits, (long long)nsm * MINB);
-  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
+  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST, R><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
 }
 
-static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs& a, long long n,
+template <class S, int MINB, bool PERSIST>
+static void launch_split(const BatchDev& bd, const HopArgs& a, long long nitems_p, int nsm,
+                         cudaStream_t s) {
+  const long long nunits = nitems_p * bd.nrhs;
+  long long grid = nunits;
+  if (PERSIST) grid = std::min<long long>(nunits, (long long)nsm * MINB);
+  DD_COUNT_LAUNCH(), k_hop_split<S, MINB, PERSIST><<<(unsigned)grid, 2 * HOP_THREADS, 0, s>>>(bd, a, nunits);
+}
+
+static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs& a, long long ni,
                          int nsm, cudaStream_t s) {
+  if (prec == DD_DF64) {
+    launch_variant<df2s, 3, false, 1>(bd, a, ni, nsm, s);
+    return;
+  }
   const HopVariant& hv = variant_of(prec, v);
+  if (hv.r == 0) {
+    if (prec == DD_F64) launch_split<double2, 2, false>(bd, a, ni, nsm, s);
+    else if (prec == DD_F32 && hv.persist) launch_split<float2, 3, true>(bd, a, ni, nsm, s);
+    else if (prec == DD_F32 && hv.minb == 4) launch_split<float2, 4, false>(bd, a, ni, nsm, s);
+    else if (prec == DD_F32) launch_split<float2, 3, false>(bd, a, ni, nsm, s);
+    else if (hv.minb == 4) launch_split<__nv_bfloat162, 4, false>(bd, a, ni, nsm, s);
+    else launch_split<__nv_bfloat162, 3, false>(bd, a, ni, nsm, s);
+    return;
+  }
   if (prec == DD_F64) {
-    if (hv.persist) launch_variant<double2, 3, true>(bd, a, n, nsm, s);
-    else if (hv.minb == 2) launch_variant<double2, 2, false>(bd, a, n, nsm, s);
-    else launch_variant<double2, 3, false>(bd, a, n, nsm, s);
+    if (hv.r == 2) launch_variant<double2, 2, false, 2>(bd, a, ni, nsm, s);
+    else if (hv.persist) launch_variant<double2, 3, true, 1>(bd, a, ni, nsm, s);
+    else if (hv.minb == 2) launch_variant<double2, 2, false, 1>(bd, a, ni, nsm, s);
+    else launch_variant<double2, 3, false, 1>(bd, a, ni, nsm, s);
   } else if (prec == DD_F32) {
-    if (hv.persist && hv.minb == 4) launch_variant<float2, 4, true>(bd, a, n, nsm, s);
-    else if (hv.persist) launch_variant<float2, 6, true>(bd, a, n, nsm, s);
-    else if (hv.minb == 4) launch_variant<float2, 4, false>(bd, a, n, nsm, s);
-    else if (hv.minb == 8) launch_variant<float2, 8, false>(bd, a, n, nsm, s);
-    else launch_variant<float2, 6, false>(bd, a, n, nsm, s);
+    if (hv.r == 4) launch_variant<float2, 3, false, 4>(bd, a, ni, nsm, s);
+    else if (hv.r == 3) launch_variant<float2, 3, false, 3>(bd, a, ni, nsm, s);
+    else if (hv.r == 2 && hv.persist) launch_variant<float2, 4, true, 2>(bd, a, ni, nsm, s);
+    else if (hv.r == 2 && hv.minb == 5) launch_variant<float2, 5, false, 2>(bd, a, ni, nsm, s);
+    else if (hv.r == 2) launch_variant<float2, 4, false, 2>(bd, a, ni, nsm, s);
+    else if (hv.persist && hv.minb == 4) launch_variant<float2, 4, true, 1>(bd, a, ni, nsm, s);
+    else if (hv.persist) launch_variant<float2, 6, true, 1>(bd, a, ni, nsm, s);
+    else if (hv.minb == 4) launch_variant<float2, 4, false, 1>(bd, a, ni, nsm, s);
+    else if (hv.minb == 8) launch_variant<float2, 8, false, 1>(bd, a, ni, nsm, s);
+    else launch_variant<float2, 6, false, 1>(bd, a, ni, nsm, s);
   } else {
-    if (hv.persist) launch_variant<__nv_bfloat162, 5, true>(bd, a, n, nsm, s);
-    else if (hv.minb == 4) launch_variant<__nv_bfloat162, 4, false>(bd, a, n, nsm, s);
-    else if (hv.minb == 8) launch_variant<__nv_bfloat162, 8, false>(bd, a, n, nsm, s);
-    else launch_variant<__nv_bfloat162, 5, false>(bd, a, n, nsm, s);
+    if (hv.r == 3) launch_variant<__nv_bfloat162, 3, false, 3>(bd, a, ni, nsm, s);
+    else if (hv.r == 2) launch_variant<__nv_bfloat162, 4, false, 2>(bd, a, ni, nsm, s);
+    else if (hv.persist) launch_variant<__nv_bfloat162, 5, true, 1>(bd, a, ni, nsm, s);
+    else if (hv.minb == 4) launch_variant<__nv_bfloat162, 4, false, 1>(bd, a, ni, nsm, s);
+    else if (hv.minb == 8) launch_variant<__nv_bfloat162, 8, false, 1>(bd, a, ni, nsm, s);
+    else launch_variant<__nv_bfloat162, 5, false, 1>(bd, a, ni, nsm, s);
   }
 }
 
@@ -249,7 +617,7 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
     }
     cudaEventCreate(&rec.a);
     cudaEventCreate(&rec.b);
-    rec.which = prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2);
+    rec.which = (prec == DD_F64 || prec == DD_DF64) ? 0 : (prec == DD_F32 ? 1 : 2);
     rec.bytes = 0.0;
     a.work_bytes = c->d_tbytes + rec.which;
     a.site_bytes = hop_site_bytes(b, prec_bytes(prec), (a.s1 ? 1 : 0) + (a.s2 ? 1 : 0));
@@ -261,8 +629,9 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
     cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (c->nsm <= 0) c->nsm = 1;
   }
-  const int pi = prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2);
-  dispatch_hop(prec, b.hop_variant[pi], bd, a, nblk, c->nsm, s);
+  const int pi = (prec == DD_F64 || prec == DD_DF64) ? 0 : (prec == DD_F32 ? 1 : 2);
+  const int v = c->forced_variant[pi] >= 0 ? c->forced_variant[pi] : b.hop_variant[pi];
+  dispatch_hop(prec, v, bd, a, b.nitems[p], c->nsm, s);
   if (tm) {
     cudaEventRecord(rec.b, s);
     c->trec.push_back(rec);
@@ -286,12 +655,11 @@ __global__ void k_pack(BatchDev bd, int p, const double2* __restrict__ user, S* 
   const int np = p ? d.n[1] : d.n[0];
   const int f = d.fmap[(p ? d.n[0] : 0) + i];
   const double2* src = user + bd.uoff[sys] + 12LL * f;
-  S* dst = v + (p ? bd.off[1] : bd.off[0])[sys] + i;
+  S* dst = v + (p ? bd.off[1] : bd.off[0])[sys];
+  C w[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    double2 x = src[k];
-    stc(dst + (long long)k * np, cmk<C>(x.x, x.y));
-  }
+  for (int k = 0; k < 12; ++k) w[k] = cmk<C>(src[k].x, src[k].y);
+  st_site<12>(dst, np, i, w);
 }
 
 template <class S>
@@ -305,12 +673,11 @@ __global__ void k_unpack(BatchDev bd, int p, const S* __restrict__ v, double2* _
   const int np = p ? d.n[1] : d.n[0];
   const int f = d.fmap[(p ? d.n[0] : 0) + i];
   double2* dst = user + bd.uoff[sys] + 12LL * f;
-  const S* src = v + (p ? bd.off[1] : bd.off[0])[sys] + i;
+  const S* src = v + (p ? bd.off[1] : bd.off[0])[sys];
+  typename StoreTraits<S>::C w[12];
+  ld_site<12>(src, np, i, w);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    auto x = ldc(src + (long long)k * np);
-    dst[k] = make_double2((double)x.x, (double)x.y);
-  }
+  for (int k = 0; k < 12; ++k) dst[k] = to_d2(w[k]);
 }
 
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
@@ -322,7 +689,8 @@ dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, v
     if (b.nitems[p] == 0) continue;
     dim3 grid(b.nitems[p], b.nrhs);
     void* v = p ? vo : ve;
-    if (prec == DD_F64) DD_COUNT_LAUNCH(), k_pack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (double2*)v);
+    if (prec == DD_DF64) DD_COUNT_LAUNCH(), k_pack<df2s><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (df2s*)v);
+    else if (prec == DD_F64) DD_COUNT_LAUNCH(), k_pack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (double2*)v);
     else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_pack<float2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (float2*)v);
     else DD_COUNT_LAUNCH(), k_pack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (__nv_bfloat162*)v);
   }
@@ -339,7 +707,8 @@ dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* v
     if (b.nitems[p] == 0) continue;
     dim3 grid(b.nitems[p], b.nrhs);
     const void* v = p ? vo : ve;
-    if (prec == DD_F64) DD_COUNT_LAUNCH(), k_unpack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)v, (double2*)user);
+    if (prec == DD_DF64) DD_COUNT_LAUNCH(), k_unpack<df2s><<<grid, 128, 0, s>>>(bd, p, (const df2s*)v, (double2*)user);
+    else if (prec == DD_F64) DD_COUNT_LAUNCH(), k_unpack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)v, (double2*)user);
     else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_unpack<float2><<<grid, 128, 0, s>>>(bd, p, (const float2*)v, (double2*)user);
     else DD_COUNT_LAUNCH(), k_unpack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const __nv_bfloat162*)v, (double2*)user);
   }
@@ -348,3 +717,16 @@ dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* v
 }
 
 }  // namespace dd
+
+extern "C" {
+
+int dd_hop_variants(dd_prec prec) { return dd::hop_variant_count(prec); }
+
+dd_status dd_set_hop_variant(dd_ctx* c, dd_prec prec, int v) {
+  if (!c || (prec != DD_F64 && prec != DD_F32 && prec != DD_BF16)) return DD_EINVAL;
+  if (v < -1 || v >= dd::hop_variant_count(prec)) return dd::fail(c, DD_EINVAL, "variant out of range");
+  c->forced_variant[prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2)] = v;
+  return DD_OK;
+}
+
+}  // extern "C"

@@ -39,7 +39,8 @@ class SolveParams(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("systems", C.c_int), ("converged", C.c_int), ("max_iters", C.c_int),
-                ("outer_cycles", C.c_int), ("max_relres", C.c_double), ("seconds", C.c_double)]
+                ("outer_cycles", C.c_int), ("max_relres", C.c_double), ("seconds", C.c_double),
+                ("hop_variant", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +92,8 @@ def lib():
             "dd_net_train": [vp, vp, ip, C.c_int, C.c_int, vp, C.POINTER(TrainParams),
                              C.POINTER(TrainStats), vp],
             "dd_set_net": [vp, vp],
+            "dd_set_hop_variant": [vp, C.c_int, C.c_int],
+            "dd_hop_variants": [C.c_int],
             "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -109,6 +112,7 @@ def exported_symbols():
             "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count", "dd_logdet_check",
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net",
+            "dd_set_hop_variant", "dd_hop_variants",
             "dd_apply_D_block_noalloc"]
 
 
@@ -308,6 +312,10 @@ class Context:
         d["logabs_omega"] = lo
         d["logabs_phi"] = lp
         return d
+
+    def set_hop_variant(self, prec, v):
+        p = PREC[prec] if isinstance(prec, str) else prec
+        self._check(lib().dd_set_hop_variant(self._h, p, v))
 
     def last_solve_stats(self):
         st = SolveStats()

@@ -91,7 +91,7 @@ def test_action_with_graph_and_autotune_matches_plain_call():
     b = ctx.multiboson_action(u, vec, dd4d.params(1e-10, inner_prec="f32", graph=True,
                                                    autotune=True))
     assert a[3] == b[3] == 0
-    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    assert abs(a[0] - b[0]) <= 1e-10 * a[0] and np.allclose(a[1], b[1], rtol=1e-9)
     S0, Sb0, Sr0 = Oracle(U, 0.13, geo).multiboson_action(u, chis)
     assert abs(b[0] - S0) <= 1e-9 * S0
 
