@@ -299,11 +299,16 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     achieved = hop32_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
+    # stored ncu traffic counts only for the launch variant they were taken on
     tr = traffic_record()
+    hv = stats["hop_variant"]
+    if tr and tr.get("variant_name") != dd4d.hop_variant_name("f32", hv):
+        tr = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": tr.get("bytes_per_launch") if tr else None,
-                "kernel": "k_hop<float2> (FP32 even-odd hop inside the inner BiCGstab)",
+                "kernel": "FP32 even-odd hop inside the inner BiCGstab, autotuned variant %d: %s"
+                          % (hv, dd4d.hop_variant_name("f32", hv)),
                 "peak_kind": peak_kind, "launches": hop32_n,
                 "avg_launch_ms": hop32_ms / hop32_n if hop32_n else None,
                 "algorithmic_bytes_per_launch": hop32_bytes / hop32_n if hop32_n else None}

@@ -179,10 +179,14 @@ dd_status dd_solve_blocks(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
 
 /* Manual choice of the stencil launch variant (0 .. dd_hop_variants(prec)-1)
  * for every batch used afterwards on the context, overriding the autotuner;
- * v = -1 returns to the defaults.  Variants differ only in launch shape
- * (resident CTAs per SM, persistent grid, rhs per thread), not in arithmetic. */
+ * v = -1 returns to the defaults.  Variants differ in launch shape (resident
+ * CTAs per SM, persistent grid, rhs per thread, direction split, links staged
+ * in shared memory by bulk copy), not in the per-site arithmetic; the fused
+ * inner products may sum in a different order.  dd_hop_variant_name returns
+ * a static description of variant v (NULL if out of range). */
 dd_status dd_set_hop_variant(dd_ctx* ctx, dd_prec prec, int v);
 int dd_hop_variants(dd_prec prec);
+const char* dd_hop_variant_name(dd_prec prec, int v);
 
 /* Statistics of the last batched solve run on the context (by any call,
  * including the block and frame solves inside dd_apply_w). */

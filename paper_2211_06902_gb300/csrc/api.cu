@@ -124,7 +124,10 @@ dd_status dd_apply_D_block(dd_ctx* c, dd_domain kind, const int* ids, int nblk, 
   g.p_out = 1; g.in = ve; g.out = oo; g.s1 = vo; g.a1 = 1.0; g.b = -c->kappa;
   if ((e = launch_hop(c, *b, prec, g, s)) != DD_OK) return e;
   if ((e = launch_unpack(c, *b, oe, oo, sg.out, prec, s)) != DD_OK) return e;
-  return unstage(c, out, ub, sg, s);
+  if ((e = unstage(c, out, ub, sg, s)) != DD_OK) return e;
+  // host buffers: the call has synchronised anyway, so report a bounded wait
+  // that gave up (device buffers leave it to the next synchronous call)
+  return (sg.in_host || sg.out_host) ? check_device_error(c, s) : DD_OK;
 }
 
 dd_status dd_solve_blocks(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs,

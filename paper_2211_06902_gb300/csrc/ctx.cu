@@ -146,7 +146,10 @@ void free_instance(Instance& in) {
   dfree(in.link32_buf);
   dfree(in.link16_buf);
   dfree(in.linkdf_buf);
+  dfree(in.lb32_buf);
+  dfree(in.lb16_buf);
   in.glob_buf = in.link64_buf = in.link32_buf = in.link16_buf = in.linkdf_buf = nullptr;
+  in.lb32_buf = in.lb16_buf = nullptr;
   in.nbr_buf.reset();
   in.fmap_buf.reset();
   in.lex_buf.reset();
@@ -290,6 +293,43 @@ __global__ void k_gather_links(const int* __restrict__ glob, int n0, int n1,
   out[link_block(p, mu, n0, np) + cidx(c, np, i)] = to_store<S>(U[(long long)g * 36 + comp]);
 }
 
+// per-chunk link bundles (layout in spinor.cuh) from the instance's gathered
+// links: one thread per (quarter, direction, lane)
+template <class S>
+__global__ void k_build_bundle(DomInst d, const S* __restrict__ lk, unsigned char* __restrict__ out,
+                               long long nquarters) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= nquarters * 8 * LB_LANES) return;
+  const int lane = (int)(k % LB_LANES);
+  const int dir = (int)((k / LB_LANES) % 8);
+  const long long qg = k / (8 * LB_LANES);
+  const int n0 = d.n[0];
+  const long long q1 = lb_quarter_base(1, n0);
+  const int p = qg < q1 ? 0 : 1;
+  const long long i = (qg - (p ? q1 : 0)) * LB_LANES + lane;
+  const int n_out = d.n[p], n_in = d.n[1 - p];
+  const int mu = dir & 3;
+  unsigned char* qb = out + qg * lb_quarter_bytes<S>();
+  S* lo = reinterpret_cast<S*>(qb);
+  int* io = reinterpret_cast<int*>(qb + lb_link_bytes<S>());
+  const int j = i < n_out ? d.nbr[(p ? 8LL * n0 : 0) + (long long)dir * n_out + i] : -1;
+  io[dir * LB_LANES + lane] = j;
+  S zero;
+  memset(&zero, 0, sizeof(S));
+  for (int e = 0; e < 5; ++e) {
+    S* dst = lo + ((long long)(dir * 5 + e) * LB_LANES + lane) * 2;
+    if (j < 0) {
+      dst[0] = zero;
+      dst[1] = zero;
+      continue;
+    }
+    const S* src = dir < 4 ? lk + link_block(p, mu, n0, n_out) + ((long long)e * n_out + i) * 2
+                           : lk + link_block(1 - p, mu, n0, n_in) + ((long long)e * n_in + j) * 2;
+    dst[0] = src[0];
+    dst[1] = src[1];
+  }
+}
+
 __global__ void k_fold_time_sign(double2* U, int V, int L0, int spatial, int sign) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= (long long)spatial * 9) return;
@@ -312,7 +352,12 @@ dd_status ensure_links(dd_ctx* c, int i, dd_prec prec) {
     dfree(in.link32_buf);
     dfree(in.link16_buf);
     dfree(in.linkdf_buf);
+    dfree(in.lb32_buf);
+    dfree(in.lb16_buf);
     in.link64_buf = in.link32_buf = in.link16_buf = in.linkdf_buf = nullptr;
+    in.lb32_buf = in.lb16_buf = nullptr;
+    in.d.lb32 = nullptr;
+    in.d.lb16 = nullptr;
     in.d.link64 = nullptr;
     in.d.link32 = nullptr;
     in.d.link16 = nullptr;
@@ -336,12 +381,43 @@ dd_status ensure_links(dd_ctx* c, int i, dd_prec prec) {
   else
     DD_COUNT_LAUNCH(), k_gather_links<df2s><<<nb, th>>>(in.d.glob, in.d.n[0], in.d.n[1], c->d_U, (df2s*)*buf);
   DD_CUDA(c, cudaGetLastError());
+  // FP32 and BF16 links also get the per-chunk bundles of the bundle hop
+  if (prec == DD_F32 || prec == DD_BF16) {
+    const long long nq = lb_quarter_base(1, in.d.n[0]) +
+                         (long long)LB_QUARTERS * ((in.d.n[1] + LB_CHUNK - 1) / LB_CHUNK);
+    void** lb = prec == DD_F32 ? &in.lb32_buf : &in.lb16_buf;
+    const size_t qbytes = prec == DD_F32 ? lb_quarter_bytes<float2>() : lb_quarter_bytes<__nv_bfloat162>();
+    if ((st = dalloc(c, lb, std::max<size_t>(1, nq) * qbytes)) != DD_OK) return st;
+    const long long tq = nq * 8 * LB_LANES;
+    if (tq > 0) {
+      if (prec == DD_F32)
+        DD_COUNT_LAUNCH(), k_build_bundle<float2><<<(tq + th - 1) / th, th>>>(in.d, (const float2*)*buf,
+                                                                             (unsigned char*)*lb, nq);
+      else
+        DD_COUNT_LAUNCH(), k_build_bundle<__nv_bfloat162><<<(tq + th - 1) / th, th>>>(
+            in.d, (const __nv_bfloat162*)*buf, (unsigned char*)*lb, nq);
+    }
+    DD_CUDA(c, cudaGetLastError());
+    hop_bundle_prepare();
+  }
   in.d.link64 = (const double2*)in.link64_buf;
   in.d.link32 = (const float2*)in.link32_buf;
   in.d.link16 = (const __nv_bfloat162*)in.link16_buf;
   in.d.linkdf = (const df2s*)in.linkdf_buf;
+  in.d.lb32 = (const unsigned char*)in.lb32_buf;
+  in.d.lb16 = (const unsigned char*)in.lb16_buf;
   c->inst_dirty = true;
   return DD_OK;
+}
+
+dd_status check_device_error(dd_ctx* c, cudaStream_t s) {
+  int h = 0;
+  DD_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  if (!h) return DD_OK;
+  DD_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  return fail(c, DD_ETIMEOUT, "a bounded device-side wait gave up (bulk copy of a link bundle)");
 }
 
 dd_status instance_of(dd_ctx* c, dd_domain kind, int id, int* out) {
@@ -510,7 +586,12 @@ dd_status dd_create(dd_ctx** out, const int L[4], int time_bc, double kappa) {
   c->kappa = kappa;
   cudaGetDevice(&c->device);
   dd_status st = dalloc(c, (void**)&c->d_U, sizeof(double2) * 36ULL * V);
+  if (st == DD_OK && (st = dalloc(c, (void**)&c->d_err, sizeof(int))) == DD_OK &&
+      cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
+    st = DD_ECUDA;
   if (st != DD_OK) {
+    dfree(c->d_U);
+    dfree(c->d_err);
     delete c;
     return st;
   }
@@ -536,6 +617,7 @@ dd_status dd_destroy(dd_ctx* c) {
   dfree(c->d_dpi_pos);
   dfree(c->d_dpi_kind);
   dfree(c->d_tbytes);
+  dfree(c->d_err);
   free_workspace(c);
   free_plan(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);

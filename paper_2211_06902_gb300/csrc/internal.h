@@ -47,6 +47,8 @@ struct DomInst {            // device-visible descriptor (plain data)
   const float2* link32;
   const __nv_bfloat162* link16;
   const df2s* linkdf;       // double-float copy (residual of the mixed solver)
+  const unsigned char* lb32;  // per-chunk link bundles (FP32 / BF16), see spinor.cuh
+  const unsigned char* lb16;
 };
 
 // Owning host record of an instance.
@@ -59,6 +61,8 @@ struct Instance {
   void* link32_buf = nullptr;
   void* link16_buf = nullptr;
   void* linkdf_buf = nullptr;
+  void* lb32_buf = nullptr;
+  void* lb16_buf = nullptr;
   std::vector<int> h_glob;      // host copy [p][n_p]
   std::vector<int> h_fmap;      // host copy [p][n_p]
   bool links_ready = false;
@@ -148,6 +152,7 @@ struct dd_ctx {
   long long t_n[3] = {0, 0, 0};
   double t_bytes[3] = {0, 0, 0};
   double* d_tbytes = nullptr;     // device accumulators of algorithmic bytes [3]
+  int* d_err = nullptr;           // device error word, set by kernels whose bounded waits give up
   // work space (krylov.cu) and cached batches
   void* scratch = nullptr;
   std::map<std::string, std::unique_ptr<dd::Batch>> batches;
@@ -202,9 +207,14 @@ struct HopArgs {
   int active_stride;
   double* work_bytes;       // timing only: algorithmic bytes of the CTAs that ran
   double site_bytes;        // algorithmic bytes per output (site, rhs)
+  int* err;                 // device error word (bounded waits that gave up)
 };
 dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s);
 int hop_variant_count(dd_prec prec);
+// sets the shared-memory attributes of the bundle kernels on the current device
+void hop_bundle_prepare();
+// reads and clears the device error word: DD_ETIMEOUT if a bounded wait gave up
+dd_status check_device_error(dd_ctx* c, cudaStream_t s);
 
 // layout conversions (stencil.cu)
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,

@@ -841,6 +841,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   DD_CUDA(c, cudaMemcpyAsync(rel.data(), vrel, sizeof(double) * nsys, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaMemcpyAsync(hst.data(), st, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
+  if ((e = check_device_error(c, s)) != DD_OK) return e;
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventDestroy(ev0);

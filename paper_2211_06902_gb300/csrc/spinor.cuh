@@ -113,6 +113,28 @@ __device__ __host__ __forceinline__ long long link_block(int p, int mu, long lon
   return (p ? 40 * n0 : 0) + (long long)mu * 10 * np;
 }
 
+// ---- per-chunk link bundles -------------------------------------------------------
+// For the bundle form of the hop, each output parity of an instance is cut
+// into chunks of LB_CHUNK sites (the batch work items) and each chunk into
+// LB_QUARTERS quarters of LB_LANES sites.  A quarter's bundle holds, for its
+// 32 output sites, the 8 links the hop multiplies with (forward: U_mu(x);
+// backward: U_mu(x - mu), stored undaggered) and the 8 neighbour indices:
+//     links [dir 8][pair 5][lane 32] x (2 S)   then   index [dir 8][lane 32] int
+// so one bulk copy brings a quarter into shared memory, and lanes read
+// consecutive 16-byte (FP32) or 8-byte (BF16) words.  Missing neighbours have
+// index -1 and zero links; lanes past the end of the parity likewise.
+constexpr int LB_LANES = 32;
+constexpr int LB_QUARTERS = 4;
+constexpr int LB_CHUNK = LB_LANES * LB_QUARTERS;
+template <class S>
+__device__ __host__ constexpr int lb_link_bytes() { return 8 * 5 * LB_LANES * 2 * (int)sizeof(S); }
+template <class S>
+__device__ __host__ constexpr int lb_quarter_bytes() { return lb_link_bytes<S>() + 8 * LB_LANES * 4; }
+// number of quarters of parity p of an instance with n[0], n[1] sites
+__device__ __host__ __forceinline__ long long lb_quarter_base(int p, int n0) {
+  return p ? (long long)LB_QUARTERS * ((n0 + LB_CHUNK - 1) / LB_CHUNK) : 0;
+}
+
 // ---- complex helpers ------------------------------------------------------------
 template <class C> __device__ __forceinline__ C cmk(double re, double im);
 template <> __device__ __forceinline__ double2 cmk<double2>(double re, double im) {

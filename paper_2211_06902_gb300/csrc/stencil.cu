@@ -508,10 +508,274 @@ __global__ void __launch_bounds__(HOP_THREADS, MINB) k_hop(BatchDev bd, HopArgs 
   }
 }
 
+// ---- bundle form: links and neighbour indices by bulk copy ----------------------
+// One CTA per (128-site chunk, group of up to LB_MAX_RHS rhs), one warp per rhs,
+// each lane one site of each of the chunk's four 32-site quarters.  Thread 0
+// starts four bulk copies (cp.async.bulk, completion counted in bytes on one
+// mbarrier per quarter) of the quarters' link bundles into shared memory; the
+// warps then read links and neighbour indices from shared memory, so all rhs
+// of the chunk share one copy and the only per-thread global loads left are
+// the neighbour spinors.  Waits are bounded: a wait that gives up sets *a.err
+// and the quarter is skipped (the host turns the flag into DD_ETIMEOUT).
+constexpr int LB_MAX_RHS = 12;
+constexpr unsigned LB_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase 0 of a once-used barrier
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
+  for (unsigned k = 0; k < LB_WAIT_LIMIT; ++k)
+    if (mbar_try_wait(bar, 0)) return true;
+  return false;
+}
+
+// plain loads of a link from a shared-memory bundle (lane's column)
+__device__ __forceinline__ void lds_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void lds_pair(const __nv_bfloat162* p, float2& a, float2& b) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  __nv_bfloat162 x, y;
+  memcpy(&x, &v.x, 4);
+  memcpy(&y, &v.y, 4);
+  a = __bfloat1622float2(x);
+  b = __bfloat1622float2(y);
+}
+__device__ __forceinline__ float2 lds_c(const float2* p) { return *p; }
+__device__ __forceinline__ float2 lds_c(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+
+template <class S, class C>
+__device__ __forceinline__ void lds_link(const S* dirblk, int lane, C (&U)[9]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) lds_pair(dirblk + (e * LB_LANES + lane) * 2, U[2 * e], U[2 * e + 1]);
+  U[8] = lds_c(dirblk + (4 * LB_LANES + lane) * 2);
+}
+
+template <int DIR, class S, class C>
+__device__ __forceinline__ void hop_one_lb(C (&acc)[12], int j, int n_in, const S* __restrict__ in_sys,
+                                           const S* qlinks, int lane) {
+  constexpr int MU = DIR & 3;
+  constexpr bool FWD = DIR < 4;
+  if (j < 0) return;
+  C psi[12];
+  ld_site<12>(in_sys, n_in, j, psi);
+  C U[9];
+  lds_link(qlinks + DIR * 5 * LB_LANES * 2, lane, U);
+  hop_dir<MU, FWD>(acc, psi, U);
+}
+
+template <class S>
+__device__ __forceinline__ const unsigned char* bundle_of(const DomInst& d);
+template <>
+__device__ __forceinline__ const unsigned char* bundle_of<float2>(const DomInst& d) { return d.lb32; }
+template <>
+__device__ __forceinline__ const unsigned char* bundle_of<__nv_bfloat162>(const DomInst& d) {
+  return d.lb16;
+}
+
+template <class S>
+constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64; }
+
+// grid: nitems[p] * ngroups CTAs (group fastest), 32 * rb threads
+template <class S, int MINB>
+__global__ void __launch_bounds__(32 * LB_MAX_RHS, MINB)
+    k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
+  typedef typename StoreTraits<S>::C C;
+  typedef typename StoreTraits<S>::T T;
+  constexpr int QB = lb_quarter_bytes<S>();
+  extern __shared__ __align__(128) unsigned char lb_smem[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + LB_QUARTERS * QB);
+  const int p = a.p_out;
+  const int item = (int)(blockIdx.x / ngroups);
+  const int g = (int)(blockIdx.x - (long long)item * ngroups);
+  const int4 it = (p ? bd.items[1] : bd.items[0])[item];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = g * rb + w;
+  const int sys = it.x * bd.nrhs + r;
+  const bool act = r < bd.nrhs && (!a.active || a.active[(long long)sys * a.active_stride]);
+  if (!__syncthreads_or(act)) return;          // every rhs of the group has converged
+  const DomInst* dp = bd.inst_tab + bd.inst[it.x];
+  const int n0 = dp->n[0];
+  const int nq = (it.z + LB_LANES - 1) / LB_LANES;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nq; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned char* src =
+        bundle_of<S>(*dp) + (lb_quarter_base(p, n0) + (long long)LB_QUARTERS * (it.y / LB_CHUNK)) * QB;
+    for (int q = 0; q < nq; ++q) {
+      mbar_expect_tx(&bar[q], QB);
+      bulk_copy_g2s(lb_smem + q * QB, src + (long long)q * QB, QB, &bar[q]);
+    }
+  }
+  if (!act) {
+    // idle warp of a busy CTA: thread 0 still sees its copies land before leaving
+    if (threadIdx.x == 0)
+      for (int q = 0; q < nq; ++q)
+        if (!mbar_wait0(&bar[q])) atomicExch(a.err, 1);
+    return;
+  }
+  if (a.work_bytes && lane == 0) atomicAdd(a.work_bytes, a.site_bytes * it.z);
+  const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
+  const S* in_sys = (const S*)a.in + (p ? bd.off[0] : bd.off[1])[sys];
+  S* out_sys = (S*)a.out + (p ? bd.off[1] : bd.off[0])[sys];
+  const long long oo = (p ? bd.off[1] : bd.off[0])[sys];
+  const auto bsc = mkscal<C>(a.b);
+  const auto a1 = mkscal<C>(a.a1);
+  const auto a2 = mkscal<C>(a.a2);
+  T tq[2] = {0, 0};
+  T ts[3] = {0, 0, 0};
+  for (int q = 0; q < nq; ++q) {
+    if (!mbar_wait0(&bar[q])) {
+      if (lane == 0) atomicExch(a.err, 1);
+      continue;
+    }
+    const int li = q * LB_LANES + lane;
+    if (li >= it.z) continue;
+    const int i = it.y + li;
+    const unsigned char* qb = lb_smem + q * QB;
+    const S* ql = reinterpret_cast<const S*>(qb);
+    const int* qi = reinterpret_cast<const int*>(qb + lb_link_bytes<S>());
+    int jn[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) jn[d] = qi[d * LB_LANES + lane];
+    C acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = cmk<C>(0.0, 0.0);
+    hop_one_lb<0, S>(acc, jn[0], n_in, in_sys, ql, lane);
+    hop_one_lb<1, S>(acc, jn[1], n_in, in_sys, ql, lane);
+    hop_one_lb<2, S>(acc, jn[2], n_in, in_sys, ql, lane);
+    hop_one_lb<3, S>(acc, jn[3], n_in, in_sys, ql, lane);
+    hop_one_lb<4, S>(acc, jn[4], n_in, in_sys, ql, lane);
+    hop_one_lb<5, S>(acc, jn[5], n_in, in_sys, ql, lane);
+    hop_one_lb<6, S>(acc, jn[6], n_in, in_sys, ql, lane);
+    hop_one_lb<7, S>(acc, jn[7], n_in, in_sys, ql, lane);
+    C out[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = scale(acc[k], bsc);
+    if (a.s1) {
+      C v[12];
+      ld_site<12>((const S*)a.s1 + oo, n_out, i, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) axpy(out[k], a1, v[k]);
+    }
+    if (a.s2) {
+      C v[12];
+      ld_site<12>((const S*)a.s2 + oo, n_out, i, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) axpy(out[k], a2, v[k]);
+    }
+    st_site<12>(out_sys, n_out, i, out);
+    if (a.dotq) {
+      C wv[12];
+      ld_site<12>((const S*)a.dotq + oo, n_out, i, wv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        tq[0] = fma(wv[k].x, out[k].x, fma(wv[k].y, out[k].y, tq[0]));
+        tq[1] = fma(wv[k].x, out[k].y, fma(-wv[k].y, out[k].x, tq[1]));
+      }
+    }
+    if (a.dots) {
+      C wv[12];
+      ld_site<12>((const S*)a.dots + oo, n_out, i, wv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        ts[0] = fma(out[k].x, wv[k].x, fma(out[k].y, wv[k].y, ts[0]));
+        ts[1] = fma(out[k].x, wv[k].y, fma(-out[k].y, wv[k].x, ts[1]));
+        ts[2] = fma(out[k].x, out[k].x, fma(out[k].y, out[k].y, ts[2]));
+      }
+    }
+  }
+  // per-warp (= per-system) partial sums of the chunk
+  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
+  const long long my = (long long)item * bd.nrhs + r;
+  if (a.dotq) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tq[k] += __shfl_down_sync(0xffffffffu, tq[k], o);
+    if (lane == 0) {
+      a.partial[2 * my] = (double)tq[0];
+      a.partial[2 * my + 1] = (double)tq[1];
+    }
+  }
+  if (a.dots) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ts[k] += __shfl_down_sync(0xffffffffu, ts[k], o);
+    if (lane == 0) {
+      double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
+      P[2 * my] = (double)ts[0];
+      P[2 * my + 1] = (double)ts[1];
+      P[2 * (slot_stride + my)] = (double)ts[2];
+      P[2 * (slot_stride + my) + 1] = 0.0;
+    }
+  }
+}
+
+template <class S, int MINB>
+static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
+  const int ngroups = (bd.nrhs + LB_MAX_RHS - 1) / LB_MAX_RHS;
+  const int rb = (bd.nrhs + ngroups - 1) / ngroups;
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB><<<(unsigned)(nitems_p * ngroups), 32 * rb, lb_smem_bytes<S>(), s>>>(
+      bd, a, ngroups, rb);
+}
+
+void hop_bundle_prepare() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_hop_lb<float2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       lb_smem_bytes<float2>());
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       lb_smem_bytes<__nv_bfloat162>());
+  cudaFuncSetAttribute(k_hop_lb<float2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       lb_smem_bytes<float2>());
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       lb_smem_bytes<__nv_bfloat162>());
+  done[dev] = true;
+}
+
 struct HopVariant {
   int minb;
   bool persist;
-  int r;          // rhs per thread (0: direction-split, 256 threads per item)
+  int r;          // rhs per thread (0: direction-split, 256 threads per item; -1: bundle form)
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -519,11 +783,12 @@ static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true,
 static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false, 1}, {6, true, 1},
                                          {4, true, 1}, {4, false, 2}, {5, false, 2}, {4, true, 2},
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
-                                         {3, true, 0}};
+                                         {3, true, 0}, {2, false, -1}, {1, false, -1}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
-                                         {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0}};
+                                         {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
+                                         {2, false, -1}, {1, false, -1}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 13 : 8); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 15 : 10); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -556,6 +821,13 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
     return;
   }
   const HopVariant& hv = variant_of(prec, v);
+  if (hv.r < 0) {
+    if (prec == DD_F32 && hv.minb == 1) launch_lb<float2, 1>(bd, a, ni, s);
+    else if (prec == DD_F32) launch_lb<float2, 2>(bd, a, ni, s);
+    else if (hv.minb == 1) launch_lb<__nv_bfloat162, 1>(bd, a, ni, s);
+    else launch_lb<__nv_bfloat162, 2>(bd, a, ni, s);
+    return;
+  }
   if (hv.r == 0) {
     if (prec == DD_F64) launch_split<double2, 2, false>(bd, a, ni, nsm, s);
     else if (prec == DD_F32 && hv.persist) launch_split<float2, 3, true>(bd, a, ni, nsm, s);
@@ -604,6 +876,7 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
   if (st != DD_OK) return st;
   BatchDev bd = batch_view(c, b);
   HopArgs a = a0;
+  a.err = c->d_err;
   int p = a.p_out;
   if (b.nitems[p] == 0) return DD_OK;
   const long long nblk = (long long)b.nitems[p] * b.nrhs;
@@ -721,6 +994,32 @@ dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* v
 extern "C" {
 
 int dd_hop_variants(dd_prec prec) { return dd::hop_variant_count(prec); }
+
+const char* dd_hop_variant_name(dd_prec prec, int v) {
+  if (prec != DD_F64 && prec != DD_F32 && prec != DD_BF16) return nullptr;
+  if (v < 0 || v >= dd::hop_variant_count(prec)) return nullptr;
+  static char names[3][16][112];
+  static bool made = false;
+  if (!made) {
+    const dd_prec ps[3] = {DD_F64, DD_F32, DD_BF16};
+    const char* ty[3] = {"double2", "float2", "bfloat162"};
+    for (int k = 0; k < 3; ++k)
+      for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 16; ++u) {
+        const dd::HopVariant& h = dd::variant_of(ps[k], u);
+        if (h.r < 0)
+          snprintf(names[k][u], sizeof names[k][u],
+                   "k_hop_lb<%s,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA", ty[k], h.minb);
+        else if (h.r == 0)
+          snprintf(names[k][u], sizeof names[k][u], "k_hop_split<%s,%d,%s>: forward/backward split",
+                   ty[k], h.minb, h.persist ? "persistent" : "grid");
+        else
+          snprintf(names[k][u], sizeof names[k][u], "k_hop<%s,%d,%s,%d>: %d rhs per thread", ty[k], h.minb,
+                   h.persist ? "persistent" : "grid", h.r, h.r);
+      }
+    made = true;
+  }
+  return names[prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2)][v];
+}
 
 dd_status dd_set_hop_variant(dd_ctx* c, dd_prec prec, int v) {
   if (!c || (prec != DD_F64 && prec != DD_F32 && prec != DD_BF16)) return DD_EINVAL;

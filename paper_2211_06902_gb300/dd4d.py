@@ -94,12 +94,14 @@ def lib():
             "dd_set_net": [vp, vp],
             "dd_set_hop_variant": [vp, C.c_int, C.c_int],
             "dd_hop_variants": [C.c_int],
+            "dd_hop_variant_name": [C.c_int, C.c_int],
             "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = C.c_char_p if name in ("dd_strerror", "dd_last_error") else C.c_int
+            f.restype = (C.c_char_p if name in ("dd_strerror", "dd_last_error", "dd_hop_variant_name")
+                         else C.c_int)
         _lib = L
     return _lib
 
@@ -112,8 +114,14 @@ def exported_symbols():
             "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count", "dd_logdet_check",
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net",
-            "dd_set_hop_variant", "dd_hop_variants",
+            "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc"]
+
+
+def hop_variant_name(prec, v):
+    """Description of stencil launch variant v at precision prec (None if out of range)."""
+    r = lib().dd_hop_variant_name(PREC[prec] if isinstance(prec, str) else prec, v)
+    return r.decode() if r else None
 
 
 def _ptr(x):

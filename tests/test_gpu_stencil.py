@@ -120,3 +120,38 @@ def test_invalid_arguments(case1):
         ctx.apply_D_block("omega", [99], 1, x, x, "f64")
     with pytest.raises(dd4d.DDError):
         ctx.apply_D_block("full", None, 0, x, x, "f64")
+
+
+@pytest.mark.parametrize("prec,nrhs", [("f64", 3), ("f32", 13), ("bf16", 13)])
+def test_every_hop_variant(prec, nrhs):
+    """Every compiled launch form of the hop (thread per site, several rhs per
+    thread, direction split, shared-memory link bundles by bulk copy) against
+    the oracle: uneven blocks whose parities end in ragged chunks and quarters,
+    the frame Lambda1 (not a box), and 13 rhs, which the bundle form splits
+    into two groups of 7 and 6 warps."""
+    L = (12, 8, 8, 10)
+    cores = [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]]
+    U, ctx, info, geo = make_case(L, 0.12, 0.5, 7, cores)
+    cases = [("omega", [0, 3, 5, 9, 15], [geo.omega_mask[b] for b in [0, 3, 5, 9, 15]],
+              [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in [0, 3, 5, 9, 15]]),
+             ("lambda1", None, [geo.Lambda1], [ctx.geom_sites(dd4d.SET_LAMBDA1)])]
+    nvar = dd4d.lib().dd_hop_variants(dd4d.PREC[prec])
+    assert nvar >= 5
+    for kind, ids, masks, sites in cases:
+        tot = sum(len(s) for s in sites)
+        psi = synth.complex_gaussian(8, synth.TAG_RHS, (nrhs * tot, 12))
+        refs = []
+        off = 0
+        for k in range(len(sites)):
+            n = len(sites[k])
+            for r in range(nrhs):
+                f = to_field(L, sites[k], psi[off:off + n])
+                refs.append(from_field(L, sites[k], apply_D_restricted(U, f, 0.12, masks[k])))
+                off += n
+        ref = np.concatenate(refs)
+        for v in range(nvar):
+            ctx.set_hop_variant(prec, v)
+            out = np.zeros_like(psi)
+            ctx.apply_D_block(kind, ids, nrhs, psi, out, prec)
+            assert relerr(out, ref) < TOL[prec], (kind, v)
+        ctx.set_hop_variant(prec, -1)
