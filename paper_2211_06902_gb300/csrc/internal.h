@@ -202,6 +202,7 @@ struct HopArgs {
   double a1, a2, b;         // out = a1*s1 + a2*s2 + b*H in
   const void* dotq;         // optional: partial (dotq, out)  [complex]
   const void* dots;         // optional: partials (out, dots) and (out, out)
+  bool dotqs;               // with dotq and s1: also the partial (dotq, s1) into slot 3
   double* partial;          // [k][nitems*nrhs] complex (2 doubles)
   const int* active;        // optional per-system flags, active[sys * active_stride]
   int active_stride;

@@ -68,9 +68,10 @@ __device__ __forceinline__ double2 sum_slot(const double* partial, int slot, lon
 // (the elementwise kernels touch the 12 components of site i of every vector
 // at the same pair-layout positions o + cidx(k, n, i))
 
+// r = r^ = p = rhs, x = 0; partial |r|^2 into slot 1
 template <class S>
 __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restrict__ rhs, S* r,
-                             S* rhat, S* p, S* v, S* x, double* partial) {
+                             S* rhat, S* p, S* x, double* partial) {
   typedef typename StoreTraits<S>::C C;
   __shared__ double red[64];
   ELEM_PROLOGUE
@@ -87,8 +88,7 @@ __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restric
     }
     st_site<12>(r + o, n, i, b);
     st_site<12>(rhat + o, n, i, b);
-    st_site<12>(p + o, n, i, z);
-    st_site<12>(v + o, n, i, z);
+    st_site<12>(p + o, n, i, b);
     st_site<12>(x + o, n, i, z);
   }
   block_reduce_t<T, 1>(t, acc, red);
@@ -101,23 +101,6 @@ __global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restric
     partial[2 * (stride + m) + 1] = 0.0;
   }
   (void)st;
-}
-
-template <class S>
-__global__ void k_p_update(BatchDev bd, const SysState* st, const S* __restrict__ r, S* p,
-                           const S* __restrict__ v) {
-  typedef typename StoreTraits<S>::C C;
-  ELEM_PROLOGUE
-  if (!live || !st[sys].active) return;
-  const C beta = cmk<C>(st[sys].beta.x, st[sys].beta.y);
-  const C om = cmk<C>(st[sys].omega.x, st[sys].omega.y);
-  C pp[12], vv[12], rr[12];
-  ld_site<12>(p + o, n, i, pp);
-  ld_site<12>(v + o, n, i, vv);
-  ld_site<12>(r + o, n, i, rr);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) pp[k] = cadd(rr[k], cmul(beta, csub(pp[k], cmul(om, vv[k]))));
-  st_site<12>(p + o, n, i, pp);
 }
 
 template <class S>
@@ -135,48 +118,54 @@ __global__ void k_s_update(BatchDev bd, const SysState* st, const S* __restrict_
   st_site<12>(s + o, n, i, rr);
 }
 
-// x += alpha p + omega s ; r = s - omega t ; partials (rhat, r) and |r|^2
+// End of a BiCGstab iteration with the next search direction fused in:
+//   x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
+// (beta of the next iteration is already known: rho_new = (r^, s) - omega (r^, t)
+// comes from the inner products fused into the t = M s hop); partial |r|^2 into
+// slot 1 for the convergence check
 template <class S>
-__global__ void k_xr_update(BatchDev bd, const SysState* st, S* x, S* r, const S* __restrict__ p,
-                            const S* __restrict__ s, const S* __restrict__ t,
-                            const S* __restrict__ rhat, double* partial) {
+__global__ void k_xrp_update(BatchDev bd, const SysState* st, S* x, S* r, S* p,
+                             const S* __restrict__ s, const S* __restrict__ t,
+                             const S* __restrict__ v, double* partial) {
   typedef typename StoreTraits<S>::C C;
-  __shared__ double red[96];
+  __shared__ double red[64];
   ELEM_PROLOGUE
   if (!st[sys].active) return;
   typedef typename StoreTraits<S>::T T;
-  double acc[3] = {0.0, 0.0, 0.0};
-  T tt[3] = {0, 0, 0};
+  double acc[1] = {0.0};
+  T tt[1] = {0};
   if (live) {
     const C al = cmk<C>(st[sys].alpha.x, st[sys].alpha.y);
     const C om = cmk<C>(st[sys].omega.x, st[sys].omega.y);
-    C xx[12], pv[12], ss[12];
-    ld_site<12>(x + o, n, i, xx);
-    ld_site<12>(p + o, n, i, pv);
-    ld_site<12>(s + o, n, i, ss);
+    const C be = cmk<C>(st[sys].beta.x, st[sys].beta.y);
+    // two components at a time (one pair-layout word per vector): few live registers
+#pragma unroll 2
+    for (int q = 0; q < 6; ++q) {
+      const long long e = o + ((long long)q * n + i) * 2;
+      C xv[2], pv[2], sv[2], tv[2], vv[2];
+      ld_pair(x + e, xv[0], xv[1]);
+      ld_pair(p + e, pv[0], pv[1]);
+      ld_pair(s + e, sv[0], sv[1]);
+      ld_pair(t + e, tv[0], tv[1]);
+      ld_pair(v + e, vv[0], vv[1]);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) xx[k] = cadd(xx[k], cadd(cmul(al, pv[k]), cmul(om, ss[k])));
-    st_site<12>(x + o, n, i, xx);
-    C tv[12], rh[12];
-    ld_site<12>(t + o, n, i, tv);
-    ld_site<12>(rhat + o, n, i, rh);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const C rr = csub(ss[k], cmul(om, tv[k]));
-      ss[k] = rr;
-      tt[0] = fma(rh[k].x, rr.x, fma(rh[k].y, rr.y, tt[0]));
-      tt[1] = fma(rh[k].x, rr.y, fma(-rh[k].y, rr.x, tt[1]));
-      tt[2] = fma(rr.x, rr.x, fma(rr.y, rr.y, tt[2]));
+      for (int k = 0; k < 2; ++k) {
+        xv[k] = cadd(xv[k], cadd(cmul(al, pv[k]), cmul(om, sv[k])));
+        const C rr = csub(sv[k], cmul(om, tv[k]));
+        tt[0] = fma(rr.x, rr.x, fma(rr.y, rr.y, tt[0]));
+        pv[k] = cadd(rr, cmul(be, csub(pv[k], cmul(om, vv[k]))));
+        sv[k] = rr;
+      }
+      st_pair(x + e, xv[0], xv[1]);
+      st_pair(r + e, sv[0], sv[1]);
+      st_pair(p + e, pv[0], pv[1]);
     }
-    st_site<12>(r + o, n, i, ss);
   }
-  block_reduce_t<T, 3>(tt, acc, red);
+  block_reduce_t<T, 1>(tt, acc, red);
   if (threadIdx.x == 0) {
     long long stride = (long long)bd.nitems[0] * bd.nrhs;
     long long m = (long long)blockIdx.x * bd.nrhs + rh;
-    partial[2 * m] = acc[0];
-    partial[2 * m + 1] = acc[1];
-    partial[2 * (stride + m)] = acc[2];
+    partial[2 * (stride + m)] = acc[0];
     partial[2 * (stride + m) + 1] = 0.0;
   }
 }
@@ -329,29 +318,24 @@ __global__ void k_sc_inner_init(ScalarArgs a, double inner_tol2, double floor_fr
   s.alpha = s.omega = make_double2(1.0, 0.0);
   s.beta = make_double2(0.0, 0.0);
   s.target2 = fmax(inner_tol2 * rr, floor_frac * s.outer2);
+  if (s.status == 2) s.status = 0;      // a breakdown ends one inner solve, not the outer loop
   s.active = s.outer_active && rr > s.target2;
 }
 
-__global__ void k_sc_beta(ScalarArgs a, int* count) {
+// start of an iteration: |r|^2 (slot 1) against the inner target; systems
+// that converged or broke down stop; the others count as running
+__global__ void k_sc_check(ScalarArgs a, int* count) {
   int sys = blockIdx.x * blockDim.x + threadIdx.x;
   if (sys >= a.nsys) return;
   SysState& s = a.st[sys];
   if (!s.active) return;
   int j = sys / a.nrhs, r = sys % a.nrhs;
-  double2 rho_new = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r);
   double rr = sum_slot(a.partial, 1, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
   s.rr = rr;
-  if (!(rr > s.target2)) {            // converged (or NaN: caught by the outer check)
+  if (!(rr > s.target2) || s.status == 2) {   // converged (or NaN: caught by the outer check)
     s.active = 0;
     return;
   }
-  if (rho_new.x == 0.0 && rho_new.y == 0.0) {
-    s.active = 0;
-    s.status = 2;
-    return;
-  }
-  s.beta = zmul(zdiv(rho_new, s.rho), zdiv(s.alpha, s.omega));
-  s.rho = rho_new;
   s.iters += 1;
   if (count) atomicAdd(count, 1);
 }
@@ -371,15 +355,31 @@ __global__ void k_sc_alpha(ScalarArgs a) {
   s.alpha = zdiv(s.rho, den);
 }
 
+// omega = (t, s) / (t, t); rho_new = (r^, r_new) = (r^, s) - omega (r^, t) from
+// fresh inner products of this iteration; beta = (rho_new / rho) (alpha / omega).
+// Slots: 0 (r^, t), 1 (t, s), 2 |t|^2, 3 (r^, s).  rho_new = 0 is a breakdown:
+// the iteration finishes its update and the system stops at the next check.
 __global__ void k_sc_omega(ScalarArgs a) {
   int sys = blockIdx.x * blockDim.x + threadIdx.x;
   if (sys >= a.nsys) return;
   SysState& s = a.st[sys];
   if (!s.active) return;
   int j = sys / a.nrhs, r = sys % a.nrhs;
-  double2 ts = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r);
-  double tt = sum_slot(a.partial, 1, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
+  const int ib0 = a.item_begin[j], ib1 = a.item_begin[j + 1];
+  double2 rt = sum_slot(a.partial, 0, a.stride, ib0, ib1, a.nrhs, r);
+  double2 ts = sum_slot(a.partial, 1, a.stride, ib0, ib1, a.nrhs, r);
+  double tt = sum_slot(a.partial, 2, a.stride, ib0, ib1, a.nrhs, r).x;
+  double2 rs = sum_slot(a.partial, 3, a.stride, ib0, ib1, a.nrhs, r);
   s.omega = tt > 0.0 ? make_double2(ts.x / tt, ts.y / tt) : make_double2(0.0, 0.0);
+  const double2 rho_new = make_double2(rs.x - (s.omega.x * rt.x - s.omega.y * rt.y),
+                                       rs.y - (s.omega.x * rt.y + s.omega.y * rt.x));
+  if ((rho_new.x == 0.0 && rho_new.y == 0.0) || (s.omega.x == 0.0 && s.omega.y == 0.0)) {
+    s.beta = make_double2(0.0, 0.0);
+    if (rho_new.x == 0.0 && rho_new.y == 0.0) s.status = 2;
+  } else {
+    s.beta = zmul(zdiv(rho_new, s.rho), zdiv(s.alpha, s.omega));
+  }
+  s.rho = rho_new;
 }
 
 }  // namespace
@@ -448,18 +448,21 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
   const int sth = 128, sbl = (nsys + sth - 1) / sth;
   dim3 eg(b.nitems[0], b.nrhs);
   const double k2 = c->kappa * c->kappa;
-  DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, st, (const S*)rhs, (S*)w.r, (S*)w.rhat, (S*)w.p, (S*)w.v,
-                                     (S*)w.x, partial);
+  DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, st, (const S*)rhs, (S*)w.r, (S*)w.rhat, (S*)w.p,
+                                                        (S*)w.x, partial);
   DD_COUNT_LAUNCH(), k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
   DD_CUDA(c, cudaGetLastError());
   const int* act = (const int*)((const char*)st + offsetof(SysState, active));
   const int act_stride = (int)(sizeof(SysState) / sizeof(int));
   // one BiCGstab iteration for every active system (van der Vorst 1992),
-  // enqueued on stream s (captured into a graph when s is the capture stream)
+  // enqueued on stream s (captured into a graph when s is the capture stream).
+  // p enters the iteration already updated (by the previous k_xrp_update, or
+  // p = r at the start), so an iteration is: check, v = M p with (r^, v),
+  // alpha, s, t = M s with (r^, t), (t, s), |t|^2, (r^, s), omega and beta,
+  // and the fused x, r, p update.
   auto iteration = [&](bool check, cudaStream_t s) -> dd_status {
     if (check) DD_CUDA(c, cudaMemsetAsync(d_count, 0, sizeof(int), s));
-    DD_COUNT_LAUNCH(), k_sc_beta<<<sbl, sth, 0, s>>>(sa, check ? d_count : nullptr);
-    DD_COUNT_LAUNCH(), k_p_update<S><<<eg, 128, 0, s>>>(bd, st, (const S*)w.r, (S*)w.p, (const S*)w.v);
+    DD_COUNT_LAUNCH(), k_sc_check<<<sbl, sth, 0, s>>>(sa, check ? d_count : nullptr);
     // v = M p = p - k^2 H_eo H_oe p ; partial (rhat, v)
     HopArgs h1{};
     h1.p_out = 1; h1.in = w.p; h1.out = w.tmp; h1.b = 1.0;
@@ -479,12 +482,12 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     if ((e = launch_hop(c, b, prec, h3, s)) != DD_OK) return e;
     HopArgs h4{};
     h4.p_out = 0; h4.in = w.tmp; h4.out = w.t; h4.s1 = w.s; h4.a1 = 1.0; h4.b = -k2;
-    h4.dots = w.s; h4.partial = partial;
+    h4.dots = w.s; h4.dotq = w.rhat; h4.dotqs = true; h4.partial = partial;
     h4.active = act; h4.active_stride = act_stride;
     if ((e = launch_hop(c, b, prec, h4, s)) != DD_OK) return e;
     DD_COUNT_LAUNCH(), k_sc_omega<<<sbl, sth, 0, s>>>(sa);
-    DD_COUNT_LAUNCH(), k_xr_update<S><<<eg, 128, 0, s>>>(bd, st, (S*)w.x, (S*)w.r, (const S*)w.p, (const S*)w.s,
-                                      (const S*)w.t, (const S*)w.rhat, partial);
+    DD_COUNT_LAUNCH(), k_xrp_update<S><<<eg, 128, 0, s>>>(bd, st, (S*)w.x, (S*)w.r, (S*)w.p, (const S*)w.s,
+                                                          (const S*)w.t, (const S*)w.v, partial);
     DD_CUDA(c, cudaGetLastError());
     return DD_OK;
   };
@@ -553,8 +556,8 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
       }
     }
   }
-  // final beta pass marks converged systems (updates rr) without a p update
-  DD_COUNT_LAUNCH(), k_sc_beta<<<sbl, sth, 0, s>>>(sa, nullptr);
+  // a final check marks the systems that converged in the last iteration
+  DD_COUNT_LAUNCH(), k_sc_check<<<sbl, sth, 0, s>>>(sa, nullptr);
   *iters_run = it;
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
@@ -666,7 +669,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   void *vpart, *vst, *vcnt, *vrel, *vpart_o;
   const long long stride = (long long)b.nitems[0] * b.nrhs;
   const long long stride_o = (long long)b.nitems[1] * b.nrhs;
-  if ((e = ws_get(c, 15, sizeof(double) * 2 * 3 * std::max<long long>(1, stride), &vpart)) ||
+  if ((e = ws_get(c, 15, sizeof(double) * 2 * 4 * std::max<long long>(1, stride), &vpart)) ||
       (e = ws_get(c, 16, sizeof(SysState) * nsys, &vst)) || (e = ws_get(c, 17, 64, &vcnt)) ||
       (e = ws_get(c, 18, sizeof(double) * nsys, &vrel)) ||
       (e = ws_get(c, 19, sizeof(double) * 2 * std::max<long long>(1, stride_o), &vpart_o)))
@@ -850,7 +853,10 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   out.systems = nsys;
   out.outer_cycles = cycles;
   out.seconds = ms * 1e-3;
-  out.hop_variant = b.hop_variant[ip == DD_F64 ? 0 : (ip == DD_F32 ? 1 : 2)];
+  {
+    const int pi = ip == DD_F64 ? 0 : (ip == DD_F32 ? 1 : 2);
+    out.hop_variant = c->forced_variant[pi] >= 0 ? c->forced_variant[pi] : b.hop_variant[pi];
+  }
   bool nan = false;
   for (int k = 0; k < nsys; ++k) {
     if (!(rel[k] == rel[k])) nan = true;

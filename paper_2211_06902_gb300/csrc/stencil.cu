@@ -157,6 +157,27 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
       P[2 * (slot_stride + my) + 1] = 0.0;
     }
   }
+  if (a.dotqs) {
+    // (dotq, s1): the self term is re-read here (it was loaded moments ago)
+    double v[2] = {0.0, 0.0};
+    T t[2] = {0, 0};
+    if (live) {
+      const long long oq = (p ? bd.off[1] : bd.off[0])[sys];
+      C wv[12], sv[12];
+      ld_site<12>((const S*)a.dotq + oq, n_out, i, wv);
+      ld_site<12>((const S*)a.s1 + oq, n_out, i, sv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        t[0] = fma(wv[k].x, sv[k].x, fma(wv[k].y, sv[k].y, t[0]));
+        t[1] = fma(wv[k].x, sv[k].y, fma(-wv[k].y, sv[k].x, t[1]));
+      }
+    }
+    block_reduce_t<T, 2>(t, v, red);
+    if (threadIdx.x == 0) {
+      a.partial[2 * (3 * slot_stride + my)] = v[0];
+      a.partial[2 * (3 * slot_stride + my) + 1] = v[1];
+    }
+  }
   }
 }
 
@@ -264,7 +285,7 @@ __device__ __forceinline__ void hop_unit_r(const BatchDev& bd, const HopArgs& a,
       st_site<12>((S*)a.out + oo[q], n_out, i, out[q]);
     }
   }
-  if (!a.dotq && !a.dots) return;
+  if (!a.dotq && !a.dots && !a.dotqs) return;
   const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -310,6 +331,25 @@ __device__ __forceinline__ void hop_unit_r(const BatchDev& bd, const HopArgs& a,
         P[2 * my + 1] = v[1];
         P[2 * (slot_stride + my)] = v[2];
         P[2 * (slot_stride + my) + 1] = 0.0;
+      }
+    }
+    if (a.dotqs) {
+      double v[2] = {0.0, 0.0};
+      T tt[2] = {0, 0};
+      if (live) {
+        C wv[12], sv[12];
+        ld_site<12>((const S*)a.dotq + oo[q], n_out, i, wv);
+        ld_site<12>((const S*)a.s1 + oo[q], n_out, i, sv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          tt[0] = fma(wv[k].x, sv[k].x, fma(wv[k].y, sv[k].y, tt[0]));
+          tt[1] = fma(wv[k].x, sv[k].y, fma(-wv[k].y, sv[k].x, tt[1]));
+        }
+      }
+      block_reduce_t<T, 2>(tt, v, red);
+      if (threadIdx.x == 0) {
+        a.partial[2 * (3 * slot_stride + my)] = v[0];
+        a.partial[2 * (3 * slot_stride + my) + 1] = v[1];
       }
     }
   }
@@ -473,6 +513,28 @@ __device__ __forceinline__ void hop_unit_split(const BatchDev& bd, const HopArgs
       P[2 * (slot_stride + my) + 1] = 0.0;
     }
   }
+  if (a.dotqs) {
+    double v[2] = {0.0, 0.0};
+    T tt[2] = {0, 0};
+    if (live) {
+      const long long oq = (p ? bd.off[1] : bd.off[0])[sys];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        C w0, w1, s0, s1v;
+        ld_pair((const S*)a.dotq + oq + ((long long)(q0 + q) * n_out + i) * 2, w0, w1);
+        ld_pair((const S*)a.s1 + oq + ((long long)(q0 + q) * n_out + i) * 2, s0, s1v);
+        tt[0] = fma(w0.x, s0.x, fma(w0.y, s0.y, tt[0]));
+        tt[1] = fma(w0.x, s0.y, fma(-w0.y, s0.x, tt[1]));
+        tt[0] = fma(w1.x, s1v.x, fma(w1.y, s1v.y, tt[0]));
+        tt[1] = fma(w1.x, s1v.y, fma(-w1.y, s1v.x, tt[1]));
+      }
+    }
+    block_reduce_t<T, 2>(tt, v, red);
+    if (threadIdx.x == 0) {
+      a.partial[2 * (3 * slot_stride + my)] = v[0];
+      a.partial[2 * (3 * slot_stride + my) + 1] = v[1];
+    }
+  }
 }
 
 template <class S, int MINB, bool PERSIST>
@@ -583,17 +645,25 @@ __device__ __forceinline__ void lds_link(const S* dirblk, int lane, C (&U)[9]) {
   U[8] = lds_c(dirblk + (4 * LB_LANES + lane) * 2);
 }
 
-template <int DIR, class S, class C>
-__device__ __forceinline__ void hop_one_lb(C (&acc)[12], int j, int n_in, const S* __restrict__ in_sys,
-                                           const S* qlinks, int lane) {
+// one direction of the hop for the RR rhs of a thread: the link is read from
+// the shared-memory bundle once and applied to each rhs's neighbour spinor
+template <int DIR, class S, class C, int RR>
+__device__ __forceinline__ void hop_lb_dir(C (&acc)[RR][12], const int* qi, const S* ql, int lane,
+                                           int n_in, const void* in, const long long* off_in,
+                                           const int (&sysk)[RR], const bool (&actk)[RR]) {
   constexpr int MU = DIR & 3;
   constexpr bool FWD = DIR < 4;
+  const int j = qi[DIR * LB_LANES + lane];
   if (j < 0) return;
-  C psi[12];
-  ld_site<12>(in_sys, n_in, j, psi);
   C U[9];
-  lds_link(qlinks + DIR * 5 * LB_LANES * 2, lane, U);
-  hop_dir<MU, FWD>(acc, psi, U);
+  lds_link(ql + DIR * 5 * LB_LANES * 2, lane, U);
+#pragma unroll
+  for (int k = 0; k < RR; ++k) {
+    if (!actk[k]) continue;
+    C psi[12];
+    ld_site<12>((const S*)in + off_in[sysk[k]], n_in, j, psi);
+    hop_dir<MU, FWD>(acc[k], psi, U);
+  }
 }
 
 template <class S>
@@ -608,9 +678,11 @@ __device__ __forceinline__ const unsigned char* bundle_of<__nv_bfloat162>(const 
 template <class S>
 constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64; }
 
-// grid: nitems[p] * ngroups CTAs (group fastest), 32 * rb threads
-template <class S, int MINB>
-__global__ void __launch_bounds__(32 * LB_MAX_RHS, MINB)
+// grid: nitems[p] * ngroups CTAs (group fastest), 32 * ceil(rb / RR) threads;
+// thread (warp w, lane) computes rhs g * rb + w * RR + k, k < RR, of one site,
+// reading each link from shared memory once for its RR rhs
+template <class S, int MINB, int RR>
+__global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
     k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<S>::T T;
@@ -622,9 +694,18 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS, MINB)
   const int g = (int)(blockIdx.x - (long long)item * ngroups);
   const int4 it = (p ? bd.items[1] : bd.items[0])[item];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = g * rb + w;
-  const int sys = it.x * bd.nrhs + r;
-  const bool act = r < bd.nrhs && (!a.active || a.active[(long long)sys * a.active_stride]);
+  bool actk[RR];
+  int sysk[RR];
+  bool act = false;
+#pragma unroll
+  for (int k = 0; k < RR; ++k) {
+    const int rr = w * RR + k;
+    const int r = g * rb + rr;
+    sysk[k] = it.x * bd.nrhs + r;
+    actk[k] = rr < rb && r < bd.nrhs &&
+              (!a.active || a.active[(long long)sysk[k] * a.active_stride]);
+    act = act || actk[k];
+  }
   if (!__syncthreads_or(act)) return;          // every rhs of the group has converged
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
   const int n0 = dp->n[0];
@@ -649,16 +730,28 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS, MINB)
         if (!mbar_wait0(&bar[q])) atomicExch(a.err, 1);
     return;
   }
-  if (a.work_bytes && lane == 0) atomicAdd(a.work_bytes, a.site_bytes * it.z);
+  if (a.work_bytes && lane == 0)
+#pragma unroll
+    for (int k = 0; k < RR; ++k)
+      if (actk[k]) atomicAdd(a.work_bytes, a.site_bytes * it.z);
   const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
-  const S* in_sys = (const S*)a.in + (p ? bd.off[0] : bd.off[1])[sys];
-  S* out_sys = (S*)a.out + (p ? bd.off[1] : bd.off[0])[sys];
-  const long long oo = (p ? bd.off[1] : bd.off[0])[sys];
+  const long long* off_in = p ? bd.off[0] : bd.off[1];
+  const long long* off_out = p ? bd.off[1] : bd.off[0];
   const auto bsc = mkscal<C>(a.b);
   const auto a1 = mkscal<C>(a.a1);
   const auto a2 = mkscal<C>(a.a2);
-  T tq[2] = {0, 0};
-  T ts[3] = {0, 0, 0};
+  // fused (out, dots) and |out|^2 in the self-term pass when the dot vector is
+  // the only self term (t = s - k^2 H tmp with (t, s)): s is read once
+  const bool dots_in_s1 = a.dots && a.dots == a.s1 && !a.s2;
+  // the end-of-iteration launch of BiCGstab (see end_mode below)
+  const bool end_mode = dots_in_s1 && a.dotq && a.dotqs;
+  T tq[RR][2], ts[RR][3], tqs[RR][2];
+#pragma unroll
+  for (int k = 0; k < RR; ++k) {
+    tq[k][0] = tq[k][1] = 0;
+    ts[k][0] = ts[k][1] = ts[k][2] = 0;
+    tqs[k][0] = tqs[k][1] = 0;
+  }
   for (int q = 0; q < nq; ++q) {
     if (!mbar_wait0(&bar[q])) {
       if (lane == 0) atomicExch(a.err, 1);
@@ -670,89 +763,155 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS, MINB)
     const unsigned char* qb = lb_smem + q * QB;
     const S* ql = reinterpret_cast<const S*>(qb);
     const int* qi = reinterpret_cast<const int*>(qb + lb_link_bytes<S>());
-    int jn[8];
+    C acc[RR][12];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) jn[d] = qi[d * LB_LANES + lane];
-    C acc[12];
+    for (int k = 0; k < RR; ++k)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = cmk<C>(0.0, 0.0);
-    hop_one_lb<0, S>(acc, jn[0], n_in, in_sys, ql, lane);
-    hop_one_lb<1, S>(acc, jn[1], n_in, in_sys, ql, lane);
-    hop_one_lb<2, S>(acc, jn[2], n_in, in_sys, ql, lane);
-    hop_one_lb<3, S>(acc, jn[3], n_in, in_sys, ql, lane);
-    hop_one_lb<4, S>(acc, jn[4], n_in, in_sys, ql, lane);
-    hop_one_lb<5, S>(acc, jn[5], n_in, in_sys, ql, lane);
-    hop_one_lb<6, S>(acc, jn[6], n_in, in_sys, ql, lane);
-    hop_one_lb<7, S>(acc, jn[7], n_in, in_sys, ql, lane);
-    C out[12];
+      for (int c = 0; c < 12; ++c) acc[k][c] = cmk<C>(0.0, 0.0);
+    // forward and backward hop of a direction back to back: along x3 and x2
+    // the two neighbour sets of a warp's 32 sites nearly coincide, so the
+    // second load finds the first one's lines in L1
+    hop_lb_dir<3, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<7, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<2, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<6, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<1, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<5, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<0, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<4, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = scale(acc[k], bsc);
-    if (a.s1) {
-      C v[12];
-      ld_site<12>((const S*)a.s1 + oo, n_out, i, v);
+    for (int k = 0; k < RR; ++k) {
+      if (!actk[k]) continue;
+      const long long oo = off_out[sysk[k]];
+      if (end_mode) {
+        // t = s - k^2 H tmp with (r^, t), (t, s), |t|^2 and (r^, s): one pass over
+        // the component pairs reads s and r^ once each
 #pragma unroll
-      for (int k = 0; k < 12; ++k) axpy(out[k], a1, v[k]);
+        for (int q = 0; q < 6; ++q) {
+          const long long e = oo + ((long long)q * n_out + i) * 2;
+          C sv[2], rv[2], ov[2];
+          ld_pair((const S*)a.s1 + e, sv[0], sv[1]);
+          ld_pair((const S*)a.dotq + e, rv[0], rv[1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            ov[h] = scale(acc[k][2 * q + h], bsc);
+            axpy(ov[h], a1, sv[h]);
+            const C o = ov[h], w = rv[h], z = sv[h];
+            ts[k][0] = fma(o.x, z.x, fma(o.y, z.y, ts[k][0]));
+            ts[k][1] = fma(o.x, z.y, fma(-o.y, z.x, ts[k][1]));
+            ts[k][2] = fma(o.x, o.x, fma(o.y, o.y, ts[k][2]));
+            tq[k][0] = fma(w.x, o.x, fma(w.y, o.y, tq[k][0]));
+            tq[k][1] = fma(w.x, o.y, fma(-w.y, o.x, tq[k][1]));
+            tqs[k][0] = fma(w.x, z.x, fma(w.y, z.y, tqs[k][0]));
+            tqs[k][1] = fma(w.x, z.y, fma(-w.y, z.x, tqs[k][1]));
+          }
+          st_pair((S*)a.out + e, ov[0], ov[1]);
+        }
+        continue;
+      }
+      C out[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) out[c] = scale(acc[k][c], bsc);
+      if (a.s1) {
+        C v[12];
+        ld_site<12>((const S*)a.s1 + oo, n_out, i, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          axpy(out[c], a1, v[c]);
+          if (dots_in_s1) {
+            ts[k][0] = fma(out[c].x, v[c].x, fma(out[c].y, v[c].y, ts[k][0]));
+            ts[k][1] = fma(out[c].x, v[c].y, fma(-out[c].y, v[c].x, ts[k][1]));
+            ts[k][2] = fma(out[c].x, out[c].x, fma(out[c].y, out[c].y, ts[k][2]));
+          }
+        }
+      }
+      if (a.s2) {
+        C v[12];
+        ld_site<12>((const S*)a.s2 + oo, n_out, i, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) axpy(out[c], a2, v[c]);
+      }
+      st_site<12>((S*)a.out + oo, n_out, i, out);
+      if (a.dotq) {
+        C wv[12];
+        ld_site<12>((const S*)a.dotq + oo, n_out, i, wv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          tq[k][0] = fma(wv[c].x, out[c].x, fma(wv[c].y, out[c].y, tq[k][0]));
+          tq[k][1] = fma(wv[c].x, out[c].y, fma(-wv[c].y, out[c].x, tq[k][1]));
+        }
+        if (a.dotqs) {
+          // (dotq, s1): the self term is re-read (it was loaded moments ago)
+          C sv[12];
+          ld_site<12>((const S*)a.s1 + oo, n_out, i, sv);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            tqs[k][0] = fma(wv[c].x, sv[c].x, fma(wv[c].y, sv[c].y, tqs[k][0]));
+            tqs[k][1] = fma(wv[c].x, sv[c].y, fma(-wv[c].y, sv[c].x, tqs[k][1]));
+          }
+        }
+      }
+      if (a.dots && !dots_in_s1) {
+        C wv[12];
+        ld_site<12>((const S*)a.dots + oo, n_out, i, wv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          ts[k][0] = fma(out[c].x, wv[c].x, fma(out[c].y, wv[c].y, ts[k][0]));
+          ts[k][1] = fma(out[c].x, wv[c].y, fma(-out[c].y, wv[c].x, ts[k][1]));
+          ts[k][2] = fma(out[c].x, out[c].x, fma(out[c].y, out[c].y, ts[k][2]));
+        }
+      }
     }
-    if (a.s2) {
-      C v[12];
-      ld_site<12>((const S*)a.s2 + oo, n_out, i, v);
+  }
+  // per-(warp, k) = per-system partial sums of the chunk
+  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) axpy(out[k], a2, v[k]);
-    }
-    st_site<12>(out_sys, n_out, i, out);
+  for (int k = 0; k < RR; ++k) {
+    // actk[k] is uniform over the warp, so the shuffles below see full warps
+    if (!actk[k]) continue;
+    const long long my = (long long)item * bd.nrhs + (sysk[k] - (long long)it.x * bd.nrhs);
     if (a.dotq) {
-      C wv[12];
-      ld_site<12>((const S*)a.dotq + oo, n_out, i, wv);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        tq[0] = fma(wv[k].x, out[k].x, fma(wv[k].y, out[k].y, tq[0]));
-        tq[1] = fma(wv[k].x, out[k].y, fma(-wv[k].y, out[k].x, tq[1]));
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tq[k][e] += __shfl_down_sync(0xffffffffu, tq[k][e], o);
+      if (lane == 0) {
+        a.partial[2 * my] = (double)tq[k][0];
+        a.partial[2 * my + 1] = (double)tq[k][1];
       }
     }
     if (a.dots) {
-      C wv[12];
-      ld_site<12>((const S*)a.dots + oo, n_out, i, wv);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        ts[0] = fma(out[k].x, wv[k].x, fma(out[k].y, wv[k].y, ts[0]));
-        ts[1] = fma(out[k].x, wv[k].y, fma(-out[k].y, wv[k].x, ts[1]));
-        ts[2] = fma(out[k].x, out[k].x, fma(out[k].y, out[k].y, ts[2]));
+      for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ts[k][e] += __shfl_down_sync(0xffffffffu, ts[k][e], o);
+      if (lane == 0) {
+        double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
+        P[2 * my] = (double)ts[k][0];
+        P[2 * my + 1] = (double)ts[k][1];
+        P[2 * (slot_stride + my)] = (double)ts[k][2];
+        P[2 * (slot_stride + my) + 1] = 0.0;
       }
     }
-  }
-  // per-warp (= per-system) partial sums of the chunk
-  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
-  const long long my = (long long)item * bd.nrhs + r;
-  if (a.dotq) {
+    if (a.dotqs) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
+      for (int e = 0; e < 2; ++e)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) tq[k] += __shfl_down_sync(0xffffffffu, tq[k], o);
-    if (lane == 0) {
-      a.partial[2 * my] = (double)tq[0];
-      a.partial[2 * my + 1] = (double)tq[1];
-    }
-  }
-  if (a.dots) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ts[k] += __shfl_down_sync(0xffffffffu, ts[k], o);
-    if (lane == 0) {
-      double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
-      P[2 * my] = (double)ts[0];
-      P[2 * my + 1] = (double)ts[1];
-      P[2 * (slot_stride + my)] = (double)ts[2];
-      P[2 * (slot_stride + my) + 1] = 0.0;
+        for (int o = 16; o > 0; o >>= 1) tqs[k][e] += __shfl_down_sync(0xffffffffu, tqs[k][e], o);
+      if (lane == 0) {
+        a.partial[2 * (3 * slot_stride + my)] = (double)tqs[k][0];
+        a.partial[2 * (3 * slot_stride + my) + 1] = (double)tqs[k][1];
+      }
     }
   }
 }
 
-template <class S, int MINB>
+template <class S, int MINB, int RR>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
   const int ngroups = (bd.nrhs + LB_MAX_RHS - 1) / LB_MAX_RHS;
   const int rb = (bd.nrhs + ngroups - 1) / ngroups;
-  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB><<<(unsigned)(nitems_p * ngroups), 32 * rb, lb_smem_bytes<S>(), s>>>(
+  const int nthreads = 32 * ((rb + RR - 1) / RR);
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR><<<(unsigned)(nitems_p * ngroups), nthreads, lb_smem_bytes<S>(), s>>>(
       bd, a, ngroups, rb);
 }
 
@@ -761,14 +920,16 @@ void hop_bundle_prepare() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || done[dev]) return;
-  cudaFuncSetAttribute(k_hop_lb<float2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       lb_smem_bytes<float2>());
-  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       lb_smem_bytes<__nv_bfloat162>());
-  cudaFuncSetAttribute(k_hop_lb<float2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       lb_smem_bytes<float2>());
-  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       lb_smem_bytes<__nv_bfloat162>());
+  const int b32 = lb_smem_bytes<float2>(), b16 = lb_smem_bytes<__nv_bfloat162>();
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 1, 1>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 2>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 3>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 1, 1>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 3, 2>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 4, 3>, at, b16);
   done[dev] = true;
 }
 
@@ -783,12 +944,13 @@ static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true,
 static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false, 1}, {6, true, 1},
                                          {4, true, 1}, {4, false, 2}, {5, false, 2}, {4, true, 2},
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
-                                         {3, true, 0}, {2, false, -1}, {1, false, -1}};
+                                         {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
+                                         {2, false, -3}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
-                                         {2, false, -1}, {1, false, -1}};
+                                         {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 15 : 10); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 17 : 12); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -822,10 +984,18 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
   }
   const HopVariant& hv = variant_of(prec, v);
   if (hv.r < 0) {
-    if (prec == DD_F32 && hv.minb == 1) launch_lb<float2, 1>(bd, a, ni, s);
-    else if (prec == DD_F32) launch_lb<float2, 2>(bd, a, ni, s);
-    else if (hv.minb == 1) launch_lb<__nv_bfloat162, 1>(bd, a, ni, s);
-    else launch_lb<__nv_bfloat162, 2>(bd, a, ni, s);
+    const int rr = -hv.r;
+    if (prec == DD_F32) {
+      if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
+      else if (rr == 2) launch_lb<float2, 2, 2>(bd, a, ni, s);
+      else if (hv.minb == 1) launch_lb<float2, 1, 1>(bd, a, ni, s);
+      else launch_lb<float2, 2, 1>(bd, a, ni, s);
+    } else {
+      if (rr == 3) launch_lb<__nv_bfloat162, 4, 3>(bd, a, ni, s);
+      else if (rr == 2) launch_lb<__nv_bfloat162, 3, 2>(bd, a, ni, s);
+      else if (hv.minb == 1) launch_lb<__nv_bfloat162, 1, 1>(bd, a, ni, s);
+      else launch_lb<__nv_bfloat162, 2, 1>(bd, a, ni, s);
+    }
     return;
   }
   if (hv.r == 0) {
@@ -1008,7 +1178,8 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
         if (h.r < 0)
           snprintf(names[k][u], sizeof names[k][u],
-                   "k_hop_lb<%s,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA", ty[k], h.minb);
+                   "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
+                   ty[k], h.minb, -h.r, -h.r);
         else if (h.r == 0)
           snprintf(names[k][u], sizeof names[k][u], "k_hop_split<%s,%d,%s>: forward/backward split",
                    ty[k], h.minb, h.persist ? "persistent" : "grid");

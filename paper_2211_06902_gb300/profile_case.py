@@ -1,6 +1,6 @@
 """One batched block solve on a chosen lattice, for profiling the kernels.
 
-    python -m paper_2211_06902_gb300.profile_case --L 24 --core 7 --nrhs 12 --inner f32
+    python -m paper_2211_06902_gb300.profile_case --L 24 --core 7 --nrhs 12 --inner f32 --variant 13
 
 Builds the lattice (links exp(i eps H)), the framed blocks of `core`^4 cores
 with a one-site frame, Gaussian right-hand sides on every block, and runs
@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--eps", type=float, default=0.5)
     ap.add_argument("--inner", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="stencil launch variant of the inner precision (-1: default)")
     a = ap.parse_args()
     import torch
     torch.cuda.init()
@@ -44,6 +46,8 @@ def main():
     b = synth.complex_gaussian(2, synth.TAG_RHS, (len(ids), a.nrhs, info["max_omega"], 12))
     bd = torch.from_numpy(b.view(np.float64)).cuda()
     xd = torch.zeros_like(bd)
+    if a.variant >= 0:
+        ctx.set_hop_variant(a.inner, a.variant)
     prm = dd4d.params(1e-10, inner_prec=a.inner)
     for _ in range(a.repeat):
         st = ctx.solve_blocks("omega", ids, a.nrhs, bd, xd, prm)
