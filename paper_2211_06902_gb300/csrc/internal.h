@@ -203,6 +203,7 @@ struct HopArgs {
   const void* dotq;         // optional: partial (dotq, out)  [complex]
   const void* dots;         // optional: partials (out, dots) and (out, out)
   bool dotqs;               // with dotq and s1: also the partial (dotq, s1) into slot 3
+  unsigned rhat_seed;       // nonzero: dotq is not read but generated (rhat_comp, spinor.cuh)
   double* partial;          // [k][nitems*nrhs] complex (2 doubles)
   const int* active;        // optional per-system flags, active[sys * active_stride]
   int active_stride;

@@ -68,39 +68,42 @@ __device__ __forceinline__ double2 sum_slot(const double* partial, int slot, lon
 // (the elementwise kernels touch the 12 components of site i of every vector
 // at the same pair-layout positions o + cidx(k, n, i))
 
-// r = r^ = p = rhs, x = 0; partial |r|^2 into slot 1
+// r = p = rhs, x = 0; partials (r^, r) into slot 0 and |r|^2 into slot 1, with
+// the generated shadow vector r^ of seed `seed` (nothing is stored for r^)
 template <class S>
-__global__ void k_inner_init(BatchDev bd, const SysState* st, const S* __restrict__ rhs, S* r,
-                             S* rhat, S* p, S* x, double* partial) {
+__global__ void k_inner_init(BatchDev bd, const S* __restrict__ rhs, S* r, S* p, S* x,
+                             unsigned seed, double* partial) {
   typedef typename StoreTraits<S>::C C;
+  typedef typename StoreTraits<S>::T T;
   __shared__ double red[64];
   ELEM_PROLOGUE
-  typedef typename StoreTraits<S>::T T;
-  double acc[1] = {0.0};
-  T t[1] = {0};
+  double acc[3] = {0.0, 0.0, 0.0};
+  T t[3] = {0, 0, 0};
   if (live) {
     C b[12], z[12];
     ld_site<12>(rhs + o, n, i, b);
+    const unsigned h = rhat_bits(seed, sys, i);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       z[k] = cmk<C>(0.0, 0.0);
-      t[0] = fma(b[k].x, b[k].x, fma(b[k].y, b[k].y, t[0]));
+      const C w = rhat_comp<C>(h, k);
+      t[0] = fma(w.x, b[k].x, fma(w.y, b[k].y, t[0]));
+      t[1] = fma(w.x, b[k].y, fma(-w.y, b[k].x, t[1]));
+      t[2] = fma(b[k].x, b[k].x, fma(b[k].y, b[k].y, t[2]));
     }
     st_site<12>(r + o, n, i, b);
-    st_site<12>(rhat + o, n, i, b);
     st_site<12>(p + o, n, i, b);
     st_site<12>(x + o, n, i, z);
   }
-  block_reduce_t<T, 1>(t, acc, red);
+  block_reduce_t<T, 3>(t, acc, red);
   if (threadIdx.x == 0) {
     long long stride = (long long)bd.nitems[0] * bd.nrhs;
     long long m = (long long)blockIdx.x * bd.nrhs + rh;
     partial[2 * m] = acc[0];
-    partial[2 * m + 1] = 0.0;
-    partial[2 * (stride + m)] = acc[0];
+    partial[2 * m + 1] = acc[1];
+    partial[2 * (stride + m)] = acc[2];
     partial[2 * (stride + m) + 1] = 0.0;
   }
-  (void)st;
 }
 
 template <class S>
@@ -306,7 +309,7 @@ __global__ void k_sc_outer(ScalarArgs a, const double* partial_o, const int* ib_
   atomicMax(maxrel, (unsigned long long)__double_as_longlong(rel == rel ? rel : 1e300));
 }
 
-// inner init: rho = |r|^2, alpha = omega = 1, threshold, active
+// inner init: rho = (r^, r), alpha = omega = 1, threshold, active
 __global__ void k_sc_inner_init(ScalarArgs a, double inner_tol2, double floor_frac) {
   int sys = blockIdx.x * blockDim.x + threadIdx.x;
   if (sys >= a.nsys) return;
@@ -314,7 +317,7 @@ __global__ void k_sc_inner_init(ScalarArgs a, double inner_tol2, double floor_fr
   SysState& s = a.st[sys];
   double rr = sum_slot(a.partial, 1, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
   s.rr = rr;
-  s.rho = make_double2(rr, 0.0);
+  s.rho = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r);
   s.alpha = s.omega = make_double2(1.0, 0.0);
   s.beta = make_double2(0.0, 0.0);
   s.target2 = fmax(inner_tol2 * rr, floor_frac * s.outer2);
@@ -373,9 +376,10 @@ __global__ void k_sc_omega(ScalarArgs a) {
   s.omega = tt > 0.0 ? make_double2(ts.x / tt, ts.y / tt) : make_double2(0.0, 0.0);
   const double2 rho_new = make_double2(rs.x - (s.omega.x * rt.x - s.omega.y * rt.y),
                                        rs.y - (s.omega.x * rt.y + s.omega.y * rt.x));
-  if ((rho_new.x == 0.0 && rho_new.y == 0.0) || (s.omega.x == 0.0 && s.omega.y == 0.0)) {
+  const bool rho0 = s.rho.x == 0.0 && s.rho.y == 0.0;
+  if ((rho_new.x == 0.0 && rho_new.y == 0.0) || (s.omega.x == 0.0 && s.omega.y == 0.0) || rho0) {
     s.beta = make_double2(0.0, 0.0);
-    if (rho_new.x == 0.0 && rho_new.y == 0.0) s.status = 2;
+    if ((rho_new.x == 0.0 && rho_new.y == 0.0) || rho0) s.status = 2;
   } else {
     s.beta = zmul(zdiv(rho_new, s.rho), zdiv(s.alpha, s.omega));
   }
@@ -448,8 +452,10 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
   const int sth = 128, sbl = (nsys + sth - 1) / sth;
   dim3 eg(b.nitems[0], b.nrhs);
   const double k2 = c->kappa * c->kappa;
-  DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, st, (const S*)rhs, (S*)w.r, (S*)w.rhat, (S*)w.p,
-                                                        (S*)w.x, partial);
+  // seed of the generated shadow vector r^ (any nonzero constant)
+  const unsigned rseed = 0x2211u;
+  DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, (const S*)rhs, (S*)w.r, (S*)w.p, (S*)w.x, rseed,
+                                                        partial);
   DD_COUNT_LAUNCH(), k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
   DD_CUDA(c, cudaGetLastError());
   const int* act = (const int*)((const char*)st + offsetof(SysState, active));
@@ -471,7 +477,7 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     if (e != DD_OK) return e;
     HopArgs h2{};
     h2.p_out = 0; h2.in = w.tmp; h2.out = w.v; h2.s1 = w.p; h2.a1 = 1.0; h2.b = -k2;
-    h2.dotq = w.rhat; h2.partial = partial;
+    h2.dotq = w.rhat; h2.rhat_seed = rseed; h2.partial = partial;
     h2.active = act; h2.active_stride = act_stride;
     if ((e = launch_hop(c, b, prec, h2, s)) != DD_OK) return e;
     DD_COUNT_LAUNCH(), k_sc_alpha<<<sbl, sth, 0, s>>>(sa);
@@ -482,7 +488,7 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     if ((e = launch_hop(c, b, prec, h3, s)) != DD_OK) return e;
     HopArgs h4{};
     h4.p_out = 0; h4.in = w.tmp; h4.out = w.t; h4.s1 = w.s; h4.a1 = 1.0; h4.b = -k2;
-    h4.dots = w.s; h4.dotq = w.rhat; h4.dotqs = true; h4.partial = partial;
+    h4.dots = w.s; h4.dotq = w.rhat; h4.dotqs = true; h4.rhat_seed = rseed; h4.partial = partial;
     h4.active = act; h4.active_stride = act_stride;
     if ((e = launch_hop(c, b, prec, h4, s)) != DD_OK) return e;
     DD_COUNT_LAUNCH(), k_sc_omega<<<sbl, sth, 0, s>>>(sa);

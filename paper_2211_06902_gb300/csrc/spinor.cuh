@@ -8,6 +8,7 @@
 // the projected spinor (h) determine the lower two, so only h (2 spins x 3
 // colours) is multiplied by the link and the lower half is rebuilt.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cstring>
 
@@ -295,6 +296,64 @@ __device__ __forceinline__ void block_reduce_t(T (&t)[NV], double (&v)[NV], doub
       for (int w = 0; w < nw; ++w) a += sh[w * NV + k];
       v[k] = a;
     }
+  }
+}
+
+// ---- generated shadow residual ------------------------------------------------------
+// The BiCGstab shadow vector r^ only enters inner products, and any r^ with
+// (r^, r_0) != 0 is admissible.  The solver generates r^ where it is used, so
+// it is never stored or read: per (seed, system, even site) a 32-bit hash h
+// (the "lowbias32" integer mixer, C. Wellons 2018: xorshift-multiply rounds
+// with multipliers 0x7feb352d and 0x846ca68b), then the 24 real parts of the
+// site's 12 components are the Weyl sequence h + m * 0x9e3779b9 (m = 0..23,
+// mod 2^32) read as signed 32-bit integers times 2^-31, i.e. values in [-1, 1)
+// with 24 or more significant bits.  Entries of that kind do not cancel
+// exactly against the few equal-magnitude entries of a sparse right-hand side
+// (a +-1 sign vector can: (r^, r_0) = 0 and the recurrence breaks down).
+// Integer arithmetic and one rounding make every kernel generate the same r^.
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ unsigned rhat_bits(unsigned seed, int sys, int i) {
+  return mix32(mix32(seed + (unsigned)sys) + (unsigned)i);
+}
+template <class C>
+__device__ __forceinline__ C rhat_comp(unsigned h, int k) {
+  const int ur = (int)(h + (unsigned)(2 * k) * 0x9e3779b9u);
+  const int ui = (int)(h + (unsigned)(2 * k + 1) * 0x9e3779b9u);
+  if constexpr (std::is_same<C, double2>::value) {
+    return make_double2((double)ur * 0x1p-31, (double)ui * 0x1p-31);
+  } else {
+    return make_float2(__int2float_rn(ur) * 0x1p-31f, __int2float_rn(ui) * 0x1p-31f);
+  }
+}
+// the 12 components of r^ at site i of system sys (from memory when seed == 0)
+template <class S, class C>
+__device__ __forceinline__ void ld_rhat(unsigned seed, int sys, const S* base, long long n, long long i,
+                                        C (&w)[12]) {
+  if (seed) {
+    const unsigned h = rhat_bits(seed, sys, (int)i);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = rhat_comp<C>(h, k);
+  } else {
+    ld_site<12>(base, n, i, w);
+  }
+}
+// components 2q, 2q + 1 of r^
+template <class S, class C>
+__device__ __forceinline__ void ld_rhat_pair(unsigned seed, int sys, const S* base, long long n,
+                                             long long i, int q, C& w0, C& w1) {
+  if (seed) {
+    const unsigned h = rhat_bits(seed, sys, (int)i);
+    w0 = rhat_comp<C>(h, 2 * q);
+    w1 = rhat_comp<C>(h, 2 * q + 1);
+  } else {
+    ld_pair(base + ((long long)q * n + i) * 2, w0, w1);
   }
 }
 

@@ -118,7 +118,7 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     if (live) {
       const S* q = (const S*)a.dotq + (p ? bd.off[1] : bd.off[0])[sys];
       C wv[12];
-      ld_site<12>(q, n_out, i, wv);
+      ld_rhat(a.rhat_seed, sys, q, n_out, i, wv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const C w = wv[k];
@@ -164,7 +164,7 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     if (live) {
       const long long oq = (p ? bd.off[1] : bd.off[0])[sys];
       C wv[12], sv[12];
-      ld_site<12>((const S*)a.dotq + oq, n_out, i, wv);
+      ld_rhat(a.rhat_seed, sys, (const S*)a.dotq + oq, n_out, i, wv);
       ld_site<12>((const S*)a.s1 + oq, n_out, i, sv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -296,7 +296,7 @@ __device__ __forceinline__ void hop_unit_r(const BatchDev& bd, const HopArgs& a,
       T tt[2] = {0, 0};
       if (live) {
         C wv[12];
-        ld_site<12>((const S*)a.dotq + oo[q], n_out, i, wv);
+        ld_rhat(a.rhat_seed, it.x * bd.nrhs + g * R + q, (const S*)a.dotq + oo[q], n_out, i, wv);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const C w = wv[k];
@@ -338,7 +338,7 @@ __device__ __forceinline__ void hop_unit_r(const BatchDev& bd, const HopArgs& a,
       T tt[2] = {0, 0};
       if (live) {
         C wv[12], sv[12];
-        ld_site<12>((const S*)a.dotq + oo[q], n_out, i, wv);
+        ld_rhat(a.rhat_seed, it.x * bd.nrhs + g * R + q, (const S*)a.dotq + oo[q], n_out, i, wv);
         ld_site<12>((const S*)a.s1 + oo[q], n_out, i, sv);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -469,7 +469,7 @@ __device__ __forceinline__ void hop_unit_split(const BatchDev& bd, const HopArgs
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         C w0, w1;
-        ld_pair(qv + ((long long)(q0 + q) * n_out + i) * 2, w0, w1);
+        ld_rhat_pair(a.rhat_seed, sys, qv, n_out, i, q0 + q, w0, w1);
         const C w[2] = {w0, w1};
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -521,7 +521,7 @@ __device__ __forceinline__ void hop_unit_split(const BatchDev& bd, const HopArgs
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         C w0, w1, s0, s1v;
-        ld_pair((const S*)a.dotq + oq + ((long long)(q0 + q) * n_out + i) * 2, w0, w1);
+        ld_rhat_pair(a.rhat_seed, sys, (const S*)a.dotq + oq, n_out, i, q0 + q, w0, w1);
         ld_pair((const S*)a.s1 + oq + ((long long)(q0 + q) * n_out + i) * 2, s0, s1v);
         tt[0] = fma(w0.x, s0.x, fma(w0.y, s0.y, tt[0]));
         tt[1] = fma(w0.x, s0.y, fma(-w0.y, s0.x, tt[1]));
@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
           const long long e = oo + ((long long)q * n_out + i) * 2;
           C sv[2], rv[2], ov[2];
           ld_pair((const S*)a.s1 + e, sv[0], sv[1]);
-          ld_pair((const S*)a.dotq + e, rv[0], rv[1]);
+          ld_rhat_pair(a.rhat_seed, sysk[k], (const S*)a.dotq + oo, n_out, i, q, rv[0], rv[1]);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             ov[h] = scale(acc[k][2 * q + h], bsc);
@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
       st_site<12>((S*)a.out + oo, n_out, i, out);
       if (a.dotq) {
         C wv[12];
-        ld_site<12>((const S*)a.dotq + oo, n_out, i, wv);
+        ld_rhat(a.rhat_seed, sysk[k], (const S*)a.dotq + oo, n_out, i, wv);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
           tq[k][0] = fma(wv[c].x, out[c].x, fma(wv[c].y, out[c].y, tq[k][0]));
