@@ -93,7 +93,7 @@ typedef struct {
   double inner_tol;    /* relative reduction per inner solve (mixed only), e.g. 1e-5 */
   int max_outer;       /* defect-correction cycles cap (mixed only) */
   int check_every;     /* iterations between host convergence checks (>= 1) */
-  int flags;           /* DD_SOLVE_GRAPH | DD_SOLVE_AUTOTUNE, or 0 */
+  int flags;           /* DD_SOLVE_* below, or-ed, or 0 */
 } dd_solve_params;
 
 /* dd_solve_params.flags */
@@ -104,6 +104,9 @@ typedef struct {
                                 keep the fastest for that batch */
 #define DD_SOLVE_NET_GUESS 4 /* framed-block batches start from x0 = N(b), the network set
                                 with dd_set_net (ignored when none is set) */
+#define DD_SOLVE_PIPELINE 8  /* page-locked host b and x: always split the blocks into
+                                chunks whose host<->device copies overlap the solves of
+                                the other chunks (done anyway from 256 MB of b) */
 
 typedef struct {
   int systems;         /* number of (block, rhs) systems solved */
@@ -169,9 +172,13 @@ dd_status dd_apply_D_block(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk
 /* ---- batched block solves (paper Sec. 3, D_Omega^-1, D_Phi^-1, D_Lambda1^-1)
  * x = D_X^{-1} b for every (block, rhs) pair, with even-odd (site parity)
  * preconditioning and BiCGstab; plain FP64, or an FP32/BF16 inner solve with
- * FP64 defect correction (FP64 residuals, norms and updates).  Layout as for
- * dd_apply_D_block.  Synchronises `stream` (the host polls convergence).
- * Returns DD_ENOCONV (with stats filled) if some system missed params->tol. */
+ * defect correction whose b, x, r, residual stencil and updates are kept in
+ * double-float (two FP32 numbers, about 44 significant bits).  Layout as for
+ * dd_apply_D_block; b and x may be device or host memory (host buffers are
+ * copied; page-locked ones of 256 MB or more, or with DD_SOLVE_PIPELINE, in
+ * chunks of blocks that overlap the copies with the solves).  Synchronises
+ * `stream` (the host polls convergence).  Returns DD_ENOCONV (with stats
+ * filled) if some system missed params->tol. */
 dd_status dd_solve_blocks(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
                           int nrhs, const double* b, double* x,
                           const dd_solve_params* params, dd_solve_stats* stats,

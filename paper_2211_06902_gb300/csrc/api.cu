@@ -86,6 +86,91 @@ static dd_status unstage(dd_ctx* c, double* out, size_t bytes, const Staged& sg,
   return DD_OK;
 }
 
+// Host-buffer solve in up to four chunks of consecutive blocks (each a
+// contiguous byte range of the caller layout).  All host-to-device copies are
+// queued at once on one copy stream; chunk k is solved once its copy has
+// landed, and its result goes back on a second copy stream while chunk k + 1
+// is solved, so only the first copy in and the last copy out are not hidden.
+static dd_status solve_pipelined(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs,
+                                 const double* bvec, double* x, size_t ub, const dd_solve_params* prm,
+                                 dd_solve_stats* stats, cudaStream_t s) {
+  dd_status e;
+  const int K = (int)std::max<size_t>(2, std::min<size_t>({4, (size_t)nblk, ub / (64ULL << 20)}));
+  void *din, *dout;
+  if ((e = workspace(c, 30, ub, &din)) != DD_OK || (e = workspace(c, 31, ub, &dout)) != DD_OK) return e;
+  if (!c->copy_in) DD_CUDA(c, cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking));
+  if (!c->copy_out) DD_CUDA(c, cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
+  // (batches are looked up again right before their solve: the batch cache may
+  // drop entries when it grows, so no pointer is kept across lookups)
+  std::vector<int> j0(K + 1);
+  std::vector<size_t> off(K + 1, 0);
+  for (int k = 0; k <= K; ++k) j0[k] = (int)((long long)nblk * k / K);
+  for (int k = 0; k < K; ++k) {
+    Batch* bk;
+    if ((e = get_batch(c, kind, ids + j0[k], j0[k + 1] - j0[k], nrhs, &bk)) != DD_OK) return e;
+    off[k + 1] = off[k] + 16ULL * bk->user_tot;
+  }
+  if (off[K] != ub) return fail(c, DD_EINVAL, "internal: chunk sizes do not add up");
+  std::vector<cudaEvent_t> ev(2 * K, nullptr);
+  for (auto& v : ev) DD_CUDA(c, cudaEventCreateWithFlags(&v, cudaEventDisableTiming));
+  // the copy stream must not start before work the caller queued on s
+  cudaEvent_t start = nullptr;
+  DD_CUDA(c, cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  DD_CUDA(c, cudaEventRecord(start, s));
+  DD_CUDA(c, cudaStreamWaitEvent(c->copy_in, start, 0));
+  for (int k = 0; k < K; ++k) {
+    DD_CUDA(c, cudaMemcpyAsync((char*)din + off[k], (const char*)bvec + off[k], off[k + 1] - off[k],
+                               cudaMemcpyHostToDevice, c->copy_in));
+    DD_CUDA(c, cudaEventRecord(ev[k], c->copy_in));
+  }
+  dd_solve_stats tot{};
+  dd_status rs = DD_OK;
+  double seconds = 0.0;
+  for (int k = 0; k < K && (rs == DD_OK || rs == DD_ENOCONV); ++k) {
+    DD_CUDA(c, cudaStreamWaitEvent(s, ev[k], 0));
+    Batch* bk;
+    if ((e = get_batch(c, kind, ids + j0[k], j0[k + 1] - j0[k], nrhs, &bk)) != DD_OK) {
+      rs = e;
+      break;
+    }
+    dd_solve_stats st{};
+    dd_status r = solve_batch(c, *bk, (const double*)((char*)din + off[k]), (double*)((char*)dout + off[k]),
+                              prm, &st, s, true);
+    if (r != DD_OK && r != DD_ENOCONV) {
+      rs = r;
+      break;
+    }
+    if (r == DD_ENOCONV) rs = DD_ENOCONV;
+    DD_CUDA(c, cudaEventRecord(ev[K + k], s));
+    DD_CUDA(c, cudaStreamWaitEvent(c->copy_out, ev[K + k], 0));
+    DD_CUDA(c, cudaMemcpyAsync((char*)x + off[k], (char*)dout + off[k], off[k + 1] - off[k],
+                               cudaMemcpyDeviceToHost, c->copy_out));
+    tot.systems += st.systems;
+    tot.converged += st.converged;
+    tot.max_iters = std::max(tot.max_iters, st.max_iters);
+    tot.outer_cycles = std::max(tot.outer_cycles, st.outer_cycles);
+    tot.max_relres = std::max(tot.max_relres, st.max_relres);
+    tot.hop_variant = st.hop_variant;
+    seconds += st.seconds;
+  }
+  // every copy has finished before the caller may touch b or x again
+  cudaStreamSynchronize(c->copy_in);
+  cudaStreamSynchronize(c->copy_out);
+  for (auto& v : ev) cudaEventDestroy(v);
+  cudaEventDestroy(start);
+  tot.seconds = seconds;
+  if (stats) *stats = tot;
+  c->last_stats = tot;
+  if (rs != DD_OK && rs != DD_ENOCONV) return rs;
+  if (rs == DD_ENOCONV) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%d of %d systems above tolerance (max relres %.3e)", tot.systems - tot.converged,
+             tot.systems, tot.max_relres);
+    return fail(c, DD_ENOCONV, buf);
+  }
+  return DD_OK;
+}
+
 }  // namespace dd
 
 using namespace dd;
@@ -144,6 +229,9 @@ dd_status dd_solve_blocks(dd_ctx* c, dd_domain kind, const int* ids, int nblk, i
   dd_status e = get_batch(c, kind, ids, nblk, nrhs, &b);
   if (e != DD_OK) return e;
   size_t ub = 16ULL * b->user_tot;
+  if ((kind == DD_DOMAIN_OMEGA || kind == DD_DOMAIN_PHI) && nblk >= 2 && is_pinned_host_ptr(bvec) &&
+      is_pinned_host_ptr(x) && ((prm->flags & DD_SOLVE_PIPELINE) || ub >= (256ULL << 20)))
+    return solve_pipelined(c, kind, ids, nblk, nrhs, bvec, x, ub, prm, stats, s);
   Staged sg;
   if ((e = stage(c, bvec, x, ub, 30, 31, sg, s)) != DD_OK) return e;
   dd_status rs = solve_batch(c, *b, sg.in, sg.out, prm, stats, s, true);

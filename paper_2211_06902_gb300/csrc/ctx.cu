@@ -48,6 +48,15 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool is_pinned_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 size_t prec_bytes(dd_prec p) { return (p == DD_F64 || p == DD_DF64) ? 16 : (p == DD_F32 ? 8 : 4); }
 
 Batch::~Batch() {
@@ -621,6 +630,8 @@ dd_status dd_destroy(dd_ctx* c) {
   free_workspace(c);
   free_plan(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->copy_in) cudaStreamDestroy(c->copy_in);
+  if (c->copy_out) cudaStreamDestroy(c->copy_out);
   c->batches.clear();
   for (auto& r : c->trec) {
     cudaEventDestroy(r.a);

@@ -160,6 +160,7 @@ struct dd_ctx {
   dd_solve_stats last_stats{};   // statistics of the last batched solve
   dd_net* net = nullptr;         // learned initial guess for block solves (not owned)
   cudaStream_t capture_stream = nullptr;   // private stream for CUDA-graph capture
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;   // host<->device copies of pipelined solves
   int forced_variant[3] = {-1, -1, -1};    // manual stencil launch variant per precision
 };
 
@@ -191,6 +192,7 @@ void dfree(void* p);
 
 // Host-or-device pointer helper: returns true when p is device-accessible memory.
 bool is_device_ptr(const void* p);
+bool is_pinned_host_ptr(const void* p);   // page-locked (registered or cudaHostAlloc) host memory
 
 // stencil launches (stencil.cu)
 struct HopArgs {

@@ -158,3 +158,41 @@ def test_graph_and_autotune_give_identical_solutions():
             res = f - apply_D_restricted(U, xf, 0.12, geo.omega_mask[blk])
             assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
             off += n
+
+
+@pytest.mark.parametrize("inner", ["f32", "f64"])
+def test_pipelined_host_buffers(inner):
+    """Page-locked host b and x with DD_SOLVE_PIPELINE: the blocks are solved in
+    chunks whose copies overlap the other chunks' solves.  Uneven blocks (the
+    chunks differ in size and byte offset); every system must meet the
+    tolerance against the oracle's operator, and agree with the same batch
+    solved from device buffers in one piece."""
+    torch = pytest.importorskip("torch")
+    L = (12, 8, 8, 10)
+    cores = [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]]
+    U, ctx, info, geo = make_case(L, 0.12, 0.5, 7, cores)
+    ids = [0, 3, 5, 6, 9, 11, 12, 15]
+    sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
+    nrhs = 3
+    tot = sum(len(s) for s in sites)
+    bflat = synth.complex_gaussian(9, synth.TAG_RHS, (nrhs * tot, 12))
+    bh = torch.from_numpy(bflat.view(np.float64).copy()).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    prm = dd4d.params(1e-10, inner_prec=inner, pipeline=True)
+    st = ctx.solve_blocks("omega", ids, nrhs, bh, xh, prm)
+    assert st["status"] == dd4d.DD_OK and st["systems"] == len(ids) * nrhs, st
+    assert st["converged"] == len(ids) * nrhs and st["max_relres"] <= 1e-10
+    bd = bh.cuda()
+    xd = torch.zeros_like(bd)
+    ctx.solve_blocks("omega", ids, nrhs, bd, xd, dd4d.params(1e-10, inner_prec=inner))
+    x = xh.numpy().view(np.complex128)
+    assert relerr(x, xd.cpu().numpy().view(np.complex128)) < 1e-8
+    off = 0
+    for k, blk in enumerate(ids):
+        n = len(sites[k])
+        for r in range(nrhs):
+            f = to_field(L, sites[k], bflat[off:off + n])
+            xf = to_field(L, sites[k], x[off:off + n])
+            res = f - apply_D_restricted(U, xf, 0.12, geo.omega_mask[blk])
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
+            off += n
