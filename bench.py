@@ -126,7 +126,7 @@ def measured_peaks():
 
 def traffic_record():
     """ncu DRAM bytes per launch of the FP32 hop kernel (profiles/), or None."""
-    path = os.path.join(ROOT, "profiles", "hop_f32_traffic.json")
+    path = os.path.join(ROOT, "profiles", "hop_lb_f32_traffic.json")
     try:
         with open(path) as f:
             return json.load(f)
@@ -304,14 +304,19 @@ def run_ours(args):
     hv = stats["hop_variant"]
     if tr and tr.get("variant_name") != dd4d.hop_variant_name("f32", hv):
         tr = None
+    alg_per_launch = hop32_bytes / hop32_n if hop32_n else None
+    # ncu DRAM bytes of fully active launches, scaled to the timed region's
+    # average launch by its algorithmic bytes (systems that converged skip)
+    traffic = tr["dram_over_algorithmic"] * alg_per_launch if (tr and alg_per_launch) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": tr.get("bytes_per_launch") if tr else None,
+                "traffic": traffic,
+                "traffic_dram_over_algorithmic": tr["dram_over_algorithmic"] if tr else None,
                 "kernel": "FP32 even-odd hop inside the inner BiCGstab, autotuned variant %d: %s"
                           % (hv, dd4d.hop_variant_name("f32", hv)),
                 "peak_kind": peak_kind, "launches": hop32_n,
                 "avg_launch_ms": hop32_ms / hop32_n if hop32_n else None,
-                "algorithmic_bytes_per_launch": hop32_bytes / hop32_n if hop32_n else None}
+                "algorithmic_bytes_per_launch": alg_per_launch}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
