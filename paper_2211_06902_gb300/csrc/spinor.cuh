@@ -172,9 +172,9 @@ template <class C> __device__ __forceinline__ C cmulmi(C a) { C r; r.x = a.y; r.
 // ---- one hop direction ------------------------------------------------------------
 // psi: the neighbour's 12 components; U: 9 link entries (row-major a*3+b);
 // FWD: (1 - gamma_mu) U psi; otherwise (1 + gamma_mu) U^+ psi; accumulated into acc.
+// spin projection of a neighbour spinor onto the 2-spin half spinor of hop (MU, FWD)
 template <int MU, bool FWD, class C>
-__device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const C (&U)[9]) {
-  C h[2][3];
+__device__ __forceinline__ void hop_project(const C (&psi)[12], C (&h)[2][3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const C p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
@@ -192,6 +192,10 @@ __device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const 
       h[1][c] = FWD ? csubi(p1, p3) : caddi(p1, p3);
     }
   }
+}
+// U (forward) or U^+ (backward) times the half spinor, rebuilt into all four spins of acc
+template <int MU, bool FWD, class C>
+__device__ __forceinline__ void hop_apply(C (&acc)[12], const C (&h)[2][3], const C (&U)[9]) {
   C uh[2][3];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
@@ -224,6 +228,12 @@ __device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const 
       acc[9 + a] = FWD ? caddi(acc[9 + a], uh[1][a]) : csubi(acc[9 + a], uh[1][a]);
     }
   }
+}
+template <int MU, bool FWD, class C>
+__device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const C (&U)[9]) {
+  C h[2][3];
+  hop_project<MU, FWD>(psi, h);
+  hop_apply<MU, FWD>(acc, h, U);
 }
 
 // ---- scalar helpers of the stencil epilogue (overloaded for double-float) ---------

@@ -1167,14 +1167,14 @@ int dd_hop_variants(dd_prec prec) { return dd::hop_variant_count(prec); }
 
 const char* dd_hop_variant_name(dd_prec prec, int v) {
   if (prec != DD_F64 && prec != DD_F32 && prec != DD_BF16) return nullptr;
-  if (v < 0 || v >= dd::hop_variant_count(prec)) return nullptr;
-  static char names[3][16][112];
+  if (v < 0 || v >= dd::hop_variant_count(prec) || v >= 32) return nullptr;
+  static char names[3][32][112];
   static bool made = false;
   if (!made) {
     const dd_prec ps[3] = {DD_F64, DD_F32, DD_BF16};
     const char* ty[3] = {"double2", "float2", "bfloat162"};
     for (int k = 0; k < 3; ++k)
-      for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 16; ++u) {
+      for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
         if (h.r < 0)
           snprintf(names[k][u], sizeof names[k][u],

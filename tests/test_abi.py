@@ -43,3 +43,13 @@ def test_strerror_and_roots_without_gpu(lib):
     assert np.allclose(u, np.cos(2 * np.pi * k / 9) + 1j * np.sqrt(0.75) * np.sin(2 * np.pi * k / 9))
     with pytest.raises(dd4d.DDError):
         dd4d.roots(5, 0.5)
+
+
+def test_hop_variant_names_distinct():
+    """Every compiled stencil launch form has its own description, per precision."""
+    for prec in ("f64", "f32", "bf16"):
+        n = dd4d.lib().dd_hop_variants(dd4d.PREC[prec])
+        names = [dd4d.hop_variant_name(prec, v) for v in range(n)]
+        assert all(names), (prec, names)
+        assert len(set(names)) == n, (prec, names)
+        assert dd4d.hop_variant_name(prec, n) is None and dd4d.hop_variant_name(prec, -1) is None
