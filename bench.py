@@ -296,6 +296,9 @@ def run_ours(args):
         action = action_rate(dd4d, synth, torch)
         if not args.no_uneven:
             uneven = uneven_action_rate(dd4d, synth, torch)
+    stencil = None
+    if rank == 0 and not args.no_stencil:
+        stencil = stencil_rates(dd4d, synth, torch, ctx, ids, b, n_om)
 
     peak, peak_kind = measured_peaks()
     achieved = hop32_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
@@ -338,6 +341,7 @@ def run_ours(args):
         "action": action,
         "action_uneven": uneven,
         "learned_guess": learned,
+        "stencil": stencil,
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline_entry(U) if world == 1 else None
@@ -384,6 +388,40 @@ def learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms_plain_guess):
             "training": train, "ms_per_step_with_net": ms, "ms_per_step_without": ms_plain_guess,
             "value_with_net": units / (ms * 1e-3), "max_iters_with_net": st["max_iters"],
             "max_relres_with_net": st["max_relres"], "status": st["status"]}
+
+
+def stencil_rates(dd4d, synth, torch, ctx, ids, b12, n_om):
+    """D_X on the config-2 framed blocks (dd_apply_D_block) per storage precision
+    and rhs count: the best launch form's algorithmic bandwidth (bytes of the
+    formula in the library's accounting / event-timed hop launches) and its
+    fraction of the measured HBM peak."""
+    peak, _ = measured_peaks()
+    out = {"workload": "32^4, 256 framed blocks of 9^4, even-odd hop launches of D_X (2 per apply)"}
+    b1 = torch.from_numpy(synth.complex_gaussian(4, synth.TAG_RHS, (len(ids), 1, n_om, 12))
+                          .view(np.float64).copy()).to(b12.device)
+    for prec, which in (("f64", 0), ("f32", 1), ("bf16", 2)):
+        for nrhs, inp in ((1, b1), (12, b12)):
+            o = torch.empty_like(inp)
+            best = None
+            for v in range(dd4d.lib().dd_hop_variants(dd4d.PREC[prec])):
+                ctx.set_hop_variant(prec, v)
+                ctx.apply_D_block("omega", ids, nrhs, inp, o, prec)
+                torch.cuda.synchronize()
+                ctx.timing_enable(True)
+                ctx.timing_get(which)
+                for _ in range(3):
+                    ctx.apply_D_block("omega", ids, nrhs, inp, o, prec)
+                ms, n, by = ctx.timing_get(which)
+                ctx.timing_enable(False)
+                gbs = by / (ms * 1e-3) / 1e9
+                if best is None or gbs > best[0]:
+                    best = (gbs, ms / n, v)
+            ctx.set_hop_variant(prec, -1)
+            del o
+            out["%s_%drhs" % (prec, nrhs)] = {
+                "GB_s": best[0], "frac_of_hbm": best[0] / peak if peak else None,
+                "ms_per_launch": best[1], "variant": dd4d.hop_variant_name(prec, best[2])}
+    return out
 
 
 def action_rate(dd4d, synth, torch, evals=5):
@@ -470,6 +508,8 @@ def main():
                     help="omit the 64x32^3 uneven-block action measurement")
     ap.add_argument("--no-learned", action="store_true",
                     help="omit the learned-initial-guess A/B measurement")
+    ap.add_argument("--no-stencil", action="store_true",
+                    help="omit the per-precision stencil bandwidth measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

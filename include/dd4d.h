@@ -135,6 +135,19 @@ dd_status dd_set_kappa(dd_ctx* ctx, double kappa);
  * operator.  Rebuilds every gathered per-domain copy.  Synchronous. */
 dd_status dd_gauge_upload(dd_ctx* ctx, const double* U_host);
 
+/* Synthetic links drawn on the device (the paper's links U_mu(x) in SU(3),
+ * Sec. 1; the synthetic recipe stands in for its Monte Carlo ensembles):
+ * U = exp(i eps H), H = sum_a h_a lambda_a / 2 over the Gell-Mann matrices,
+ * h_a ~ N(0, 1) from the counter-based SplitMix64 stream of (seed, tag 1)
+ * with Box-Muller normals, link l = 4 site + mu taking draws 8l .. 8l+7.
+ * Bit-for-bit the same draws as the seeded host generator; the exponential
+ * agrees with an eigen-decomposition to FP64 rounding.  Synchronous. */
+dd_status dd_gauge_random(dd_ctx* ctx, double eps, unsigned long long seed);
+
+/* Copy of the current links into a host buffer of the dd_gauge_upload layout
+ * (time-boundary sign not applied).  Synchronous. */
+dd_status dd_gauge_download(dd_ctx* ctx, double* U_host);
+
 /* ---- geometry (paper Sec. 2) ------------------------------------------
  * Per direction mu a sorted list of core intervals [lo, hi] (inclusive,
  * 0 <= lo <= hi < L_mu) separated by at least one frame site (periodic);
@@ -270,6 +283,14 @@ dd_status dd_net_create(dd_ctx* ctx, int nlayers, const int* channels, const dou
                         dd_net** net);
 dd_status dd_net_destroy(dd_net* net);
 dd_status dd_net_weights(const dd_net* net, double* weights);  /* FP32 masters -> host */
+/* Network to / from a file (the learned block preconditioner of the rows
+ * above; the paper has no learned component in its method): layer channels,
+ * FP32 master weights and the Adam state, so training resumes exactly.
+ * dd_net_save returns DD_EINVAL if the file cannot be written; dd_net_load
+ * returns DD_EINVAL (text in dd_last_error) for a missing or foreign file and
+ * creates the network on ctx's device like dd_net_create. */
+dd_status dd_net_save(const dd_net* net, const char* path);
+dd_status dd_net_load(dd_ctx* ctx, const char* path, dd_net** net);
 /* out = N(in) on framed blocks ids (device pointers, caller layout of dd_solve_blocks). */
 dd_status dd_net_apply(dd_ctx* ctx, dd_net* net, const int* ids, int nblk, int nrhs,
                        const double* in, double* out, void* stream);

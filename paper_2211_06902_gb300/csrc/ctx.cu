@@ -419,6 +419,22 @@ dd_status ensure_links(dd_ctx* c, int i, dd_prec prec) {
   return DD_OK;
 }
 
+// after new links in d_U: fold the time-boundary sign, mark every gathered
+// per-domain copy stale
+dd_status gauge_finish(dd_ctx* c) {
+  const int spatial = c->V / c->L[0];
+  if (c->time_bc != 1) {
+    const long long n = 9LL * spatial;
+    DD_COUNT_LAUNCH(), k_fold_time_sign<<<(n + 255) / 256, 256>>>(c->d_U, c->V, c->L[0], spatial, c->time_bc);
+    DD_CUDA(c, cudaGetLastError());
+  }
+  DD_CUDA(c, cudaDeviceSynchronize());
+  for (auto& in : c->inst) in.links_ready = false;
+  c->gauge_ready = true;
+  c->inst_dirty = true;
+  return DD_OK;
+}
+
 dd_status check_device_error(dd_ctx* c, cudaStream_t s) {
   int h = 0;
   DD_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -651,17 +667,7 @@ dd_status dd_gauge_upload(dd_ctx* c, const double* U) {
   if (!c || !U) return fail(c, DD_EINVAL, "null argument");
   size_t bytes = sizeof(double2) * 36ULL * c->V;
   DD_CUDA(c, cudaMemcpy(c->d_U, U, bytes, cudaMemcpyDefault));
-  int spatial = c->V / c->L[0];
-  if (c->time_bc != 1) {
-    long long n = 9LL * spatial;
-    DD_COUNT_LAUNCH(), k_fold_time_sign<<<(n + 255) / 256, 256>>>(c->d_U, c->V, c->L[0], spatial, c->time_bc);
-    DD_CUDA(c, cudaGetLastError());
-  }
-  DD_CUDA(c, cudaDeviceSynchronize());
-  for (auto& in : c->inst) in.links_ready = false;
-  c->gauge_ready = true;
-  c->inst_dirty = true;
-  return DD_OK;
+  return gauge_finish(c);
 }
 
 dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, const int* core_hi,

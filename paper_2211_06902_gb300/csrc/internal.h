@@ -219,6 +219,8 @@ int hop_variant_count(dd_prec prec);
 void hop_bundle_prepare();
 // reads and clears the device error word: DD_ETIMEOUT if a bounded wait gave up
 dd_status check_device_error(dd_ctx* c, cudaStream_t s);
+// after new links in d_U (ctx.cu): time sign, stale per-domain copies
+dd_status gauge_finish(dd_ctx* c);
 
 // layout conversions (stencil.cu)
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,

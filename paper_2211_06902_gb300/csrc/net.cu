@@ -1,3 +1,6 @@
+#include <cstdint>
+#include <string>
+#include <cstdio>
 // Learned block preconditioner: a gauge-covariant network of linear
 // parallel-transport convolutions on the framed blocks Omega0^a, trained on
 // the GPU on pairs (b, D_Omega^{-1} b) produced by the library's own solver,
@@ -538,6 +541,62 @@ dd_status dd_net_create(dd_ctx* c, int nlayers, const int* channels, const doubl
     return st;
   }
   *out = n;
+  return DD_OK;
+}
+
+// File format (little-endian, as written by this library on its host):
+// "DD4DNET1", int32 layers, int32 channels[layers + 1], int64 Adam step,
+// then FP32 masters, Adam first and second moments (2 * complex count floats each).
+static const char kNetMagic[8] = {'D', 'D', '4', 'D', 'N', 'E', 'T', '1'};
+
+dd_status dd_net_save(const dd_net* n, const char* path) {
+  if (!n || !path) return DD_EINVAL;
+  FILE* f = fopen(path, "wb");
+  if (!f) return DD_EINVAL;
+  const int32_t nl = n->nl;
+  int32_t ch[8];
+  for (int l = 0; l <= nl; ++l) ch[l] = n->ch[l];
+  const int64_t t = n->adam_t;
+  bool ok = fwrite(kNetMagic, 1, 8, f) == 8 && fwrite(&nl, 4, 1, f) == 1 &&
+            fwrite(ch, 4, nl + 1, f) == (size_t)(nl + 1) && fwrite(&t, 8, 1, f) == 1;
+  const size_t m = n->master.size();
+  ok = ok && fwrite(n->master.data(), 4, m, f) == m && fwrite(n->m.data(), 4, m, f) == m &&
+       fwrite(n->v.data(), 4, m, f) == m;
+  ok = (fclose(f) == 0) && ok;
+  return ok ? DD_OK : DD_EINVAL;
+}
+
+dd_status dd_net_load(dd_ctx* c, const char* path, dd_net** out) {
+  if (!c || !path || !out) return fail(c, DD_EINVAL, "null argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, DD_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t nl = 0;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kNetMagic, 8) == 0 && fread(&nl, 4, 1, f) == 1 &&
+            nl >= 1 && nl <= 7;
+  int32_t ch[8] = {0};
+  int64_t t = 0;
+  ok = ok && fread(ch, 4, nl + 1, f) == (size_t)(nl + 1) && fread(&t, 8, 1, f) == 1 && t >= 0;
+  long long tot = 0;
+  for (int l = 0; ok && l < nl; ++l) {
+    if (ch[l] < 1 || ch[l] > 64 || ch[l + 1] < 1 || ch[l + 1] > 64) ok = false;
+    else tot += 9LL * ch[l] * ch[l + 1];
+  }
+  std::vector<float> w(ok ? 2 * tot : 0), m1(w.size()), m2(w.size());
+  ok = ok && fread(w.data(), 4, w.size(), f) == w.size() && fread(m1.data(), 4, w.size(), f) == w.size() &&
+       fread(m2.data(), 4, w.size(), f) == w.size();
+  fclose(f);
+  if (!ok) return fail(c, DD_EINVAL, std::string("not a network file of this library: ") + path);
+  std::vector<double> wd(w.begin(), w.end());     // FP32 values are exact in FP64
+  int chi[8];
+  for (int l = 0; l <= nl; ++l) chi[l] = ch[l];
+  dd_status st = dd_net_create(c, nl, chi, wd.data(), out);
+  if (st != DD_OK) return st;
+  (*out)->m = m1;
+  (*out)->v = m2;
+  (*out)->adam_t = t;
+  (*out)->dirty = true;
   return DD_OK;
 }
 

@@ -70,6 +70,8 @@ def lib():
             "dd_last_error": [vp],
             "dd_set_kappa": [vp, C.c_double],
             "dd_gauge_upload": [vp, vp],
+            "dd_gauge_random": [vp, C.c_double, C.c_ulonglong],
+            "dd_gauge_download": [vp, vp],
             "dd_set_geometry": [vp, ip, ip, ip, C.POINTER(GeomInfo)],
             "dd_geom_sites": [vp, C.c_int, C.c_int, ip, ip],
             "dd_geom_block": [vp, C.c_int, ip, ip, ip, ip],
@@ -94,6 +96,8 @@ def lib():
             "dd_set_net": [vp, vp],
             "dd_set_hop_variant": [vp, C.c_int, C.c_int],
             "dd_hop_variants": [C.c_int],
+            "dd_net_save": [vp, C.c_char_p],
+            "dd_net_load": [vp, C.c_char_p, C.POINTER(vp)],
             "dd_hop_variant_name": [C.c_int, C.c_int],
             "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
         }
@@ -109,11 +113,11 @@ def lib():
 def exported_symbols():
     """Names of the C ABI entry points the binding expects."""
     return ["dd_create", "dd_destroy", "dd_strerror", "dd_last_error", "dd_set_kappa",
-            "dd_gauge_upload", "dd_set_geometry", "dd_geom_sites", "dd_geom_block",
+            "dd_gauge_upload", "dd_gauge_random", "dd_gauge_download", "dd_set_geometry", "dd_geom_sites", "dd_geom_block",
             "dd_apply_D_block", "dd_solve_blocks", "dd_apply_w", "dd_multiboson_action",
             "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count", "dd_logdet_check",
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
-            "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net",
+            "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc"]
 
@@ -231,6 +235,16 @@ class Context:
         if U.shape != self.L + (4, 3, 3):
             raise ValueError("gauge field shape must be L + (4, 3, 3)")
         self._check(lib().dd_gauge_upload(self._h, C.c_void_p(U.ctypes.data)))
+
+    def gauge_random(self, eps, seed):
+        """Synthetic links exp(i eps H) drawn on the device from the (seed, gauge) stream."""
+        self._check(lib().dd_gauge_random(self._h, float(eps), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def gauge_download(self):
+        """The current links, layout L + (4, 3, 3) complex128 (time-boundary sign not applied)."""
+        U = np.empty(self.L + (4, 3, 3), dtype=np.complex128)
+        self._check(lib().dd_gauge_download(self._h, C.c_void_p(U.ctypes.data)))
+        return U
 
     def set_geometry(self, cores):
         nc = (C.c_int * 4)(*[len(c) for c in cores])
@@ -363,6 +377,27 @@ class Net:
         if self._h:
             lib().dd_net_destroy(self._h)
             self._h = C.c_void_p()
+
+    def save(self, path):
+        """Channels, FP32 master weights and Adam state to `path`."""
+        st = lib().dd_net_save(self._h, os.fsencode(path))
+        if st:
+            raise DDError(st, "cannot write network file %s" % path)
+
+    @classmethod
+    def load(cls, ctx, path):
+        """A network read from `path` (written by save) on ctx's device."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self._h = C.c_void_p()
+        ctx._check(lib().dd_net_load(ctx._h, os.fsencode(path), C.byref(self._h)))
+        with open(path, "rb") as f:
+            head = f.read(12)
+            nl = int(np.frombuffer(head[8:12], dtype=np.int32)[0])
+            ch = np.frombuffer(f.read(4 * (nl + 1)), dtype=np.int32)
+        self.channels = tuple(int(c) for c in ch)
+        self.shapes = [(9, self.channels[l + 1], self.channels[l]) for l in range(nl)]
+        return self
 
     def __del__(self):
         try:

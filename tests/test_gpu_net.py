@@ -111,3 +111,38 @@ def test_training_and_initial_guess():
             res = f - apply_D_restricted(U, to_field(L, sites, x1[blk, r]), 0.13, geo.omega_mask[blk])
             assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
     net.detach()
+
+
+def test_save_and_load_resume_exactly(tmp_path):
+    """A saved network loads with the same weights and Adam state: it applies
+    identically and a further training step gives identical weights."""
+    torch = pytest.importorskip("torch")
+    U, ctx, info, geo = config1()
+    ids = list(range(4))
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    bt = torch.from_numpy(synth.complex_gaussian(9, synth.TAG_RHS, (len(ids), 2, n, 12))
+                          .view(np.float64).copy()).cuda()
+    net = dd4d.Net(ctx, onet.init_weights(5))
+    net.train(ids, 2, bt, steps=3, lr=3e-3)
+    path = tmp_path / "net.bin"
+    net.save(path)
+    other = dd4d.Net.load(ctx, path)
+    assert other.channels == net.channels
+    for a, b in zip(net.weights(), other.weights()):
+        assert np.array_equal(a, b)
+    b = torch.from_numpy(synth.complex_gaussian(10, synth.TAG_RHS, (len(ids), 2, n, 12))
+                         .view(np.float64).copy()).cuda()
+    ya, yb = torch.zeros_like(b), torch.zeros_like(b)
+    net.apply(ids, 2, b, ya)
+    other.apply(ids, 2, b, yb)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb) and float(ya.abs().max()) > 0
+    net.train(ids, 2, bt, steps=2, lr=3e-3)
+    other.train(ids, 2, bt, steps=2, lr=3e-3)
+    for a, b in zip(net.weights(), other.weights()):
+        assert np.array_equal(a, b)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a network")
+    with pytest.raises(dd4d.DDError) as e:
+        dd4d.Net.load(ctx, bad)
+    assert e.value.status == dd4d.DD_EINVAL
