@@ -193,6 +193,25 @@ class Oracle:
         W[np.ix_(comp_index(cs), comp_index(bsites))] = -G[rows_in_l1]
         return W
 
+    def heatbath(self, u, etas):
+        """Multi-boson fields by heat-bath (Sec. 4, after Eq. WW): the weight
+        exp(-|W_u chi|^2) is sampled exactly by chi = W_u^{-1} eta with eta a
+        complex Gaussian of density exp(-|eta|^2).  Definition written out: a
+        dense solve of (u - w) chi = eta on dPi for each root u_k and source
+        eta_k (fields on the full lattice, supported on dPi)."""
+        g = self.g
+        dpi = g.sites(g.dPi)
+        W = self.w_matrix()
+        n = W.shape[0]
+        out = []
+        for uk, eta in zip(u, etas):
+            e = eta.reshape(-1, 12)[dpi].reshape(-1)
+            chi = np.linalg.solve(uk * np.eye(n) - W, e)
+            f = np.zeros_like(eta).reshape(-1, 12)
+            f[dpi] = chi.reshape(-1, 12)
+            out.append(f.reshape(eta.shape))
+        return out
+
     def logdet_factors(self):
         """slogdet of D, W_1, D_{Lambda1}, D_{Omega0^a}, D_{Phi1^a} (dense LU)."""
         g = self.g

@@ -194,3 +194,24 @@ def test_iterative_solver_matches_direct_lu():
     xi, rel = bicgstab(lambda v: M @ v, b, 1e-13)
     assert rel < 1e-12
     assert np.linalg.norm(xi - xd) < 1e-11 * np.linalg.norm(xd)
+
+
+def test_heatbath_fields_reproduce_their_gaussian_sources():
+    """chi_k = W_{u_k}^{-1} eta_k (dense solve) makes the multi-boson action,
+    evaluated independently by the vector form of w, equal sum_k |eta_k|^2
+    (Sec. 4, Eqs. WW / MBaction); the fields live on dPi only; a plausible
+    mistake (solving with the conjugate roots) breaks the identity."""
+    U = synth.gauge_field(L44, 0.3, 1)
+    g = Decomposition(L44, uniform_cores(L44, 1, 1))
+    o = Oracle(U, 0.13, g)
+    u = field_roots(4, 0.5)
+    etas = [synth.complex_gaussian(3, 40 + k, L44 + (4, 3)) * g.dPi[..., None, None]
+            for k in range(len(u))]
+    chis = o.heatbath(u, etas)
+    S, _, _ = o.multiboson_action(u, chis)
+    ref = sum(float(np.vdot(e, e).real) for e in etas)
+    assert abs(S - ref) <= 1e-10 * ref
+    assert all(np.all(c[~g.dPi] == 0) for c in chis)
+    bad = o.heatbath(np.conj(u), etas)
+    S_bad, _, _ = o.multiboson_action(u, bad)
+    assert abs(S_bad - ref) > 1e-3 * ref
