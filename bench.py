@@ -291,9 +291,10 @@ def run_ours(args):
     del bh, xh
 
     # multi-boson action on the 8^4 lattice (16 blocks of 5^4, N = 4, 2 fields)
-    action = uneven = None
+    action = uneven = heatbath = None
     if rank == 0:
         action = action_rate(dd4d, synth, torch)
+        heatbath = heatbath_rate(dd4d, synth, torch)
         if not args.no_uneven:
             uneven = uneven_action_rate(dd4d, synth, torch)
     stencil = None
@@ -340,6 +341,7 @@ def run_ours(args):
                       "residual_hop_ms_in_mixed_step": hop64_ms / args.steps},
         "action": action,
         "action_uneven": uneven,
+        "heatbath": heatbath,
         "learned_guess": learned,
         "stencil": stencil,
     }
@@ -449,6 +451,35 @@ def action_rate(dd4d, synth, torch, evals=5):
             "workload": "8^4, kappa 0.13, eps 0.3, 16 blocks of 5^4 + frame in one batch, "
                         "N = 4 (2 fields), FP64 solves to 1e-10, CUDA graphs, autotuned",
             "S": S, "max_relres": stats["max_relres"]}
+
+
+def heatbath_rate(dd4d, synth, torch, reps=3):
+    """Multi-boson fields by heat-bath on the 8^4 lattice: chi_k = W_{u_k}^{-1} eta_k for
+    the N/2 = 4 fields of N = 8 (c = 0.5), checked by S_MB(chi) = sum |eta|^2."""
+    L = (8, 8, 8, 8)
+    c = dd4d.Context(L, 0.13)
+    c.gauge_random(0.3, 1)
+    c.set_geometry(cores_uniform(L, 3, 1))
+    dpi = c.geom_sites(dd4d.SET_DPI)
+    u = dd4d.roots(8, 0.5)
+    eta = synth.complex_gaussian(1, synth.TAG_CHI, (len(u), len(dpi), 12))
+    de = torch.from_numpy(eta.view(np.float64)).cuda()
+    dx = torch.zeros_like(de)
+    prm = dd4d.params(1e-11, inner_prec="f64", graph=True, autotune=True)
+    c.multiboson_heatbath(u, de, dx, tol=1e-10, prm=prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        st = c.multiboson_heatbath(u, de, dx, tol=1e-10, prm=prm)
+    dt = (time.perf_counter() - t0) / reps
+    S = c.multiboson_action(u, dx, prm)[0]
+    ref = float(np.vdot(eta, eta).real)
+    c.close()
+    return {"metric": "heat-bath field sets/s", "value": 1.0 / dt, "unit": "sets/s",
+            "workload": "8^4, kappa 0.13, eps 0.3 (links drawn on the device), 16 blocks of 5^4 + frame, "
+                        "N = 8 (4 fields), BiCGstab on dPi to 1e-10 over apply_w with FP64 solves to 1e-11",
+            "iterations": st["iterations"], "matvecs": st["matvecs"], "max_relres": st["max_relres"],
+            "action_identity_relerr": abs(S - ref) / ref}
 
 
 def uneven_action_rate(dd4d, synth, torch, evals=2):

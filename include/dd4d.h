@@ -230,6 +230,27 @@ dd_status dd_multiboson_action(dd_ctx* ctx, int n_f, const double* u, const doub
                                double* S, double* S_block, double* S_r,
                                const dd_solve_params* params, void* stream);
 
+/* ---- multi-boson fields by heat-bath (paper Sec. 4, the fields of Eq. WW)
+ * chi_k = W_{u_k}^{-1} eta_k for n_f fields, so that chi_k has the weight
+ * exp(-|W_{u_k} chi_k|^2) when eta_k is complex Gaussian with density
+ * exp(-|eta|^2).  u: 2*n_f doubles (re, im), no root zero; eta, chi: layout of
+ * dd_apply_w, device or host.  BiCGstab on dPi over all fields at once, each
+ * matvec one dd_apply_w batch (block and frame solves to params->tol), from
+ * chi = eta / u, until |eta - W_u chi| <= tol |eta| per field or maxiter
+ * iterations.  Returns DD_ENOCONV (stats filled) if a field missed tol.
+ * Synchronises. */
+typedef struct {
+  int iterations;      /* BiCGstab iterations run (all fields together) */
+  int matvecs;         /* dd_apply_w batches */
+  int converged;       /* fields with relative residual <= tol */
+  double max_relres;   /* largest |eta - W_u chi| / |eta| (recursive residual) */
+  double seconds;      /* device time of the call */
+} dd_heatbath_stats;
+dd_status dd_multiboson_heatbath(dd_ctx* ctx, int n_f, const double* u, const double* eta,
+                                 double* chi, double tol, int maxiter,
+                                 const dd_solve_params* params, dd_heatbath_stats* stats,
+                                 void* stream);
+
 /* ---- roots (paper Sec. 4) --------------------------------------------------
  * u_k = 1 - z_k = cos(2 pi k/(N+1)) + i sqrt(1-c^2) sin(2 pi k/(N+1)),
  * k = 1..N/2: the roots that carry the N/2 multi-boson fields (conjugates

@@ -10,6 +10,7 @@
 // and frame solves go through the batched solver; extraction and the FP64
 // reductions follow in fixed order (deterministic).
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "internal.h"
@@ -163,6 +164,55 @@ __global__ void k_action_blocks(const int* __restrict__ grp_begin, const int* __
   }
   block_reduce<1>(acc, red);
   if (threadIdx.x == 0) out[a] = acc[0];
+}
+
+// ---- heat-bath of the multi-boson fields: BLAS-1 on dPi vectors [f][n] ---------
+// y_f = u_f x_f - wx_f (the operator W_u = u - w applied through w)
+__global__ void k_hb_wu(int n_f, long long n, const double2* __restrict__ u, const double2* __restrict__ x,
+                        const double2* __restrict__ wx, double2* __restrict__ y) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (k >= n) return;
+  const long long o = (long long)f * n + k;
+  const double2 a = x[o], b = wx[o], uf = u[f];
+  y[o] = make_double2(uf.x * a.x - uf.y * a.y - b.x, uf.x * a.y + uf.y * a.x - b.y);
+}
+// y_f = c1_f x1_f + c2_f x2_f + c3_f x3_f (any x may be null), for fields with active[f]
+__global__ void k_hb_lin(int n_f, long long n, const int* __restrict__ active, const double2* __restrict__ c,
+                         const double2* x1, const double2* x2, const double2* x3, double2* y) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (k >= n || (active && !active[f])) return;
+  const long long o = (long long)f * n + k;
+  double2 acc = make_double2(0.0, 0.0);
+  const double2* xs[3] = {x1, x2, x3};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    if (!xs[m]) continue;
+    const double2 cf = c[3 * f + m], v = xs[m][o];
+    acc.x += cf.x * v.x - cf.y * v.y;
+    acc.y += cf.x * v.y + cf.y * v.x;
+  }
+  y[o] = acc;
+}
+// per-field partial sums of conj(a) . b over fixed chunks (grid (nchunk, n_f), 256 threads)
+__global__ void k_hb_dot(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
+                         double* __restrict__ partial) {
+  __shared__ double red[64];
+  const int f = blockIdx.y;
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long k0 = blockIdx.x * chunk, k1 = min(n, k0 + chunk);
+  double acc[2] = {0.0, 0.0};
+  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const double2 x = a[(long long)f * n + k], y = b[(long long)f * n + k];
+    acc[0] += x.x * y.x + x.y * y.y;
+    acc[1] += x.x * y.y - x.y * y.x;
+  }
+  block_reduce<2>(acc, red);
+  if (threadIdx.x == 0) {
+    partial[2 * ((long long)f * gridDim.x + blockIdx.x)] = acc[0];
+    partial[2 * ((long long)f * gridDim.x + blockIdx.x) + 1] = acc[1];
+  }
 }
 
 }  // namespace
@@ -319,6 +369,170 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
   return DD_OK;
 }
 
+// Heat-bath of the multi-boson fields (paper Sec. 4): chi_f = W_{u_f}^{-1} eta_f on
+// dPi for every field f, by BiCGstab (van der Vorst 1992) over all fields at
+// once; each matvec is one dd_apply_w batch (every block and frame solve of all
+// fields) followed by u chi - w chi.  The start chi = eta / u is already close
+// (w is small where the frame is thick).  Per-field scalars live on the host
+// (the matvecs dominate); inner products are summed in a fixed order.
+static constexpr int HB_CHUNKS = 64;
+
+static dd_status hb_dot(dd_ctx* c, int n_f, long long n, const double2* a, const double2* b, double* dpart,
+                        std::vector<double2>& out, cudaStream_t s) {
+  DD_COUNT_LAUNCH(), k_hb_dot<<<dim3(HB_CHUNKS, n_f), 256, 0, s>>>(n, a, b, dpart);
+  DD_CUDA(c, cudaGetLastError());
+  std::vector<double> h(2 * (size_t)n_f * HB_CHUNKS);
+  DD_CUDA(c, cudaMemcpyAsync(h.data(), dpart, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  out.assign(n_f, make_double2(0.0, 0.0));
+  for (int f = 0; f < n_f; ++f)
+    for (int k = 0; k < HB_CHUNKS; ++k) {
+      out[f].x += h[2 * ((size_t)f * HB_CHUNKS + k)];
+      out[f].y += h[2 * ((size_t)f * HB_CHUNKS + k) + 1];
+    }
+  return DD_OK;
+}
+
+static double2 zdiv_h(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+static double2 zmul_h(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+static dd_status heatbath_dev(dd_ctx* c, int n_f, const double2* u_h, const double2* eta, double2* x,
+                              double tol, int maxiter, const dd_solve_params* prm, dd_heatbath_stats* out,
+                              cudaStream_t s) {
+  const long long n = 12LL * c->info.n_dpi;
+  const size_t vb = sizeof(double2) * (size_t)n_f * n;
+  void *vr, *vrh, *vp, *vv, *vs, *vt, *vw, *vu, *vc, *va, *vpart;
+  dd_status e;
+  if ((e = workspace(c, 200, vb, &vr)) || (e = workspace(c, 201, vb, &vrh)) || (e = workspace(c, 202, vb, &vp)) ||
+      (e = workspace(c, 203, vb, &vv)) || (e = workspace(c, 204, vb, &vs)) || (e = workspace(c, 205, vb, &vt)) ||
+      (e = workspace(c, 206, vb, &vw)) || (e = workspace(c, 207, sizeof(double2) * n_f, &vu)) ||
+      (e = workspace(c, 208, sizeof(double2) * 3 * n_f, &vc)) || (e = workspace(c, 209, sizeof(int) * n_f, &va)) ||
+      (e = workspace(c, 210, sizeof(double) * 2 * n_f * HB_CHUNKS, &vpart)))
+    return e;
+  double2 *r = (double2*)vr, *rh = (double2*)vrh, *p = (double2*)vp, *v = (double2*)vv, *sv = (double2*)vs,
+          *t = (double2*)vt, *wx = (double2*)vw, *du = (double2*)vu, *dc = (double2*)vc;
+  int* dact = (int*)va;
+  double* dpart = (double*)vpart;
+  const dim3 grid((unsigned)((n + 255) / 256), n_f);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  DD_CUDA(c, cudaMemcpyAsync(du, u_h, sizeof(double2) * n_f, cudaMemcpyHostToDevice, s));
+  std::vector<double2> cf(3 * n_f);
+  std::vector<int> act(n_f, 1);
+  auto set_coef = [&](const std::vector<double2>& c3) -> dd_status {
+    DD_CUDA(c, cudaMemcpyAsync(dc, c3.data(), sizeof(double2) * 3 * n_f, cudaMemcpyHostToDevice, s));
+    DD_CUDA(c, cudaMemcpyAsync(dact, act.data(), sizeof(int) * n_f, cudaMemcpyHostToDevice, s));
+    return DD_OK;
+  };
+  int matvecs = 0;
+  // y = W_u z
+  auto matvec = [&](const double2* z, double2* y) -> dd_status {
+    dd_status r0 = apply_w_dev(c, n_f, (const double*)z, (double*)wx, prm, s);
+    if (r0 != DD_OK) return r0;
+    DD_COUNT_LAUNCH(), k_hb_wu<<<grid, 256, 0, s>>>(n_f, n, du, z, wx, y);
+    DD_CUDA(c, cudaGetLastError());
+    ++matvecs;
+    return DD_OK;
+  };
+  auto lin = [&](double2* y, const double2* x1, const double2* x2, const double2* x3) -> dd_status {
+    if ((e = set_coef(cf)) != DD_OK) return e;
+    DD_COUNT_LAUNCH(), k_hb_lin<<<grid, 256, 0, s>>>(n_f, n, dact, dc, x1, x2, x3, y);
+    DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  };
+  // x = eta / u ; r = eta - W_u x ; rhat = p = r
+  for (int f = 0; f < n_f; ++f) {
+    cf[3 * f] = zdiv_h(make_double2(1.0, 0.0), u_h[f]);
+    cf[3 * f + 1] = cf[3 * f + 2] = make_double2(0.0, 0.0);
+  }
+  if ((e = lin(x, eta, nullptr, nullptr)) != DD_OK) return e;
+  if ((e = matvec(x, t)) != DD_OK) return e;
+  for (int f = 0; f < n_f; ++f) {
+    cf[3 * f] = make_double2(1.0, 0.0);
+    cf[3 * f + 1] = make_double2(-1.0, 0.0);
+  }
+  if ((e = lin(r, eta, t, nullptr)) != DD_OK) return e;
+  DD_CUDA(c, cudaMemcpyAsync(rh, r, vb, cudaMemcpyDeviceToDevice, s));
+  DD_CUDA(c, cudaMemcpyAsync(p, r, vb, cudaMemcpyDeviceToDevice, s));
+  std::vector<double2> eta2, rho, rr, tmp, ts, tt;
+  if ((e = hb_dot(c, n_f, n, eta, eta, dpart, eta2, s)) != DD_OK) return e;
+  if ((e = hb_dot(c, n_f, n, rh, r, dpart, rho, s)) != DD_OK) return e;
+  if ((e = hb_dot(c, n_f, n, r, r, dpart, rr, s)) != DD_OK) return e;
+  std::vector<double2> alpha(n_f), omega(n_f);
+  int it = 0;
+  auto relres = [&](int f) { return eta2[f].x > 0 ? sqrt(rr[f].x / eta2[f].x) : sqrt(rr[f].x); };
+  for (; it < maxiter; ++it) {
+    int live = 0;
+    for (int f = 0; f < n_f; ++f) {
+      act[f] = act[f] && relres(f) > tol && (rho[f].x != 0.0 || rho[f].y != 0.0);
+      live += act[f];
+    }
+    if (!live) break;
+    if ((e = matvec(p, v)) != DD_OK) return e;
+    if ((e = hb_dot(c, n_f, n, rh, v, dpart, tmp, s)) != DD_OK) return e;
+    for (int f = 0; f < n_f; ++f) {
+      alpha[f] = (tmp[f].x != 0.0 || tmp[f].y != 0.0) ? zdiv_h(rho[f], tmp[f]) : make_double2(0.0, 0.0);
+      cf[3 * f] = make_double2(1.0, 0.0);
+      cf[3 * f + 1] = make_double2(-alpha[f].x, -alpha[f].y);
+    }
+    if ((e = lin(sv, r, v, nullptr)) != DD_OK) return e;     // s = r - alpha v
+    if ((e = matvec(sv, t)) != DD_OK) return e;
+    if ((e = hb_dot(c, n_f, n, t, sv, dpart, ts, s)) != DD_OK) return e;
+    if ((e = hb_dot(c, n_f, n, t, t, dpart, tt, s)) != DD_OK) return e;
+    for (int f = 0; f < n_f; ++f) {
+      omega[f] = tt[f].x > 0 ? make_double2(ts[f].x / tt[f].x, ts[f].y / tt[f].x) : make_double2(0.0, 0.0);
+      cf[3 * f] = make_double2(1.0, 0.0);
+      cf[3 * f + 1] = alpha[f];
+      cf[3 * f + 2] = omega[f];
+    }
+    if ((e = lin(x, x, p, sv)) != DD_OK) return e;           // x += alpha p + omega s
+    for (int f = 0; f < n_f; ++f) {
+      cf[3 * f] = make_double2(1.0, 0.0);
+      cf[3 * f + 1] = make_double2(-omega[f].x, -omega[f].y);
+      cf[3 * f + 2] = make_double2(0.0, 0.0);
+    }
+    if ((e = lin(r, sv, t, nullptr)) != DD_OK) return e;     // r = s - omega t
+    std::vector<double2> rho_new;
+    if ((e = hb_dot(c, n_f, n, rh, r, dpart, rho_new, s)) != DD_OK) return e;
+    if ((e = hb_dot(c, n_f, n, r, r, dpart, rr, s)) != DD_OK) return e;
+    for (int f = 0; f < n_f; ++f) {
+      const bool ok = (omega[f].x != 0.0 || omega[f].y != 0.0) && (rho[f].x != 0.0 || rho[f].y != 0.0);
+      const double2 beta = ok ? zmul_h(zdiv_h(rho_new[f], rho[f]), zdiv_h(alpha[f], omega[f])) : make_double2(0.0, 0.0);
+      rho[f] = rho_new[f];
+      cf[3 * f] = make_double2(1.0, 0.0);                    // p = r + beta p - beta omega v
+      cf[3 * f + 1] = beta;
+      cf[3 * f + 2] = zmul_h(make_double2(-beta.x, -beta.y), omega[f]);
+    }
+    if ((e = lin(p, r, p, v)) != DD_OK) return e;
+  }
+  cudaEventRecord(e1, s);
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dd_heatbath_stats st{};
+  st.iterations = it;
+  st.matvecs = matvecs;
+  st.seconds = ms * 1e-3;
+  int conv = 0;
+  for (int f = 0; f < n_f; ++f) {
+    const double rel = relres(f);
+    if (!(rel == rel)) return fail(c, DD_ENAN, "NaN in the heat-bath residual");
+    st.max_relres = std::max(st.max_relres, rel);
+    conv += rel <= tol;
+  }
+  st.converged = conv;
+  if (out) *out = st;
+  if (conv < n_f) return fail(c, DD_ENOCONV, "heat-bath: some field above tolerance");
+  return DD_OK;
+}
+
 }  // namespace dd
 
 using namespace dd;
@@ -397,6 +611,41 @@ dd_status dd_multiboson_action(dd_ctx* c, int n_f, const double* u, const double
   for (int k = 0; k < P.n_cgrp; ++k) sr += h[nb + k];
   *S_r = sr;
   *S = sb + sr;
+  return r;
+}
+
+dd_status dd_multiboson_heatbath(dd_ctx* c, int n_f, const double* u, const double* eta, double* chi,
+                                 double tol, int maxiter, const dd_solve_params* prm, dd_heatbath_stats* stats,
+                                 void* stream) {
+  if (!c || !u || !eta || !chi || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (n_f > 65535) return fail(c, DD_EINVAL, "n_f must be <= 65535");
+  if (!(tol > 0) || maxiter < 1) return fail(c, DD_EINVAL, "bad heat-bath tolerance or iteration cap");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  for (int f = 0; f < n_f; ++f)
+    if (u[2 * f] == 0.0 && u[2 * f + 1] == 0.0) return fail(c, DD_EINVAL, "root u_k = 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
+  const double* din = eta;
+  double* dout = chi;
+  const bool hin = !is_device_ptr(eta), hout = !is_device_ptr(chi);
+  dd_status e;
+  if (hin) {
+    void* p;
+    if ((e = workspace(c, 211, bytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, eta, bytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  if (hout) {
+    void* p;
+    if ((e = workspace(c, 212, bytes, &p)) != DD_OK) return e;
+    dout = (double*)p;
+  }
+  std::vector<double2> uh(n_f);
+  for (int f = 0; f < n_f; ++f) uh[f] = make_double2(u[2 * f], u[2 * f + 1]);
+  dd_status r = heatbath_dev(c, n_f, uh.data(), (const double2*)din, (double2*)dout, tol, maxiter, prm, stats, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  if (hout) DD_CUDA(c, cudaMemcpyAsync(chi, dout, bytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
   return r;
 }
 

@@ -46,6 +46,14 @@ class SolveStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class HeatbathStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("matvecs", C.c_int), ("converged", C.c_int),
+                ("max_relres", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("dd4d status %d: %s" % (status, msg))
@@ -96,6 +104,8 @@ def lib():
             "dd_set_net": [vp, vp],
             "dd_set_hop_variant": [vp, C.c_int, C.c_int],
             "dd_hop_variants": [C.c_int],
+            "dd_multiboson_heatbath": [vp, C.c_int, dp, vp, vp, C.c_double, C.c_int,
+                                       C.POINTER(SolveParams), C.POINTER(HeatbathStats), vp],
             "dd_net_save": [vp, C.c_char_p],
             "dd_net_load": [vp, C.c_char_p, C.POINTER(vp)],
             "dd_hop_variant_name": [C.c_int, C.c_int],
@@ -117,7 +127,7 @@ def exported_symbols():
             "dd_apply_D_block", "dd_solve_blocks", "dd_apply_w", "dd_multiboson_action",
             "dd_roots", "dd_timing_enable", "dd_timing_get", "dd_launch_count", "dd_logdet_check",
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
-            "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load",
+            "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc"]
 
@@ -303,6 +313,20 @@ class Context:
         st = self._check(lib().dd_apply_w(self._h, n_f, _ptr(chi), _ptr(w_chi), C.byref(prm),
                                           _stream(stream)))
         return st
+
+    def multiboson_heatbath(self, u, eta, chi, tol=1e-10, maxiter=200, prm=None, stream=None):
+        """chi_k = W_{u_k}^{-1} eta_k for the fields of eta (layout of apply_w); stats dict."""
+        u = np.asarray(u, dtype=np.complex128)
+        uu = np.empty(2 * len(u))
+        uu[0::2], uu[1::2] = u.real, u.imag
+        prm = prm or params()
+        st = HeatbathStats()
+        s = self._check(lib().dd_multiboson_heatbath(
+            self._h, len(u), uu.ctypes.data_as(C.POINTER(C.c_double)), _ptr(eta), _ptr(chi),
+            float(tol), int(maxiter), C.byref(prm), C.byref(st), _stream(stream)))
+        d = st.as_dict()
+        d["status"] = s
+        return d
 
     def multiboson_action(self, u, chi, prm=None, stream=None):
         u = np.asarray(u, dtype=np.complex128)
