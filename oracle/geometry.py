@@ -60,10 +60,20 @@ class Decomposition:
         L = tuple(int(v) for v in L)
         self.L = L
         self.cores = [list(map(tuple, c)) for c in cores]
+        # an empty core list: the direction is not decomposed (a single core
+        # spanning its whole periodic extent, no frame and no hyperplane); the
+        # one-dimensional decomposition in thick time slices of Sec. 3 is the
+        # case with only direction 0 decomposed
+        self.decomposed = [len(c) > 0 for c in self.cores]
+        if not any(self.decomposed):
+            raise ValueError("at least one direction must be decomposed")
         for mu in range(4):
             c = self.cores[mu]
+            if not self.decomposed[mu]:
+                self.cores[mu] = [(0, L[mu] - 1)]
+                continue
             if len(c) < 2:
-                raise ValueError("need at least two cores per direction")
+                raise ValueError("need at least two cores per decomposed direction")
             for i, (lo, hi) in enumerate(c):
                 if not (0 <= lo <= hi < L[mu]):
                     raise ValueError("core outside the lattice")
@@ -74,7 +84,8 @@ class Decomposition:
         coords = np.indices(L)
 
         # hyperplane coordinates per direction
-        planes = [sorted({v for iv in self.cores[mu] for v in iv}) for mu in range(4)]
+        planes = [sorted({v for iv in self.cores[mu] for v in iv}) if self.decomposed[mu] else []
+                  for mu in range(4)]
         on_plane = np.zeros(L, dtype=bool)
         for mu in range(4):
             on_plane |= np.isin(coords[mu], planes[mu])
@@ -92,6 +103,10 @@ class Decomposition:
                         core = [self.cores[mu][idx[mu]] for mu in range(4)]
                         start, length = [], []
                         for mu in range(4):
+                            if not self.decomposed[mu]:
+                                start.append(0)
+                                length.append(L[mu])
+                                continue
                             prev_hi = self.cores[mu][(idx[mu] - 1) % nc[mu]][1]
                             next_lo = self.cores[mu][(idx[mu] + 1) % nc[mu]][0]
                             s = (prev_hi + 1) % L[mu]
@@ -108,7 +123,8 @@ class Decomposition:
                            for mu in range(4)])
             edge = np.zeros(L, dtype=bool)
             for mu in range(4):
-                edge |= (coords[mu] == b.core[mu][0]) | (coords[mu] == b.core[mu][1])
+                if self.decomposed[mu]:
+                    edge |= (coords[mu] == b.core[mu][0]) | (coords[mu] == b.core[mu][1])
             self.core_mask.append(cm)
             self.B_mask.append(cm & edge)
             self.omega_mask.append(om)

@@ -215,3 +215,33 @@ def test_heatbath_fields_reproduce_their_gaussian_sources():
     bad = o.heatbath(np.conj(u), etas)
     S_bad, _, _ = o.multiboson_action(u, bad)
     assert abs(S_bad - ref) > 1e-3 * ref
+
+
+L1D = (8, 4, 4, 2)
+CORES1D = [[(0, 1), (4, 5)], [], [], []]      # thick time slices: only x0 decomposed
+
+
+def test_one_dimensional_decomposition_formula():
+    """Sec. 3, 1D case (Fig. 1dDD): with only time decomposed, dPi1 is empty,
+    every frame slice lies in two Phi's, so prod det D_Phi = (det D_Lambda1)^2,
+    and Eq. (detD) becomes det D = det W_1 prod_a det D_Omega^a / det D_Lambda1."""
+    U = synth.gauge_field(L1D, 0.4, 6)
+    g = Decomposition(L1D, CORES1D)
+    assert g.nblocks == 2 and not g.C.any() and np.array_equal(g.dPi, g.B)
+    cover = sum(m.astype(int) for m in g.phi_mask)
+    assert np.all(cover[g.Lambda1] == 2) and np.all(cover[g.Lambda0] == 0)
+    f = Oracle(U, 0.13, g).logdet_factors()
+    phi = sum(x[1] for x in f["Phi"])
+    assert abs(phi - 2 * f["Lambda1"][1]) < 1e-10
+    one_d = f["W1"][1] + sum(x[1] for x in f["Omega"]) - f["Lambda1"][1]
+    assert abs(f["D"][1] - one_d) < 1e-10
+
+
+def test_undecomposed_direction_adds_no_hyperplane():
+    g1 = Decomposition(L1D, CORES1D)
+    t = np.indices(L1D)[0]
+    assert np.array_equal(g1.dPi, np.isin(t, [0, 1, 4, 5]))
+    with pytest.raises(ValueError):
+        Decomposition(L1D, [[], [], [], []])
+    with pytest.raises(ValueError):
+        Decomposition(L1D, [[(0, 1)], [], [], []])
