@@ -151,7 +151,11 @@ dd_status dd_gauge_download(dd_ctx* ctx, double* U_host);
 /* ---- geometry (paper Sec. 2) ------------------------------------------
  * Per direction mu a sorted list of core intervals [lo, hi] (inclusive,
  * 0 <= lo <= hi < L_mu) separated by at least one frame site (periodic);
- * at least two per direction.  ncores[mu] entries for direction mu are
+ * at least two per decomposed direction.  ncores[mu] = 0 leaves direction mu
+ * undecomposed: one core spans its whole periodic extent, without frame or
+ * hyperplanes, and every domain wraps around in mu (ncores = {n, 0, 0, 0} is
+ * the one-dimensional decomposition in thick time slices of Sec. 3, where
+ * dPi1 is empty).  At least one direction is decomposed.  ncores[mu] entries for direction mu are
  * taken in turn from core_lo / core_hi (direction 0 first).  Blocks
  * Lambda0^a are the products of one interval per direction, numbered
  * lexicographically in the interval indices with direction 3 fastest.

@@ -87,7 +87,9 @@ struct Shape {
 // used only when the box is the whole lattice).  Parity is local (sum of box
 // coordinates) plus parity_shift.
 template <class Member>
-Shape build_shape(const int dims[4], bool periodic, int parity_shift, Member member) {
+// periodic: bit mu set = the box wraps around in direction mu (it spans the
+// lattice's whole extent there); otherwise hops leaving the box are dropped
+Shape build_shape(const int dims[4], int periodic, int parity_shift, Member member) {
   Shape sh;
   long long nloc = 1LL * dims[0] * dims[1] * dims[2] * dims[3];
   std::vector<int> eo(nloc, -1), par(nloc, 0);
@@ -128,7 +130,7 @@ Shape build_shape(const int dims[4], bool periodic, int parity_shift, Member mem
         int y[4] = {x[0], x[1], x[2], x[3]};
         y[mu] += step;
         if (y[mu] < 0 || y[mu] >= dims[mu]) {
-          if (!periodic) continue;
+          if (!((periodic >> mu) & 1)) continue;
           y[mu] = (y[mu] + dims[mu]) % dims[mu];
         }
         long long t = ((1LL * y[0] * dims[1] + y[1]) * dims[2] + y[2]) * dims[3] + y[3];
@@ -167,7 +169,7 @@ void free_instance(Instance& in) {
 // Creates an instance for the site set `member` inside the box (dims, origin).
 template <class Member>
 dd_status add_instance(dd_ctx* c, int kind, int block, const int dims[4], const int origin[4],
-                       bool periodic, int parity_shift, const std::string& key, Member member,
+                       int periodic, int parity_shift, const std::string& key, Member member,
                        int* out_index) {
   Instance in;
   in.block = block;
@@ -480,7 +482,7 @@ dd_status ensure_phi(dd_ctx* c) {
       hi[m] = lo[m] + bd.core_hi[m] - bd.core_lo[m];
     }
     std::ostringstream key;
-    key << "PHI";
+    key << "PHI p" << c->undecomposed;
     for (int m = 0; m < 4; ++m) key << ' ' << bd.side[m] << ' ' << lo[m] << ' ' << hi[m];
     const int* dims = bd.side;
     auto member = [&](long long s) {
@@ -494,7 +496,7 @@ dd_status ensure_phi(dd_ctx* c) {
       return false;
     };
     int idx;
-    dd_status st = add_instance(c, DD_DOMAIN_PHI, b, bd.side, bd.origin, false, 0, key.str(),
+    dd_status st = add_instance(c, DD_DOMAIN_PHI, b, bd.side, bd.origin, c->undecomposed, 0, key.str(),
                                 member, &idx);
     if (st != DD_OK) return st;
   }
@@ -622,7 +624,7 @@ dd_status dd_create(dd_ctx** out, const int L[4], int time_bc, double kappa) {
   }
   int zero[4] = {0, 0, 0, 0};
   int idx;
-  st = add_instance(c, DD_DOMAIN_FULL, -1, L, zero, true, 0, "", [](long long) { return true; }, &idx);
+  st = add_instance(c, DD_DOMAIN_FULL, -1, L, zero, 0xF, 0, "", [](long long) { return true; }, &idx);
   if (st != DD_OK) {
     dd_destroy(c);
     return st;
@@ -676,8 +678,21 @@ dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, co
   if (c->geom_ready) return fail(c, DD_EINVAL, "geometry already set for this context");
   std::vector<std::vector<int>> lo(4), hi(4);
   int k = 0;
+  // ncores[m] == 0: direction m is not decomposed (one virtual core spanning its
+  // whole periodic extent, no frame, no hyperplane; boxes wrap around in m)
+  int und = 0, ndec = 0;
+  int nc[4];
   for (int m = 0; m < 4; ++m) {
-    if (ncores[m] < 2) return fail(c, DD_EINVAL, "need at least two cores per direction");
+    if (ncores[m] == 0) {
+      und |= 1 << m;
+      lo[m].push_back(0);
+      hi[m].push_back(c->L[m] - 1);
+      nc[m] = 1;
+      continue;
+    }
+    ++ndec;
+    nc[m] = ncores[m];
+    if (ncores[m] < 2) return fail(c, DD_EINVAL, "need at least two cores per decomposed direction");
     for (int i = 0; i < ncores[m]; ++i, ++k) {
       lo[m].push_back(core_lo[k]);
       hi[m].push_back(core_hi[k]);
@@ -689,24 +704,31 @@ dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, co
     if (lo[m][0] + c->L[m] - hi[m].back() < 2)
       return fail(c, DD_EINVAL, "cores must be separated by a frame across the boundary");
   }
+  if (ndec == 0) return fail(c, DD_EINVAL, "at least one direction must be decomposed");
+  c->undecomposed = und;
   c->cores_lo = lo;
   c->cores_hi = hi;
   const int* L = c->L;
   int V = c->V;
   // block descriptors, lexicographic in the interval indices, direction 3 fastest
   c->blocks.clear();
-  int nb = ncores[0] * ncores[1] * ncores[2] * ncores[3];
+  int nb = nc[0] * nc[1] * nc[2] * nc[3];
   for (int b = 0; b < nb; ++b) {
     int idx[4], r = b;
     for (int m = 3; m >= 0; --m) {
-      idx[m] = r % ncores[m];
-      r /= ncores[m];
+      idx[m] = r % nc[m];
+      r /= nc[m];
     }
     BlockDesc bd;
     for (int m = 0; m < 4; ++m) {
-      int n = ncores[m];
+      int n = nc[m];
       bd.core_lo[m] = lo[m][idx[m]];
       bd.core_hi[m] = hi[m][idx[m]];
+      if ((und >> m) & 1) {
+        bd.origin[m] = 0;
+        bd.side[m] = L[m];
+        continue;
+      }
       int prev_hi = hi[m][(idx[m] + n - 1) % n];
       int next_lo = lo[m][(idx[m] + 1) % n];
       bd.origin[m] = (prev_hi + 1) % L[m];
@@ -720,12 +742,13 @@ dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, co
   std::vector<std::vector<char>> isplane(4);
   for (int m = 0; m < 4; ++m) {
     isplane[m].assign(L[m], 0);
-    for (int i = 0; i < ncores[m]; ++i) isplane[m][lo[m][i]] = isplane[m][hi[m][i]] = 1;
+    if (!((und >> m) & 1))
+      for (int i = 0; i < nc[m]; ++i) isplane[m][lo[m][i]] = isplane[m][hi[m][i]] = 1;
   }
   std::vector<std::vector<int>> coreidx(4);
   for (int m = 0; m < 4; ++m) {
     coreidx[m].assign(L[m], -1);
-    for (int i = 0; i < ncores[m]; ++i)
+    for (int i = 0; i < nc[m]; ++i)
       for (int x = lo[m][i]; x <= hi[m][i]; ++x) coreidx[m][x] = i;
   }
   for (int s = 0; s < V; ++s) {
@@ -735,7 +758,7 @@ dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, co
     for (int m = 0; m < 4; ++m) {
       if (isplane[m][x[m]]) plane[s] = 1;
       if (coreidx[m][x[m]] < 0) in0 = false;
-      else b = b * ncores[m] + coreidx[m][x[m]];
+      else b = b * nc[m] + coreidx[m][x[m]];
     }
     if (in0) core_of[s] = b;
   }
@@ -775,7 +798,7 @@ dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, co
   dd_status st;
   int zero[4] = {0, 0, 0, 0};
   int idx;
-  st = add_instance(c, DD_DOMAIN_LAMBDA1, -1, L, zero, true, 0, "",
+  st = add_instance(c, DD_DOMAIN_LAMBDA1, -1, L, zero, 0xF, 0, "",
                     [&](long long s) { return core_of[s] < 0; }, &idx);
   if (st != DD_OK) return st;
   c->lambda1 = idx;
@@ -784,8 +807,9 @@ dd_status dd_set_geometry(dd_ctx* c, const int ncores[4], const int* core_lo, co
   for (int b = 0; b < nb; ++b) {
     const BlockDesc& bd = c->blocks[b];
     std::ostringstream key;
-    key << "OMEGA " << bd.side[0] << ' ' << bd.side[1] << ' ' << bd.side[2] << ' ' << bd.side[3];
-    st = add_instance(c, DD_DOMAIN_OMEGA, b, bd.side, bd.origin, false, 0, key.str(),
+    key << "OMEGA " << bd.side[0] << ' ' << bd.side[1] << ' ' << bd.side[2] << ' ' << bd.side[3] << " p"
+        << c->undecomposed;
+    st = add_instance(c, DD_DOMAIN_OMEGA, b, bd.side, bd.origin, c->undecomposed, 0, key.str(),
                       [](long long) { return true; }, &idx);
     if (st != DD_OK) return st;
     int no = c->inst[idx].d.nsites;

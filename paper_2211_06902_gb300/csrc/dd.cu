@@ -89,6 +89,7 @@ __global__ void k_inject_omega(BatchDev bd, InjectArgs a) {
     const int mu = dir & 3, step = dir < 4 ? 1 : -1;
     const int y = x[mu] + step;
     if (y >= 0 && y < dims[mu]) continue;           // hop stays inside the box
+    if (dims[mu] == a.L[mu]) continue;              // box wraps (direction not decomposed)
     int gy[4] = {g[0], g[1], g[2], g[3]};
     gy[mu] = (g[mu] + step + a.L[mu]) % a.L[mu];
     add_exterior_hop(acc, dir, gx, glob_index(gy, a.L), a, f);

@@ -160,6 +160,7 @@ struct dd_ctx {
   dd_solve_stats last_stats{};   // statistics of the last batched solve
   dd_net* net = nullptr;         // learned initial guess for block solves (not owned)
   cudaStream_t capture_stream = nullptr;   // private stream for CUDA-graph capture
+  int undecomposed = 0;                    // bit m: direction m not decomposed (boxes wrap in m)
   cudaStream_t copy_in = nullptr, copy_out = nullptr;   // host<->device copies of pipelined solves
   int forced_variant[3] = {-1, -1, -1};    // manual stencil launch variant per precision
 };
