@@ -207,6 +207,7 @@ struct HopArgs {
   const void* dots;         // optional: partials (out, dots) and (out, out)
   bool dotqs;               // with dotq and s1: also the partial (dotq, s1) into slot 3
   unsigned rhat_seed;       // nonzero: dotq is not read but generated (rhat_comp, spinor.cuh)
+  bool norm_out;            // double-float output: |out|^2 per (item, rhs) into partial slot 0
   double* partial;          // [k][nitems*nrhs] complex (2 doubles)
   const int* active;        // optional per-system flags, active[sys * active_stride]
   int active_stride;
@@ -224,6 +225,10 @@ dd_status check_device_error(dd_ctx* c, cudaStream_t s);
 dd_status gauge_finish(dd_ctx* c);
 
 // layout conversions (stencil.cu)
+// b -> b, r = b (outer precision F64 or double-float), x = 0, |b|^2 partials (slot 0)
+dd_status launch_pack_init(dd_ctx* c, const Batch& b, const double* user, void* be, void* bo, void* re,
+                           void* ro, void* xe, void* xo, dd_prec prec, double* partial_e, double* partial_o,
+                           cudaStream_t s);
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
                       dd_prec prec, cudaStream_t s);
 dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* vo, double* user,

@@ -237,27 +237,54 @@ __global__ void k_convert(BatchDev bd, int p, SD* y, const SS* __restrict__ x, c
 
 // outer x += sign * e (e of type S) on parity p, for systems still in the
 // outer loop; the outer vector is FP64 (double2) or double-float (df2s)
+// (with partial: |x|^2 per (item, rhs) into slot 0 afterwards, for every
+// system, updated or not, so the outer check needs no separate norm pass)
 template <class O, class S>
 __global__ void k_axpy64(BatchDev bd, int p, O* x, const S* __restrict__ e, double sign,
-                         const SysState* st) {
+                         const SysState* st, double* partial) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<O>::C CO;
+  __shared__ double red[64];
   ELEM_PROLOGUE_P
-  if (!live || !st[sys].outer_active) return;
-  C v[12];
-  CO a[12];
-  ld_site<12>(e + o, n, i, v);
-  ld_site<12>(x + o, n, i, a);
+  const bool upd = live && st[sys].outer_active;
+  if (!partial && !upd) return;
+  double acc[1] = {0.0};
+  if (live) {
+    CO a[12];
+    ld_site<12>(x + o, n, i, a);
+    if (upd) {
+      C v[12];
+      ld_site<12>(e + o, n, i, v);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    if constexpr (std::is_same<CO, dfc>::value) {
-      df_add(a[k].h.x, a[k].l.x, (float)sign * (float)v[k].x, 0.f);
-      df_add(a[k].h.y, a[k].l.y, (float)sign * (float)v[k].y, 0.f);
-    } else {
-      a[k] = make_double2(fma(sign, (double)v[k].x, a[k].x), fma(sign, (double)v[k].y, a[k].y));
+      for (int k = 0; k < 12; ++k) {
+        if constexpr (std::is_same<CO, dfc>::value) {
+          df_add(a[k].h.x, a[k].l.x, (float)sign * (float)v[k].x, 0.f);
+          df_add(a[k].h.y, a[k].l.y, (float)sign * (float)v[k].y, 0.f);
+        } else {
+          a[k] = make_double2(fma(sign, (double)v[k].x, a[k].x), fma(sign, (double)v[k].y, a[k].y));
+        }
+      }
+      st_site<12>(x + o, n, i, a);
+    }
+    if (partial) {
+      if constexpr (std::is_same<CO, dfc>::value) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) t += nrm2f(a[k]);
+        acc[0] = t;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[0] += a[k].x * a[k].x + a[k].y * a[k].y;
+      }
     }
   }
-  st_site<12>(x + o, n, i, a);
+  if (!partial) return;
+  block_reduce<1>(acc, red);
+  if (threadIdx.x == 0) {
+    const long long m = (long long)blockIdx.x * bd.nrhs + rh;
+    partial[2 * m] = acc[0];
+    partial[2 * m + 1] = 0.0;
+  }
 }
 
 __global__ void k_zero64(double2* x, long long n) {
@@ -611,18 +638,20 @@ dd_status tune_hop(dd_ctx* c, const Batch& b, dd_prec prec, const void* in, void
 // double-float (mixed solve); `sp` is the precision of the added vector
 template <class O>
 void axpy_outer_t(const BatchDev& bd, dim3 g, int p, void* x, const void* v, dd_prec sp, double sign,
-                  const SysState* st, cudaStream_t s) {
+                  const SysState* st, double* partial, cudaStream_t s) {
   if (sp == DD_F64)
-    DD_COUNT_LAUNCH(), k_axpy64<O, double2><<<g, 128, 0, s>>>(bd, p, (O*)x, (const double2*)v, sign, st);
+    DD_COUNT_LAUNCH(), k_axpy64<O, double2><<<g, 128, 0, s>>>(bd, p, (O*)x, (const double2*)v, sign, st, partial);
   else if (sp == DD_F32)
-    DD_COUNT_LAUNCH(), k_axpy64<O, float2><<<g, 128, 0, s>>>(bd, p, (O*)x, (const float2*)v, sign, st);
+    DD_COUNT_LAUNCH(), k_axpy64<O, float2><<<g, 128, 0, s>>>(bd, p, (O*)x, (const float2*)v, sign, st, partial);
   else
-    DD_COUNT_LAUNCH(), k_axpy64<O, __nv_bfloat162><<<g, 128, 0, s>>>(bd, p, (O*)x, (const __nv_bfloat162*)v, sign, st);
+    DD_COUNT_LAUNCH(), k_axpy64<O, __nv_bfloat162><<<g, 128, 0, s>>>(bd, p, (O*)x, (const __nv_bfloat162*)v, sign,
+                                                                     st, partial);
 }
+// x += sign v on parity p; with partial, also |x|^2 per (item, rhs) into slot 0
 void axpy_outer(bool dfo, const BatchDev& bd, dim3 g, int p, void* x, const void* v, dd_prec sp,
-                double sign, const SysState* st, cudaStream_t s) {
-  if (dfo) axpy_outer_t<df2s>(bd, g, p, x, v, sp, sign, st, s);
-  else axpy_outer_t<double2>(bd, g, p, x, v, sp, sign, st, s);
+                double sign, const SysState* st, cudaStream_t s, double* partial = nullptr) {
+  if (dfo) axpy_outer_t<df2s>(bd, g, p, x, v, sp, sign, st, partial, s);
+  else axpy_outer_t<double2>(bd, g, p, x, v, sp, sign, st, partial, s);
 }
 void norm2_outer(bool dfo, const BatchDev& bd, dim3 g, int p, const void* v, double* partial,
                  cudaStream_t s) {
@@ -702,16 +731,12 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   cudaEventCreate(&ev1);
   cudaEventRecord(ev0, s);
 
-  if ((e = launch_pack(c, b, b_user, be, bo, op, s)) != DD_OK) return e;
-  norm2_outer(dfo, bd, eg, 0, be, partial, s);
-  if (has_odd) norm2_outer(dfo, bd, og, 1, bo, partial_o, s);
+  // b, r = b, x = 0 and |b|^2 (= |r|^2) partials in one pass
+  if ((e = launch_pack_init(c, b, b_user, be, bo, re, ro, xe, xo, op, partial, partial_o, s)) != DD_OK)
+    return e;
   DD_COUNT_LAUNCH(), k_sc_bnorm<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o, prm->tol * prm->tol);
-  // x = 0 (all-zero bytes in both storages), r = b
-  DD_COUNT_LAUNCH(), k_zero64<<<(ne + 255) / 256, 256, 0, s>>>((double2*)xe, ne);
-  if (no) DD_COUNT_LAUNCH(), k_zero64<<<(no + 255) / 256, 256, 0, s>>>((double2*)xo, no);
-  DD_CUDA(c, cudaMemcpyAsync(re, be, ne * c64, cudaMemcpyDeviceToDevice, s));
-  if (no) DD_CUDA(c, cudaMemcpyAsync(ro, bo, no * c64, cudaMemcpyDeviceToDevice, s));
-  DD_CUDA(c, cudaGetLastError());
+  // the |r|^2 partials of the next outer check are already written
+  bool norms_ready = true;
   // learned initial guess: x = N(b), r = b - D x with D x in FP32 (the first
   // correction cycle is followed by an FP64 residual, which absorbs its rounding)
   bool all_omega = true;
@@ -736,8 +761,8 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     HopArgs g{};
     g.p_out = 1; g.in = ge; g.out = to; g.s1 = go; g.a1 = 1.0; g.b = -kap;
     if ((e = launch_hop(c, b, DD_F32, g, s)) != DD_OK) return e;
-    axpy_outer(dfo, bd, eg, 0, re, te, DD_F32, -1.0, st, s);
-    if (has_odd) axpy_outer(dfo, bd, og, 1, ro, to, DD_F32, -1.0, st, s);
+    axpy_outer(dfo, bd, eg, 0, re, te, DD_F32, -1.0, st, s, partial);
+    if (has_odd) axpy_outer(dfo, bd, og, 1, ro, to, DD_F32, -1.0, st, s, partial_o);
     DD_CUDA(c, cudaGetLastError());
   }
 
@@ -766,8 +791,11 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   double maxrel = 1.0;
   for (int cyc = 0;; ++cyc) {
     // |r|^2 of both parities -> convergence
-    norm2_outer(dfo, bd, eg, 0, re, partial, s);
-    if (has_odd) norm2_outer(dfo, bd, og, 1, ro, partial_o, s);
+    if (!norms_ready) {
+      norm2_outer(dfo, bd, eg, 0, re, partial, s);
+      if (has_odd) norm2_outer(dfo, bd, og, 1, ro, partial_o, s);
+    }
+    norms_ready = false;
     DD_CUDA(c, cudaMemsetAsync(vcnt, 0, 64, s));
     DD_COUNT_LAUNCH(), k_sc_outer<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o,
                                                      last_true ? 1.0 : 0.25, d_count, d_maxrel,
@@ -824,9 +852,15 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       // r = b - D x at the outer precision
       HopArgs h{};
       h.p_out = 0; h.in = xo; h.out = re; h.s1 = be; h.a1 = 1.0; h.s2 = xe; h.a2 = -1.0; h.b = kap;
-      if ((e = launch_hop(c, b, op, h, s)) != DD_OK) return e;
       HopArgs g{};
       g.p_out = 1; g.in = xe; g.out = ro; g.s1 = bo; g.a1 = 1.0; g.s2 = xo; g.a2 = -1.0; g.b = kap;
+      if (dfo) {     // the double-float residual also writes the |r|^2 partials
+        h.norm_out = g.norm_out = true;
+        h.partial = partial;
+        g.partial = partial_o;
+        norms_ready = true;
+      }
+      if ((e = launch_hop(c, b, op, h, s)) != DD_OK) return e;
       if ((e = launch_hop(c, b, op, g, s)) != DD_OK) return e;
     } else {
       // r -= D e with D e at the inner precision
@@ -836,8 +870,9 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       HopArgs g{};
       g.p_out = 1; g.in = w.x; g.out = w.tmp; g.s1 = eo; g.a1 = 1.0; g.b = -kap;
       if ((e = launch_hop(c, b, ip, g, s)) != DD_OK) return e;
-      axpy_outer(dfo, bd, eg, 0, re, w.t, ip, -1.0, st, s);
-      if (has_odd) axpy_outer(dfo, bd, og, 1, ro, w.tmp, ip, -1.0, st, s);
+      axpy_outer(dfo, bd, eg, 0, re, w.t, ip, -1.0, st, s, partial);
+      if (has_odd) axpy_outer(dfo, bd, og, 1, ro, w.tmp, ip, -1.0, st, s, partial_o);
+      norms_ready = true;
     }
     last_true = true_residual;
     DD_CUDA(c, cudaGetLastError());

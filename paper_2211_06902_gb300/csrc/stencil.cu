@@ -107,7 +107,22 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     st_site<12>(out_sys, n_out, i, out);
   }
   if constexpr (std::is_same<C, dfc>::value) {
-    return;      // the double-float residual kernel takes no fused inner products
+    // the double-float residual kernel: optionally |out|^2 (high parts, FP32 per
+    // thread, FP64 across threads) per (item, rhs) into partial slot 0
+    if (a.norm_out) {
+      float t[1] = {0.f};
+      double v[1] = {0.0};
+      if (live)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) t[0] += nrm2f(out[k]);
+      block_reduce_t<float, 1>(t, v, red);
+      if (threadIdx.x == 0) {
+        const long long my = (long long)item * bd.nrhs + r;
+        a.partial[2 * my] = v[0];
+        a.partial[2 * my + 1] = 0.0;
+      }
+    }
+    return;
   } else {
   const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
   const long long my = (long long)item * bd.nrhs + r;
@@ -1327,6 +1342,67 @@ __global__ void k_unpack(BatchDev bd, int p, const S* __restrict__ v, double2* _
   ld_site<12>(src, np, i, w);
 #pragma unroll
   for (int k = 0; k < 12; ++k) dst[k] = to_d2(w[k]);
+}
+
+// start of a solve in one pass: b (caller layout) -> b and r = b at the outer
+// precision, x = 0, and |b|^2 per (item, rhs) into partial slot 0
+template <class S>
+__global__ void k_pack_init(BatchDev bd, int p, const double2* __restrict__ user, S* __restrict__ bv,
+                            S* __restrict__ rv, S* __restrict__ xv, double* __restrict__ partial) {
+  typedef typename StoreTraits<S>::C C;
+  __shared__ double red[64];
+  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+  const int r = blockIdx.y;
+  const int sys = it.x * bd.nrhs + r;
+  double acc[1] = {0.0};
+  if (threadIdx.x < it.z) {
+    const DomInst* d = bd.inst_tab + bd.inst[it.x];
+    const int i = it.y + threadIdx.x;
+    const int np = p ? d->n[1] : d->n[0];
+    const int f = d->fmap[(p ? d->n[0] : 0) + i];
+    const double2* src = user + bd.uoff[sys] + 12LL * f;
+    const long long o = (p ? bd.off[1] : bd.off[0])[sys];
+    C w[12], z[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const double2 v = src[k];
+      w[k] = cmk<C>(v.x, v.y);
+      z[k] = cmk<C>(0.0, 0.0);
+      acc[0] += v.x * v.x + v.y * v.y;
+    }
+    st_site<12>(bv + o, np, i, w);
+    st_site<12>(rv + o, np, i, w);
+    st_site<12>(xv + o, np, i, z);
+  }
+  block_reduce<1>(acc, red);
+  if (threadIdx.x == 0) {
+    const long long m = (long long)blockIdx.x * bd.nrhs + r;
+    partial[2 * m] = acc[0];
+    partial[2 * m + 1] = 0.0;
+  }
+}
+
+dd_status launch_pack_init(dd_ctx* c, const Batch& b, const double* user, void* be, void* bo, void* re,
+                           void* ro, void* xe, void* xo, dd_prec prec, double* partial_e, double* partial_o,
+                           cudaStream_t s) {
+  dd_status st = sync_instances(c);
+  if (st != DD_OK) return st;
+  if (prec != DD_F64 && prec != DD_DF64) return fail(c, DD_EINVAL, "internal: outer precision");
+  BatchDev bd = batch_view(c, b);
+  for (int p = 0; p < 2; ++p) {
+    if (b.nitems[p] == 0) continue;
+    dim3 grid(b.nitems[p], b.nrhs);
+    double* part = p ? partial_o : partial_e;
+    if (prec == DD_DF64)
+      DD_COUNT_LAUNCH(), k_pack_init<df2s><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (df2s*)(p ? bo : be),
+                                                                  (df2s*)(p ? ro : re), (df2s*)(p ? xo : xe), part);
+    else
+      DD_COUNT_LAUNCH(), k_pack_init<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user,
+                                                                     (double2*)(p ? bo : be), (double2*)(p ? ro : re),
+                                                                     (double2*)(p ? xo : xe), part);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  return DD_OK;
 }
 
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
