@@ -291,12 +291,18 @@ def run_ours(args):
     del bh, xh
 
     # multi-boson action on the 8^4 lattice (16 blocks of 5^4, N = 4, 2 fields)
-    action = uneven = heatbath = None
+    action = uneven = heatbath = config5 = None
     if rank == 0:
         action = action_rate(dd4d, synth, torch)
         heatbath = heatbath_rate(dd4d, synth, torch)
         if not args.no_uneven:
             uneven = uneven_action_rate(dd4d, synth, torch)
+        if not args.no_config5:
+            torch.cuda.empty_cache()
+            try:
+                config5 = config5_action_rate(dd4d, synth, torch)
+            except (dd4d.DDError, RuntimeError) as err:      # e.g. device memory
+                config5 = {"unavailable": str(err)[:200]}
     stencil = None
     if rank == 0 and not args.no_stencil:
         stencil = stencil_rates(dd4d, synth, torch, ctx, ids, b, n_om)
@@ -341,6 +347,7 @@ def run_ours(args):
                       "residual_hop_ms_in_mixed_step": hop64_ms / args.steps},
         "action": action,
         "action_uneven": uneven,
+        "action_48x4": config5,
         "heatbath": heatbath,
         "learned_guess": learned,
         "stencil": stencil,
@@ -482,6 +489,42 @@ def heatbath_rate(dd4d, synth, torch, reps=3):
             "action_identity_relerr": abs(S - ref) / ref}
 
 
+def config5_action_rate(dd4d, synth, torch, group=8):
+    """Multi-boson action on 48^4 (1296 framed blocks of 9^4, N = 48: 24 fields), FP32
+    inner solves with double-float defect correction to 1e-10.  The 24 fields go
+    through the action in groups (S is a sum over fields), which keeps the block
+    and frame solves of one group within one GPU's memory."""
+    L = (48, 48, 48, 48)
+    c = dd4d.Context(L, 0.1365)
+    c.gauge_random(0.6, 5)
+    info = c.set_geometry(cores_uniform(L, 7, 1))
+    n_dpi = info["n_dpi"]
+    u = dd4d.roots(48, 0.5)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    prm = dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, autotune=True)
+    groups = [u[k:k + group] for k in range(0, len(u), group)]
+    chis = [torch.randn((len(g), n_dpi, 24), generator=gen, device="cuda", dtype=torch.float64) * (0.5 ** 0.5)
+            for g in groups]
+    c.multiboson_action(groups[0], chis[0], prm)        # autotune the batch shape
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S, relres = 0.0, 0.0
+    for g, ch in zip(groups, chis):
+        S += c.multiboson_action(g, ch, prm)[0]
+        relres = max(relres, c.last_solve_stats()["max_relres"])
+    dt = time.perf_counter() - t0
+    site_rhs = len(u) * (info["nblocks"] * info["max_omega"] + info["n_lambda1"])
+    c.close()
+    return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s",
+            "workload": "48^4, kappa 0.1365, eps 0.6 (links drawn on the device, seed 5), 1296 framed blocks "
+                        "of 9^4 + frame Lambda1, N = 48 (24 fields, c = 0.5, Gaussian chi on dPi from a seeded "
+                        "device generator), FP32 inner + double-float defect correction to 1e-10, fields in "
+                        "groups of %d" % group,
+            "seconds_per_eval": dt, "block_and_frame_site_rhs_per_eval": site_rhs,
+            "site_rhs_per_s": site_rhs / dt, "S": S, "max_relres": relres}
+
+
 def uneven_action_rate(dd4d, synth, torch, evals=2):
     """Multi-boson action on 64x32^3 with uneven blocks (cores 6 and 8 mixed,
     frame 1: 512 framed blocks of 8^4..10^4 sites in 16 shapes) plus the frame
@@ -539,6 +582,8 @@ def main():
                     help="omit the 64x32^3 uneven-block action measurement")
     ap.add_argument("--no-learned", action="store_true",
                     help="omit the learned-initial-guess A/B measurement")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="omit the 48^4, 24-field action measurement")
     ap.add_argument("--no-stencil", action="store_true",
                     help="omit the per-precision stencil bandwidth measurement")
     args = ap.parse_args()
