@@ -281,8 +281,9 @@ typedef struct {
 dd_status dd_logdet_check(dd_ctx* ctx, const dd_solve_params* params, double* logabs_omega,
                           double* logabs_phi, dd_logdet_report* report, void* stream);
 
-/* ---- learned block preconditioner (BASELINE north star part 4; the paper's
+/* ---- learned block preconditioner (no counterpart in the paper's method: its
  * only learning-related passage, Sec. 5 on flow-based models, is different).
+ * Used as the initial guess of the framed-block solves.
  * A gauge-covariant network of linear parallel-transport convolutions on a
  * framed block Omega0^a (Dirichlet boundary): one layer maps C_in channels of
  * colour 3-vectors to C_out,

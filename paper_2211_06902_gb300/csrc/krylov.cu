@@ -287,11 +287,6 @@ __global__ void k_axpy64(BatchDev bd, int p, O* x, const S* __restrict__ e, doub
   }
 }
 
-__global__ void k_zero64(double2* x, long long n) {
-  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k < n) x[k] = make_double2(0.0, 0.0);
-}
-
 // ---- per-system scalar kernels (one thread per system) ----------------------------
 struct ScalarArgs {
   SysState* st;
