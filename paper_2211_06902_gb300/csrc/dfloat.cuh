@@ -23,10 +23,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
-__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
+// Accumulation is lazy: h collects the FP32 sum exactly split by TwoSum and l
+// every rounding error and low-order term, without renormalising after each
+// step (h + l stays exact to ~2^-48 of the terms; |l| grows to a few ulp(h)).
+// Values are renormalised once, where they are stored (stc / df_renorm).
 // (h, l) += a * b for double-float a, b
 __device__ __forceinline__ void df_fma(float& h, float& l, float ah, float al, float bh, float bl) {
   const float p = ah * bh;
@@ -35,14 +35,21 @@ __device__ __forceinline__ void df_fma(float& h, float& l, float ah, float al, f
   e = fmaf(al, bh, e);
   float s, t;
   two_sum(h, p, s, t);
-  t += l + e;
-  quick_two_sum(s, t, h, l);
+  h = s;
+  l += t + e;
 }
 __device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
   float s, t;
   two_sum(h, bh, s, t);
-  t += l + bl;
-  quick_two_sum(s, t, h, l);
+  h = s;
+  l += t + bl;
+}
+// (h, l) -> the nearest FP32 h and the remainder l (|l| <= ulp(h) / 2)
+__device__ __forceinline__ void df_renorm(float& h, float& l) {
+  float s, t;
+  two_sum(h, l, s, t);
+  h = s;
+  l = t;
 }
 
 // ---- complex helpers used by the generic stencil code -------------------------------
@@ -50,7 +57,15 @@ __device__ __forceinline__ dfc ldc(const df2s* p) {
   const float4 v = __ldg(&p->v);
   return dfc{make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
-__device__ __forceinline__ void stc(df2s* p, dfc v) { p->v = make_float4(v.h.x, v.h.y, v.l.x, v.l.y); }
+__device__ __forceinline__ void stc(df2s* p, dfc v) {
+  df_renorm(v.h.x, v.l.x);
+  df_renorm(v.h.y, v.l.y);
+  p->v = make_float4(v.h.x, v.h.y, v.l.x, v.l.y);
+}
+__device__ __forceinline__ void df_renorm(dfc& v) {
+  df_renorm(v.h.x, v.l.x);
+  df_renorm(v.h.y, v.l.y);
+}
 __device__ __forceinline__ void ld_pair(const df2s* p, dfc& a, dfc& b) {
   a = ldc(p);
   b = ldc(p + 1);
@@ -64,6 +79,7 @@ __device__ __forceinline__ void st_pair(df2s* p, dfc a, dfc b) {
   stc(p, a);
   stc(p + 1, b);
 }
+// (st_pair renormalises through stc)
 __device__ __forceinline__ float2 split_d(double x) {
   const float h = (float)x;
   return make_float2(h, (float)(x - (double)h));

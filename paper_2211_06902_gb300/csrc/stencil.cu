@@ -114,7 +114,11 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
       double v[1] = {0.0};
       if (live)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) t[0] += nrm2f(out[k]);
+        for (int k = 0; k < 12; ++k) {
+          dfc o = out[k];
+          df_renorm(o);                 // the stored (nearest) high part
+          t[0] += nrm2f(o);
+        }
       block_reduce_t<float, 1>(t, v, red);
       if (threadIdx.x == 0) {
         const long long my = (long long)item * bd.nrhs + r;
