@@ -1199,7 +1199,7 @@ static void launch_split(const BatchDev& bd, const HopArgs& a, long long nitems_
 static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs& a, long long ni,
                          int nsm, cudaStream_t s) {
   if (prec == DD_DF64) {
-    launch_variant<df2s, 3, false, 1>(bd, a, ni, nsm, s);
+    launch_variant<df2s, 4, false, 1>(bd, a, ni, nsm, s);
     return;
   }
   const HopVariant& hv = variant_of(prec, v);
