@@ -68,6 +68,7 @@ Batch::~Batch() {
     dfree(d_items[p]);
     dfree(d_item_begin[p]);
   }
+  dfree(d_fitems);
 }
 
 // ---------------------------------------------------------------------------
@@ -80,6 +81,7 @@ struct Shape {
   std::vector<int> nbr;    // [p][8][n_p]
   std::vector<int> fmap;   // [p][n_p]
   std::vector<int> lex;    // [p][n_p]
+  std::vector<int> ifm;    // [field position] -> (p << 30) | i
 };
 
 // Builds the per-parity site lists and neighbour tables of a set of sites
@@ -112,6 +114,7 @@ Shape build_shape(const int dims[4], int periodic, int parity_shift, Member memb
   sh.nbr.assign(8LL * (sh.n[0] + sh.n[1]), -1);
   sh.fmap.resize(sh.n[0] + sh.n[1]);
   sh.lex.resize(sh.n[0] + sh.n[1]);
+  sh.ifm.resize(sh.n[0] + sh.n[1]);
   for (int p = 0; p < 2; ++p) {
     int np = sh.n[p];
     long long nb_base = p ? 8LL * sh.n[0] : 0;
@@ -125,6 +128,7 @@ Shape build_shape(const int dims[4], int periodic, int parity_shift, Member memb
       x[0] = s / (1LL * dims[3] * dims[2] * dims[1]);
       sh.fmap[m_base + i] = fpos[s];
       sh.lex[m_base + i] = (int)s;
+      sh.ifm[fpos[s]] = (p << 30) | i;
       for (int dir = 0; dir < 8; ++dir) {
         int mu = dir & 3, step = dir < 4 ? 1 : -1;
         int y[4] = {x[0], x[1], x[2], x[3]};
@@ -162,6 +166,7 @@ void free_instance(Instance& in) {
   in.glob_buf = in.link64_buf = in.link32_buf = in.link16_buf = in.linkdf_buf = nullptr;
   in.lb32_buf = in.lb16_buf = nullptr;
   in.nbr_buf.reset();
+  in.ifm_buf.reset();
   in.fmap_buf.reset();
   in.lex_buf.reset();
 }
@@ -191,12 +196,15 @@ dd_status add_instance(dd_ctx* c, int kind, int block, const int dims[4], const 
     if (st != DD_OK) return st;
     in.lex_buf = upload_shared(c, sh.lex, &st);
     if (st != DD_OK) return st;
+    in.ifm_buf = upload_shared(c, sh.ifm, &st);
+    if (st != DD_OK) return st;
     in.h_fmap = sh.fmap;
     lex = sh.lex;
     if (!key.empty()) {
       c->shape_cache[key + "/nbr"] = in.nbr_buf;
       c->shape_cache[key + "/fmap"] = in.fmap_buf;
       c->shape_cache[key + "/lex"] = in.lex_buf;
+      c->shape_cache[key + "/ifm"] = in.ifm_buf;
       auto* meta = new std::vector<int>();
       meta->push_back(sh.n[0]);
       meta->push_back(sh.n[1]);
@@ -209,6 +217,7 @@ dd_status add_instance(dd_ctx* c, int kind, int block, const int dims[4], const 
     in.nbr_buf = it->second;
     in.fmap_buf = c->shape_cache[key + "/fmap"];
     in.lex_buf = c->shape_cache[key + "/lex"];
+    in.ifm_buf = c->shape_cache[key + "/ifm"];
     auto* meta = (std::vector<int>*)c->shape_cache[key + "/meta"].get();
     in.d.n[0] = (*meta)[0];
     in.d.n[1] = (*meta)[1];
@@ -237,6 +246,7 @@ dd_status add_instance(dd_ctx* c, int kind, int block, const int dims[4], const 
   in.d.nbr = (const int*)in.nbr_buf.get();
   in.d.fmap = (const int*)in.fmap_buf.get();
   in.d.lex = (const int*)in.lex_buf.get();
+  in.d.ifm = (const int*)in.ifm_buf.get();
   in.d.glob = (const int*)in.glob_buf;
   *out_index = (int)c->inst.size();
   c->inst.push_back(std::move(in));
@@ -538,8 +548,19 @@ dd_status make_batch(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch& b
     b.item_begin[p][b.nb] = (int)items[p].size();
     b.nitems[p] = (int)items[p].size();
   }
+  // runs of CH consecutive field positions (both parities) for the caller-layout kernels
+  std::vector<int4> fitems;
+  for (int j = 0; j < b.nb; ++j) {
+    const int ns = c->inst[inst[j]].d.nsites;
+    for (int f = 0; f < ns; f += CH) fitems.push_back(make_int4(j, f, std::min(CH, ns - f), 0));
+  }
+  b.nfitems = (int)fitems.size();
   b.user_tot = utot;
   dd_status st;
+  if ((st = dalloc(c, (void**)&b.d_fitems, sizeof(int4) * std::max<size_t>(1, fitems.size()))) != DD_OK)
+    return st;
+  if (!fitems.empty())
+    cudaMemcpy(b.d_fitems, fitems.data(), sizeof(int4) * fitems.size(), cudaMemcpyHostToDevice);
   if ((st = dalloc(c, (void**)&b.d_inst, sizeof(int) * b.nb)) != DD_OK) return st;
   cudaMemcpy(b.d_inst, inst.data(), sizeof(int) * b.nb, cudaMemcpyHostToDevice);
   if ((st = dalloc(c, (void**)&b.d_uoff, sizeof(long long) * uoff.size())) != DD_OK) return st;
@@ -569,6 +590,8 @@ BatchDev batch_view(dd_ctx* c, const Batch& b) {
     v.item_begin[p] = b.d_item_begin[p];
     v.nitems[p] = b.nitems[p];
   }
+  v.fitems = b.d_fitems;
+  v.nfitems = b.nfitems;
   v.nb = b.nb;
   v.nrhs = b.nrhs;
   return v;

@@ -43,6 +43,7 @@ struct DomInst {            // device-visible descriptor (plain data)
   const int* fmap;          // [p][n_p]
   const int* glob;          // [p][n_p]
   const int* lex;           // [p][n_p] (boxes), nullptr otherwise
+  const int* ifm;           // [field position] -> (parity << 30) | index in the parity
   const double2* link64;    // [p][4][9][n_p]
   const float2* link32;
   const __nv_bfloat162* link16;
@@ -55,7 +56,7 @@ struct DomInst {            // device-visible descriptor (plain data)
 struct Instance {
   DomInst d{};
   int block = -1;
-  std::shared_ptr<void> nbr_buf, fmap_buf, lex_buf;   // shared between same-shape boxes
+  std::shared_ptr<void> nbr_buf, fmap_buf, lex_buf, ifm_buf;   // shared between same-shape boxes
   void* glob_buf = nullptr;
   void* link64_buf = nullptr;
   void* link32_buf = nullptr;
@@ -86,6 +87,8 @@ struct Batch {
   int4* d_items[2] = {nullptr, nullptr};    // {j, start, count, 0}
   int nitems[2] = {0, 0};
   int* d_item_begin[2] = {nullptr, nullptr}; // [nb+1] first item of instance j
+  int4* d_fitems = nullptr;                 // {j, first field position, count, 0}: 128-site runs in
+  int nfitems = 0;                          // field order (caller layout), both parities together
   std::vector<int> item_begin[2];
   int maxn[2] = {0, 0};
   // tuned hop launch variant per precision (f64, f32, bf16) and CUDA graphs of
@@ -104,6 +107,8 @@ struct BatchDev {           // device-visible view of a Batch
   const int4* items[2];
   const int* item_begin[2];
   int nitems[2];
+  const int4* fitems;
+  int nfitems;
   int nb, nrhs;
 };
 
@@ -225,10 +230,9 @@ dd_status check_device_error(dd_ctx* c, cudaStream_t s);
 dd_status gauge_finish(dd_ctx* c);
 
 // layout conversions (stencil.cu)
-// b -> b, r = b (outer precision F64 or double-float), x = 0, |b|^2 partials (slot 0)
+// b -> b, r = b (outer precision F64 or double-float), x = 0, in caller field order
 dd_status launch_pack_init(dd_ctx* c, const Batch& b, const double* user, void* be, void* bo, void* re,
-                           void* ro, void* xe, void* xo, dd_prec prec, double* partial_e, double* partial_o,
-                           cudaStream_t s);
+                           void* ro, void* xe, void* xo, dd_prec prec, cudaStream_t s);
 dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, void* vo,
                       dd_prec prec, cudaStream_t s);
 dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* vo, double* user,

@@ -1310,101 +1310,98 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
 
 // ---- caller layout <-> internal SoA --------------------------------------------
 // caller: [j][r][field-order site][12] complex128; internal: per parity, per
-// system 12 x n_p complex at the storage precision.  grid: (nitems[p], nrhs).
-template <class S>
-__global__ void k_pack(BatchDev bd, int p, const double2* __restrict__ user, S* __restrict__ v) {
-  typedef typename StoreTraits<S>::C C;
-  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
-  const int r = blockIdx.y;
-  if (threadIdx.x >= it.z) return;
-  const int sys = it.x * bd.nrhs + r;
-  const DomInst d = bd.inst_tab[bd.inst[it.x]];
-  const int i = it.y + threadIdx.x;
-  const int np = p ? d.n[1] : d.n[0];
-  const int f = d.fmap[(p ? d.n[0] : 0) + i];
-  const double2* src = user + bd.uoff[sys] + 12LL * f;
-  S* dst = v + (p ? bd.off[1] : bd.off[0])[sys];
-  C w[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) w[k] = cmk<C>(src[k].x, src[k].y);
-  st_site<12>(dst, np, i, w);
+// system 12 x n_p complex at the storage precision.  grid: (nfitems, nrhs), one
+// thread per field position, so a warp reads or writes one contiguous 6 KB run
+// of the caller layout; each parity's share of it is a contiguous run too.
+struct FieldSite {
+  int p, i, np, f;
+  bool live;
+};
+__device__ __forceinline__ FieldSite field_site(const BatchDev& bd, const DomInst* d, int4 it) {
+  FieldSite fs;
+  fs.live = threadIdx.x < it.z;
+  fs.f = it.y + (fs.live ? threadIdx.x : 0);
+  const int v = d->ifm[fs.f];
+  fs.p = v >> 30;
+  fs.i = v & ((1 << 30) - 1);
+  fs.np = fs.p ? d->n[1] : d->n[0];
+  return fs;
 }
 
 template <class S>
-__global__ void k_unpack(BatchDev bd, int p, const S* __restrict__ v, double2* __restrict__ user) {
-  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+__global__ void k_pack(BatchDev bd, const double2* __restrict__ user, S* __restrict__ ve, S* __restrict__ vo) {
+  typedef typename StoreTraits<S>::C C;
+  const int4 it = bd.fitems[blockIdx.x];
   const int r = blockIdx.y;
   if (threadIdx.x >= it.z) return;
   const int sys = it.x * bd.nrhs + r;
-  const DomInst d = bd.inst_tab[bd.inst[it.x]];
-  const int i = it.y + threadIdx.x;
-  const int np = p ? d.n[1] : d.n[0];
-  const int f = d.fmap[(p ? d.n[0] : 0) + i];
-  double2* dst = user + bd.uoff[sys] + 12LL * f;
-  const S* src = v + (p ? bd.off[1] : bd.off[0])[sys];
+  const DomInst* d = bd.inst_tab + bd.inst[it.x];
+  const FieldSite fs = field_site(bd, d, it);
+  const double2* src = user + bd.uoff[sys] + 12LL * fs.f;
+  S* dst = (fs.p ? vo + bd.off[1][sys] : ve + bd.off[0][sys]);
+  C w[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) w[k] = cmk<C>(src[k].x, src[k].y);
+  st_site<12>(dst, fs.np, fs.i, w);
+}
+
+template <class S>
+__global__ void k_unpack(BatchDev bd, const S* __restrict__ ve, const S* __restrict__ vo,
+                         double2* __restrict__ user) {
+  const int4 it = bd.fitems[blockIdx.x];
+  const int r = blockIdx.y;
+  if (threadIdx.x >= it.z) return;
+  const int sys = it.x * bd.nrhs + r;
+  const DomInst* d = bd.inst_tab + bd.inst[it.x];
+  const FieldSite fs = field_site(bd, d, it);
+  double2* dst = user + bd.uoff[sys] + 12LL * fs.f;
+  const S* src = (fs.p ? vo + bd.off[1][sys] : ve + bd.off[0][sys]);
   typename StoreTraits<S>::C w[12];
-  ld_site<12>(src, np, i, w);
+  ld_site<12>(src, fs.np, fs.i, w);
 #pragma unroll
   for (int k = 0; k < 12; ++k) dst[k] = to_d2(w[k]);
 }
 
 // start of a solve in one pass: b (caller layout) -> b and r = b at the outer
-// precision, x = 0, and |b|^2 per (item, rhs) into partial slot 0
+// precision (FP64 or double-float), x = 0
 template <class S>
-__global__ void k_pack_init(BatchDev bd, int p, const double2* __restrict__ user, S* __restrict__ bv,
-                            S* __restrict__ rv, S* __restrict__ xv, double* __restrict__ partial) {
+__global__ void k_pack_init(BatchDev bd, const double2* __restrict__ user, S* be, S* bo, S* re, S* ro, S* xe,
+                            S* xo) {
   typedef typename StoreTraits<S>::C C;
-  __shared__ double red[64];
-  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+  const int4 it = bd.fitems[blockIdx.x];
   const int r = blockIdx.y;
+  if (threadIdx.x >= it.z) return;
   const int sys = it.x * bd.nrhs + r;
-  double acc[1] = {0.0};
-  if (threadIdx.x < it.z) {
-    const DomInst* d = bd.inst_tab + bd.inst[it.x];
-    const int i = it.y + threadIdx.x;
-    const int np = p ? d->n[1] : d->n[0];
-    const int f = d->fmap[(p ? d->n[0] : 0) + i];
-    const double2* src = user + bd.uoff[sys] + 12LL * f;
-    const long long o = (p ? bd.off[1] : bd.off[0])[sys];
-    C w[12], z[12];
+  const DomInst* d = bd.inst_tab + bd.inst[it.x];
+  const FieldSite fs = field_site(bd, d, it);
+  const double2* src = user + bd.uoff[sys] + 12LL * fs.f;
+  const long long o = fs.p ? bd.off[1][sys] : bd.off[0][sys];
+  C w[12], z[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const double2 v = src[k];
-      w[k] = cmk<C>(v.x, v.y);
-      z[k] = cmk<C>(0.0, 0.0);
-      acc[0] += v.x * v.x + v.y * v.y;
-    }
-    st_site<12>(bv + o, np, i, w);
-    st_site<12>(rv + o, np, i, w);
-    st_site<12>(xv + o, np, i, z);
+  for (int k = 0; k < 12; ++k) {
+    w[k] = cmk<C>(src[k].x, src[k].y);
+    z[k] = cmk<C>(0.0, 0.0);
   }
-  block_reduce<1>(acc, red);
-  if (threadIdx.x == 0) {
-    const long long m = (long long)blockIdx.x * bd.nrhs + r;
-    partial[2 * m] = acc[0];
-    partial[2 * m + 1] = 0.0;
-  }
+  st_site<12>((fs.p ? bo : be) + o, fs.np, fs.i, w);
+  st_site<12>((fs.p ? ro : re) + o, fs.np, fs.i, w);
+  st_site<12>((fs.p ? xo : xe) + o, fs.np, fs.i, z);
 }
 
 dd_status launch_pack_init(dd_ctx* c, const Batch& b, const double* user, void* be, void* bo, void* re,
-                           void* ro, void* xe, void* xo, dd_prec prec, double* partial_e, double* partial_o,
-                           cudaStream_t s) {
+                           void* ro, void* xe, void* xo, dd_prec prec, cudaStream_t s) {
   dd_status st = sync_instances(c);
   if (st != DD_OK) return st;
   if (prec != DD_F64 && prec != DD_DF64) return fail(c, DD_EINVAL, "internal: outer precision");
+  if (b.nfitems == 0) return DD_OK;
   BatchDev bd = batch_view(c, b);
-  for (int p = 0; p < 2; ++p) {
-    if (b.nitems[p] == 0) continue;
-    dim3 grid(b.nitems[p], b.nrhs);
-    double* part = p ? partial_o : partial_e;
-    if (prec == DD_DF64)
-      DD_COUNT_LAUNCH(), k_pack_init<df2s><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (df2s*)(p ? bo : be),
-                                                                  (df2s*)(p ? ro : re), (df2s*)(p ? xo : xe), part);
-    else
-      DD_COUNT_LAUNCH(), k_pack_init<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user,
-                                                                     (double2*)(p ? bo : be), (double2*)(p ? ro : re),
-                                                                     (double2*)(p ? xo : xe), part);
-  }
+  dim3 grid(b.nfitems, b.nrhs);
+  const double2* u = (const double2*)user;
+  if (prec == DD_DF64)
+    DD_COUNT_LAUNCH(), k_pack_init<df2s><<<grid, 128, 0, s>>>(bd, u, (df2s*)be, (df2s*)bo, (df2s*)re, (df2s*)ro,
+                                                              (df2s*)xe, (df2s*)xo);
+  else
+    DD_COUNT_LAUNCH(), k_pack_init<double2><<<grid, 128, 0, s>>>(bd, u, (double2*)be, (double2*)bo, (double2*)re,
+                                                                 (double2*)ro, (double2*)xe, (double2*)xo);
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
 }
@@ -1413,34 +1410,36 @@ dd_status launch_pack(dd_ctx* c, const Batch& b, const double* user, void* ve, v
                       dd_prec prec, cudaStream_t s) {
   dd_status st = sync_instances(c);
   if (st != DD_OK) return st;
+  if (b.nfitems == 0) return DD_OK;
   BatchDev bd = batch_view(c, b);
-  for (int p = 0; p < 2; ++p) {
-    if (b.nitems[p] == 0) continue;
-    dim3 grid(b.nitems[p], b.nrhs);
-    void* v = p ? vo : ve;
-    if (prec == DD_DF64) DD_COUNT_LAUNCH(), k_pack<df2s><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (df2s*)v);
-    else if (prec == DD_F64) DD_COUNT_LAUNCH(), k_pack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (double2*)v);
-    else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_pack<float2><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (float2*)v);
-    else DD_COUNT_LAUNCH(), k_pack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const double2*)user, (__nv_bfloat162*)v);
-  }
+  dim3 grid(b.nfitems, b.nrhs);
+  const double2* u = (const double2*)user;
+  if (prec == DD_DF64) DD_COUNT_LAUNCH(), k_pack<df2s><<<grid, 128, 0, s>>>(bd, u, (df2s*)ve, (df2s*)vo);
+  else if (prec == DD_F64) DD_COUNT_LAUNCH(), k_pack<double2><<<grid, 128, 0, s>>>(bd, u, (double2*)ve, (double2*)vo);
+  else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_pack<float2><<<grid, 128, 0, s>>>(bd, u, (float2*)ve, (float2*)vo);
+  else
+    DD_COUNT_LAUNCH(), k_pack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, u, (__nv_bfloat162*)ve, (__nv_bfloat162*)vo);
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
 }
 
-dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* vo, double* user,
-                        dd_prec prec, cudaStream_t s) {
+dd_status launch_unpack(dd_ctx* c, const Batch& b, const void* ve, const void* vo, double* user, dd_prec prec,
+                        cudaStream_t s) {
   dd_status st = sync_instances(c);
   if (st != DD_OK) return st;
+  if (b.nfitems == 0) return DD_OK;
   BatchDev bd = batch_view(c, b);
-  for (int p = 0; p < 2; ++p) {
-    if (b.nitems[p] == 0) continue;
-    dim3 grid(b.nitems[p], b.nrhs);
-    const void* v = p ? vo : ve;
-    if (prec == DD_DF64) DD_COUNT_LAUNCH(), k_unpack<df2s><<<grid, 128, 0, s>>>(bd, p, (const df2s*)v, (double2*)user);
-    else if (prec == DD_F64) DD_COUNT_LAUNCH(), k_unpack<double2><<<grid, 128, 0, s>>>(bd, p, (const double2*)v, (double2*)user);
-    else if (prec == DD_F32) DD_COUNT_LAUNCH(), k_unpack<float2><<<grid, 128, 0, s>>>(bd, p, (const float2*)v, (double2*)user);
-    else DD_COUNT_LAUNCH(), k_unpack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, p, (const __nv_bfloat162*)v, (double2*)user);
-  }
+  dim3 grid(b.nfitems, b.nrhs);
+  double2* u = (double2*)user;
+  if (prec == DD_DF64)
+    DD_COUNT_LAUNCH(), k_unpack<df2s><<<grid, 128, 0, s>>>(bd, (const df2s*)ve, (const df2s*)vo, u);
+  else if (prec == DD_F64)
+    DD_COUNT_LAUNCH(), k_unpack<double2><<<grid, 128, 0, s>>>(bd, (const double2*)ve, (const double2*)vo, u);
+  else if (prec == DD_F32)
+    DD_COUNT_LAUNCH(), k_unpack<float2><<<grid, 128, 0, s>>>(bd, (const float2*)ve, (const float2*)vo, u);
+  else
+    DD_COUNT_LAUNCH(), k_unpack<__nv_bfloat162><<<grid, 128, 0, s>>>(bd, (const __nv_bfloat162*)ve,
+                                                                     (const __nv_bfloat162*)vo, u);
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
 }
