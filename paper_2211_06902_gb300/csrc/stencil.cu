@@ -725,13 +725,20 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
               (!a.active || a.active[(long long)sysk[k] * a.active_stride]);
     act = act || actk[k];
   }
-  if (!__syncthreads_or(act)) return;          // every rhs of the group has converged
+  // active rhs of the CTA: each warp contributes its count as that many lanes
+  int nact_rhs = 0;
+#pragma unroll
+  for (int k = 0; k < RR; ++k) nact_rhs += actk[k] ? 1 : 0;
+  const int cta_rhs = __syncthreads_count(lane < nact_rhs);   // lanes 0 .. nact_rhs-1 of each warp
+  if (cta_rhs == 0) return;                    // every rhs of the group has converged
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
   const int n0 = dp->n[0];
   const int nq = (it.z + LB_LANES - 1) / LB_LANES;
   if (threadIdx.x == 0) {
     for (int q = 0; q < nq; ++q) mbar_init(&bar[q], 1);
     mbar_fence_init();
+    // one atomic per CTA for the algorithmic-byte accounting (timing only)
+    if (a.work_bytes) atomicAdd(a.work_bytes, a.site_bytes * it.z * cta_rhs);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -749,10 +756,6 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
         if (!mbar_wait0(&bar[q])) atomicExch(a.err, 1);
     return;
   }
-  if (a.work_bytes && lane == 0)
-#pragma unroll
-    for (int k = 0; k < RR; ++k)
-      if (actk[k]) atomicAdd(a.work_bytes, a.site_bytes * it.z);
   const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
   const long long* off_in = p ? bd.off[0] : bd.off[1];
   const long long* off_out = p ? bd.off[1] : bd.off[0];
@@ -934,203 +937,6 @@ static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, 
       bd, a, ngroups, rb);
 }
 
-// one hop direction of one rhs: neighbour spinor from global memory, link from the bundle
-template <int DIR, class S, class C>
-__device__ __forceinline__ void hop_one_lb(C (&acc)[12], int j, int n_in, const S* __restrict__ in_sys,
-                                           const S* ql, int lane) {
-  if (j < 0) return;
-  C psi[12];
-  ld_site<12>(in_sys, n_in, j, psi);
-  C U[9];
-  lds_link(ql + DIR * 5 * LB_LANES * 2, lane, U);
-  hop_dir<DIR & 3, (DIR < 4)>(acc, psi, U);
-}
-
-// ---- bundle form, warps of 8 sites x 4 rhs --------------------------------------------
-// As k_hop_lb (links and neighbour indices of a 128-site item by bulk copy into
-// shared memory), but a warp covers 8 consecutive sites of a quarter for 4 rhs
-// (lane = 8 * rhs-in-quad + site) instead of 32 sites of one rhs: each link word
-// read from shared memory serves the 4 rhs lanes of a site by broadcast (one
-// 128-byte wavefront per 8 sites instead of four per 32), and each neighbour
-// spinor load is still four full 128-byte lines (8 consecutive sites per rhs).
-// The per-system inner products are summed over the 8 site lanes by shuffles
-// and over the CTA's 4 site octets in shared memory, in a fixed order.
-template <class S, int MINB>
-__global__ void __launch_bounds__(32 * LB_MAX_RHS, MINB)
-    k_hop_lb8(BatchDev bd, HopArgs a, int ngroups, int rb) {
-  typedef typename StoreTraits<S>::C C;
-  typedef typename StoreTraits<S>::T T;
-  constexpr int QB = lb_quarter_bytes<S>();
-  extern __shared__ __align__(128) unsigned char lb_smem[];
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + LB_QUARTERS * QB);
-  double* red = reinterpret_cast<double*>(lb_smem + LB_QUARTERS * QB + 64);   // [12 rhs][4 octets][7]
-  const int p = a.p_out;
-  const int item = (int)(blockIdx.x / ngroups);
-  const int g = (int)(blockIdx.x - (long long)item * ngroups);
-  const int4 it = (p ? bd.items[1] : bd.items[0])[item];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int oct = w & 3, s8 = l & 7;
-  const int rr = (w >> 2) * 4 + (l >> 3);          // rhs within the group
-  const int r = g * rb + rr;
-  const int sys = it.x * bd.nrhs + r;
-  const bool act = rr < rb && r < bd.nrhs && (!a.active || a.active[(long long)sys * a.active_stride]);
-  if (!__syncthreads_or(act)) return;          // every rhs of the group has converged
-  const DomInst* dp = bd.inst_tab + bd.inst[it.x];
-  const int n0 = dp->n[0];
-  const int nq = (it.z + LB_LANES - 1) / LB_LANES;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < nq; ++q) mbar_init(&bar[q], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned char* src =
-        bundle_of<S>(*dp) + (lb_quarter_base(p, n0) + (long long)LB_QUARTERS * (it.y / LB_CHUNK)) * QB;
-    for (int q = 0; q < nq; ++q) {
-      mbar_expect_tx(&bar[q], QB);
-      bulk_copy_g2s(lb_smem + q * QB, src + (long long)q * QB, QB, &bar[q]);
-    }
-  }
-  if (act && a.work_bytes && oct == 0 && s8 == 0) atomicAdd(a.work_bytes, a.site_bytes * it.z);
-  const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
-  const S* in_sys = act ? (const S*)a.in + (p ? bd.off[0] : bd.off[1])[sys] : (const S*)a.in;
-  const long long oo = act ? (p ? bd.off[1] : bd.off[0])[sys] : 0;
-  const int bl = 8 * oct + s8;                      // site lane within a quarter's bundle
-  const auto bsc = mkscal<C>(a.b);
-  const auto a1 = mkscal<C>(a.a1);
-  const auto a2 = mkscal<C>(a.a2);
-  const bool dots_in_s1 = a.dots && a.dots == a.s1 && !a.s2;
-  T tq[2] = {0, 0}, ts[3] = {0, 0, 0}, tqs[2] = {0, 0};
-  for (int q = 0; q < nq; ++q) {
-    // every thread waits, so the CTA never leaves with a copy in flight
-    const bool ok = mbar_wait0(&bar[q]);
-    if (!ok && l == 0) atomicExch(a.err, 1);
-    const int li = q * LB_LANES + bl;
-    if (!(act && ok && li < it.z)) continue;
-    const int i = it.y + li;
-    const unsigned char* qb = lb_smem + q * QB;
-    const S* ql = reinterpret_cast<const S*>(qb);
-    const int* qi = reinterpret_cast<const int*>(qb + lb_link_bytes<S>());
-    C acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = cmk<C>(0.0, 0.0);
-    hop_one_lb<3, S>(acc, qi[3 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<7, S>(acc, qi[7 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<2, S>(acc, qi[2 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<6, S>(acc, qi[6 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<1, S>(acc, qi[1 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<5, S>(acc, qi[5 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<0, S>(acc, qi[0 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    hop_one_lb<4, S>(acc, qi[4 * LB_LANES + bl], n_in, in_sys, ql, bl);
-    // epilogue one component pair at a time: self terms, store, fused inner products
-#pragma unroll
-    for (int pq = 0; pq < 6; ++pq) {
-      const long long e = oo + ((long long)pq * n_out + i) * 2;
-      C ov[2], sv[2];
-      ov[0] = scale(acc[2 * pq], bsc);
-      ov[1] = scale(acc[2 * pq + 1], bsc);
-      if (a.s1) {
-        ld_pair((const S*)a.s1 + e, sv[0], sv[1]);
-        axpy(ov[0], a1, sv[0]);
-        axpy(ov[1], a1, sv[1]);
-      }
-      if (a.s2) {
-        C v2[2];
-        ld_pair((const S*)a.s2 + e, v2[0], v2[1]);
-        axpy(ov[0], a2, v2[0]);
-        axpy(ov[1], a2, v2[1]);
-      }
-      st_pair((S*)a.out + e, ov[0], ov[1]);
-      if (a.dots) {
-        C dv[2];
-        if (dots_in_s1) {
-          dv[0] = sv[0];
-          dv[1] = sv[1];
-        } else {
-          ld_pair((const S*)a.dots + e, dv[0], dv[1]);
-        }
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const C o = ov[hh], z = dv[hh];
-          ts[0] = fma(o.x, z.x, fma(o.y, z.y, ts[0]));
-          ts[1] = fma(o.x, z.y, fma(-o.y, z.x, ts[1]));
-          ts[2] = fma(o.x, o.x, fma(o.y, o.y, ts[2]));
-        }
-      }
-      if (a.dotq) {
-        C rv[2];
-        ld_rhat_pair(a.rhat_seed, sys, (const S*)a.dotq + oo, n_out, i, pq, rv[0], rv[1]);
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const C o = ov[hh], wq = rv[hh];
-          tq[0] = fma(wq.x, o.x, fma(wq.y, o.y, tq[0]));
-          tq[1] = fma(wq.x, o.y, fma(-wq.y, o.x, tq[1]));
-        }
-        if (a.dotqs) {
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const C wq = rv[hh], z = sv[hh];
-            tqs[0] = fma(wq.x, z.x, fma(wq.y, z.y, tqs[0]));
-            tqs[1] = fma(wq.x, z.y, fma(-wq.y, z.x, tqs[1]));
-          }
-        }
-      }
-    }
-  }
-  if (!a.dotq && !a.dots) return;
-  // sums over the 8 site lanes of each rhs (every lane takes part; idle lanes hold 0)
-  T v[7] = {tq[0], tq[1], ts[0], ts[1], ts[2], tqs[0], tqs[1]};
-#pragma unroll
-  for (int k = 0; k < 7; ++k)
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  if (s8 == 0 && rr < LB_MAX_RHS)
-#pragma unroll
-    for (int k = 0; k < 7; ++k) red[(rr * 4 + oct) * 7 + k] = (double)v[k];
-  __syncthreads();
-  // one thread per rhs adds its 4 octets in order and writes the partial slots
-  if (threadIdx.x >= rb) return;
-  const int rq = threadIdx.x;
-  const int rg = g * rb + rq;
-  if (rg >= bd.nrhs) return;
-  const int sq = it.x * bd.nrhs + rg;
-  if (a.active && !a.active[(long long)sq * a.active_stride]) return;
-  double t[7];
-#pragma unroll
-  for (int k = 0; k < 7; ++k)
-    t[k] = ((red[(rq * 4 + 0) * 7 + k] + red[(rq * 4 + 1) * 7 + k]) + red[(rq * 4 + 2) * 7 + k]) +
-           red[(rq * 4 + 3) * 7 + k];
-  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
-  const long long my = (long long)item * bd.nrhs + rg;
-  if (a.dotq) {
-    a.partial[2 * my] = t[0];
-    a.partial[2 * my + 1] = t[1];
-  }
-  if (a.dots) {
-    double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
-    P[2 * my] = t[2];
-    P[2 * my + 1] = t[3];
-    P[2 * (slot_stride + my)] = t[4];
-    P[2 * (slot_stride + my) + 1] = 0.0;
-  }
-  if (a.dotqs) {
-    a.partial[2 * (3 * slot_stride + my)] = t[5];
-    a.partial[2 * (3 * slot_stride + my) + 1] = t[6];
-  }
-}
-
-template <class S>
-constexpr int lb8_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64 + LB_MAX_RHS * 4 * 7 * 8; }
-
-template <class S, int MINB>
-static void launch_lb8(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
-  const int ngroups = (bd.nrhs + LB_MAX_RHS - 1) / LB_MAX_RHS;
-  const int rb = (bd.nrhs + ngroups - 1) / ngroups;
-  const int nthreads = 128 * ((rb + 3) / 4);
-  DD_COUNT_LAUNCH(), k_hop_lb8<S, MINB><<<(unsigned)(nitems_p * ngroups), nthreads, lb8_smem_bytes<S>(), s>>>(
-      bd, a, ngroups, rb);
-}
-
 void hop_bundle_prepare() {
   static bool done[64] = {false};
   int dev = 0;
@@ -1146,16 +952,14 @@ void hop_bundle_prepare() {
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 1, 1>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 3, 2>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 4, 3>, at, b16);
-  cudaFuncSetAttribute(k_hop_lb8<float2, 2>, at, lb8_smem_bytes<float2>());
-  cudaFuncSetAttribute(k_hop_lb8<__nv_bfloat162, 2>, at, lb8_smem_bytes<__nv_bfloat162>());
   done[dev] = true;
 }
 
 struct HopVariant {
   int minb;
   bool persist;
-  int r;          // rhs per thread (0: direction-split, 256 threads per item; -k, k < 10: bundle form
-                  // with k rhs per thread; -30: bundle form with warps of 8 sites x 4 rhs)
+  int r;          // rhs per thread (0: direction-split, 256 threads per item; -k: bundle form
+                  // with k rhs per thread)
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -1164,13 +968,12 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {4, true, 1}, {4, false, 2}, {5, false, 2}, {4, true, 2},
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
-                                         {2, false, -3}, {2, false, -30}};
+                                         {2, false, -3}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
-                                         {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
-                                         {2, false, -30}};
+                                         {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 18 : 13); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 17 : 12); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1205,11 +1008,6 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
   const HopVariant& hv = variant_of(prec, v);
   if (hv.r < 0) {
     const int rr = -hv.r;
-    if (rr == 30) {         // bundle form, warps of 8 sites x 4 rhs
-      if (prec == DD_F32) launch_lb8<float2, 2>(bd, a, ni, s);
-      else launch_lb8<__nv_bfloat162, 2>(bd, a, ni, s);
-      return;
-    }
     if (prec == DD_F32) {
       if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
       else if (rr == 2) launch_lb<float2, 2, 2>(bd, a, ni, s);
@@ -1461,11 +1259,7 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.r == -30)
-          snprintf(names[k][u], sizeof names[k][u],
-                   "k_hop_lb8<%s,%d>: links by bulk copy, warps of 8 sites x 4 rhs (broadcast link reads)",
-                   ty[k], h.minb);
-        else if (h.r < 0)
+        if (h.r < 0)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);
