@@ -269,6 +269,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
 
+    # BF16-storage inner solve of the same batch (FP32 arithmetic, double-float residuals)
+    bf16 = None
+    if rank == 0:
+        bprm = dd4d.params(TOL, inner_prec="bf16", inner_tol=1e-3, check_every=8, autotune=True)
+        try:
+            step(bprm)
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            qst = step(bprm)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            bms = q0.elapsed_time(q1)
+            bf16 = {"value": units / (bms * 1e-3), "ms_per_step": bms, "inner_tol": 1e-3,
+                    "max_iters": qst["max_iters"], "outer_cycles": qst["outer_cycles"],
+                    "max_relres": qst["max_relres"], "hop_variant": dd4d.hop_variant_name("bf16", qst["hop_variant"])}
+        except (dd4d.DDError, RuntimeError) as err:
+            bf16 = {"unavailable": str(err)[:200]}
+
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms)
@@ -342,6 +361,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "solver": {"max_relres": stats["max_relres"], "max_iters": stats["max_iters"],
                    "outer_cycles": stats["outer_cycles"], "hop_variant": stats["hop_variant"]},
+        "bf16_inner": bf16,
         "plain_f64": {"value": world * units / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                       "max_iters": pst["max_iters"], "speedup_of_mixed": plain_ms / ms,
                       "residual_hop_ms_in_mixed_step": hop64_ms / args.steps},
