@@ -127,3 +127,36 @@ def test_invalid_geometries():
         Decomposition((8,) * 4, [[(0, 6)]] + [[(0, 2), (4, 6)]] * 3)
     with pytest.raises(ValueError):
         Decomposition((8,) * 4, [[(0, 2), (3, 6)]] + [[(0, 2), (4, 6)]] * 3)
+
+
+def _cores(period_sizes):
+    """Core intervals from (core size, frame) pairs laid end to end from x = 0."""
+    out, x = [], 0
+    for size, frame in period_sizes:
+        out.append((x, x + size - 1))
+        x += size + frame
+    return out
+
+
+SURVEY_CONFIGS = {
+    # L, cores, (blocks, Lambda1, dPi, B, C, E, A), set of Omega sizes
+    "32^4": ((32,) * 4, [_cores([(7, 1)] * 4)] * 4,
+             (256, 433920, 716800, 454656, 262144, 171776, 160000), {6561}),
+    "64x32^3": ((64, 32, 32, 32), [_cores([(6, 1), (8, 1)] * 4)] + [_cores([(6, 1), (8, 1)] * 2)] * 3,
+                (512, 867840, 1433600, 909312, 524288, 343552, 320000), None),
+    "48^4": ((48,) * 4, [_cores([(7, 1)] * 6)] * 4,
+             (1296, 2196720, 3628800, 2301696, 1327104, 869616, 810000), {6561}),
+}
+
+
+@pytest.mark.parametrize("name", list(SURVEY_CONFIGS))
+def test_large_configuration_sizes(name):
+    """Closed-form set sizes of the benchmark geometries (counted per direction,
+    no lattice masks) against the tabulated values."""
+    L, cores, ref, omegas = SURVEY_CONFIGS[name]
+    c = _closed_form(L, cores)
+    assert (c["nblocks"], c["Lambda1"], c["dPi"], c["B"], c["C"], c["E"], c["A"]) == ref
+    if omegas is not None:
+        assert set(c["omega"]) == omegas
+    else:
+        assert len(set(c["omega"])) == 5 and min(c["omega"]) == 4096 and max(c["omega"]) == 10000
