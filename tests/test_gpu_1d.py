@@ -74,3 +74,17 @@ def test_one_dimensional_det_formula(case):
     one_d = rep["logabs_W1"] + float(np.sum(rep["logabs_omega"])) - rep["logabs_Lambda1"]
     assert abs(rep["logabs_D"] - one_d) < 1e-8
     assert abs(float(np.sum(rep["logabs_phi"])) - 2 * rep["logabs_Lambda1"]) < 1e-9
+
+
+def test_two_dimensional_decomposition_identity():
+    """Time and x1 decomposed (corners: dPi1 not empty), x2 and x3 wrapping:
+    the dense check of Eq. (detD) against the oracle."""
+    L2 = (8, 8, 2, 2)
+    cores = [[(0, 1), (4, 5)], [(0, 1), (4, 5)], [], []]
+    U, ctx, info, geo = make_case(L2, 0.13, 0.4, 7, cores)
+    assert info["nblocks"] == 4 and info["n_C"] > 0
+    rep = ctx.logdet_check(dd4d.params(1e-13, maxiter=5000))
+    assert abs(rep["residual"]) < 1e-9, rep
+    f = Oracle(U, 0.13, geo).logdet_factors()
+    assert abs(rep["logabs_D"] - f["D"][1]) < 1e-9
+    assert abs(rep["logabs_W1"] - f["W1"][1]) < 1e-8

@@ -245,3 +245,16 @@ def test_undecomposed_direction_adds_no_hyperplane():
         Decomposition(L1D, [[], [], [], []])
     with pytest.raises(ValueError):
         Decomposition(L1D, [[(0, 1)], [], [], []])
+
+
+def test_two_dimensional_decomposition_identity():
+    """Time and x1 decomposed, x2 and x3 not: the frame has corners (dPi1 is not
+    empty) and the domains wrap around in x2, x3; Eq. (detD) holds as in 4D."""
+    L = (8, 8, 2, 2)
+    cores = [[(0, 1), (4, 5)], [(0, 1), (4, 5)], [], []]
+    U = synth.gauge_field(L, 0.4, 7)
+    g = Decomposition(L, cores)
+    assert g.nblocks == 4 and g.C.any()
+    f = Oracle(U, 0.13, g).logdet_factors()
+    rhs = f["W1"][1] + f["Lambda1"][1] + sum(x[1] for x in f["Omega"]) - sum(x[1] for x in f["Phi"])
+    assert abs(f["D"][1] - rhs) < 1e-10
