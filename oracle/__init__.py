@@ -17,8 +17,9 @@ factorization of the fermion determinant", Lattice 2022):
                  dLambda0, dPi, dPi1, Omega0^a, Phi1^a and exterior boundaries).
 * ``dd``       - block and frame solves, the operator w = 1 - W_1 (Eqs. Wz,
                  offdiagW1), the roots u_k (Sec. 4), the multi-boson action
-                 (Eqs. MBaction, localMB, globalMB) and the dense log-det
-                 factors of Eq. (detD).
+                 (Eqs. MBaction, localMB, globalMB), the dense log-det
+                 factors of Eq. (detD) and the stochastic samples of the
+                 reweighting factor of Eq. (rw).
 
 Parity status: every function is pinned by a CPU test against closed forms,
 identities of the paper or brute force, except the agreement of W_1 with the

@@ -212,6 +212,27 @@ class Oracle:
             out.append(f.reshape(eta.shape))
         return out
 
+    def reweight_apply(self, N, c, eta):
+        """M eta with M = 1 - R_{N+1}(W_1) = W_1 P_N(W_1) (Sec. 4, Eq. rw), in the
+        paper's product form P_N(z) = c_N prod_{k=1..N} (z - z_k): each factor
+        W_1 - z_k = u_k - w, then W_1 = 1 - w, then the constant c_N."""
+        y = eta.copy()
+        for uk in roots(N, c):
+            y = uk * y - self.apply_w(y)
+        y = y - self.apply_w(y)
+        return pn_leading(N, c) * y
+
+    def reweight_samples(self, N, c, etas):
+        """Per source eta (complex Gaussian, density exp(-|eta|^2), on dPi):
+        s = |eta|^2 - |M eta|^2.  E[exp(s)] = 1/det(M^dag M) = |W_N|^-2, the
+        stochastic estimate of the reweighting factor of Eq. (rw) (reading:
+        the paper names the factor but no estimator)."""
+        out = []
+        for eta in etas:
+            m = self.reweight_apply(N, c, eta)
+            out.append(float(np.sum(np.abs(eta) ** 2) - np.sum(np.abs(m) ** 2)))
+        return np.array(out)
+
     def logdet_factors(self):
         """slogdet of D, W_1, D_{Lambda1}, D_{Omega0^a}, D_{Phi1^a} (dense LU)."""
         g = self.g
@@ -245,3 +266,23 @@ def field_roots(N, c):
     if N % 2:
         raise ValueError("N must be even")
     return roots(N, c)[: N // 2]
+
+
+def chebyshev_T(n, x):
+    """T_n(x) = cosh(n arccosh x) for x >= 1."""
+    return math.cosh(n * math.acosh(x))
+
+
+def pn_leading(N, c):
+    """c_N of P_N(z) = c_N prod_k (z - z_k) (Sec. 4) for the roots above.
+
+    With R_{N+1}(z) = T_{N+1}((1 - z)/c) / T_{N+1}(1/c) (reading of c), the
+    leading coefficient of 1 - R_{N+1}(z) = z P_N(z) is
+    -2^N (-1/c)^{N+1} / T_{N+1}(1/c) = 2^N / (c^{N+1} T_{N+1}(1/c)) for N even;
+    at c = 0, R_{N+1}(z) = (1 - z)^{N+1} and c_N = 1.
+    """
+    if N % 2:
+        raise ValueError("N must be even")
+    if c == 0.0:
+        return 1.0
+    return 2.0 ** N / (c ** (N + 1) * chebyshev_T(N + 1, 1.0 / c))
