@@ -310,10 +310,11 @@ def run_ours(args):
     del bh, xh
 
     # multi-boson action on the 8^4 lattice (16 blocks of 5^4, N = 4, 2 fields)
-    action = uneven = heatbath = config5 = None
+    action = uneven = heatbath = reweight = config5 = None
     if rank == 0:
         action = action_rate(dd4d, synth, torch)
         heatbath = heatbath_rate(dd4d, synth, torch)
+        reweight = reweight_rate(dd4d, synth, torch)
         if not args.no_uneven:
             uneven = uneven_action_rate(dd4d, synth, torch)
         if not args.no_config5:
@@ -369,6 +370,7 @@ def run_ours(args):
         "action_uneven": uneven,
         "action_48x4": config5,
         "heatbath": heatbath,
+        "reweight": reweight,
         "learned_guess": learned,
         "stencil": stencil,
     }
@@ -507,6 +509,34 @@ def heatbath_rate(dd4d, synth, torch, reps=3):
                         "N = 8 (4 fields), BiCGstab on dPi to 1e-10 over apply_w with FP64 solves to 1e-11",
             "iterations": st["iterations"], "matvecs": st["matvecs"], "max_relres": st["max_relres"],
             "action_identity_relerr": abs(S - ref) / ref}
+
+
+def reweight_rate(dd4d, synth, torch, n_src=16, N=12, cpar=0.5, reps=2):
+    """Stochastic samples of the reweighting factor W_N = det{1 - R_{N+1}(W_1)} (Eq. rw)
+    on the 8^4 lattice: s = |eta|^2 - |M eta|^2 for 16 complex Gaussian sources, each
+    R_{N+1}(W_1) eta built from N + 1 = 13 apply_w batches; mean(exp(s)) estimates |W_N|^-2."""
+    L = (8, 8, 8, 8)
+    c = dd4d.Context(L, 0.13)
+    c.gauge_random(0.3, 1)
+    c.set_geometry(cores_uniform(L, 3, 1))
+    dpi = c.geom_sites(dd4d.SET_DPI)
+    eta = synth.complex_gaussian(2, synth.TAG_CHI, (n_src, len(dpi), 12))
+    de = torch.from_numpy(eta.view(np.float64)).cuda()
+    prm = dd4d.params(1e-11, inner_prec="f64", graph=True, autotune=True)
+    c.reweight_samples(N, cpar, de, None, prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        smp, st = c.reweight_samples(N, cpar, de, None, prm)
+    dt = (time.perf_counter() - t0) / reps
+    c.close()
+    ex = np.exp(smp)
+    mean, err = float(ex.mean()), float(ex.std(ddof=1) / np.sqrt(n_src))
+    return {"metric": "reweighting samples/s", "value": n_src / dt, "unit": "samples/s",
+            "workload": "8^4, kappa 0.13, eps 0.3 (links drawn on the device), 16 blocks of 5^4 + frame, "
+                        "N = 12, c = 0.5, 16 sources, 13 apply_w batches with FP64 solves to 1e-11",
+            "status": st, "mean_exp_s": mean, "stderr": err,
+            "ln_abs_W_N": -0.5 * float(np.log(mean))}
 
 
 def config5_action_rate(dd4d, synth, torch, group=8):

@@ -255,6 +255,27 @@ dd_status dd_multiboson_heatbath(dd_ctx* ctx, int n_f, const double* u, const do
                                  const dd_solve_params* params, dd_heatbath_stats* stats,
                                  void* stream);
 
+/* ---- reweighting factor (paper Sec. 4, Eq. rw) ------------------------------
+ * W_N = det{1 - R_{N+1}(W_1)}, W_1 = 1 - w on dPi, with the polynomial of the
+ * roots below: R_{N+1}(z) = T_{N+1}((1-z)/c) / T_{N+1}(1/c) for c > 0 and
+ * (1-z)^{N+1} for c = 0 (T the Chebyshev polynomials).  The paper gives no
+ * estimator; this call returns, for each of n_src sources eta (complex
+ * Gaussian of density exp(-|eta|^2), drawn by the caller, layout of
+ * dd_apply_w, device or host), the sample
+ *   s = |eta|^2 - |M eta|^2,  M = 1 - R_{N+1}(W_1),
+ * whose exponential has the mean E[exp(s)] = 1/det(M^dag M) = |W_N|^-2 (finite
+ * variance when every eigenvalue of M^dag M exceeds 1/2, i.e. R small: thick
+ * frames).  R eta is built from N + 1 dd_apply_w batches over all sources
+ * (Chebyshev recurrence in w, block and frame solves to params->tol) and s is
+ * formed as 2 Re(eta, R eta) - |R eta|^2 (FP64, fixed-order sums).
+ * N even >= 2, 0 <= c < 1, 1 <= n_src <= 65535.  s: host, n_src doubles.
+ * r_eta: NULL, or a device or host buffer of the layout of eta that receives
+ * R_{N+1}(W_1) eta.  Returns DD_ENOCONV (samples filled) if an inner solve
+ * missed its tolerance.  Synchronises. */
+dd_status dd_reweight_samples(dd_ctx* ctx, int N, double c, int n_src, const double* eta,
+                              double* s, double* r_eta, const dd_solve_params* params,
+                              void* stream);
+
 /* ---- roots (paper Sec. 4) --------------------------------------------------
  * u_k = 1 - z_k = cos(2 pi k/(N+1)) + i sqrt(1-c^2) sin(2 pi k/(N+1)),
  * k = 1..N/2: the roots that carry the N/2 multi-boson fields (conjugates

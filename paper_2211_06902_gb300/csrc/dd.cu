@@ -534,6 +534,76 @@ static dd_status heatbath_dev(dd_ctx* c, int n_f, const double2* u_h, const doub
   return DD_OK;
 }
 
+// ---- reweighting factor of Eq. (rw): samples s = |eta|^2 - |M eta|^2 ------------
+// M = 1 - R_{N+1}(W_1) and 1 - W_1 = w, so R_{N+1}(W_1) = T_{N+1}(w/c) / T_{N+1}(1/c)
+// (w^{N+1} at c = 0).  R eta by the three-term recurrence in w, normalised so that
+// every iterate stays O(|eta|): t_j = T_j(w/c) eta / T_j(1/c), t_0 = eta, t_1 = w eta,
+// t_{j+1} = a_j w t_j - b_j t_{j-1} with a_j = (2/c) T_j/T_{j+1}, b_j = T_{j-1}/T_{j+1}
+// (a = 1, b = 0 at c = 0).  N + 1 dd_apply_w batches over all sources.  The sample is
+// formed as 2 Re(eta, R eta) - |R eta|^2, which equals |eta|^2 - |eta - R eta|^2
+// without the cancellation of two nearly equal norms.
+static dd_status reweight_dev(dd_ctx* c, int N, double cpar, int n_src, const double2* eta, double* s_out,
+                              double2** r_eta_dev, const dd_solve_params* prm, cudaStream_t s) {
+  const long long n = 12LL * c->info.n_dpi;
+  const size_t vb = sizeof(double2) * (size_t)n_src * n;
+  void *va, *vb2, *vw, *vc, *vpart;
+  dd_status e;
+  if ((e = workspace(c, 213, vb, &va)) || (e = workspace(c, 214, vb, &vb2)) || (e = workspace(c, 215, vb, &vw)) ||
+      (e = workspace(c, 216, sizeof(double2) * 3 * n_src, &vc)) ||
+      (e = workspace(c, 217, sizeof(double) * 2 * n_src * HB_CHUNKS, &vpart)))
+    return e;
+  double2 *A = (double2*)va, *B = (double2*)vb2, *wt = (double2*)vw, *dc = (double2*)vc;
+  double* dpart = (double*)vpart;
+  const dim3 grid((unsigned)((n + 255) / 256), n_src);
+  // T_j(1/c), j = 0..N+1 (host scalars; the recurrence is exact in exact arithmetic)
+  std::vector<double> T(N + 2, 1.0);
+  if (cpar > 0.0) {
+    T[1] = 1.0 / cpar;
+    for (int j = 1; j <= N; ++j) T[j + 1] = 2.0 / cpar * T[j] - T[j - 1];
+  }
+  bool noconv = false;
+  auto w_of = [&](const double2* x, double2* y) -> dd_status {
+    dd_status r0 = apply_w_dev(c, n_src, (const double*)x, (double*)y, prm, s);
+    if (r0 == DD_ENOCONV) noconv = true;
+    else if (r0 != DD_OK) return r0;
+    return DD_OK;
+  };
+  std::vector<double2> cf(3 * n_src);
+  // t_1 = w eta
+  if ((e = w_of(eta, A)) != DD_OK) return e;
+  const double2* prev = eta;
+  double2* cur = A;
+  for (int j = 1; j <= N; ++j) {
+    double2* next = (prev == eta) ? B : const_cast<double2*>(prev);
+    if (cpar > 0.0) {
+      if ((e = w_of(cur, wt)) != DD_OK) return e;
+      const double a = 2.0 / cpar * T[j] / T[j + 1], b = T[j - 1] / T[j + 1];
+      for (int f = 0; f < n_src; ++f) {
+        cf[3 * f] = make_double2(a, 0.0);
+        cf[3 * f + 1] = make_double2(-b, 0.0);
+        cf[3 * f + 2] = make_double2(0.0, 0.0);
+      }
+      DD_CUDA(c, cudaMemcpyAsync(dc, cf.data(), sizeof(double2) * 3 * n_src, cudaMemcpyHostToDevice, s));
+      DD_COUNT_LAUNCH(), k_hb_lin<<<grid, 256, 0, s>>>(n_src, n, nullptr, dc, wt, prev, nullptr, next);
+      DD_CUDA(c, cudaGetLastError());
+    } else {
+      if ((e = w_of(cur, next)) != DD_OK) return e;
+    }
+    prev = cur;
+    cur = next;
+  }
+  std::vector<double2> er, rr;
+  if ((e = hb_dot(c, n_src, n, eta, cur, dpart, er, s)) != DD_OK) return e;
+  if ((e = hb_dot(c, n_src, n, cur, cur, dpart, rr, s)) != DD_OK) return e;
+  for (int f = 0; f < n_src; ++f) {
+    s_out[f] = 2.0 * er[f].x - rr[f].x;
+    if (!(s_out[f] == s_out[f])) return fail(c, DD_ENAN, "NaN in a reweighting sample");
+  }
+  if (r_eta_dev) *r_eta_dev = cur;
+  if (noconv) return fail(c, DD_ENOCONV, "a block or frame solve missed its tolerance");
+  return DD_OK;
+}
+
 }  // namespace dd
 
 using namespace dd;
@@ -646,6 +716,31 @@ dd_status dd_multiboson_heatbath(dd_ctx* c, int n_f, const double* u, const doub
   dd_status r = heatbath_dev(c, n_f, uh.data(), (const double2*)din, (double2*)dout, tol, maxiter, prm, stats, s);
   if (r != DD_OK && r != DD_ENOCONV) return r;
   if (hout) DD_CUDA(c, cudaMemcpyAsync(chi, dout, bytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  return r;
+}
+
+dd_status dd_reweight_samples(dd_ctx* c, int N, double cpar, int n_src, const double* eta, double* s_out,
+                              double* r_eta, const dd_solve_params* prm, void* stream) {
+  if (!c || !eta || !s_out || !prm || n_src < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (n_src > 65535) return fail(c, DD_EINVAL, "n_src must be <= 65535");
+  if (N < 2 || N % 2) return fail(c, DD_EINVAL, "N must be even and >= 2");
+  if (!(cpar >= 0.0 && cpar < 1.0)) return fail(c, DD_EINVAL, "c must lie in [0, 1)");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = 16ULL * n_src * c->info.n_dpi * 12;
+  const double* din = eta;
+  dd_status e;
+  if (!is_device_ptr(eta)) {
+    void* p;
+    if ((e = workspace(c, 218, bytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, eta, bytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  double2* rdev = nullptr;
+  dd_status r = reweight_dev(c, N, cpar, n_src, (const double2*)din, s_out, &rdev, prm, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  if (r_eta) DD_CUDA(c, cudaMemcpyAsync(r_eta, rdev, bytes, cudaMemcpyDefault, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
   return r;
 }

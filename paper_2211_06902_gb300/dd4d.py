@@ -110,6 +110,8 @@ def lib():
             "dd_net_load": [vp, C.c_char_p, C.POINTER(vp)],
             "dd_hop_variant_name": [C.c_int, C.c_int],
             "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
+            "dd_reweight_samples": [vp, C.c_int, C.c_double, C.c_int, vp, dp, vp,
+                                    C.POINTER(SolveParams), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -129,7 +131,7 @@ def exported_symbols():
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
-            "dd_apply_D_block_noalloc"]
+            "dd_apply_D_block_noalloc", "dd_reweight_samples"]
 
 
 def hop_variant_name(prec, v):
@@ -327,6 +329,17 @@ class Context:
         d = st.as_dict()
         d["status"] = s
         return d
+
+    def reweight_samples(self, N, c, eta, r_eta=None, prm=None, stream=None):
+        """Samples s = |eta|^2 - |M eta|^2, M = 1 - R_{N+1}(W_1), one per source of eta
+        (layout of apply_w); mean(exp(s)) estimates |W_N|^-2 (Eq. rw).  Returns
+        (s, status); r_eta, if given, receives R_{N+1}(W_1) eta."""
+        n_src = int(eta.shape[0])
+        out = np.zeros(n_src)
+        st = self._check(lib().dd_reweight_samples(
+            self._h, int(N), float(c), n_src, _ptr(eta), out.ctypes.data_as(C.POINTER(C.c_double)),
+            None if r_eta is None else _ptr(r_eta), C.byref(prm or params()), _stream(stream)))
+        return out, st
 
     def multiboson_action(self, u, chi, prm=None, stream=None):
         u = np.asarray(u, dtype=np.complex128)
