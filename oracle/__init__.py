@@ -18,8 +18,9 @@ factorization of the fermion determinant", Lattice 2022):
 * ``dd``       - block and frame solves, the operator w = 1 - W_1 (Eqs. Wz,
                  offdiagW1), the roots u_k (Sec. 4), the multi-boson action
                  (Eqs. MBaction, localMB, globalMB), the dense log-det
-                 factors of Eq. (detD) and the stochastic samples of the
-                 reweighting factor of Eq. (rw).
+                 factors of Eq. (detD), the stochastic samples of the
+                 reweighting factor of Eq. (rw) and the force of the
+                 factorized multi-boson action on the active links.
 
 Parity status: every function is pinned by a CPU test against closed forms,
 identities of the paper or brute force, except the agreement of W_1 with the

@@ -27,7 +27,7 @@ import math
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from .lattice import apply_D, dirac_block, dirac_matrix
+from .lattice import apply_D, dirac_block, dirac_matrix, gammas
 
 
 class DomainSolver:
@@ -63,6 +63,18 @@ class DomainSolver:
         """b: field [L0..L3,4,3] supported on X; returns D_X^{-1} b as a field."""
         V = int(np.prod(self.L))
         x = self.solve_vec(b.reshape(V, 12)[self.sites].ravel())
+        out = np.zeros((V, 12), dtype=np.complex128)
+        out[self.sites] = x.reshape(-1, 12)
+        return out.reshape(b.shape)
+
+    def solve_adjoint_field(self, b):
+        """(D_X^dag)^{-1} b for a field supported on X (BiCGstab on the conjugate
+        transpose of the assembled matrix)."""
+        V = int(np.prod(self.L))
+        MH = self.M.conj().T.tocsr()
+        x, relres = bicgstab(lambda v: MH @ v, b.reshape(V, 12)[self.sites].ravel(), self.TOL)
+        if not relres <= 10 * self.TOL:
+            raise RuntimeError("oracle adjoint solve did not converge: %g" % relres)
         out = np.zeros((V, 12), dtype=np.complex128)
         out[self.sites] = x.reshape(-1, 12)
         return out.reshape(b.shape)
@@ -212,6 +224,65 @@ class Oracle:
             out.append(f.reshape(eta.shape))
         return out
 
+    # -- force of the factorized multi-boson action on the active links -----
+    def active_links(self, a):
+        """Links (x, mu) of block a with both end points in its core Lambda0^a
+        (the links a multi-level update of block a changes; Sec. 4: S^r and the
+        S^b, b != a, do not depend on them)."""
+        g = self.g
+        cm = g.core_mask[a]
+        out = []
+        for mu in range(4):
+            nxt = np.roll(cm, -1, axis=mu)                     # x + mu in the core
+            for x in np.argwhere(cm & nxt):
+                out.append((tuple(int(v) for v in x), mu))
+        return out
+
+    def mb_force(self, u, chis):
+        """F[x, mu, t] = d S_MB / d eps at U_mu(x) -> exp(i eps T_t) U_mu(x),
+        T_t = lambda_t / 2, for the active links of every block (zero elsewhere).
+
+        Only S^a of the link's block depends on it, through D_{Omega0^a}
+        (Eq. localMB): with y_k = D_Omega^{-1} D_{Omega,ext} chi_k and
+        r_k = P_{dLambda0^a}(u_k chi_k + y_k), S^a = sum_k |r_k|^2 and
+        dy = -D_Omega^{-1} dD y, so dS = -2 Re sum_k <z_k, dD y_k> with
+        z_k = (D_Omega^dag)^{-1} r_k.  dD has the two entries of the link in
+        the definition of D: row x, column x+mu: -kappa (1 - gamma_mu) (i T U);
+        row x+mu, column x: -kappa (1 + gamma_mu) (-i U^dag T) (times the time
+        boundary sign where the link crosses x0 = L0-1 -> 0)."""
+        g = self.g
+        L = g.L
+        gam, _ = gammas()
+        one = np.eye(4)
+        T = gell_mann() / 2
+        F = np.zeros(tuple(L) + (4, 8))
+        for a in range(g.nblocks):
+            links = self.active_links(a)
+            if not links:
+                continue
+            om = self.omega_solver(a)
+            ext = g.ext_mask[a][..., None, None]
+            pairs = []
+            for uk, chi in zip(u, chis):
+                y = om.solve_field(g.omega_mask[a][..., None, None] * self.D(chi * ext))
+                r = g.B_mask[a][..., None, None] * (uk * chi + y)
+                pairs.append((y, om.solve_adjoint_field(r)))
+            for x, mu in links:
+                xp = list(x)
+                xp[mu] = (xp[mu] + 1) % L[mu]
+                xp = tuple(xp)
+                bc = self.time_bc if (mu == 0 and x[0] == L[0] - 1) else 1.0
+                Uxm = self.U[x + (mu,)]
+                for t in range(8):
+                    dfwd = -self.kappa * bc * np.kron(one - gam[mu], 1j * T[t] @ Uxm)
+                    dbwd = -self.kappa * bc * np.kron(one + gam[mu], -1j * Uxm.conj().T @ T[t])
+                    val = 0.0
+                    for y, z in pairs:
+                        val += np.vdot(z[x].ravel(), dfwd @ y[xp].ravel())
+                        val += np.vdot(z[xp].ravel(), dbwd @ y[x].ravel())
+                    F[x + (mu, t)] = -2.0 * val.real
+        return F
+
     def reweight_apply(self, N, c, eta):
         """M eta with M = 1 - R_{N+1}(W_1) = W_1 P_N(W_1) (Sec. 4, Eq. rw), in the
         paper's product form P_N(z) = c_N prod_{k=1..N} (z - z_k): each factor
@@ -266,6 +337,20 @@ def field_roots(N, c):
     if N % 2:
         raise ValueError("N must be even")
     return roots(N, c)[: N // 2]
+
+
+def gell_mann():
+    """The eight Gell-Mann matrices lambda_1..lambda_8, shape [8, 3, 3]."""
+    lam = np.zeros((8, 3, 3), dtype=np.complex128)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1], lam[1][1, 0] = -1j, 1j
+    lam[2][0, 0], lam[2][1, 1] = 1, -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2], lam[4][2, 0] = -1j, 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2], lam[6][2, 1] = -1j, 1j
+    lam[7] = np.diag([1, 1, -2]) / math.sqrt(3)
+    return lam
 
 
 def chebyshev_T(n, x):
