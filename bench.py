@@ -326,6 +326,12 @@ def run_ours(args):
     stencil = None
     if rank == 0 and not args.no_stencil:
         stencil = stencil_rates(dd4d, synth, torch, ctx, ids, b, n_om)
+    force = None
+    if rank == 0:
+        try:
+            force = force_rate(dd4d, torch, ctx, info, mixed)
+        except (dd4d.DDError, RuntimeError) as err:          # e.g. device memory
+            force = {"unavailable": str(err)[:200]}
 
     peak, peak_kind = measured_peaks()
     achieved = hop32_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
@@ -371,6 +377,7 @@ def run_ours(args):
         "action_48x4": config5,
         "heatbath": heatbath,
         "reweight": reweight,
+        "force": force,
         "learned_guess": learned,
         "stencil": stencil,
     }
@@ -537,6 +544,45 @@ def reweight_rate(dd4d, synth, torch, n_src=16, N=12, cpar=0.5, reps=2):
                         "N = 12, c = 0.5, 16 sources, 13 apply_w batches with FP64 solves to 1e-11",
             "status": st, "mean_exp_s": mean, "stderr": err,
             "ln_abs_W_N": -0.5 * float(np.log(mean))}
+
+
+def force_rate(dd4d, torch, ctx, info, prm, n_f=12, reps=2):
+    """Force of the multi-boson action on the active links of the 32^4 lattice (256
+    blocks, cores 7^4): 12 fields (N = 24, c = 0.5), two batched block solves of
+    3072 systems each (mixed precision to 1e-10) and one FP64 thread per link."""
+    n_dpi = info["n_dpi"]
+    L = LATTICE
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    chi = torch.randn((n_f, n_dpi, 24), generator=gen, device="cuda", dtype=torch.float64) * (0.5 ** 0.5)
+    F = torch.zeros(tuple(L) + (4, 8), dtype=torch.float64, device="cuda")
+    u = dd4d.roots(2 * n_f, 0.5)
+    ctx.mb_force(u, chi, F=F, prm=prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, st = ctx.mb_force(u, chi, F=F, prm=prm)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    # the force kernel alone (CUDA events on its stream), one more call
+    ctx.timing_get(3)
+    ctx.timing_enable(True)
+    ctx.mb_force(u, chi, F=F, prm=prm)
+    ctx.timing_enable(False)
+    kms, kn, kflops = ctx.timing_get(3)
+    for w in range(3):
+        ctx.timing_get(w)
+    links = int((F != 0).any(dim=-1).sum().item())
+    fmax = float(F.abs().max().item())
+    del chi, F
+    return {"metric": "force evaluations/s", "value": 1.0 / dt, "unit": "evals/s",
+            "workload": "32^4 bench lattice, 256 blocks (cores 7^4, frame 1), 12 fields (N = 24, c = 0.5), "
+                        "two batched block solves of 3072 systems (FP32 inner + double-float correction "
+                        "to 1e-10), FP64 force kernel",
+            "seconds_per_eval": dt, "active_links": links, "links_per_s": links / dt,
+            "force_kernel_ms": kms / max(kn, 1),
+            "force_kernel_fp64_gflops": kflops / max(kn, 1) / (kms / max(kn, 1) * 1e-3) / 1e9 if kms > 0 else None,
+            "max_abs_force": fmax, "status": st}
 
 
 def config5_action_rate(dd4d, synth, torch, group=8):

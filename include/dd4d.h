@@ -255,6 +255,24 @@ dd_status dd_multiboson_heatbath(dd_ctx* ctx, int n_f, const double* u, const do
                                  const dd_solve_params* params, dd_heatbath_stats* stats,
                                  void* stream);
 
+/* ---- force of the factorized multi-boson action (paper Sec. 4, Eq. localMB) --
+ * The active links of block a are the links U_mu(x) with x and x + mu both in
+ * its core Lambda0^a (an undecomposed direction's core is its whole periodic
+ * extent).  Of S = sum_a S^a + S^r only S^a depends on them, through
+ * D_{Omega0^a}.  For each active link and each generator T_t = lambda_t / 2
+ * (Gell-Mann, t = 0..7) the call returns
+ *   F[x][mu][t] = d S / d eps  at  U_mu(x) -> exp(i eps T_t) U_mu(x),
+ * with y_k = D_Omega^{-1} D_{Omega,ext} chi_k, r_k = P_{dLambda0^a}(u_k chi_k + y_k),
+ * z_k = (D_Omega^dag)^{-1} r_k = gamma_5 D_Omega^{-1} gamma_5 r_k and
+ * dS = -2 Re sum_k <z_k, dD_Omega y_k>: two batched block solves (all blocks,
+ * all fields, params as for dd_solve_blocks) and one thread per link (FP64).
+ * u: 2*n_f doubles (re, im); chi: layout of dd_apply_w, device or host.
+ * F: device or host, V*4*8 doubles, [global site (x3 fastest)][mu][t]; zero
+ * on every link that is not active.  Returns DD_ENOCONV (F filled) if a block
+ * solve missed its tolerance.  Synchronises. */
+dd_status dd_mb_force(dd_ctx* ctx, int n_f, const double* u, const double* chi, double* F,
+                      const dd_solve_params* params, void* stream);
+
 /* ---- reweighting factor (paper Sec. 4, Eq. rw) ------------------------------
  * W_N = det{1 - R_{N+1}(W_1)}, W_1 = 1 - w on dPi, with the polynomial of the
  * roots below: R_{N+1}(z) = T_{N+1}((1-z)/c) / T_{N+1}(1/c) for c > 0 and
@@ -358,10 +376,12 @@ dd_status dd_set_net(dd_ctx* ctx, dd_net* net);
 
 /* ---- kernel timing -----------------------------------------------------
  * With timing on, the library brackets every launch of its stencil kernels
- * with CUDA events on the launching stream.  dd_timing_get returns, for
- * kernel class `which` (0: FP64 hop, 1: FP32 hop, 2: BF16 hop), the summed
- * device time in ms, the number of launches and the summed algorithmic
- * bytes, then clears the record.  Synchronises. */
+ * with CUDA events on the launching stream, and so every launch of the force
+ * kernel of dd_mb_force.  dd_timing_get returns, for kernel class `which`
+ * (0: FP64 hop, 1: FP32 hop, 2: BF16 hop, 3: force), the summed device time
+ * in ms, the number of launches and the summed algorithmic bytes (class 3:
+ * algorithmic FP64 flops, 576 per active link and field: 72 complex
+ * multiply-adds), then clears the record.  Synchronises. */
 dd_status dd_timing_enable(dd_ctx* ctx, int on);
 dd_status dd_timing_get(dd_ctx* ctx, int which, double* ms, long long* launches,
                         double* bytes);

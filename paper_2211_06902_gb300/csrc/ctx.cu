@@ -939,7 +939,7 @@ dd_status dd_timing_enable(dd_ctx* c, int on) {
 }
 
 dd_status dd_timing_get(dd_ctx* c, int which, double* ms, long long* launches, double* bytes) {
-  if (!c || which < 0 || which > 2) return DD_EINVAL;
+  if (!c || which < 0 || which > 3) return DD_EINVAL;
   for (auto& r : c->trec) {
     cudaEventSynchronize(r.b);
     float t = 0;

@@ -220,6 +220,132 @@ __global__ void k_hb_dot(long long n, const double2* __restrict__ a, const doubl
 
 // ---------------------------------------------------------------------------
 
+// ---- force of the factorized multi-boson action on the active links ----------
+// rhs of the adjoint solves: gamma_5 P_{dLambda0^a}(u_f chi_f + y_f) at the B sites
+// of every block (the buffer is zero elsewhere); D_Omega^dag = gamma_5 D_Omega gamma_5
+__global__ void k_force_rhs(const int* __restrict__ b_blk, const long long* __restrict__ b_loc,
+                            const int* __restrict__ b_dpi, int nB, int n_f, int n_dpi,
+                            const long long* __restrict__ uoff, const double2* __restrict__ u,
+                            const double2* __restrict__ chi, const double2* __restrict__ y,
+                            double2* __restrict__ rhs) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (k >= nB) return;
+  const long long o = uoff[(long long)b_blk[k] * n_f + f] + b_loc[k];
+  const double2* c = chi + ((long long)f * n_dpi + b_dpi[k]) * 12;
+  const double2 uf = u[f];
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    const double2 x = c[e], yv = y[o + e];
+    double2 r = make_double2(uf.x * x.x - uf.y * x.y + yv.x, uf.x * x.y + uf.y * x.x + yv.y);
+    if (e >= 6) r = make_double2(-r.x, -r.y);
+    rhs[o + e] = r;
+  }
+}
+
+// half spinors: with P = 1 -/+ gamma_mu (P^2 = 2P, the lower two spins of P psi a
+// unitary recombination of the upper two), a^dag P b = sum_{s=0,1} h_s(a)^dag h_s(b)
+// for h = the upper half of P psi (hop_project).  So
+//   z(x)^dag [P_fwd (x) T U] y(x+mu)   = sum_s h_s(z(x))^dag T U h_s(y(x+mu))
+//   z(x+mu)^dag [P_bwd (x) U^dag T] y(x) = sum_s (U h_s(z(x+mu)))^dag T h_s(y(x))
+template <int MU>
+__device__ __forceinline__ void force_link(const double2 (&U)[9], const double2* __restrict__ yx,
+                                           const double2* __restrict__ yxp, const double2* __restrict__ zx,
+                                           const double2* __restrict__ zxp, double2 (&N)[9]) {
+  double2 v[12], hy[2][3], hz[2][3];
+  // N -= sum_s conj(h_s(z(x)))_a (U h_s(y(x+mu)))_b
+#pragma unroll
+  for (int c = 0; c < 12; ++c) v[c] = yxp[c];
+  hop_project<MU, true>(v, hy);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) v[c] = c >= 6 ? make_double2(-zx[c].x, -zx[c].y) : zx[c];
+  hop_project<MU, true>(v, hz);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    double2 uh[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      uh[a] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) cfma(uh[a], U[a * 3 + b], hy[sp][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double2 zc = hz[sp][a], qb = uh[b];
+        N[a * 3 + b].x -= zc.x * qb.x + zc.y * qb.y;
+        N[a * 3 + b].y -= zc.x * qb.y - zc.y * qb.x;
+      }
+  }
+  // N += sum_s conj(U h_s(z(x+mu)))_a h_s(y(x))_b
+#pragma unroll
+  for (int c = 0; c < 12; ++c) v[c] = yx[c];
+  hop_project<MU, false>(v, hy);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) v[c] = c >= 6 ? make_double2(-zxp[c].x, -zxp[c].y) : zxp[c];
+  hop_project<MU, false>(v, hz);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    double2 uz[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      uz[a] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) cfma(uz[a], U[a * 3 + b], hz[sp][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double2 pc = uz[a], rb = hy[sp][b];
+        N[a * 3 + b].x += pc.x * rb.x + pc.y * rb.y;
+        N[a * 3 + b].y += pc.x * rb.y - pc.y * rb.x;
+      }
+  }
+}
+
+// one thread per active link: F_t = 2 kappa Im sum_ab (T_t)_ab N_ab summed over the
+// fields, N = sum_f [ conj(U h(z(x+mu))) (x) h(y(x)) - conj(h(z(x))) (x) U h(y(x+mu)) ]
+// (half spinors of the backward / forward projectors, see force_link), T_t = lambda_t/2,
+// z = gamma_5 times the solution of the gamma_5-rotated adjoint system
+__global__ void __launch_bounds__(128) k_mb_force(const int4* __restrict__ al, const long long* __restrict__ al_loc, long long n_al,
+                           int n_f, const long long* __restrict__ uoff, const double2* __restrict__ gU,
+                           const double2* __restrict__ y, const double2* __restrict__ zg, double kappa,
+                           double* __restrict__ F) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_al) return;
+  const int4 e = al[k];
+  const int blk = e.x, xg = e.y, mu = e.z;
+  double2 U[9];
+  const double2* lp = gU + (long long)xg * 36 + mu * 9;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) U[m] = lp[m];
+  double2 N[9];
+#pragma unroll
+  for (int m = 0; m < 9; ++m) N[m] = make_double2(0.0, 0.0);
+  for (int f = 0; f < n_f; ++f) {
+    const long long base = uoff[(long long)blk * n_f + f];
+    const long long ox = base + al_loc[2 * k], oxp = base + al_loc[2 * k + 1];
+    switch (mu) {
+      case 0: force_link<0>(U, y + ox, y + oxp, zg + ox, zg + oxp, N); break;
+      case 1: force_link<1>(U, y + ox, y + oxp, zg + ox, zg + oxp, N); break;
+      case 2: force_link<2>(U, y + ox, y + oxp, zg + ox, zg + oxp, N); break;
+      default: force_link<3>(U, y + ox, y + oxp, zg + ox, zg + oxp, N); break;
+    }
+  }
+  double* o = F + ((long long)xg * 4 + mu) * 8;
+  const double h = kappa;            // 2 kappa * (1/2 of lambda)
+  o[0] = h * (N[1].y + N[3].y);
+  o[1] = h * (N[3].x - N[1].x);
+  o[2] = h * (N[0].y - N[4].y);
+  o[3] = h * (N[2].y + N[6].y);
+  o[4] = h * (N[6].x - N[2].x);
+  o[5] = h * (N[5].y + N[7].y);
+  o[6] = h * (N[7].x - N[5].x);
+  o[7] = h * (N[0].y + N[4].y - 2.0 * N[8].y) / sqrt(3.0);
+}
+
 struct WPlan {           // host-built gather lists, one per context
   int n_l1 = 0;
   int* d_l1_glob = nullptr;          // [n_l1] global site of Lambda1 field index
@@ -232,6 +358,11 @@ struct WPlan {           // host-built gather lists, one per context
   int* d_c_dpi = nullptr;            // [n_C]
   int* d_c_grp = nullptr;            // C sites split into chunks for the S^r partials
   int n_cgrp = 0;
+  // active links (both end points in one core), built on the first force call
+  bool force_ready = false;
+  long long n_al = 0;
+  int4* d_al = nullptr;              // [n_al] (block, global site x, mu, unused)
+  long long* d_al_loc = nullptr;     // [n_al][2] 12 * field position of x, x + mu in Omega0^b
 };
 
 void free_plan(dd_ctx* c) {
@@ -239,6 +370,7 @@ void free_plan(dd_ctx* c) {
   if (!P) return;
   dfree(P->d_l1_glob); dfree(P->d_in_l1); dfree(P->d_b_blk); dfree(P->d_b_loc);
   dfree(P->d_b_dpi); dfree(P->d_b_grp); dfree(P->d_c_loc); dfree(P->d_c_dpi); dfree(P->d_c_grp);
+  dfree(P->d_al); dfree(P->d_al_loc);
   delete P;
   c->wplan = nullptr;
 }
@@ -302,6 +434,53 @@ static dd_status build_plan(dd_ctx* c, WPlan** out) {
   P->n_l1 = (int)l1_glob.size();
   P->n_cgrp = (int)c_grp.size() - 1;
   *out = P;
+  return DD_OK;
+}
+
+// active links of every block: (x, mu) with x and x + mu both in the core
+// Lambda0^b (cores are intervals that do not wrap, except an undecomposed
+// direction's virtual core spanning the whole periodic extent)
+static dd_status build_force_plan(dd_ctx* c, WPlan& P) {
+  if (P.force_ready) return DD_OK;
+  const int* L = c->L;
+  const int nb = (int)c->blocks.size();
+  std::vector<int4> al;
+  std::vector<long long> loc;
+  std::vector<int> fpos(c->V, -1);
+  for (int b = 0; b < nb; ++b) {
+    const Instance& om = c->inst[c->omega0 + b];
+    for (int k = 0; k < om.d.nsites; ++k) fpos[om.h_glob[k]] = om.h_fmap[k];
+    const BlockDesc& bd = c->blocks[b];
+    auto in_core = [&](int m, int v) { return v >= bd.core_lo[m] && v <= bd.core_hi[m]; };
+    int x[4];
+    for (x[0] = bd.core_lo[0]; x[0] <= bd.core_hi[0]; ++x[0])
+      for (x[1] = bd.core_lo[1]; x[1] <= bd.core_hi[1]; ++x[1])
+        for (x[2] = bd.core_lo[2]; x[2] <= bd.core_hi[2]; ++x[2])
+          for (x[3] = bd.core_lo[3]; x[3] <= bd.core_hi[3]; ++x[3]) {
+            const int gx = ((x[0] * L[1] + x[1]) * L[2] + x[2]) * L[3] + x[3];
+            for (int mu = 0; mu < 4; ++mu) {
+              int y[4] = {x[0], x[1], x[2], x[3]};
+              y[mu] = (y[mu] + 1) % L[mu];
+              if (!in_core(mu, y[mu])) continue;
+              const int gy = ((y[0] * L[1] + y[1]) * L[2] + y[2]) * L[3] + y[3];
+              if (fpos[gx] < 0 || fpos[gy] < 0) return fail(c, DD_EINVAL, "core site outside its block");
+              al.push_back(make_int4(b, gx, mu, 0));
+              loc.push_back(12LL * fpos[gx]);
+              loc.push_back(12LL * fpos[gy]);
+            }
+          }
+    for (int k = 0; k < om.d.nsites; ++k) fpos[om.h_glob[k]] = -1;
+  }
+  dd_status e;
+  if ((e = dalloc(c, (void**)&P.d_al, sizeof(int4) * std::max<size_t>(1, al.size()))) ||
+      (e = dalloc(c, (void**)&P.d_al_loc, sizeof(long long) * std::max<size_t>(1, loc.size()))))
+    return e;
+  if (!al.empty()) {
+    DD_CUDA(c, cudaMemcpy(P.d_al, al.data(), sizeof(int4) * al.size(), cudaMemcpyHostToDevice));
+    DD_CUDA(c, cudaMemcpy(P.d_al_loc, loc.data(), sizeof(long long) * loc.size(), cudaMemcpyHostToDevice));
+  }
+  P.n_al = (long long)al.size();
+  P.force_ready = true;
   return DD_OK;
 }
 
@@ -718,6 +897,103 @@ dd_status dd_multiboson_heatbath(dd_ctx* c, int n_f, const double* u, const doub
   if (hout) DD_CUDA(c, cudaMemcpyAsync(chi, dout, bytes, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
   return r;
+}
+
+dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, double* F,
+                      const dd_solve_params* prm, void* stream) {
+  if (!c || !u || !chi || !F || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (n_f > 65535) return fail(c, DD_EINVAL, "n_f must be <= 65535");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)c->blocks.size();
+  const size_t vbytes = 16ULL * n_f * c->info.n_dpi * 12;
+  const size_t fbytes = sizeof(double) * 32ULL * c->V;
+  dd_status e;
+  const double* din = chi;
+  if (!is_device_ptr(chi)) {
+    void* p;
+    if ((e = workspace(c, 230, vbytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, chi, vbytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  double* dF = F;
+  const bool hF = !is_device_ptr(F);
+  if (hF) {
+    void* p;
+    if ((e = workspace(c, 236, fbytes, &p)) != DD_OK) return e;
+    dF = (double*)p;
+  }
+  std::vector<int> insts(nb);
+  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
+  Batch* ob;
+  if ((e = get_batch_insts(c, insts, n_f, &ob)) != DD_OK) return e;
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  if ((e = build_force_plan(c, P)) != DD_OK) return e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  void *vsrc, *vy, *vrhs, *vz, *vu;
+  if ((e = workspace(c, 231, 16ULL * ob->user_tot, &vsrc)) || (e = workspace(c, 232, 16ULL * ob->user_tot, &vy)) ||
+      (e = workspace(c, 233, 16ULL * ob->user_tot, &vrhs)) || (e = workspace(c, 234, 16ULL * ob->user_tot, &vz)) ||
+      (e = workspace(c, 235, 16ULL * n_f, &vu)))
+    return e;
+  DD_CUDA(c, cudaMemcpyAsync(vu, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
+  // y = D_Omega^{-1} D_{Omega,ext} chi for every block and field
+  InjectArgs a;
+  a.U = c->d_U;
+  a.chi = (const double2*)din;
+  a.dpi_pos = c->d_dpi_pos;
+  for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
+  a.n_dpi = c->info.n_dpi;
+  a.n_f = n_f;
+  a.kappa = c->kappa;
+  a.src = (double2*)vsrc;
+  BatchDev bd = batch_view(c, *ob);
+  dim3 g1((c->info.max_omega + 127) / 128, n_f, nb);
+  DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
+  DD_CUDA(c, cudaGetLastError());
+  bool noconv = false;
+  dd_solve_stats st1{};
+  dd_status r1 = solve_batch(c, *ob, (const double*)vsrc, (double*)vy, prm, &st1, s, true);
+  if (r1 == DD_ENOCONV) noconv = true;
+  else if (r1 != DD_OK) return r1;
+  // z = (D_Omega^dag)^{-1} P_B (u chi + y) = gamma_5 D_Omega^{-1} gamma_5 P_B (u chi + y)
+  DD_CUDA(c, cudaMemsetAsync(vrhs, 0, 16ULL * ob->user_tot, s));
+  const int nB = c->info.n_B;
+  if (nB) {
+    dim3 g((nB + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_force_rhs<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
+                                                     ob->d_uoff, (const double2*)vu, (const double2*)din,
+                                                     (const double2*)vy, (double2*)vrhs);
+    DD_CUDA(c, cudaGetLastError());
+  }
+  dd_status r2 = solve_batch(c, *ob, (const double*)vrhs, (double*)vz, prm, &st1, s, true);
+  if (r2 == DD_ENOCONV) noconv = true;
+  else if (r2 != DD_OK) return r2;
+  DD_CUDA(c, cudaMemsetAsync(dF, 0, fbytes, s));
+  if (P.n_al > 0) {
+    TimingRec rec{};
+    if (c->timing) {
+      cudaEventCreate(&rec.a);
+      cudaEventCreate(&rec.b);
+      rec.which = 3;
+      rec.bytes = 576.0 * (double)P.n_al * n_f;     // algorithmic FP64 flops
+      cudaEventRecord(rec.a, s);
+    }
+    DD_COUNT_LAUNCH(), k_mb_force<<<(unsigned)((P.n_al + 127) / 128), 128, 0, s>>>(
+        P.d_al, P.d_al_loc, P.n_al, n_f, ob->d_uoff, (const double2*)c->d_U, (const double2*)vy,
+        (const double2*)vz, c->kappa, dF);
+    if (c->timing) {
+      cudaEventRecord(rec.b, s);
+      c->trec.push_back(rec);
+    }
+    DD_CUDA(c, cudaGetLastError());
+  }
+  if (hF) DD_CUDA(c, cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  if (noconv) return fail(c, DD_ENOCONV, "a block solve missed its tolerance");
+  return DD_OK;
 }
 
 dd_status dd_reweight_samples(dd_ctx* c, int N, double cpar, int n_src, const double* eta, double* s_out,

@@ -153,9 +153,9 @@ struct dd_ctx {
   // timing
   bool timing = false;
   std::vector<dd::TimingRec> trec;
-  double t_ms[3] = {0, 0, 0};
-  long long t_n[3] = {0, 0, 0};
-  double t_bytes[3] = {0, 0, 0};
+  double t_ms[4] = {0, 0, 0, 0};          // per timing class (hop F64/F32/BF16, force)
+  long long t_n[4] = {0, 0, 0, 0};
+  double t_bytes[4] = {0, 0, 0, 0};
   double* d_tbytes = nullptr;     // device accumulators of algorithmic bytes [3]
   int* d_err = nullptr;           // device error word, set by kernels whose bounded waits give up
   // work space (krylov.cu) and cached batches

@@ -112,6 +112,7 @@ def lib():
             "dd_apply_D_block_noalloc": [vp, C.c_int, ip, C.c_int, C.c_int, vp, vp, vp],
             "dd_reweight_samples": [vp, C.c_int, C.c_double, C.c_int, vp, dp, vp,
                                     C.POINTER(SolveParams), vp],
+            "dd_mb_force": [vp, C.c_int, dp, vp, vp, C.POINTER(SolveParams), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -131,7 +132,7 @@ def exported_symbols():
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
-            "dd_apply_D_block_noalloc", "dd_reweight_samples"]
+            "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force"]
 
 
 def hop_variant_name(prec, v):
@@ -329,6 +330,20 @@ class Context:
         d = st.as_dict()
         d["status"] = s
         return d
+
+    def mb_force(self, u, chi, F=None, prm=None, stream=None):
+        """Force of the multi-boson action on the active links: F[x0,x1,x2,x3,mu,t] =
+        dS/d eps at U_mu(x) -> exp(i eps lambda_t/2) U_mu(x), zero off the active links.
+        chi: layout of apply_w.  F: optional device tensor of V*4*8 doubles.
+        Returns (F, status); F is a numpy array unless a tensor was given."""
+        u = np.asarray(u, dtype=np.complex128)
+        uu = np.empty(2 * len(u))
+        uu[0::2], uu[1::2] = u.real, u.imag
+        out = F if F is not None else np.zeros(self.L + (4, 8))
+        st = self._check(lib().dd_mb_force(
+            self._h, len(u), uu.ctypes.data_as(C.POINTER(C.c_double)), _ptr(chi), _ptr(out),
+            C.byref(prm or params()), _stream(stream)))
+        return out, st
 
     def reweight_samples(self, N, c, eta, r_eta=None, prm=None, stream=None):
         """Samples s = |eta|^2 - |M eta|^2, M = 1 - R_{N+1}(W_1), one per source of eta
