@@ -11,8 +11,9 @@ Plain, slow and written to be checked by eye against the paper
 (Saccardi & Giusti, "Four-dimensional domain decomposition for the
 factorization of the fermion determinant", Lattice 2022):
 
-* ``lattice``  - gamma matrices, the Wilson-Dirac operator D[U] of Sec. 1/3,
-                 its restrictions D_X = P_X D P_X and sparse matrices of them.
+* ``lattice``  - gamma matrices, the Wilson-Dirac operator D[U] of Sec. 1/3
+                 (optionally with the site-local clover term), its
+                 restrictions D_X = P_X D P_X and sparse matrices of them.
 * ``geometry`` - the domain decomposition of Sec. 2 (Lambda0^a, Lambda1,
                  dLambda0, dPi, dPi1, Omega0^a, Phi1^a and exterior boundaries).
 * ``dd``       - block and frame solves, the operator w = 1 - W_1 (Eqs. Wz,

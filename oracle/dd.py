@@ -40,10 +40,10 @@ class DomainSolver:
 
     TOL = 1e-13
 
-    def __init__(self, U, kappa, mask, time_bc=-1):
+    def __init__(self, U, kappa, mask, time_bc=-1, csw=0.0):
         self.L = U.shape[:4]
         self.sites = np.flatnonzero(mask.ravel())
-        self.M = dirac_matrix(U, kappa, self.sites, time_bc)
+        self.M = dirac_matrix(U, kappa, self.sites, time_bc, csw)
         self._lu = None
 
     @property
@@ -112,19 +112,20 @@ def bicgstab(matvec, b, tol=1e-13, maxiter=100000):
 class Oracle:
     """D, the decomposition and the solvers for one gauge field."""
 
-    def __init__(self, U, kappa, geom, time_bc=-1):
+    def __init__(self, U, kappa, geom, time_bc=-1, csw=0.0):
         self.U = U
         self.kappa = kappa
         self.g = geom
         self.time_bc = time_bc
+        self.csw = csw
         self._solvers = {}
 
     def D(self, psi):
-        return apply_D(self.U, psi, self.kappa, self.time_bc)
+        return apply_D(self.U, psi, self.kappa, self.time_bc, self.csw)
 
     def solver(self, key, mask):
         if key not in self._solvers:
-            self._solvers[key] = DomainSolver(self.U, self.kappa, mask, self.time_bc)
+            self._solvers[key] = DomainSolver(self.U, self.kappa, mask, self.time_bc, self.csw)
         return self._solvers[key]
 
     def omega_solver(self, a):
@@ -187,7 +188,7 @@ class Oracle:
         for a in range(g.nblocks):
             om = g.sites(g.omega_mask[a])
             ex = g.sites(g.ext_mask[a])
-            rhs = dirac_block(self.U, self.kappa, om, ex, self.time_bc).toarray()
+            rhs = dirac_block(self.U, self.kappa, om, ex, self.time_bc, self.csw).toarray()
             G = self.omega_solver(a).lu.solve(rhs)
             opos = np.full(V, -1, dtype=np.int64)
             opos[om] = np.arange(len(om))
@@ -196,7 +197,7 @@ class Oracle:
             W[np.ix_(comp_index(bs), comp_index(ex))] = -G[rows_in_om]
         l1 = g.sites(g.Lambda1)
         bsites = g.sites(g.B)
-        rhs = dirac_block(self.U, self.kappa, l1, bsites, self.time_bc).toarray()
+        rhs = dirac_block(self.U, self.kappa, l1, bsites, self.time_bc, self.csw).toarray()
         G = self.frame_solver().lu.solve(rhs)
         lpos = np.full(V, -1, dtype=np.int64)
         lpos[l1] = np.arange(len(l1))
@@ -250,6 +251,8 @@ class Oracle:
         the definition of D: row x, column x+mu: -kappa (1 - gamma_mu) (i T U);
         row x+mu, column x: -kappa (1 + gamma_mu) (-i U^dag T) (times the time
         boundary sign where the link crosses x0 = L0-1 -> 0)."""
+        if self.csw:
+            raise NotImplementedError("the force of the clover term is not part of this oracle")
         g = self.g
         L = g.L
         gam, _ = gammas()
@@ -308,7 +311,7 @@ class Oracle:
         """slogdet of D, W_1, D_{Lambda1}, D_{Omega0^a}, D_{Phi1^a} (dense LU)."""
         g = self.g
         V = int(np.prod(g.L))
-        D = dirac_matrix(self.U, self.kappa, np.arange(V), self.time_bc).toarray()
+        D = dirac_matrix(self.U, self.kappa, np.arange(V), self.time_bc, self.csw).toarray()
         out = {"D": np.linalg.slogdet(D)}
         del D
         w = self.w_matrix()
