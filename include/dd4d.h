@@ -129,6 +129,24 @@ const char* dd_strerror(dd_status s);
 const char* dd_last_error(const dd_ctx* ctx);
 dd_status dd_set_kappa(dd_ctx* ctx, double kappa);
 
+/* ---- clover term (paper Sec. 1: D may carry a site-local term) --------------
+ * c_sw != 0 adds to D the Sheikholeslami-Wohlert term in kappa normalisation,
+ * D = A - kappa H with A(x) = 1 + i kappa c_sw sum_{mu<nu} sigma_mu_nu F_mu_nu(x),
+ * sigma_mu_nu = (i/2)[gamma_mu, gamma_nu] and F_mu_nu = (Q_mu_nu - Q_mu_nu^+)/8
+ * from the four plaquettes Q_mu_nu of the mu-nu plane at x (each traversed mu
+ * first; the links without the time boundary sign).  A and A^{-1} (two 6x6
+ * chiral blocks per site, FP64) are rebuilt on every gauge upload and kappa
+ * change.  With the term on: dd_apply_D_block computes A psi - kappa H psi
+ * (DD_F64 only); dd_solve_blocks and everything built on it (dd_apply_w, the
+ * action, the heat-bath, the reweighting samples, dd_logdet_check) solve
+ * (1 - kappa A^{-1} H) x = A^{-1} b with the even-odd Schur form
+ * 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe, FP64 inner solves only
+ * (inner_prec DD_F64, else DD_EINVAL), so the tolerance applies to the
+ * residual A^{-1}(b - D x) relative to A^{-1} b.  dd_mb_force and
+ * dd_apply_D_block_noalloc return DD_EINVAL with the term on.  c_sw = 0 turns
+ * it off (the default). */
+dd_status dd_set_clover(dd_ctx* ctx, double c_sw);
+
 /* Gauge links U_mu(x) in SU(3) (paper Sec. 1).  Host buffer, layout
  * [site (global index)][mu 0..3][3][3] complex128 (row-major 3x3).  The
  * stored links are not modified; the time boundary sign is applied by the

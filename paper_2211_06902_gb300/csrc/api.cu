@@ -187,12 +187,14 @@ dd_status dd_apply_D_block(dd_ctx* c, dd_domain kind, const int* ids, int nblk, 
                            const double* in, double* out, dd_prec prec, void* stream) {
   if (!c || !in || !out) return fail(c, DD_EINVAL, "null argument");
   if (prec != DD_F64 && prec != DD_F32 && prec != DD_BF16) return fail(c, DD_EINVAL, "bad precision");
+  if (c->csw != 0.0 && prec != DD_F64) return fail(c, DD_EINVAL, "the clover term is applied in FP64 only");
   cudaStream_t s = (cudaStream_t)stream;
   Batch* b;
   dd_status e = get_batch(c, kind, ids, nblk, nrhs, &b);
   if (e != DD_OK) return e;
   for (int j = 0; j < b->nb; ++j)
     if ((e = ensure_links(c, b->inst[j], prec)) != DD_OK) return e;
+  if (c->csw != 0.0 && !c->clover_ready && (e = clover_build(c)) != DD_OK) return e;
   size_t ub = 16ULL * b->user_tot;
   Staged sg;
   if ((e = stage(c, in, out, ub, 30, 31, sg, s)) != DD_OK) return e;
@@ -202,11 +204,23 @@ dd_status dd_apply_D_block(dd_ctx* c, dd_domain kind, const int* ids, int nblk, 
       (e = workspace(c, 22, cb * b->tot[0], &oe)) || (e = workspace(c, 23, cb * b->tot[1], &oo)))
     return e;
   if ((e = launch_pack(c, *b, sg.in, ve, vo, prec, s)) != DD_OK) return e;
+  // the self term: psi, or A psi with the clover term (site-local, FP64)
+  const void *se = ve, *so = vo;
+  if (c->csw != 0.0) {
+    void *ae, *ao;
+    if ((e = workspace(c, 240, cb * b->tot[0], &ae)) || (e = workspace(c, 241, cb * b->tot[1], &ao)))
+      return e;
+    DD_CUDA(c, cudaMemcpyAsync(ae, ve, cb * b->tot[0], cudaMemcpyDeviceToDevice, s));
+    if (b->tot[1] > 0) DD_CUDA(c, cudaMemcpyAsync(ao, vo, cb * b->tot[1], cudaMemcpyDeviceToDevice, s));
+    if ((e = clover_apply(c, *b, ae, ao, false, s)) != DD_OK) return e;
+    se = ae;
+    so = ao;
+  }
   HopArgs h{};
-  h.p_out = 0; h.in = vo; h.out = oe; h.s1 = ve; h.a1 = 1.0; h.b = -c->kappa;
+  h.p_out = 0; h.in = vo; h.out = oe; h.s1 = se; h.a1 = 1.0; h.b = -c->kappa;
   if ((e = launch_hop(c, *b, prec, h, s)) != DD_OK) return e;
   HopArgs g{};
-  g.p_out = 1; g.in = ve; g.out = oo; g.s1 = vo; g.a1 = 1.0; g.b = -c->kappa;
+  g.p_out = 1; g.in = ve; g.out = oo; g.s1 = so; g.a1 = 1.0; g.b = -c->kappa;
   if ((e = launch_hop(c, *b, prec, g, s)) != DD_OK) return e;
   if ((e = launch_unpack(c, *b, oe, oo, sg.out, prec, s)) != DD_OK) return e;
   if ((e = unstage(c, out, ub, sg, s)) != DD_OK) return e;

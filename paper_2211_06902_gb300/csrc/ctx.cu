@@ -444,7 +444,7 @@ dd_status gauge_finish(dd_ctx* c) {
   for (auto& in : c->inst) in.links_ready = false;
   c->gauge_ready = true;
   c->inst_dirty = true;
-  return DD_OK;
+  return clover_build(c);        // no-op without the clover term
 }
 
 dd_status check_device_error(dd_ctx* c, cudaStream_t s) {
@@ -668,6 +668,8 @@ dd_status dd_destroy(dd_ctx* c) {
   dfree(c->d_dpi_kind);
   dfree(c->d_tbytes);
   dfree(c->d_err);
+  dfree(c->d_clov);
+  dfree(c->d_clovi);
   free_workspace(c);
   free_plan(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -685,7 +687,7 @@ dd_status dd_destroy(dd_ctx* c) {
 dd_status dd_set_kappa(dd_ctx* c, double kappa) {
   if (!c) return DD_EINVAL;
   c->kappa = kappa;
-  return DD_OK;
+  return clover_build(c);        // A depends on kappa (no-op without the clover term)
 }
 
 dd_status dd_gauge_upload(dd_ctx* c, const double* U) {

@@ -905,6 +905,7 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
   if (n_f > 65535) return fail(c, DD_EINVAL, "n_f must be <= 65535");
   if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
   if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  if (c->csw != 0.0) return fail(c, DD_EINVAL, "the force does not include the clover term");
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = (int)c->blocks.size();
   const size_t vbytes = 16ULL * n_f * c->info.n_dpi * 12;

@@ -157,6 +157,12 @@ struct dd_ctx {
   long long t_n[4] = {0, 0, 0, 0};
   double t_bytes[4] = {0, 0, 0, 0};
   double* d_tbytes = nullptr;     // device accumulators of algorithmic bytes [3]
+  // clover term (clover.cu): A and A^{-1} per site, [V][2][6][6] complex FP64
+  double csw = 0.0;
+  double2* d_clov = nullptr;
+  double2* d_clovi = nullptr;
+  bool clover_ready = false;
+  bool clover_active = false;     // inside a solve: FP64 hops apply A^{-1} (clov_inv)
   int* d_err = nullptr;           // device error word, set by kernels whose bounded waits give up
   // work space (krylov.cu) and cached batches
   void* scratch = nullptr;
@@ -219,6 +225,8 @@ struct HopArgs {
   double* work_bytes;       // timing only: algorithmic bytes of the CTAs that ran
   double site_bytes;        // algorithmic bytes per output (site, rhs)
   int* err;                 // device error word (bounded waits that gave up)
+  const double2* clov_inv;  // FP64 only: A^{-1} [V][72] of the clover term applied to the
+                            // hop sum at the output site (left-preconditioned solves)
 };
 dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s);
 int hop_variant_count(dd_prec prec);
@@ -228,6 +236,10 @@ void hop_bundle_prepare();
 dd_status check_device_error(dd_ctx* c, cudaStream_t s);
 // after new links in d_U (ctx.cu): time sign, stale per-domain copies
 dd_status gauge_finish(dd_ctx* c);
+// clover term (clover.cu): build A, A^{-1} from d_U (no-op at c_sw = 0), and
+// v <- A v or A^{-1} v on both parity vectors of a batch (FP64)
+dd_status clover_build(dd_ctx* c);
+dd_status clover_apply(dd_ctx* c, const Batch& b, void* ve, void* vo, bool inverse, cudaStream_t s);
 
 // layout conversions (stencil.cu)
 // b -> b, r = b (outer precision F64 or double-float), x = 0, in caller field order

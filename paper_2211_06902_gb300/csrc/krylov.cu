@@ -680,6 +680,18 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const int nsys = b.nb * b.nrhs;
   const dd_prec ip = prm->inner_prec;
   const size_t c64 = 16, cin = prec_bytes(ip);
+  // clover term: left preconditioning by A^{-1} (clover.cu), FP64 solves only
+  const bool clov = c->csw != 0.0;
+  if (clov) {
+    if (ip != DD_F64) return fail(c, DD_EINVAL, "the clover term needs inner_prec f64");
+    if (prm->flags & DD_SOLVE_NET_GUESS) return fail(c, DD_EINVAL, "no learned guess with the clover term");
+    if (!c->clover_ready && (e = clover_build(c)) != DD_OK) return e;
+  }
+  struct ActiveGuard {
+    dd_ctx* c;
+    ActiveGuard(dd_ctx* cc, bool on) : c(cc) { c->clover_active = on; }
+    ~ActiveGuard() { c->clover_active = false; }
+  } guard(c, clov);
   const long long ne = b.tot[0], no = b.tot[1];
   // Outer vectors b, x, r (both parities), 16 bytes per complex number: FP64
   // for the plain FP64 solve; double-float for the mixed solves, whose true
@@ -735,6 +747,12 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   // b, r = b and x = 0 in one pass over the caller layout; |b|^2 (= |r|^2)
   // partials by a coalesced pass over the parity vectors
   if ((e = launch_pack_init(c, b, b_user, be, bo, re, ro, xe, xo, op, s)) != DD_OK) return e;
+  if (clov) {
+    // solve (1 - kappa A^{-1} H) x = A^{-1} b: b and r = b preconditioned once
+    if ((e = clover_apply(c, b, be, bo, true, s)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(re, be, ne * c64, cudaMemcpyDeviceToDevice, s));
+    if (no > 0) DD_CUDA(c, cudaMemcpyAsync(ro, bo, no * c64, cudaMemcpyDeviceToDevice, s));
+  }
   norm2_outer(dfo, bd, eg, 0, be, partial, s);
   if (has_odd) norm2_outer(dfo, bd, og, 1, bo, partial_o, s);
   DD_COUNT_LAUNCH(), k_sc_bnorm<<<sbl, sth, 0, s>>>(sa, partial_o, b.d_item_begin[1], stride_o, prm->tol * prm->tol);

@@ -143,6 +143,7 @@ extern "C" dd_status dd_apply_D_block_noalloc(dd_ctx* c, dd_domain kind, const i
   if (!c || !in || !out) return fail(c, DD_EINVAL, "null argument");
   if (nrhs < 1) return fail(c, DD_EINVAL, "nrhs must be >= 1");
   if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  if (c->csw != 0.0) return fail(c, DD_EINVAL, "dd_apply_D_block_noalloc has no clover term");
   if (!is_device_ptr(in) || !is_device_ptr(out))
     return fail(c, DD_EINVAL, "dd_apply_D_block_noalloc takes device pointers only");
   // instances (no lazily built ones: those would allocate)

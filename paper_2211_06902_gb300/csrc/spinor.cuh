@@ -236,6 +236,28 @@ __device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const 
   hop_apply<MU, FWD>(acc, h, U);
 }
 
+// v <- M v for a site-local matrix in the chiral basis: two 6x6 blocks (components
+// 0..5 and 6..11), M row-major [2][6][6] (the clover term A or its inverse)
+__device__ __forceinline__ void clover_mul(const double2* __restrict__ M, double2 (&v)[12]) {
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    double2 w[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const double2 m = M[ch * 36 + r * 6 + c], x = v[ch * 6 + c];
+        acc.x = fma(m.x, x.x, fma(-m.y, x.y, acc.x));
+        acc.y = fma(m.x, x.y, fma(m.y, x.x, acc.y));
+      }
+      w[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) v[ch * 6 + r] = w[r];
+  }
+}
+
 // ---- scalar helpers of the stencil epilogue (overloaded for double-float) ---------
 template <class C> struct ScalOf;
 template <> struct ScalOf<float2> { typedef float type; };

@@ -85,6 +85,10 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     hop_one<5, S>(acc, n0, p, i, n_out, n_in, jn[5], in_sys, lk);
     hop_one<6, S>(acc, n0, p, i, n_out, n_in, jn[6], in_sys, lk);
     hop_one<7, S>(acc, n0, p, i, n_out, n_in, jn[7], in_sys, lk);
+    if constexpr (std::is_same<C, double2>::value) {
+      // clover term: the hop sum times A^{-1} of the output site
+      if (a.clov_inv) clover_mul(a.clov_inv + 72LL * dp->glob[(p ? n0 : 0) + i], acc);
+    }
     const auto b = mkscal<C>(a.b);
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = scale(acc[k], b);
@@ -1005,6 +1009,10 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
     launch_variant<df2s, 4, false, 1>(bd, a, ni, nsm, s);
     return;
   }
+  if (prec == DD_F64 && a.clov_inv) {      // the clover epilogue lives in the plain form
+    launch_variant<double2, 3, false, 1>(bd, a, ni, nsm, s);
+    return;
+  }
   const HopVariant& hv = variant_of(prec, v);
   if (hv.r < 0) {
     const int rr = -hv.r;
@@ -1070,6 +1078,7 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
   BatchDev bd = batch_view(c, b);
   HopArgs a = a0;
   a.err = c->d_err;
+  a.clov_inv = (c->clover_active && prec == DD_F64) ? c->d_clovi : nullptr;
   int p = a.p_out;
   if (b.nitems[p] == 0) return DD_OK;
   const long long nblk = (long long)b.nitems[p] * b.nrhs;

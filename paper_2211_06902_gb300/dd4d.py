@@ -113,6 +113,7 @@ def lib():
             "dd_reweight_samples": [vp, C.c_int, C.c_double, C.c_int, vp, dp, vp,
                                     C.POINTER(SolveParams), vp],
             "dd_mb_force": [vp, C.c_int, dp, vp, vp, C.POINTER(SolveParams), vp],
+            "dd_set_clover": [vp, C.c_double],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -132,7 +133,7 @@ def exported_symbols():
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
-            "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force"]
+            "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover"]
 
 
 def hop_variant_name(prec, v):
@@ -242,6 +243,10 @@ class Context:
 
     def set_kappa(self, kappa):
         self._check(lib().dd_set_kappa(self._h, float(kappa)))
+
+    def set_clover(self, csw):
+        """Clover term c_sw (0 = off): A(x) = 1 + i kappa c_sw sum sigma F in D."""
+        self._check(lib().dd_set_clover(self._h, float(csw)))
 
     def gauge_upload(self, U):
         U = np.ascontiguousarray(U, dtype=np.complex128)
