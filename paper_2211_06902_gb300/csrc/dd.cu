@@ -597,9 +597,8 @@ static dd_status heatbath_dev(dd_ctx* c, int n_f, const double2* u_h, const doub
   int* dact = (int*)va;
   double* dpart = (double*)vpart;
   const dim3 grid((unsigned)((n + 255) / 256), n_f);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  EventPair evs;
+  cudaEvent_t e0 = evs.a, e1 = evs.b;
   cudaEventRecord(e0, s);
   DD_CUDA(c, cudaMemcpyAsync(du, u_h, sizeof(double2) * n_f, cudaMemcpyHostToDevice, s));
   std::vector<double2> cf(3 * n_f);
@@ -694,8 +693,6 @@ static dd_status heatbath_dev(dd_ctx* c, int n_f, const double2* u_h, const doub
   DD_CUDA(c, cudaStreamSynchronize(s));
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   dd_heatbath_stats st{};
   st.iterations = it;
   st.matvecs = matvecs;

@@ -112,6 +112,21 @@ struct BatchDev {           // device-visible view of a Batch
   int nb, nrhs;
 };
 
+// two CUDA events destroyed on scope exit (also on the early error returns)
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+};
+
 struct TimingRec {
   cudaEvent_t a, b;
   int which;

@@ -739,9 +739,8 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const double kap = c->kappa;
   const bool has_odd = b.nitems[1] > 0;
 
-  cudaEvent_t ev0, ev1;
-  cudaEventCreate(&ev0);
-  cudaEventCreate(&ev1);
+  EventPair evs;
+  cudaEvent_t ev0 = evs.a, ev1 = evs.b;
   cudaEventRecord(ev0, s);
 
   // b, r = b and x = 0 in one pass over the caller layout; |b|^2 (= |r|^2)
@@ -909,8 +908,6 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   if ((e = check_device_error(c, s)) != DD_OK) return e;
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
   dd_solve_stats out{};
   out.systems = nsys;
   out.outer_cycles = cycles;
