@@ -286,6 +286,54 @@ class Oracle:
                     F[x + (mu, t)] = -2.0 * val.real
         return F
 
+    def logdet_force(self, max_dim=6000):
+        """G[x, mu, t] = d ln|det D_{Omega0^a}| / d eps at U_mu(x) -> exp(i eps T_t) U_mu(x)
+        for the active links of every block a (zero elsewhere): Re Tr[D_Omega^{-1} dD_Omega],
+        with the two entries of dD_Omega as in mb_force and D_Omega^{-1} the dense inverse
+        (small blocks only: 12 |Omega0^a| <= max_dim)."""
+        if self.csw:
+            raise NotImplementedError("the force of the clover term is not part of this oracle")
+        g = self.g
+        L = g.L
+        V = int(np.prod(L))
+        gam, _ = gammas()
+        one = np.eye(4)
+        T = gell_mann() / 2
+        G = np.zeros(tuple(L) + (4, 8))
+        for a in range(g.nblocks):
+            links = self.active_links(a)
+            if not links:
+                continue
+            om = self.omega_solver(a)
+            if 12 * len(om.sites) > max_dim:
+                raise ValueError("block too large for the dense inverse")
+            Minv = np.linalg.inv(om.M.toarray())
+            pos = np.full(V, -1, dtype=np.int64)
+            pos[om.sites] = np.arange(len(om.sites))
+
+            def blk(r, c):                      # (D_Omega^{-1})_{r, c}, 12 x 12
+                i, j = pos[np.ravel_multi_index(r, L)], pos[np.ravel_multi_index(c, L)]
+                return Minv[12 * i:12 * i + 12, 12 * j:12 * j + 12]
+            for x, mu in links:
+                xp = list(x)
+                xp[mu] = (xp[mu] + 1) % L[mu]
+                xp = tuple(xp)
+                bc = self.time_bc if (mu == 0 and x[0] == L[0] - 1) else 1.0
+                Uxm = self.U[x + (mu,)]
+                g_xpx, g_xxp = blk(xp, x), blk(x, xp)
+                for t in range(8):
+                    dfwd = -self.kappa * bc * np.kron(one - gam[mu], 1j * T[t] @ Uxm)
+                    dbwd = -self.kappa * bc * np.kron(one + gam[mu], -1j * Uxm.conj().T @ T[t])
+                    G[x + (mu, t)] = np.trace(g_xpx @ dfwd + g_xxp @ dbwd).real
+        return G
+
+    def effective_force(self, u, chis):
+        """Force of the block-local part of the factorized effective action (Sec. 4,
+        Eq. SFeffN) on the active links: d/d eps of sum_a [-ln|det D_{Omega0^a}| + sum_k
+        S^a_MB]; the other terms (ln det D_{Phi1^a}, ln det D_{Lambda1}, S^r) do not
+        depend on the active links."""
+        return self.mb_force(u, chis) - self.logdet_force()
+
     def reweight_apply(self, N, c, eta):
         """M eta with M = 1 - R_{N+1}(W_1) = W_1 P_N(W_1) (Sec. 4, Eq. rw), in the
         paper's product form P_N(z) = c_N prod_{k=1..N} (z - z_k): each factor

@@ -20,6 +20,9 @@
   total action S along exp(i eps T_t) equal the block-local analytic force (so S^r and
   the other blocks do not depend on those links), including a link across the
   antiperiodic time boundary; planted sign, projector, boundary and adjoint mistakes fail.
+* d ln|det D_Omega0^a| / d eps on active links against finite differences of the dense
+  slogdet; the block-local effective force against finite differences of the whole
+  factorized effective action of Eq. (SFeffN).
 """
 
 import math
@@ -412,3 +415,53 @@ def test_mb_force_support_and_time_boundary():
     fd = (_perturbed_action(U, 0.13, g, u, chis, x, mu, t, eps)
           - _perturbed_action(U, 0.13, g, u, chis, x, mu, t, -eps)) / (2 * eps)
     assert abs(fd - F[x + (mu, t)]) < 1e-6 * max(1.0, abs(fd))
+
+
+def _fd_links(U, fn, x, mu, t, eps=1e-4):
+    from scipy.linalg import expm
+    vals = []
+    for e in (eps, -eps):
+        Up = U.copy()
+        Up[tuple(x) + (mu,)] = expm(1j * e * gell_mann()[t] / 2) @ U[tuple(x) + (mu,)]
+        vals.append(fn(Up))
+    return (vals[0] - vals[1]) / (2 * eps)
+
+
+def test_logdet_force_matches_finite_differences():
+    """d ln|det D_Omega0^a| / d eps on active links against central differences of the
+    dense slogdet of the assembled block matrix."""
+    L, cores = (8, 4, 4, 2), [[(0, 1), (4, 5)], [], [], []]
+    U = synth.gauge_field(L, 0.4, 3)
+    g = Decomposition(L, cores)
+    o = Oracle(U, 0.13, g)
+    G = o.logdet_force()
+    for a, n, t in [(0, 0, 2), (0, 5, 7), (1, 3, 0)]:
+        x, mu = o.active_links(a)[n]
+        sites = g.sites(g.omega_mask[a])
+        fd = _fd_links(U, lambda Up: np.linalg.slogdet(dirac_matrix(Up, 0.13, sites).toarray())[1], x, mu, t)
+        assert abs(fd - G[x + (mu, t)]) < 1e-6 * max(1.0, abs(fd)), (a, x, mu, t, fd, G[x + (mu, t)])
+    assert np.abs(G).max() > 1e-3
+
+
+def test_effective_force_matches_finite_differences_of_the_effective_action():
+    """The block-local force equals the derivative of the whole factorized effective
+    action of Eq. (SFeffN): sum_a [-ln|det D_Omega0^a| + ln|det D_Phi1^a|] - ln|det D_Lambda1|
+    + S_MB (dense log-dets, total multi-boson action)."""
+    L, cores = (8, 4, 4, 2), [[(0, 1), (4, 5)], [], [], []]
+    U = synth.gauge_field(L, 0.4, 3)
+    g = Decomposition(L, cores)
+    o = Oracle(U, 0.13, g)
+    u = field_roots(2, 0.5)
+    chis = [synth.complex_gaussian(4, synth.TAG_CHI, L + (4, 3)) * g.dPi[..., None, None]]
+
+    def seff(Up):
+        ld = lambda m: np.linalg.slogdet(dirac_matrix(Up, 0.13, g.sites(m)).toarray())[1]
+        val = -ld(g.Lambda1) + Oracle(Up, 0.13, g).multiboson_action(u, chis)[0]
+        for a in range(g.nblocks):
+            val += -ld(g.omega_mask[a]) + ld(g.phi_mask[a])
+        return val
+    F = o.effective_force(u, chis)
+    for a, n, t in [(0, 2, 1), (1, 6, 5)]:
+        x, mu = o.active_links(a)[n]
+        fd = _fd_links(U, seff, x, mu, t)
+        assert abs(fd - F[x + (mu, t)]) < 1e-6 * max(1.0, abs(fd)), (a, x, mu, t, fd, F[x + (mu, t)])
