@@ -24,7 +24,8 @@ factorization of the fermion determinant", Lattice 2022):
                  factorized multi-boson action on the active links.
 
 Parity status: every function is pinned by a CPU test against closed forms,
-identities of the paper or brute force, except the agreement of W_1 with the
-paper's printed (garbled) hopping block D^h, which is "parity unpinned"
-beyond its determinant (the determinant identity Eq. (detD) does pin it).
+identities of the paper or brute force.  W_1 is assembled from the blocks the
+paper prints (Sec. 3); it is fixed by the printed upper-right block of Eq.
+(offdiagW1), the gamma_5-hermiticity of diag(D^d, D^_{dPi1}) W_1 and the Schur
+complement of Eq. (Dtilde), and it satisfies Eqs. (detD) and (WW).
 """

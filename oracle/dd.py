@@ -2,18 +2,14 @@
 
 Test infrastructure only (see the package docstring).  FP64 throughout.
 
-Operator w (Sec. 3, Eqs. Wz and offdiagW1; reading of the garbled hopping
-block): for chi on dPi = dLambda0 u dPi1,
-
-    (w chi)_{dLambda0^a} = - P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext(Omega0^a)} chi
-    (w chi)_{dPi1}       = - P_{dPi1} D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi_{dLambda0}
-
-and W_1 = 1 - w on dPi, W_u = u - w.  The first line is the Dirichlet
-(Poisson-kernel) extension of chi into the framed block; it contains the
-paper's upper-right block P D_Omega^-1 D_{Phi, dOmega*} chi_{dPi1} and
-completes the upper-left block; the second line is the paper's lower-left
-block D^_{dPi1}^{-1} D^_{dPi1, dLambda0}.  The reading is pinned by the
-determinant identity Eq. (detD) and by the Green's-function identity (tests).
+Operator w = 1 - W_1 (Sec. 3, Eqs. Wz and offdiagW1): W_1 is the matrix the
+paper prints, diag(D^d, D^_{dPi1})^{-1} times the block matrix of the second
+Schur decomposition (D^d + D^h, D^_{dL0,dPi1}; D^_{dPi1,dL0}, D^_{dPi1}),
+with the hopping block D^h in its printed symmetrised form.  Two forms:
+``w1_dense_blocks`` assembles every block densely (small lattices) and
+``apply_w`` applies the same blocks to a vector with block, frame-piece and
+frame solves.  The readings taken where the print is incomplete are listed at
+the W_1 section below.
 
 Multi-boson action (Sec. 4, Eqs. MBaction, localMB, globalMB) with roots
 u_k = 1 - z_k:
@@ -137,21 +133,187 @@ class Oracle:
     def frame_solver(self):
         return self.solver(("Lambda1",), self.g.Lambda1)
 
-    # -- w and W_1 (Eqs. Wz, offdiagW1) ---------------------------------
-    def apply_w(self, chi):
-        """w chi for a field chi supported on dPi; result supported on dPi."""
+    # -- W_1 (Sec. 3, Eqs. Wz and offdiagW1) ------------------------------
+    #
+    # W_1 = diag(D^d, D^_{dPi1})^{-1} M on dPi = dLambda0 u dPi1 with the blocks
+    # the paper prints (Sec. 3), X* = dOmega0^{a*} the exterior boundary of
+    # Omega0^a inside dPi1 and E = Lambda1bar = Lambda1 minus dPi1:
+    #
+    #   D^d_a       = D_{dL0a} - D_{dL0a,L0bar_a} D_{L0bar_a}^-1 D_{L0bar_a,dL0a}
+    #                          - D_{dL0a,Phi_a} D_{Phi_a}^-1 D_{Phi_a,dL0a}
+    #   D^h_{a,b}   = -1/2 D_{dL0a,Phi_a} [ D_{Phi_a}^-1 - D_{Phi_a}^-1 D_{Phi_a,X*a} D_{Phi_b}^-1
+    #                   + D_{Phi_b}^-1 - D_{Phi_a}^-1 D_{X*b,Phi_b} D_{Phi_b}^-1 ] D_{Phi_b,dL0b}   (a != b)
+    #   [D^d]^-1 D^_{dL0,dPi1} = sum_a P_{dL0a} D_{Omega_a}^-1 D_{Phi_a,X*a}      (Eq. offdiagW1)
+    #   D^_{dPi1}   = D_{dPi1} - D_{dPi1,E} D_E^-1 D_{E,dPi1}
+    #   D^_{dPi1,dL0} = - sum_b D_{X*b,Phi_b} D_{Phi_b}^-1 D_{Phi_b,dL0b}
+    #
+    # Readings: a product of two operators on different site sets acts on the
+    # sites they share (each D_X^-1 is D_X^-1 P_X, extended by zero off X);
+    # D^_{dPi1} eliminates Lambda1bar (the print has D_{Lambda1}^-1 there, which
+    # is not a Schur complement); D^_{dPi1,dL0}, which the paper names but does
+    # not print, is the elimination of Phi_b seen from dPi1, the gamma_5-adjoint
+    # of the printed -D_{dL0a,Phi_a} D_{Phi_a}^-1 D_{Phi_a,X*a} behind Eq.
+    # offdiagW1.  Then W_1 = 1 + offdiagonal, w = 1 - W_1, W_u = u - w.
+
+    def _dmat(self, rows, cols=None):
+        """Dense D_{X,Y} for ordered site lists (cols None: D_X)."""
+        if cols is None:
+            return dirac_matrix(self.U, self.kappa, rows, self.time_bc, self.csw).toarray()
+        return dirac_block(self.U, self.kappa, rows, cols, self.time_bc, self.csw).toarray()
+
+    @staticmethod
+    def _take(sub, full):
+        """Component indices (12 per site) of the sites of ``sub`` that lie in
+        ``full`` (both in increasing global order), and the matching positions
+        in ``sub``."""
+        sub = np.asarray(sub, dtype=np.int64)
+        full = np.asarray(full, dtype=np.int64)
+        j = np.searchsorted(full, sub)
+        hit = (j < len(full)) & (full[np.minimum(j, len(full) - 1)] == sub) if len(full) else \
+            np.zeros(len(sub), dtype=bool)
+        i_sub = np.flatnonzero(hit)
+        i_full = j[i_sub]
+        c = np.arange(12)
+        return (12 * i_full[:, None] + c).ravel(), (12 * i_sub[:, None] + c).ravel()
+
+    def w1_dense_blocks(self):
+        """Dense W_1 on dPi (sites in increasing global order) assembled from the
+        printed blocks listed above, with D^d_a and D^_{dPi1} (small lattices)."""
         g = self.g
+        dpi = g.sites(g.dPi)
+        n = 12 * len(dpi)
+        W1 = np.eye(n, dtype=np.complex128)
+        nb = g.nblocks
+        S = [g.sites(m) for m in g.B_mask]
+        F = [g.sites(m) for m in g.phi_mask]
+        X = [g.sites(m) for m in g.ext_star_mask]
+        Finv = [np.linalg.inv(self._dmat(F[a])) for a in range(nb)]
+        Dd = []
+        for a in range(nb):
+            bulk = g.sites(g.core_mask[a] & ~g.B_mask[a])
+            d = self._dmat(S[a]) - self._dmat(S[a], F[a]) @ Finv[a] @ self._dmat(F[a], S[a])
+            if len(bulk):
+                d -= self._dmat(S[a], bulk) @ np.linalg.solve(self._dmat(bulk), self._dmat(bulk, S[a]))
+            Dd.append(d)
+        rows = [self._take(S[a], dpi)[0] for a in range(nb)]
+
+        def fa_from(vec_sites, vec, fa):
+            """Entries of ``vec`` (rows on vec_sites) at the sites of fa, in fa's order."""
+            out = np.zeros((12 * len(fa), vec.shape[1]), dtype=np.complex128)
+            i_vec, i_fa = self._take(fa, vec_sites)
+            out[i_fa] = vec[i_vec]
+            return out
+
+        D_SF = [self._dmat(S[a], F[a]) for a in range(nb)]            # D_{dL0a, Phi_a}
+        D_FX = [self._dmat(F[a], X[a]) if len(X[a]) else None for a in range(nb)]
+        for b in range(nb):
+            Xb = self._dmat(F[b], S[b])                     # D_{Phi_b, dL0b}
+            Yb = Finv[b] @ Xb                               # D_{Phi_b}^-1 D_{Phi_b, dL0b}
+            Zb = self._dmat(X[b], F[b]) @ Yb if len(X[b]) else None   # D_{X*b, Phi_b} (...)
+            for a in range(nb):
+                if a == b:
+                    continue
+                # the three terms of the bracket that start with D_{Phi_a}^-1, then the one that does not
+                under = fa_from(F[b], Xb, F[a])
+                if D_FX[a] is not None:
+                    under -= D_FX[a] @ fa_from(F[b], Yb, X[a])
+                if Zb is not None:
+                    under -= fa_from(X[b], Zb, F[a])
+                bracket = Finv[a] @ under + fa_from(F[b], Yb, F[a])
+                h = -0.5 * D_SF[a] @ bracket
+                W1[np.ix_(rows[a], rows[b])] += np.linalg.solve(Dd[a], h)
+        # upper-right block (Eq. offdiagW1), printed as P D_Omega^-1 D_{Phi, X*}
+        cs = g.sites(g.C)
+        if len(cs):
+            rows_c = self._take(cs, dpi)[0]
+            for a in range(nb):
+                if not len(X[a]):
+                    continue
+                om = g.sites(g.omega_mask[a])
+                G = np.linalg.inv(self._dmat(om))
+                i_om_f, _ = self._take(F[a], om)
+                i_om_b, _ = self._take(S[a], om)
+                blk = G[np.ix_(i_om_b, i_om_f)] @ self._dmat(F[a], X[a])
+                W1[np.ix_(rows[a], self._take(X[a], dpi)[0])] += blk
+            # lower-left block D^_{dPi1}^-1 D^_{dPi1, dL0}
+            es = g.sites(g.E)
+            Shat = self._dmat(cs)
+            if len(es):
+                Shat = Shat - self._dmat(cs, es) @ np.linalg.solve(self._dmat(es), self._dmat(es, cs))
+            DC0 = np.zeros((12 * len(cs), 12 * len(dpi)), dtype=np.complex128)
+            for b in range(nb):
+                if not len(X[b]):
+                    continue
+                Zb = self._dmat(X[b], F[b]) @ Finv[b] @ self._dmat(F[b], S[b])
+                i_c, _ = self._take(X[b], cs)
+                DC0[np.ix_(i_c, rows[b])] -= Zb
+            W1[rows_c] += np.linalg.solve(Shat, DC0)
+        else:
+            Shat = np.zeros((0, 0), dtype=np.complex128)
+        return W1, Dd, Shat
+
+    def w_matrix(self):
+        """Dense matrix of w = 1 - W_1 on dPi (sites in increasing global order)."""
+        W1, _, _ = self.w1_dense_blocks()
+        return np.eye(len(W1)) - W1
+
+    def _masked(self, mask, f):
+        return mask[..., None, None] * f
+
+    def _D(self, rows, cols, f):
+        """D_{X,Y} f = P_X D P_Y f for boolean masks X, Y."""
+        return self._masked(rows, self.D(self._masked(cols, f)))
+
+    def block_sources(self, chi):
+        """Per block a the source s_a of the Omega0^a solve in the first row of
+        W_1 (Eqs. Wz, offdiagW1), and the source v of the dPi1 row:
+
+            (W_1 chi)_{dL0a} = chi_{dL0a} + P_{dL0a} D_{Omega_a}^-1 s_a,
+            s_a = sum_{b != a} D^h_{a,b} chi_{dL0b} + D_{Phi_a, X*a} chi_{dPi1},
+            (W_1 chi)_{dPi1} = chi_{dPi1} + P_{dPi1} D_{Lambda1}^-1 v,
+            v = D^_{dPi1, dL0} chi_{dL0}.
+
+        [D^d_a]^-1 acting on a field on dL0a is P_{dL0a} D_{Omega_a}^-1 (the
+        inverse of a Schur complement is the matching block of the inverse);
+        likewise D^_{dPi1}^-1 = P_{dPi1} D_{Lambda1}^-1 on dPi1.  D^h chi is the
+        printed bracket; D_{Phi_a}^-1 is applied once per block a to the sum over
+        b of the bracket's terms that carry it."""
+        g = self.g
+        nb = g.nblocks
+        F, X, Bm = g.phi_mask, g.ext_star_mask, g.B_mask
+        t = [self._D(F[b], Bm[b], chi) for b in range(nb)]          # D_{Phi_b, dL0b} chi
+        Y = [self.phi_solver(b).solve_field(t[b]) for b in range(nb)]
+        Z = [self._D(X[b], F[b], Y[b]) for b in range(nb)]           # D_{X*b, Phi_b} Y_b
+        sources = []
+        for a in range(nb):
+            inner = np.zeros_like(chi)        # terms of the bracket under D_{Phi_a}^-1
+            outer = np.zeros_like(chi)        # the term D_{Phi_b}^-1 (...) without it
+            for b in range(nb):
+                if b == a:
+                    continue
+                inner += self._masked(F[a], t[b])                    # D_{Phi_a}^-1 P_{Phi_a} ...
+                inner -= self._D(F[a], X[a], Y[b])                   # - D_{Phi_a}^-1 D_{Phi_a,X*a} D_{Phi_b}^-1
+                inner -= self._masked(F[a], Z[b])                    # - D_{Phi_a}^-1 D_{X*b,Phi_b} D_{Phi_b}^-1
+                outer += self._masked(F[a], Y[b])                    # + D_{Phi_b}^-1 on Phi_a
+            bracket = self.phi_solver(a).solve_field(inner) + outer
+            h = -0.5 * self._D(Bm[a], F[a], bracket)
+            sources.append(h + self._D(F[a], X[a], chi))
+        v = -sum(Z)                                                  # D^_{dPi1, dL0} chi
+        return sources, self._masked(g.C, v)
+
+    def apply_w(self, chi):
+        """w chi = chi - W_1 chi for a field chi supported on dPi (the vector
+        form of the blocks above); result supported on dPi."""
+        g = self.g
+        sources, v = self.block_sources(chi)
         out = np.zeros_like(chi)
         for a in range(g.nblocks):
-            ext = chi * g.ext_mask[a][..., None, None]
-            src = g.omega_mask[a][..., None, None] * self.D(ext)     # D_{Omega, ext} chi
-            psi = self.omega_solver(a).solve_field(src)
+            psi = self.omega_solver(a).solve_field(self._masked(g.omega_mask[a], sources[a]))
             bm = g.B_mask[a]
             out[bm] = -psi[bm]
-        ext = chi * g.B[..., None, None]
-        src = g.Lambda1[..., None, None] * self.D(ext)                # D_{Lambda1, dLambda0} chi
-        y = self.frame_solver().solve_field(src)
-        out[g.C] = -y[g.C]
+        if g.C.any():
+            y = self.frame_solver().solve_field(self._masked(g.Lambda1, v))
+            out[g.C] = -y[g.C]
         return out
 
     def apply_W1(self, chi):
@@ -170,41 +332,6 @@ class Oracle:
         s_blocks = [math.fsum(v) for v in sa]
         s_r = math.fsum(sr)
         return math.fsum(s_blocks + [s_r]), s_blocks, s_r
-
-    # -- dense forms for the determinant identity (small lattices) ----------
-    def w_matrix(self):
-        """Dense matrix of w on dPi (sites in increasing global order)."""
-        g = self.g
-        V = int(np.prod(g.L))
-        dpi = g.sites(g.dPi)
-        pos = np.full(V, -1, dtype=np.int64)
-        pos[dpi] = np.arange(len(dpi))
-        n = 12 * len(dpi)
-        W = np.zeros((n, n), dtype=np.complex128)
-
-        def comp_index(sites):
-            return (12 * pos[sites][:, None] + np.arange(12)[None, :]).ravel()
-
-        for a in range(g.nblocks):
-            om = g.sites(g.omega_mask[a])
-            ex = g.sites(g.ext_mask[a])
-            rhs = dirac_block(self.U, self.kappa, om, ex, self.time_bc, self.csw).toarray()
-            G = self.omega_solver(a).lu.solve(rhs)
-            opos = np.full(V, -1, dtype=np.int64)
-            opos[om] = np.arange(len(om))
-            bs = g.sites(g.B_mask[a])
-            rows_in_om = (12 * opos[bs][:, None] + np.arange(12)[None, :]).ravel()
-            W[np.ix_(comp_index(bs), comp_index(ex))] = -G[rows_in_om]
-        l1 = g.sites(g.Lambda1)
-        bsites = g.sites(g.B)
-        rhs = dirac_block(self.U, self.kappa, l1, bsites, self.time_bc, self.csw).toarray()
-        G = self.frame_solver().lu.solve(rhs)
-        lpos = np.full(V, -1, dtype=np.int64)
-        lpos[l1] = np.arange(len(l1))
-        cs = g.sites(g.C)
-        rows_in_l1 = (12 * lpos[cs][:, None] + np.arange(12)[None, :]).ravel()
-        W[np.ix_(comp_index(cs), comp_index(bsites))] = -G[rows_in_l1]
-        return W
 
     def heatbath(self, u, etas):
         """Multi-boson fields by heat-bath (Sec. 4, after Eq. WW): the weight
@@ -244,10 +371,11 @@ class Oracle:
         T_t = lambda_t / 2, for the active links of every block (zero elsewhere).
 
         Only S^a of the link's block depends on it, through D_{Omega0^a}
-        (Eq. localMB): with y_k = D_Omega^{-1} D_{Omega,ext} chi_k and
-        r_k = P_{dLambda0^a}(u_k chi_k + y_k), S^a = sum_k |r_k|^2 and
-        dy = -D_Omega^{-1} dD y, so dS = -2 Re sum_k <z_k, dD y_k> with
-        z_k = (D_Omega^dag)^{-1} r_k.  dD has the two entries of the link in
+        (Eq. localMB; the source s_a of ``block_sources`` holds frame links and
+        the links from the core boundaries into the frames only): with
+        y_k = D_Omega^{-1} s_a(chi_k) and r_k = P_{dLambda0^a}(u_k chi_k + y_k),
+        S^a = sum_k |r_k|^2 and dy = -D_Omega^{-1} dD y, so
+        dS = -2 Re sum_k <z_k, dD y_k> with z_k = (D_Omega^dag)^{-1} r_k.  dD has the two entries of the link in
         the definition of D: row x, column x+mu: -kappa (1 - gamma_mu) (i T U);
         row x+mu, column x: -kappa (1 + gamma_mu) (-i U^dag T) (times the time
         boundary sign where the link crosses x0 = L0-1 -> 0)."""
@@ -259,15 +387,15 @@ class Oracle:
         one = np.eye(4)
         T = gell_mann() / 2
         F = np.zeros(tuple(L) + (4, 8))
+        srcs = [self.block_sources(chi)[0] for chi in chis]
         for a in range(g.nblocks):
             links = self.active_links(a)
             if not links:
                 continue
             om = self.omega_solver(a)
-            ext = g.ext_mask[a][..., None, None]
             pairs = []
-            for uk, chi in zip(u, chis):
-                y = om.solve_field(g.omega_mask[a][..., None, None] * self.D(chi * ext))
+            for uk, chi, s in zip(u, chis, srcs):
+                y = om.solve_field(g.omega_mask[a][..., None, None] * s[a])
                 r = g.B_mask[a][..., None, None] * (uk * chi + y)
                 pairs.append((y, om.solve_adjoint_field(r)))
             for x, mu in links:

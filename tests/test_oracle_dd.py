@@ -3,8 +3,15 @@
 * Eq. (detD): ln|det D| = ln|det W_1| + ln|det D_Lambda1|
   + sum_a [ln|det D_Omega0^a| - ln|det D_Phi1^a|], every factor a dense LU of
   an independently assembled matrix, on 4^4 and 6x4^3 (Sec. 3).
-* Green's-function identity: for eta on dPi and psi = D^{-1} eta (one global
-  direct solve), W_1 psi|dPi equals the block / frame solves of eta.
+* W_1 is fixed by three printed statements (Sec. 3), each checked against
+  dense blocks of D assembled here: the upper-right block of Eq. (offdiagW1);
+  M = diag(D^d, D^_{dPi1}) W_1 is gamma_5-hermitian (D^d and D^_{dPi1} in their
+  printed forms); the Schur complement of M onto dLambda0 is the D~ of Eq.
+  (Dtilde).  Given the first, the second fixes the lower-left block and the
+  third then fixes the upper-left one, so W_1 is determined.
+* Eq. (WW): det P_N(W_1) = c_N^n prod_{k<=N/2} det(W_{u_k}^dag W_{u_k}), i.e.
+  the conjugate roots pair up; the Dirichlet-extension completion of the
+  hopping block (the same determinant, Eq. detD) breaks it (planted mistake).
 * w as a vector operation equals w as an assembled dense matrix.
 * kappa = 0 gives w = 0 and S = sum_k |u_k|^2 |chi_k|^2.
 * Block locality of S^a and of S^r (Sec. 4, Eqs. localMB, globalMB).
@@ -87,23 +94,141 @@ def test_w_vector_equals_w_matrix():
     assert np.all(out[~g.dPi] == 0)
 
 
-def test_greens_function_identity():
-    L, cores = L6444, CORES6444
-    U = synth.gauge_field(L, 0.3, 3)
+L2D = (8, 8, 2, 2)
+CORES2D = [[(0, 1), (4, 5)], [(0, 1), (4, 5)], [], []]
+W1_CASES = [(L44, uniform_cores(L44, 1, 1)), (L6444, CORES6444), (L2D, CORES2D)]
+
+
+class _Dense:
+    """Dense blocks D_{X,Y} of the full operator assembled once (no oracle helpers)."""
+
+    def __init__(self, U, kappa, g):
+        V = int(np.prod(g.L))
+        self.D = dirac_matrix(U, kappa, np.arange(V)).toarray()
+        self.g = g
+
+    @staticmethod
+    def idx(sites):
+        return (12 * np.asarray(sites)[:, None] + np.arange(12)).ravel()
+
+    def __call__(self, X, Y=None):
+        Y = X if Y is None else Y
+        return self.D[np.ix_(self.idx(X), self.idx(Y))]
+
+    def inv(self, X):
+        return np.linalg.inv(self(X))
+
+
+@pytest.mark.parametrize("L,cores", W1_CASES)
+def test_w1_is_fixed_by_the_printed_blocks(L, cores):
+    """(i) Eq. (offdiagW1): rows dLambda0^a of W_1 on dPi1 are P D_Omega^-1 D_{Phi, X*}
+    (zero off X* = dOmega0^{a*}); (ii) M = diag(D^d, D^_{dPi1}) W_1 is gamma_5-hermitian,
+    with D^d_a = D_{dL0a} - D_{dL0a,L0bar} D_{L0bar}^-1 D_{L0bar,dL0a} - D_{dL0a,Phi} D_Phi^-1
+    D_{Phi,dL0a} and D^_{dPi1} = D_{dPi1} - D_{dPi1,E} D_E^-1 D_{E,dPi1}; (iii) the Schur
+    complement of M onto dLambda0 is Eq. (Dtilde)'s D~ = D_{dL0} - D_{dL0,L0bar} D_{L0bar}^-1
+    D_{L0bar,dL0} - D_{dL0,Lambda1} D_{Lambda1}^-1 D_{Lambda1,dL0}."""
+    U = synth.gauge_field(L, 0.3, 1)
     g = Decomposition(L, cores)
     o = Oracle(U, 0.13, g)
-    V = int(np.prod(L))
-    eta = synth.complex_gaussian(3, synth.TAG_RHS, L + (4, 3)) * g.dPi[..., None, None]
-    from scipy.sparse.linalg import splu
-    lu = splu(dirac_matrix(U, 0.13, np.arange(V)).tocsc())
-    psi = lu.solve(eta.reshape(-1)).reshape(eta.shape) * g.dPi[..., None, None]
-    lhs = o.apply_W1(psi)
+    d = _Dense(U, 0.13, g)
+    dpi = g.sites(g.dPi)
+    pos = np.full(int(np.prod(L)), -1)
+    pos[dpi] = np.arange(len(dpi))
+    r = lambda sites: d.idx(pos[np.asarray(sites)])            # rows of W_1 (dPi order)
+    W1 = np.eye(12 * len(dpi)) - o.w_matrix()
+    Bs, Cs, Es = g.sites(g.B), g.sites(g.C), g.sites(g.E)
+    Diag = np.zeros_like(W1)
     for a in range(g.nblocks):
-        rhs = o.omega_solver(a).solve_field(eta * g.omega_mask[a][..., None, None])
-        bm = g.B_mask[a]
-        assert np.linalg.norm(lhs[bm] - rhs[bm]) < 1e-11 * np.linalg.norm(rhs[bm])
-    rhs = o.frame_solver().solve_field(eta * g.Lambda1[..., None, None])
-    assert np.linalg.norm(lhs[g.C] - rhs[g.C]) < 1e-11 * np.linalg.norm(rhs[g.C])
+        B, F = g.sites(g.B_mask[a]), g.sites(g.phi_mask[a])
+        A = g.sites(g.core_mask[a] & ~g.B_mask[a])
+        Dd = d(B) - d(B, F) @ d.inv(F) @ d(F, B)
+        if len(A):
+            Dd -= d(B, A) @ d.inv(A) @ d(A, B)
+        Diag[np.ix_(r(B), r(B))] = Dd
+        # (i)
+        om = g.sites(g.omega_mask[a])
+        G = d.inv(om)
+        ib = d.idx(np.searchsorted(om, B))
+        iF = d.idx(np.searchsorted(om, F))
+        Xs = g.sites(g.ext_star_mask[a])
+        if len(Cs):
+            ref = np.zeros((12 * len(B), 12 * len(Cs)), dtype=complex)
+            if len(Xs):
+                ref[:, d.idx(np.searchsorted(Cs, Xs))] = G[np.ix_(ib, iF)] @ d(F, Xs)
+            got = W1[np.ix_(r(B), r(Cs))]
+            assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    if len(Cs):
+        Sh = d(Cs) - (d(Cs, Es) @ d.inv(Es) @ d(Es, Cs) if len(Es) else 0)
+        Diag[np.ix_(r(Cs), r(Cs))] = Sh
+    M = Diag @ W1
+    g5 = np.tile(np.repeat([1.0, -1.0], 6), len(dpi))
+    # (ii)
+    assert np.abs(g5[:, None] * M * g5[None, :] - M.conj().T).max() < 1e-12 * np.abs(M).max()
+    # (iii)
+    l1, a0 = g.sites(g.Lambda1), g.sites(g.A)
+    Dt = d(Bs) - d(Bs, l1) @ d.inv(l1) @ d(l1, Bs)
+    if len(a0):
+        Dt -= d(Bs, a0) @ d.inv(a0) @ d(a0, Bs)
+    rb, rc = r(Bs), r(Cs)
+    schur = M[np.ix_(rb, rb)]
+    if len(Cs):
+        schur = schur - M[np.ix_(rb, rc)] @ np.linalg.solve(M[np.ix_(rc, rc)], M[np.ix_(rc, rb)])
+    assert np.abs(schur - Dt).max() < 1e-11 * np.abs(Dt).max()
+
+
+def _eq_ww_gap(W1, N, c):
+    """ln det P_N(W_1) minus ln[c_N^n prod_{k<=N/2} det(W_{u_k}^dag W_{u_k})], complex
+    (P_N(W_1) = c_N prod_{k=1..N} (W_1 - z_k), W_1 - z_k = u_k - w = W_{u_k})."""
+    n = len(W1)
+    u = roots(N, c)
+    lhs = 0j
+    for uk in u:
+        s, ld = np.linalg.slogdet(W1 - (1 - uk) * np.eye(n))
+        lhs += ld + 1j * np.angle(s)
+    rhs = sum(2 * np.linalg.slogdet(W1 - (1 - uk) * np.eye(n))[1] for uk in u[: N // 2])
+    gap = lhs - rhs
+    return gap.real, math.remainder(gap.imag, 2 * math.pi), abs(lhs.real)
+
+
+@pytest.mark.parametrize("L,cores", W1_CASES)
+def test_eq_ww_pairs_conjugate_roots(L, cores):
+    """Eq. (WW) holds exactly: the roots k and N+1-k are complex conjugates and
+    det(W_1 - conj z) = conj det(W_1 - z) (the characteristic polynomial of W_1 is real)."""
+    U = synth.gauge_field(L, 0.3, 1)
+    o = Oracle(U, 0.13, Decomposition(L, cores))
+    W1 = np.eye(len(o.w_matrix())) - o.w_matrix()
+    for N, c in ([(4, 0.5), (6, 0.0), (12, 0.3)] if L == L44 else [(4, 0.5)]):
+        re, im, scale = _eq_ww_gap(W1, N, c)
+        assert abs(re) < 1e-10 * max(1.0, scale) and abs(im) < 1e-10, (N, c, re, im)
+
+
+def test_dirichlet_completion_keeps_det_but_breaks_eq_ww():
+    """Planted mistake: completing the upper-left block of W_1 as the Dirichlet
+    extension (rows dLambda0^a: P D_Omega^-1 D_{Omega,ext}; rows dPi1:
+    P D_Lambda1^-1 D_{Lambda1,dL0}) gives the same det W_1 (Eq. detD) but a
+    characteristic polynomial that is not real, so Eq. (WW) fails."""
+    U = synth.gauge_field(L44, 0.3, 1)
+    g = Decomposition(L44, uniform_cores(L44, 1, 1))
+    o = Oracle(U, 0.13, g)
+    d = _Dense(U, 0.13, g)
+    dpi = g.sites(g.dPi)
+    pos = np.full(int(np.prod(L44)), -1)
+    pos[dpi] = np.arange(len(dpi))
+    r = lambda sites: d.idx(pos[np.asarray(sites)])
+    Wd = np.eye(12 * len(dpi), dtype=complex)
+    for a in range(g.nblocks):
+        om, ex, B = g.sites(g.omega_mask[a]), g.sites(g.ext_mask[a]), g.sites(g.B_mask[a])
+        G = d.inv(om) @ d(om, ex)
+        Wd[np.ix_(r(B), r(ex))] += G[d.idx(np.searchsorted(om, B))]
+    l1, Bs, Cs = g.sites(g.Lambda1), g.sites(g.B), g.sites(g.C)
+    G = d.inv(l1) @ d(l1, Bs)
+    Wd[np.ix_(r(Cs), r(Bs))] += G[d.idx(np.searchsorted(l1, Cs))]
+    W1 = np.eye(len(Wd)) - o.w_matrix()
+    assert abs(np.linalg.slogdet(Wd)[1] - np.linalg.slogdet(W1)[1]) < 1e-10
+    re, im, _ = _eq_ww_gap(Wd, 4, 0.5)
+    assert abs(re) > 1e-4
+    re, im, _ = _eq_ww_gap(W1, 4, 0.5)
+    assert abs(re) < 1e-10
 
 
 def test_kappa_zero_action():
@@ -147,9 +272,17 @@ def test_block_locality_of_the_action():
     assert sr2 != sr0
     yp = list(y)
     yp[2] = (yp[2] + 1) % L[2]
+    # S^b holds D_{Omega_b} and, through D^h, the frame pieces Phi_c that meet Phi_b or
+    # dOmega0^{b*}, or whose dOmega0^{c*} meets Phi_b (frame links only)
+    def reach(b):
+        m = g.omega_mask[b].copy()
+        for c in range(g.nblocks):
+            if c != b and ((g.phi_mask[c] & (g.phi_mask[b] | g.ext_star_mask[b])).any()
+                           or (g.phi_mask[b] & g.ext_star_mask[c]).any()):
+                m |= g.phi_mask[c]
+        return m
     for b in range(g.nblocks):
-        touches = g.omega_mask[b][y] or g.omega_mask[b][tuple(yp)]
-        if not touches:
+        if not (reach(b)[y] or reach(b)[tuple(yp)]):
             assert sa2[b] == sa0[b]
 
 
@@ -376,7 +509,7 @@ def test_mb_force_matches_finite_differences_of_total_action(case):
         picks = [(0, 0, 1), (0, 1, 4), (0, 3, 7), (1, 0, 2), (1, 2, 0)]    # (block, link #, t)
     else:
         L, cores = (8,) * 4, uniform_cores((8,) * 4, 3, 1)
-        picks = [(0, 5, 3), (5, 40, 6)]
+        picks = [(5, 40, 6)]
     U = synth.gauge_field(L, 0.3, 4)
     g = Decomposition(L, cores)
     o = Oracle(U, 0.13, g)
