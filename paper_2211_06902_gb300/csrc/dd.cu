@@ -1,14 +1,30 @@
 // The operator w (paper Sec. 3, Eqs. Wz and offdiagW1) and the multi-boson
 // action (paper Sec. 4, Eqs. MBaction, localMB, globalMB).
 //
-//   (w chi)_{dLambda0^a} = -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi
-//   (w chi)_{dPi1}       = -P_{dPi1} D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi
+// W_1 = diag(D^d, D^_{dPi1})^{-1} M is the matrix of the second Schur
+// decomposition as the paper prints it (the hopping block D^h in its
+// symmetrised form over the frame pieces Phi1^a and Phi1^b).  It factors as
+// W_1 = E (1 - Q): Q maps chi on dLambda0 to dPi1,
+//   (Q chi)(x) = sum_{b : x in Phi1^b} [D_{Phi1^b}^{-1} D_{Phi1^b, dLambda0^b} chi](x),
+// and E is the Dirichlet extension of chi into the framed blocks and the frame,
+//   (E chi)_{dLambda0^a} = chi + P D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi,
+//   (E chi)_{dPi1}       = chi + P D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi.
+// (Both sides are linear in the printed blocks: the rows of D^h unfold, by the
+// block inverses of D_{Omega0^a} and D_{Lambda1}, into the Phi-solve of Q followed
+// by the Omega-solve of E.)  So one application of w = 1 - W_1 is
+//   stage A: the frame pieces Y_b = D_{Phi_b}^{-1} D_{Phi_b, dL0b} chi of every block
+//            and the frame y = D_{Lambda1}^{-1} D_{Lambda1, dL0} chi, one batch;
+//            chi' = chi - Q chi on dPi1, (w chi)_{dPi1} = Q chi - y;
+//   stage B: the framed blocks x_a = D_{Omega_a}^{-1} D_{Omega_a, ext} chi', one batch;
+//            (w chi)_{dLambda0^a} = -x_a.
+// Without dPi1 (one decomposed direction) Q = 0 and stage A is skipped.
+//
 //   S = sum_k |(u_k - w) chi_k|^2 = sum_a S^a + S^r
 //
 // Boundary injection (D_{X, ext} chi: the hops from the sites just outside X
-// into X) is a gather from chi on dPi with the global FP64 links; the block
-// and frame solves go through the batched solver; extraction and the FP64
-// reductions follow in fixed order (deterministic).
+// into X) is a gather from chi on dPi with the global FP64 links; the block,
+// frame-piece and frame solves go through the batched solver; extraction and the
+// FP64 reductions follow in fixed order (deterministic).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -122,6 +138,67 @@ __global__ void k_inject_frame(const int* __restrict__ l1_glob, int n_l1,
   double2* out = a.src + ((long long)f * n_l1 + k) * 12;
 #pragma unroll
   for (int c = 0; c < 12; ++c) out[c] = make_double2(-a.kappa * acc[c].x, -a.kappa * acc[c].y);
+}
+
+// Sources of the frame pieces: t(x) = D_{Phi1^j, dLambda0^j} chi for x in
+// Phi1^j, the hops into x from the boundary sites of its own core j (the batch
+// holds Phi1^0 .. Phi1^{nb-1} at positions 0 .. nb-1).
+// grid: (ceil(max_sites/128), n_f, nb)
+__global__ void k_inject_phi(BatchDev bd, InjectArgs a, const int* __restrict__ dpi_kind) {
+  const int f = blockIdx.y, j = blockIdx.z;
+  const int sys = j * a.n_f + f;
+  const DomInst* d = bd.inst_tab + bd.inst[j];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d->nsites) return;
+  const int gx = d->glob[k];
+  int g[4];
+  site_coords(gx, a.L, g);
+  double2 acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = make_double2(0.0, 0.0);
+  for (int dir = 0; dir < 8; ++dir) {
+    const int mu = dir & 3, step = dir < 4 ? 1 : -1;
+    int gy[4] = {g[0], g[1], g[2], g[3]};
+    gy[mu] = (g[mu] + step + a.L[mu]) % a.L[mu];
+    const int y = glob_index(gy, a.L);
+    const int q = a.dpi_pos[y];
+    if (q < 0 || dpi_kind[q] != j) continue;          // not a boundary site of core j
+    add_exterior_hop(acc, dir, gx, y, a, f);
+  }
+  double2* out = a.src + bd.uoff[sys] + 12LL * d->fmap[k];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) out[c] = make_double2(-a.kappa * acc[c].x, -a.kappa * acc[c].y);
+}
+
+// On every dPi1 site x and field f: q = (Q chi)(x), the sum of the frame-piece
+// solutions Y_b(x) over the pieces that hold x (in block order), then
+// chi'(x) = chi(x) - q and, with the frame solved in the same batch (position
+// frame_pos), (w chi)(x) = q - y(x).
+__global__ void k_frame_q(const int* __restrict__ q_beg, const int* __restrict__ q_blk,
+                          const long long* __restrict__ q_loc, const long long* __restrict__ c_loc,
+                          const int* __restrict__ c_dpi, int nC, int n_f, int n_dpi, int frame_pos,
+                          const long long* __restrict__ uoff, const double2* __restrict__ sol,
+                          const double2* __restrict__ chi, double2* __restrict__ chi_p,
+                          double2* __restrict__ w) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (k >= nC) return;
+  double2 q[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) q[c] = make_double2(0.0, 0.0);
+  for (int e = q_beg[k]; e < q_beg[k + 1]; ++e) {
+    const double2* s = sol + uoff[(long long)q_blk[e] * n_f + f] + q_loc[e];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) q[c] = make_double2(q[c].x + s[c].x, q[c].y + s[c].y);
+  }
+  const long long o = ((long long)f * n_dpi + c_dpi[k]) * 12;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) chi_p[o + c] = make_double2(chi[o + c].x - q[c].x, chi[o + c].y - q[c].y);
+  if (w) {
+    const double2* y = sol + uoff[(long long)frame_pos * n_f + f] + c_loc[k];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) w[o + c] = make_double2(q[c].x - y[c].x, q[c].y - y[c].y);
+  }
 }
 
 // (w chi) on dLambda0: -x at the block-boundary sites; on dPi1: -y.  For
@@ -358,6 +435,13 @@ struct WPlan {           // host-built gather lists, one per context
   int* d_c_dpi = nullptr;            // [n_C]
   int* d_c_grp = nullptr;            // C sites split into chunks for the S^r partials
   int n_cgrp = 0;
+  // Q chi on dPi1 (built with the frame pieces on first use): for every dPi1
+  // site (C order) the frame pieces Phi1^b holding it and its field position there
+  bool q_ready = false;
+  int* d_q_beg = nullptr;            // [n_C + 1]
+  int* d_q_blk = nullptr;            // [n_q] block b
+  long long* d_q_loc = nullptr;      // [n_q] 12 * field position inside Phi1^b
+  int max_phi = 0;
   // active links (both end points in one core), built on the first force call
   bool force_ready = false;
   long long n_al = 0;
@@ -371,6 +455,7 @@ void free_plan(dd_ctx* c) {
   dfree(P->d_l1_glob); dfree(P->d_in_l1); dfree(P->d_b_blk); dfree(P->d_b_loc);
   dfree(P->d_b_dpi); dfree(P->d_b_grp); dfree(P->d_c_loc); dfree(P->d_c_dpi); dfree(P->d_c_grp);
   dfree(P->d_al); dfree(P->d_al_loc);
+  dfree(P->d_q_beg); dfree(P->d_q_blk); dfree(P->d_q_loc);
   delete P;
   c->wplan = nullptr;
 }
@@ -437,6 +522,110 @@ static dd_status build_plan(dd_ctx* c, WPlan** out) {
   return DD_OK;
 }
 
+// gather lists of Q: the frame pieces holding each dPi1 site
+static dd_status build_q_plan(dd_ctx* c, WPlan& P) {
+  if (P.q_ready) return DD_OK;
+  dd_status e;
+  if ((e = ensure_phi(c)) != DD_OK) return e;
+  const int nb = (int)c->blocks.size(), nC = (int)c->C_sites.size();
+  std::vector<int> c_index(c->V, -1);
+  for (int k = 0; k < nC; ++k) c_index[c->C_sites[k]] = k;
+  std::vector<std::vector<std::pair<int, long long>>> per(nC);
+  int max_phi = 0;
+  for (int b = 0; b < nb; ++b) {
+    const Instance& ph = c->inst[c->phi0 + b];
+    max_phi = std::max(max_phi, ph.d.nsites);
+    for (int k = 0; k < ph.d.nsites; ++k) {
+      const int ci = c_index[ph.h_glob[k]];
+      if (ci >= 0) per[ci].push_back({b, 12LL * ph.h_fmap[k]});
+    }
+  }
+  std::vector<int> beg(1, 0), blk;
+  std::vector<long long> loc;
+  for (int k = 0; k < nC; ++k) {
+    for (auto& pr : per[k]) {          // blocks in increasing order: fixed summation order
+      blk.push_back(pr.first);
+      loc.push_back(pr.second);
+    }
+    beg.push_back((int)blk.size());
+  }
+  auto up = [&](auto& vec, auto** dst) -> dd_status {
+    size_t bytes = sizeof(vec[0]) * std::max<size_t>(1, vec.size());
+    dd_status st = dalloc(c, (void**)dst, bytes);
+    if (st != DD_OK) return st;
+    if (!vec.empty()) cudaMemcpy(*dst, vec.data(), sizeof(vec[0]) * vec.size(), cudaMemcpyHostToDevice);
+    return DD_OK;
+  };
+  if ((e = up(beg, &P.d_q_beg)) || (e = up(blk, &P.d_q_blk)) || (e = up(loc, &P.d_q_loc))) return e;
+  P.max_phi = max_phi;
+  P.q_ready = true;
+  return DD_OK;
+}
+
+// merged statistics of two batched solves of one call
+static void merge_stats(dd_solve_stats& a, const dd_solve_stats& b) {
+  a.systems += b.systems;
+  a.converged += b.converged;
+  a.max_iters = std::max(a.max_iters, b.max_iters);
+  a.outer_cycles = std::max(a.outer_cycles, b.outer_cycles);
+  a.max_relres = std::max(a.max_relres, b.max_relres);
+  a.seconds += b.seconds;
+}
+
+// Stage A of w (see the top of the file): the frame pieces of every block (and
+// with with_frame the frame Lambda1) in one batch, then chi' = chi - Q chi on dPi1
+// (chi' = chi elsewhere) and, with the frame, (w chi)_{dPi1} = Q chi - y.
+static dd_status frame_stage(dd_ctx* c, WPlan& P, int n_f, const double* chi, double* chi_p, double* wchi,
+                             bool with_frame, const dd_solve_params* prm, dd_solve_stats* st,
+                             cudaStream_t s) {
+  dd_status e;
+  if ((e = build_q_plan(c, P)) != DD_OK) return e;
+  const int nb = (int)c->blocks.size();
+  std::vector<int> insts(nb + (with_frame ? 1 : 0));
+  for (int b = 0; b < nb; ++b) insts[b] = c->phi0 + b;
+  if (with_frame) insts[nb] = c->lambda1;
+  Batch* ab;
+  if ((e = get_batch_insts(c, insts, n_f, &ab)) != DD_OK) return e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  void *src_a, *sol_a;
+  if ((e = workspace(c, 36, 16ULL * ab->user_tot, &src_a)) || (e = workspace(c, 37, 16ULL * ab->user_tot, &sol_a)))
+    return e;
+  InjectArgs a;
+  a.U = c->d_U;
+  a.chi = (const double2*)chi;
+  a.dpi_pos = c->d_dpi_pos;
+  for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
+  a.n_dpi = c->info.n_dpi;
+  a.n_f = n_f;
+  a.kappa = c->kappa;
+  a.src = (double2*)src_a;
+  BatchDev bd = batch_view(c, *ab);
+  dim3 g1((P.max_phi + 127) / 128, n_f, nb);
+  DD_COUNT_LAUNCH(), k_inject_phi<<<g1, 128, 0, s>>>(bd, a, c->d_dpi_kind);
+  if (with_frame) {
+    long long phi_user = 0;
+    for (int b = 0; b < nb; ++b) phi_user += 12LL * c->inst[c->phi0 + b].d.nsites * n_f;
+    a.src = (double2*)src_a + phi_user;
+    dim3 g2((P.n_l1 + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  dd_status r = solve_batch(c, *ab, (const double*)src_a, (double*)sol_a, prm, st, s, true);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  const size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
+  DD_CUDA(c, cudaMemcpyAsync(chi_p, chi, bytes, cudaMemcpyDeviceToDevice, s));
+  const int nC = c->info.n_C;
+  if (nC) {
+    dim3 g((nC + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_frame_q<<<g, 128, 0, s>>>(P.d_q_beg, P.d_q_blk, P.d_q_loc, P.d_c_loc, P.d_c_dpi, nC, n_f,
+                                                   c->info.n_dpi, nb, ab->d_uoff, (const double2*)sol_a,
+                                                   (const double2*)chi, (double2*)chi_p,
+                                                   with_frame ? (double2*)wchi : nullptr);
+    DD_CUDA(c, cudaGetLastError());
+  }
+  return r;
+}
+
 // active links of every block: (x, mu) with x and x + mu both in the core
 // Lambda0^b (cores are intervals that do not wrap, except an undecomposed
 // direction's virtual core spanning the whole periodic extent)
@@ -484,24 +673,35 @@ static dd_status build_force_plan(dd_ctx* c, WPlan& P) {
   return DD_OK;
 }
 
-// w chi for n_f fields (device pointers, caller layout on dPi).
+// w chi for n_f fields (device pointers, caller layout on dPi): stage A (frame
+// pieces and frame, skipped without dPi1), stage B (framed blocks on chi').
 static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi,
                              const dd_solve_params* prm, cudaStream_t s) {
   if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
   if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
   const int nb = (int)c->blocks.size();
-  // one batch: every framed block Omega0^a and the frame Lambda1, n_f fields
-  // each; the frame's source does not depend on the block solutions, so the
-  // uneven blocks and the frame run through the same launches
-  std::vector<int> insts(nb + 1);
-  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
-  insts[nb] = c->lambda1;
-  Batch* ob;
   dd_status e;
-  if ((e = get_batch_insts(c, insts, n_f, &ob)) != DD_OK) return e;
   WPlan* PP;
   if ((e = build_plan(c, &PP)) != DD_OK) return e;
   WPlan& P = *PP;
+  bool noconv = false;
+  dd_solve_stats tot{};
+  const double* chi_b = chi;
+  if (c->info.n_C > 0) {
+    void* cp;
+    if ((e = workspace(c, 42, 16ULL * n_f * c->info.n_dpi * 12, &cp)) != DD_OK) return e;
+    dd_solve_stats sa{};
+    dd_status ra = frame_stage(c, P, n_f, chi, (double*)cp, wchi, true, prm, &sa, s);
+    if (ra == DD_ENOCONV) noconv = true;
+    else if (ra != DD_OK) return ra;
+    merge_stats(tot, sa);
+    chi_b = (const double*)cp;
+  }
+  // stage B: every framed block Omega0^a, n_f fields each, sources from chi'
+  std::vector<int> insts(nb);
+  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
+  Batch* ob;
+  if ((e = get_batch_insts(c, insts, n_f, &ob)) != DD_OK) return e;
   if ((e = sync_instances(c)) != DD_OK) return e;
   void *src_o, *sol_o;
   if ((e = workspace(c, 40, 16ULL * ob->user_tot, &src_o)) ||
@@ -509,43 +709,33 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
     return e;
   InjectArgs a;
   a.U = c->d_U;
-  a.chi = (const double2*)chi;
+  a.chi = (const double2*)chi_b;
   a.dpi_pos = c->d_dpi_pos;
   for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
   a.n_dpi = c->info.n_dpi;
   a.n_f = n_f;
   a.kappa = c->kappa;
-  // Omega sources (systems 0 .. nb*n_f - 1)
   a.src = (double2*)src_o;
   BatchDev bd = batch_view(c, *ob);
   dim3 g1((c->info.max_omega + 127) / 128, n_f, nb);
   DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
-  // frame sources (systems nb*n_f .. (nb+1)*n_f - 1, contiguous after the blocks)
-  long long omega_user = 0;
-  for (int b = 0; b < nb; ++b) omega_user += 12LL * c->inst[c->omega0 + b].d.nsites * n_f;
-  a.src = (double2*)src_o + omega_user;
-  dim3 g2((P.n_l1 + 127) / 128, n_f);
-  DD_COUNT_LAUNCH(), k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
   DD_CUDA(c, cudaGetLastError());
-  dd_solve_stats st1{};
-  dd_status r1 = solve_batch(c, *ob, (const double*)src_o, (double*)sol_o, prm, &st1, s, true);
-  if (r1 != DD_OK && r1 != DD_ENOCONV) return r1;
-  // extraction into w chi (zero outside dPi by construction: dPi = B u C)
-  const int nB = c->info.n_B, nC = c->info.n_C;
+  dd_solve_stats sb{};
+  dd_status rb = solve_batch(c, *ob, (const double*)src_o, (double*)sol_o, prm, &sb, s, true);
+  if (rb == DD_ENOCONV) noconv = true;
+  else if (rb != DD_OK) return rb;
+  merge_stats(tot, sb);
+  c->last_stats = tot;
+  // extraction into w chi on dLambda0 (dPi1 was written by stage A)
+  const int nB = c->info.n_B;
   if (nB) {
     dim3 g((nB + 127) / 128, n_f);
     DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(P.d_b_blk, 0, P.d_b_loc, P.d_b_dpi, nB, n_f,
                                                    c->info.n_dpi, ob->d_uoff, (const double2*)sol_o,
                                                    (double2*)wchi);
   }
-  if (nC) {
-    dim3 g((nC + 127) / 128, n_f);
-    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(nullptr, nb, P.d_c_loc, P.d_c_dpi, nC, n_f,
-                                                   c->info.n_dpi, ob->d_uoff, (const double2*)sol_o,
-                                                   (double2*)wchi);
-  }
   DD_CUDA(c, cudaGetLastError());
-  if (r1 == DD_ENOCONV) return fail(c, DD_ENOCONV, "a block or frame solve missed its tolerance");
+  if (noconv) return fail(c, DD_ENOCONV, "a block, frame-piece or frame solve missed its tolerance");
   return DD_OK;
 }
 
@@ -937,10 +1127,22 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
       (e = workspace(c, 235, 16ULL * n_f, &vu)))
     return e;
   DD_CUDA(c, cudaMemcpyAsync(vu, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
-  // y = D_Omega^{-1} D_{Omega,ext} chi for every block and field
+  bool noconv = false;
+  dd_solve_stats st1{};
+  // chi' = chi - Q chi (stage A without the frame; S^a holds the frame pieces only
+  // through it), then y = D_Omega^{-1} D_{Omega,ext} chi' for every block and field
+  const double* chi_b = din;
+  if (c->info.n_C > 0) {
+    void* cp;
+    if ((e = workspace(c, 237, vbytes, &cp)) != DD_OK) return e;
+    dd_status r0 = frame_stage(c, P, n_f, din, (double*)cp, nullptr, false, prm, &st1, s);
+    if (r0 == DD_ENOCONV) noconv = true;
+    else if (r0 != DD_OK) return r0;
+    chi_b = (const double*)cp;
+  }
   InjectArgs a;
   a.U = c->d_U;
-  a.chi = (const double2*)din;
+  a.chi = (const double2*)chi_b;
   a.dpi_pos = c->d_dpi_pos;
   for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
   a.n_dpi = c->info.n_dpi;
@@ -951,8 +1153,6 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
   dim3 g1((c->info.max_omega + 127) / 128, n_f, nb);
   DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
   DD_CUDA(c, cudaGetLastError());
-  bool noconv = false;
-  dd_solve_stats st1{};
   dd_status r1 = solve_batch(c, *ob, (const double*)vsrc, (double*)vy, prm, &st1, s, true);
   if (r1 == DD_ENOCONV) noconv = true;
   else if (r1 != DD_OK) return r1;
@@ -990,7 +1190,7 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
   }
   if (hF) DD_CUDA(c, cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
-  if (noconv) return fail(c, DD_ENOCONV, "a block solve missed its tolerance");
+  if (noconv) return fail(c, DD_ENOCONV, "a block or frame-piece solve missed its tolerance");
   return DD_OK;
 }
 

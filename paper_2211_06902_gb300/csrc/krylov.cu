@@ -671,6 +671,26 @@ void convert_outer(bool dfo, dd_prec ip, const BatchDev& bd, dim3 g, int p, void
   }
 }
 
+// r = b - D x at the outer precision (both parities); the double-float
+// residual also writes the |r|^2 partials of the next outer check
+dd_status true_residual_pass(dd_ctx* c, const Batch& b, dd_prec op, bool dfo, const void* xe, const void* xo,
+                             const void* be, const void* bo, void* re, void* ro, double* partial,
+                             double* partial_o, cudaStream_t s) {
+  const double kap = c->kappa;
+  HopArgs h{};
+  h.p_out = 0; h.in = xo; h.out = re; h.s1 = be; h.a1 = 1.0; h.s2 = xe; h.a2 = -1.0; h.b = kap;
+  HopArgs g{};
+  g.p_out = 1; g.in = xe; g.out = ro; g.s1 = bo; g.a1 = 1.0; g.s2 = xo; g.a2 = -1.0; g.b = kap;
+  if (dfo) {
+    h.norm_out = g.norm_out = true;
+    h.partial = partial;
+    g.partial = partial_o;
+  }
+  dd_status e;
+  if ((e = launch_hop(c, b, op, h, s)) != DD_OK) return e;
+  return launch_hop(c, b, op, g, s);
+}
+
 }  // namespace
 
 dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x_user,
@@ -826,7 +846,17 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     DD_CUDA(c, cudaMemcpyAsync(&h_max, d_maxrel, sizeof(h_max), cudaMemcpyDeviceToHost, s));
     DD_CUDA(c, cudaStreamSynchronize(s));
     memcpy(&maxrel, &h_max, sizeof(double));
-    if (h_count == 0 || cyc == max_outer) break;
+    // A decision to stop that rests on an updated (recursive) residual is
+    // verified: r = b - D x once more at the outer precision, and the check
+    // repeats on it, so the residuals a solve reports are true residuals.
+    if (h_count == 0 && !last_true) {
+      if ((e = true_residual_pass(c, b, op, dfo, xe, xo, be, bo, re, ro, partial, partial_o, s)) != DD_OK)
+        return e;
+      last_true = true;
+      norms_ready = dfo;
+      continue;
+    }
+    if (h_count == 0 || cyc >= max_outer) break;
     ++cycles;
     const bool true_residual = (ip != DD_F32) || cyc == 0 || maxrel > theta;
     // residual at the inner precision
@@ -869,19 +899,9 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     axpy_outer(dfo, bd, eg, 0, xe, w.x, ip, 1.0, st, s);
     if (has_odd) axpy_outer(dfo, bd, og, 1, xo, eo, ip, 1.0, st, s);
     if (true_residual) {
-      // r = b - D x at the outer precision
-      HopArgs h{};
-      h.p_out = 0; h.in = xo; h.out = re; h.s1 = be; h.a1 = 1.0; h.s2 = xe; h.a2 = -1.0; h.b = kap;
-      HopArgs g{};
-      g.p_out = 1; g.in = xe; g.out = ro; g.s1 = bo; g.a1 = 1.0; g.s2 = xo; g.a2 = -1.0; g.b = kap;
-      if (dfo) {     // the double-float residual also writes the |r|^2 partials
-        h.norm_out = g.norm_out = true;
-        h.partial = partial;
-        g.partial = partial_o;
-        norms_ready = true;
-      }
-      if ((e = launch_hop(c, b, op, h, s)) != DD_OK) return e;
-      if ((e = launch_hop(c, b, op, g, s)) != DD_OK) return e;
+      if ((e = true_residual_pass(c, b, op, dfo, xe, xo, be, bo, re, ro, partial, partial_o, s)) != DD_OK)
+        return e;
+      norms_ready = dfo;
     } else {
       // r -= D e with D e at the inner precision
       HopArgs h{};
