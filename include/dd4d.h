@@ -227,6 +227,16 @@ dd_status dd_solve_blocks(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
  * inner products may sum in a different order.  dd_hop_variant_name returns
  * a static description of variant v (NULL if out of range). */
 dd_status dd_set_hop_variant(dd_ctx* ctx, dd_prec prec, int v);
+
+/* Test hook of the failure path (no counterpart in the paper).  While on != 0,
+ * every launch of the shared-memory bundle form of the FP32/BF16 stencil lets
+ * its first CTA arm the barrier of its last link quarter without issuing the
+ * bulk copy, and bounds that CTA's waits to 64 polls of about 1 us: the wait
+ * gives up with nothing in flight, the kernel sets the device error word, and
+ * the next synchronising call returns DD_ETIMEOUT (that CTA's output is left
+ * incomplete).  on = 0 restores normal launches; the context stays usable.
+ * Host-only, no sync. */
+dd_status dd_debug_wait_fault(dd_ctx* ctx, int on);
 int dd_hop_variants(dd_prec prec);
 const char* dd_hop_variant_name(dd_prec prec, int v);
 
@@ -235,10 +245,19 @@ const char* dd_hop_variant_name(dd_prec prec, int v);
 dd_status dd_last_solve_stats(const dd_ctx* ctx, dd_solve_stats* stats);
 
 /* ---- the operator w (paper Sec. 3, Eqs. Wz and offdiagW1) ----------------
- * For n_f fields chi on dPi (layout [f][dPi site in dd_geom_sites order][12]):
- *   (w chi)_{dLambda0^a} = -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi
- *   (w chi)_{dPi1}       = -P_{dPi1} D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi
- * i.e. W_1 = 1 - w, W_u = u - w.  Solves to params->tol.  Synchronises. */
+ * w = 1 - W_1 on dPi, W_1 = diag(D^d, D^_{dPi1})^{-1} M the matrix of the second
+ * Schur decomposition with the blocks the paper prints (the hopping block D^h
+ * in its symmetrised form over the frame pieces Phi1^a).  For n_f fields chi on
+ * dPi (layout [f][dPi site in dd_geom_sites order][12]) it is applied as
+ *   Y_b = D_{Phi1^b}^{-1} D_{Phi1^b, dLambda0^b} chi           (every block b)
+ *   (Q chi)(x) = sum_{b : x in Phi1^b} Y_b(x)  on dPi1,  chi' = chi - Q chi
+ *   (w chi)_{dLambda0^a} = -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi'
+ *   (w chi)_{dPi1}       = (Q chi)_{dPi1} - P_{dPi1} D_{Lambda1}^{-1} D_{Lambda1, dLambda0} chi
+ * (the block inverses of D_Phi, D_Omega and D_Lambda1 turn the printed blocks
+ * into these two stages: frame pieces and frame in one batched solve, then the
+ * framed blocks in a second).  W_u = u - w.  Without dPi1 (one decomposed
+ * direction) Q = 0.  Solves to params->tol; dd_last_solve_stats merges both
+ * stages.  Synchronises. */
 dd_status dd_apply_w(dd_ctx* ctx, int n_f, const double* chi, double* w_chi,
                      const dd_solve_params* params, void* stream);
 
@@ -280,16 +299,34 @@ dd_status dd_multiboson_heatbath(dd_ctx* ctx, int n_f, const double* u, const do
  * D_{Omega0^a}.  For each active link and each generator T_t = lambda_t / 2
  * (Gell-Mann, t = 0..7) the call returns
  *   F[x][mu][t] = d S / d eps  at  U_mu(x) -> exp(i eps T_t) U_mu(x),
- * with y_k = D_Omega^{-1} D_{Omega,ext} chi_k, r_k = P_{dLambda0^a}(u_k chi_k + y_k),
+ * with y_k = D_Omega^{-1} D_{Omega,ext} chi'_k (chi' = chi - Q chi as in
+ * dd_apply_w: frame links only), r_k = P_{dLambda0^a}(u_k chi_k + y_k),
  * z_k = (D_Omega^dag)^{-1} r_k = gamma_5 D_Omega^{-1} gamma_5 r_k and
- * dS = -2 Re sum_k <z_k, dD_Omega y_k>: two batched block solves (all blocks,
- * all fields, params as for dd_solve_blocks) and one thread per link (FP64).
+ * dS = -2 Re sum_k <z_k, dD_Omega y_k>: a batched frame-piece solve (for Q),
+ * two batched block solves (all blocks, all fields, params as for
+ * dd_solve_blocks) and one thread per link (FP64).
  * u: 2*n_f doubles (re, im); chi: layout of dd_apply_w, device or host.
  * F: device or host, V*4*8 doubles, [global site (x3 fastest)][mu][t]; zero
  * on every link that is not active.  Returns DD_ENOCONV (F filled) if a block
  * solve missed its tolerance.  Synchronises. */
 dd_status dd_mb_force(dd_ctx* ctx, int n_f, const double* u, const double* chi, double* F,
                       const dd_solve_params* params, void* stream);
+
+/* ---- force of ln|det D_Omega0^a| (paper Sec. 4, Eq. SFeffN) -------------------
+ * The other block-local term of the factorized effective action: for every
+ * active link (as for dd_mb_force) and generator T_t, the noise estimate
+ *   G[x][mu][t] = (1/n) sum_k Re <(D_Omega^dag)^{-1} eta_k, dD_Omega/d eps eta_k>
+ * of d ln|det D_Omega0^a| / d eps = Re Tr[D_Omega^{-1} dD_Omega/d eps]
+ * (unbiased for noise with E[eta eta^dag] = 1, e.g. complex Gaussians with
+ * Re, Im ~ N(0, 1/2)).  eta: n_noise noise vectors per framed block, the caller
+ * layout of dd_solve_blocks on all blocks ([block][k][Omega site][12]), device or
+ * host, drawn by the caller.  One batched solve z = gamma_5 D_Omega^{-1} gamma_5 eta
+ * (params as for dd_solve_blocks) and one thread per link (FP64).  G: device or
+ * host, V*4*8 doubles, zero off the active links.  The block-local force of the
+ * factorized effective action is dd_mb_force's F minus G.  Returns DD_ENOCONV
+ * (G filled) if a solve missed its tolerance.  Synchronises. */
+dd_status dd_logdet_force(dd_ctx* ctx, int n_noise, const double* eta, double* G,
+                          const dd_solve_params* params, void* stream);
 
 /* ---- reweighting factor (paper Sec. 4, Eq. rw) ------------------------------
  * W_N = det{1 - R_{N+1}(W_1)}, W_1 = 1 - w on dPi, with the polynomial of the
@@ -420,11 +457,23 @@ dd_status dd_timing_get(dd_ctx* ctx, int which, double* ms, long long* launches,
  * dd_solve_blocks call on them.  Every call shares the array: calls whose GPU
  * work overlaps (other streams or threads) race, so serialise them.  The first
  * call on each device resolves the array's address (cudaGetSymbolAddress);
- * make it before any stream capture.  Asynchronous on `stream`; calls no
- * allocating routine. */
+ * with lazy module loading that first call also loads the module on the device
+ * and commits the array, so it is the one call that takes device memory: make
+ * it during set-up.  The launch descriptors pass through one host staging
+ * buffer shared by all calls, threads and devices (a lock serialises it until
+ * the copy has read it); a call on a stream that is being captured returns
+ * DD_EINVAL, since a recorded copy would read that buffer only when the graph
+ * runs.  Asynchronous on `stream`; calls no allocating routine. */
 #define DD_NOALLOC_SCRATCH_BYTES (64u << 20)
 dd_status dd_apply_D_block_noalloc(dd_ctx* ctx, dd_domain kind, const int* ids, int nblk,
                                    int nrhs, const double* in, double* out, void* stream);
+
+/* Measured FP64 fused multiply-add rate of the current device in TFLOP/s
+ * (best of three timed launches of independent FMA chains on every SM, after
+ * one warm-up launch; clocks as they are).  The ALU roofline of the FP64
+ * kernels (the force contraction, the plain FP64 stencil).  No counterpart in
+ * the paper.  Synchronises the legacy default stream. */
+dd_status dd_fp64_fma_rate(double* tflops);
 
 /* Number of CUDA kernel launches the library has issued in this process
  * (all contexts), for launch accounting by callers.  Host-only, no sync. */

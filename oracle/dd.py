@@ -455,6 +455,49 @@ class Oracle:
                     G[x + (mu, t)] = np.trace(g_xpx @ dfwd + g_xxp @ dbwd).real
         return G
 
+    def logdet_force_stochastic(self, etas):
+        """Noise estimate of G = d ln|det D_{Omega0^a}| / d eps on the active links
+        (Sec. 4, Eq. SFeffN): ln|det D| = Re ln det D and d ln det D = Tr[D^{-1} dD];
+        with noise vectors eta_k on Omega0^a of E[eta eta^dag] = 1 (the complex
+        Gaussians of the input recipe), Tr[D^{-1} dD] = E[<(D^dag)^{-1} eta, dD eta>],
+        so G = (1/n) sum_k Re <z_k, dD eta_k>, z_k = (D_Omega^dag)^{-1} eta_k.
+        etas[a][k]: field on the full lattice supported on Omega0^a (noise k of
+        block a).  Returns G (zero off the active links) and the per-link sample
+        standard deviation of the n terms."""
+        if self.csw:
+            raise NotImplementedError("the force of the clover term is not part of this oracle")
+        g = self.g
+        L = g.L
+        gam, _ = gammas()
+        one = np.eye(4)
+        T = gell_mann() / 2
+        G = np.zeros(tuple(L) + (4, 8))
+        SD = np.zeros(tuple(L) + (4, 8))
+        for a in range(g.nblocks):
+            links = self.active_links(a)
+            if not links:
+                continue
+            om = self.omega_solver(a)
+            pairs = [(eta, om.solve_adjoint_field(eta)) for eta in etas[a]]
+            n = len(pairs)
+            for x, mu in links:
+                xp = list(x)
+                xp[mu] = (xp[mu] + 1) % L[mu]
+                xp = tuple(xp)
+                bc = self.time_bc if (mu == 0 and x[0] == L[0] - 1) else 1.0
+                Uxm = self.U[x + (mu,)]
+                for t in range(8):
+                    dfwd = -self.kappa * bc * np.kron(one - gam[mu], 1j * T[t] @ Uxm)
+                    dbwd = -self.kappa * bc * np.kron(one + gam[mu], -1j * Uxm.conj().T @ T[t])
+                    terms = []
+                    for eta, z in pairs:
+                        v = np.vdot(z[x].ravel(), dfwd @ eta[xp].ravel())
+                        v += np.vdot(z[xp].ravel(), dbwd @ eta[x].ravel())
+                        terms.append(v.real)
+                    G[x + (mu, t)] = np.mean(terms)
+                    SD[x + (mu, t)] = np.std(terms, ddof=1) if n > 1 else 0.0
+        return G, SD
+
     def effective_force(self, u, chis):
         """Force of the block-local part of the factorized effective action (Sec. 4,
         Eq. SFeffN) on the active links: d/d eps of sum_a [-ln|det D_{Omega0^a}| + sum_k

@@ -229,6 +229,53 @@ dd_status dd_apply_D_block(dd_ctx* c, dd_domain kind, const int* ids, int nblk, 
   return (sg.in_host || sg.out_host) ? check_device_error(c, s) : DD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// FP64 FMA throughput probe: 8 independent dependency chains per thread, the
+// result kept live through one conditional store
+constexpr int FP64_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_fp64_fma(int iters, double a, double b, double* sink) {
+  double v[FP64_CHAINS];
+#pragma unroll
+  for (int k = 0; k < FP64_CHAINS; ++k) v[k] = (double)(threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < FP64_CHAINS; ++k) v[k] = fma(v[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < FP64_CHAINS; ++k) s += v[k];
+  if (s == 1.2345e-300) sink[0] = s;
+}
+}  // namespace
+
+extern "C" {
+
+dd_status dd_fp64_fma_rate(double* tflops) {
+  if (!tflops) return DD_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    return DD_ECUDA;
+  const int blocks = nsm * 8, threads = 256, iters = 1 << 14;
+  dd::EventPair ev;
+  double best = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {      // the first launch warms up
+    cudaEventRecord(ev.a, 0);
+    DD_COUNT_LAUNCH(), k_fp64_fma<<<blocks, threads>>>(iters, 0.999999, 1e-7, nullptr);
+    cudaEventRecord(ev.b, 0);
+    if (cudaEventSynchronize(ev.b) != cudaSuccess) return DD_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev.a, ev.b);
+    const double flops = 2.0 * FP64_CHAINS * (double)iters * blocks * threads;
+    if (rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  if (cudaGetLastError() != cudaSuccess) return DD_ECUDA;
+  *tflops = best;
+  return DD_OK;
+}
+
 dd_status dd_solve_blocks(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs,
                           const double* bvec, double* x, const dd_solve_params* prm,
                           dd_solve_stats* stats, void* stream) {

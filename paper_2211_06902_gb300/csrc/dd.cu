@@ -423,6 +423,19 @@ __global__ void __launch_bounds__(128) k_mb_force(const int4* __restrict__ al, c
   o[7] = h * (N[0].y + N[4].y - 2.0 * N[8].y) / sqrt(3.0);
 }
 
+// v -> gamma_5 v on caller-layout spinors (components 6..11 of a site change sign)
+__global__ void k_gamma5(long long n, const double2* __restrict__ in, double2* __restrict__ out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double2 v = in[k];
+  out[k] = (k % 12) >= 6 ? make_double2(-v.x, -v.y) : v;
+}
+
+__global__ void k_scale(long long n, double a, double* __restrict__ v) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) v[k] *= a;
+}
+
 struct WPlan {           // host-built gather lists, one per context
   int n_l1 = 0;
   int* d_l1_glob = nullptr;          // [n_l1] global site of Lambda1 field index
@@ -1191,6 +1204,69 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
   if (hF) DD_CUDA(c, cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
   if (noconv) return fail(c, DD_ENOCONV, "a block or frame-piece solve missed its tolerance");
+  return DD_OK;
+}
+
+dd_status dd_logdet_force(dd_ctx* c, int n_noise, const double* eta, double* G, const dd_solve_params* prm,
+                          void* stream) {
+  if (!c || !eta || !G || !prm || n_noise < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (n_noise > 65535) return fail(c, DD_EINVAL, "n_noise must be <= 65535");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  if (c->csw != 0.0) return fail(c, DD_EINVAL, "the force does not include the clover term");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)c->blocks.size();
+  const size_t fbytes = sizeof(double) * 32ULL * c->V;
+  std::vector<int> insts(nb);
+  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
+  Batch* ob;
+  dd_status e;
+  if ((e = get_batch_insts(c, insts, n_noise, &ob)) != DD_OK) return e;
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  if ((e = build_force_plan(c, P)) != DD_OK) return e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  const size_t vbytes = 16ULL * ob->user_tot;
+  const double* din = eta;
+  if (!is_device_ptr(eta)) {
+    void* p;
+    if ((e = workspace(c, 250, vbytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, eta, vbytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  double* dG = G;
+  const bool hG = !is_device_ptr(G);
+  if (hG) {
+    void* p;
+    if ((e = workspace(c, 251, fbytes, &p)) != DD_OK) return e;
+    dG = (double*)p;
+  }
+  void *vrhs, *vz;
+  if ((e = workspace(c, 252, vbytes, &vrhs)) || (e = workspace(c, 253, vbytes, &vz))) return e;
+  // z = (D_Omega^dag)^{-1} eta = gamma_5 D_Omega^{-1} gamma_5 eta (the outer gamma_5 is
+  // applied by the link kernel when it reads z)
+  const long long ntot = ob->user_tot;
+  DD_COUNT_LAUNCH(), k_gamma5<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(ntot, (const double2*)din,
+                                                                           (double2*)vrhs);
+  DD_CUDA(c, cudaGetLastError());
+  dd_solve_stats st1{};
+  dd_status r = solve_batch(c, *ob, (const double*)vrhs, (double*)vz, prm, &st1, s, true);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  DD_CUDA(c, cudaMemsetAsync(dG, 0, fbytes, s));
+  if (P.n_al > 0) {
+    // the link kernel returns -2 Re sum_k <z_k, dD eta_k>; G is its mean over the
+    // noise vectors without the factor -2
+    DD_COUNT_LAUNCH(), k_mb_force<<<(unsigned)((P.n_al + 127) / 128), 128, 0, s>>>(
+        P.d_al, P.d_al_loc, P.n_al, n_noise, ob->d_uoff, (const double2*)c->d_U, (const double2*)din,
+        (const double2*)vz, c->kappa, dG);
+    const long long nf = 32LL * c->V;
+    DD_COUNT_LAUNCH(), k_scale<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, -0.5 / n_noise, dG);
+    DD_CUDA(c, cudaGetLastError());
+  }
+  if (hG) DD_CUDA(c, cudaMemcpyAsync(G, dG, fbytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  if (r == DD_ENOCONV) return fail(c, DD_ENOCONV, "a block solve missed its tolerance");
   return DD_OK;
 }
 

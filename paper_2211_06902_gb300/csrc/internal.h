@@ -189,6 +189,7 @@ struct dd_ctx {
   int undecomposed = 0;                    // bit m: direction m not decomposed (boxes wrap in m)
   cudaStream_t copy_in = nullptr, copy_out = nullptr;   // host<->device copies of pipelined solves
   int forced_variant[3] = {-1, -1, -1};    // manual stencil launch variant per precision
+  bool debug_wait_fault = false;           // test hook: see dd_debug_wait_fault
 };
 
 // ---- helpers shared by the translation units --------------------------------
@@ -242,6 +243,8 @@ struct HopArgs {
   int* err;                 // device error word (bounded waits that gave up)
   const double2* clov_inv;  // FP64 only: A^{-1} [V][72] of the clover term applied to the
                             // hop sum at the output site (left-preconditioned solves)
+  int lb_fault;             // test hook of the bundle form (dd_debug_wait_fault): CTA 0 leaves
+                            // one quarter's bulk copy unissued and waits a few microseconds
 };
 dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s);
 int hop_variant_count(dd_prec prec);

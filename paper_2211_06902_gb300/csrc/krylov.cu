@@ -858,7 +858,11 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     }
     if (h_count == 0 || cyc >= max_outer) break;
     ++cycles;
-    const bool true_residual = (ip != DD_F32) || cyc == 0 || maxrel > theta;
+    // the cycle whose inner target is the floor for every system (inner_tol
+    // times the largest residual already below tol/4) is expected to end the
+    // solve: its residual is computed as b - D x straight away
+    const bool last_cycle = prm->inner_tol * maxrel <= 0.25 * prm->tol;
+    const bool true_residual = (ip != DD_F32) || cyc == 0 || maxrel > theta || last_cycle;
     // residual at the inner precision
     const void *rin_e = re, *rin_o = ro;
     if (ip != DD_F64) {

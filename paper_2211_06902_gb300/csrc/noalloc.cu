@@ -19,9 +19,19 @@
 // word it later reads.  Calls whose GPU work overlaps (different streams, or
 // different host threads) race on the array: serialise them.  The first call
 // on a device resolves the array's device address with cudaGetSymbolAddress
-// (once per device, with that device current); make that first call before
-// any stream capture.
+// (once per device, with that device current); with lazy module loading that
+// first call also loads this module on the device and commits the array, so it
+// is the one call that takes device memory.
+//
+// The launch descriptors are written into a host staging buffer shared by all
+// calls and devices and copied with cudaMemcpyAsync; a lock serialises the
+// staging between host threads until the copy has taken the bytes (a copy from
+// pageable memory returns once its source has been read).  A memcpy recorded
+// into a CUDA graph would instead read the buffer when the graph is launched,
+// after later calls may have rewritten it, so a call on a stream that is being
+// captured returns DD_EINVAL.
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "spinor.cuh"
@@ -37,8 +47,10 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // device address of g_scratch per device (host code must not use the symbol itself)
 static void* g_scratch_addr[kMaxDevices];
-// host staging of the descriptors (copied into the scratch on the call's stream)
+// host staging of the descriptors (copied into the scratch on the call's stream),
+// guarded by g_desc_lock from the first write until the copy has read it
 static unsigned char g_desc_host[kDescBytes];
+static std::mutex g_desc_lock;
 
 struct NaView {
   const dd::DomInst* inst;     // [nb]
@@ -198,6 +210,12 @@ extern "C" dd_status dd_apply_D_block_noalloc(dd_ctx* c, dd_domain kind, const i
              "point has %zu (%zu)", need, desc, kScratchBytes, kDescBytes);
     return fail(c, DD_EINVAL, buf);
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  DD_CUDA(c, cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(c, DD_EINVAL, "dd_apply_D_block_noalloc stages its launch descriptors through a "
+                              "host buffer and does not run on a stream that is being captured");
   // one-time per device: device address of the scratch array
   int dev = 0;
   DD_CUDA(c, cudaGetDevice(&dev));
@@ -209,6 +227,7 @@ extern "C" dd_status dd_apply_D_block_noalloc(dd_ctx* c, dd_domain kind, const i
     g_scratch_addr[dev] = p;
   }
   unsigned char* base = (unsigned char*)g_scratch_addr[dev];
+  std::unique_lock<std::mutex> staging(g_desc_lock);
   unsigned char* h = g_desc_host;
   DomInst* hi = (DomInst*)(h + o_inst);
   long long* hoff0 = (long long*)(h + o_off0);
@@ -237,8 +256,8 @@ extern "C" dd_status dd_apply_D_block_noalloc(dd_ctx* c, dd_domain kind, const i
     for (int s = 0; s < d.n[1]; s += kThreads)
       hit1[k1++] = make_int4(j, s, d.n[1] - s < kThreads ? d.n[1] - s : kThreads, 0);
   }
-  cudaStream_t s = (cudaStream_t)stream;
   DD_CUDA(c, cudaMemcpyAsync(base, h, desc, cudaMemcpyHostToDevice, s));
+  staging.unlock();
   NaView v;
   v.inst = (const DomInst*)(base + o_inst);
   v.off[0] = (const long long*)(base + o_off0);

@@ -637,8 +637,28 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// bounded wait for phase 0 of a once-used barrier
-__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
+// the same test with a suspend-time hint (ns): each unsuccessful poll returns
+// after at most about that long
+__device__ __forceinline__ bool mbar_try_wait_hint(unsigned long long* bar, unsigned parity, unsigned ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// test-hook limit: 64 polls of at most ~1 us
+constexpr unsigned LB_FAULT_POLLS = 64;
+constexpr unsigned LB_FAULT_POLL_NS = 1000;
+// bounded wait for phase 0 of a once-used barrier (short: the test hook's CTA)
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, bool short_wait = false) {
+  if (short_wait) {
+    for (unsigned k = 0; k < LB_FAULT_POLLS; ++k)
+      if (mbar_try_wait_hint(bar, 0, LB_FAULT_POLL_NS)) return true;
+    return false;
+  }
   for (unsigned k = 0; k < LB_WAIT_LIMIT; ++k)
     if (mbar_try_wait(bar, 0)) return true;
   return false;
@@ -704,18 +724,27 @@ constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64;
 // grid: nitems[p] * ngroups CTAs (group fastest), 32 * ceil(rb / RR) threads;
 // thread (warp w, lane) computes rhs g * rb + w * RR + k, k < RR, of one site,
 // reading each link from shared memory once for its RR rhs
-template <class S, int MINB, int RR>
-__global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
+// QPC: quarters of the item per CTA (4: the whole item; 2: half of it, so two
+// CTAs share an item and add their inner-product partials atomically onto
+// zeroed slots); MAXR: most rhs per CTA.
+template <class S, int MINB, int RR, int QPC, int MAXR>
+__global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<S>::T T;
   constexpr int QB = lb_quarter_bytes<S>();
+  constexpr int NH = LB_QUARTERS / QPC;
   extern __shared__ __align__(128) unsigned char lb_smem[];
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + LB_QUARTERS * QB);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + QPC * QB);
   const int p = a.p_out;
-  const int item = (int)(blockIdx.x / ngroups);
-  const int g = (int)(blockIdx.x - (long long)item * ngroups);
+  const int item = (int)(blockIdx.x / (ngroups * NH));
+  const int rem = (int)(blockIdx.x - (long long)item * ngroups * NH);
+  const int hh = NH == 1 ? 0 : rem / ngroups;
+  const int g = rem - hh * ngroups;
   const int4 it = (p ? bd.items[1] : bd.items[0])[item];
+  const int q0 = hh * QPC;
+  const int nq = min(QPC, (it.z + LB_LANES - 1) / LB_LANES - q0);   // quarters of this CTA
+  if (nq <= 0) return;                         // the item is shorter than this part (uniform)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   bool actk[RR];
   int sysk[RR];
@@ -737,27 +766,37 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
   if (cta_rhs == 0) return;                    // every rhs of the group has converged
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
   const int n0 = dp->n[0];
-  const int nq = (it.z + LB_LANES - 1) / LB_LANES;
+  // test hook: CTA 0 arms the barrier of its last quarter without issuing the
+  // copy, so that wait gives up (nothing is in flight for it) after a short limit
+  const bool fault = a.lb_fault && blockIdx.x == 0;
+  const int fq = fault ? nq - 1 : -1;
   if (threadIdx.x == 0) {
     for (int q = 0; q < nq; ++q) mbar_init(&bar[q], 1);
     mbar_fence_init();
     // one atomic per CTA for the algorithmic-byte accounting (timing only)
-    if (a.work_bytes) atomicAdd(a.work_bytes, a.site_bytes * it.z * cta_rhs);
+    if (a.work_bytes)
+      atomicAdd(a.work_bytes, a.site_bytes * min(it.z - q0 * LB_LANES, nq * LB_LANES) * cta_rhs);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned char* src =
-        bundle_of<S>(*dp) + (lb_quarter_base(p, n0) + (long long)LB_QUARTERS * (it.y / LB_CHUNK)) * QB;
+    const unsigned char* src = bundle_of<S>(*dp) +
+        (lb_quarter_base(p, n0) + (long long)LB_QUARTERS * (it.y / LB_CHUNK) + q0) * QB;
     for (int q = 0; q < nq; ++q) {
       mbar_expect_tx(&bar[q], QB);
-      bulk_copy_g2s(lb_smem + q * QB, src + (long long)q * QB, QB, &bar[q]);
+      if (q != fq) bulk_copy_g2s(lb_smem + q * QB, src + (long long)q * QB, QB, &bar[q]);
     }
   }
+  // Thread 0 waits on every quarter on each path.  If a wait on an issued copy
+  // gives up, thread 0 at once waits for that copy once more (bounded), so the
+  // CTA's shared memory outlives every copy it started.
   if (!act) {
     // idle warp of a busy CTA: thread 0 still sees its copies land before leaving
     if (threadIdx.x == 0)
       for (int q = 0; q < nq; ++q)
-        if (!mbar_wait0(&bar[q])) atomicExch(a.err, 1);
+        if (!mbar_wait0(&bar[q], fault)) {
+          atomicExch(a.err, 1);
+          if (q != fq) mbar_wait0(&bar[q]);
+        }
     return;
   }
   const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
@@ -779,11 +818,12 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
     tqs[k][0] = tqs[k][1] = 0;
   }
   for (int q = 0; q < nq; ++q) {
-    if (!mbar_wait0(&bar[q])) {
+    if (!mbar_wait0(&bar[q], fault)) {
       if (lane == 0) atomicExch(a.err, 1);
+      if (threadIdx.x == 0 && q != fq) mbar_wait0(&bar[q]);
       continue;
     }
-    const int li = q * LB_LANES + lane;
+    const int li = (q0 + q) * LB_LANES + lane;
     if (li >= it.z) continue;
     const int i = it.y + li;
     const unsigned char* qb = lb_smem + q * QB;
@@ -896,14 +936,20 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
     // actk[k] is uniform over the warp, so the shuffles below see full warps
     if (!actk[k]) continue;
     const long long my = (long long)item * bd.nrhs + (sysk[k] - (long long)it.x * bd.nrhs);
+    // one CTA per item stores its partials; with parts (NH > 1) each part adds
+    // its own onto the zeroed slot (two addends onto zero: order-independent)
+    auto put = [&](double* dst, double v) {
+      if (NH == 1) *dst = v;
+      else atomicAdd(dst, v);
+    };
     if (a.dotq) {
 #pragma unroll
       for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tq[k][e] += __shfl_down_sync(0xffffffffu, tq[k][e], o);
       if (lane == 0) {
-        a.partial[2 * my] = (double)tq[k][0];
-        a.partial[2 * my + 1] = (double)tq[k][1];
+        put(&a.partial[2 * my], (double)tq[k][0]);
+        put(&a.partial[2 * my + 1], (double)tq[k][1]);
       }
     }
     if (a.dots) {
@@ -913,10 +959,10 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
         for (int o = 16; o > 0; o >>= 1) ts[k][e] += __shfl_down_sync(0xffffffffu, ts[k][e], o);
       if (lane == 0) {
         double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
-        P[2 * my] = (double)ts[k][0];
-        P[2 * my + 1] = (double)ts[k][1];
-        P[2 * (slot_stride + my)] = (double)ts[k][2];
-        P[2 * (slot_stride + my) + 1] = 0.0;
+        put(&P[2 * my], (double)ts[k][0]);
+        put(&P[2 * my + 1], (double)ts[k][1]);
+        put(&P[2 * (slot_stride + my)], (double)ts[k][2]);
+        if (NH == 1) P[2 * (slot_stride + my) + 1] = 0.0;
       }
     }
     if (a.dotqs) {
@@ -925,20 +971,32 @@ __global__ void __launch_bounds__(32 * LB_MAX_RHS / RR, MINB)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tqs[k][e] += __shfl_down_sync(0xffffffffu, tqs[k][e], o);
       if (lane == 0) {
-        a.partial[2 * (3 * slot_stride + my)] = (double)tqs[k][0];
-        a.partial[2 * (3 * slot_stride + my) + 1] = (double)tqs[k][1];
+        put(&a.partial[2 * (3 * slot_stride + my)], (double)tqs[k][0]);
+        put(&a.partial[2 * (3 * slot_stride + my) + 1], (double)tqs[k][1]);
       }
     }
   }
 }
 
-template <class S, int MINB, int RR>
+template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
-  const int ngroups = (bd.nrhs + LB_MAX_RHS - 1) / LB_MAX_RHS;
+  const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
   const int rb = (bd.nrhs + ngroups - 1) / ngroups;
   const int nthreads = 32 * ((rb + RR - 1) / RR);
-  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR><<<(unsigned)(nitems_p * ngroups), nthreads, lb_smem_bytes<S>(), s>>>(
-      bd, a, ngroups, rb);
+  constexpr int NH = LB_QUARTERS / QPC;
+  if (NH > 1 && a.partial) {
+    // the slots this launch writes start at zero (its parts add onto them)
+    const long long stride = nitems_p * bd.nrhs;
+    auto zero = [&](int slot) { cudaMemsetAsync(a.partial + 2 * slot * stride, 0, 16 * stride, s); };
+    if (a.dotq) zero(0);
+    if (a.dots) {
+      zero(a.dotq ? 1 : 0);
+      zero(a.dotq ? 2 : 1);
+    }
+    if (a.dotqs) zero(3);
+  }
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR>
+      <<<(unsigned)(nitems_p * ngroups * NH), nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb);
 }
 
 void hop_bundle_prepare() {
@@ -947,15 +1005,21 @@ void hop_bundle_prepare() {
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || done[dev]) return;
   const int b32 = lb_smem_bytes<float2>(), b16 = lb_smem_bytes<__nv_bfloat162>();
+  const int h32 = 2 * lb_quarter_bytes<float2>() + 64, h16 = 2 * lb_quarter_bytes<__nv_bfloat162>() + 64;
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 1, 1>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 2>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 3>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1>, at, b16);
-  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 1, 1>, at, b16);
-  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 3, 2>, at, b16);
-  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 4, 3>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 1, 1, 4, 12>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 2, 4, 12>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 3, 4, 12>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 2, 12>, at, h32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 5, 1, 2, 6>, at, h32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 4, 1, 2, 6>, at, h32);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 4, 12>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 1, 1, 4, 12>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 3, 2, 4, 12>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 4, 3, 4, 12>, at, b16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 2, 12>, at, h16);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 5, 1, 2, 6>, at, h16);
   done[dev] = true;
 }
 
@@ -964,6 +1028,8 @@ struct HopVariant {
   bool persist;
   int r;          // rhs per thread (0: direction-split, 256 threads per item; -k: bundle form
                   // with k rhs per thread)
+  int qpc = 4;    // bundle form: link quarters of the 128-site item per CTA
+  int maxr = 12;  // bundle form: most rhs per CTA
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -972,12 +1038,14 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {4, true, 1}, {4, false, 2}, {5, false, 2}, {4, true, 2},
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
-                                         {2, false, -3}};
+                                         {2, false, -3}, {2, false, -1, 2, 12}, {5, false, -1, 2, 6},
+                                         {4, false, -1, 2, 6}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
-                                         {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3}};
+                                         {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
+                                         {2, false, -1, 2, 12}, {5, false, -1, 2, 6}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 17 : 12); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 20 : 14); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1017,12 +1085,17 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
   if (hv.r < 0) {
     const int rr = -hv.r;
     if (prec == DD_F32) {
-      if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
+      if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
+      else if (hv.qpc == 2 && hv.maxr == 6) launch_lb<float2, 4, 1, 2, 6>(bd, a, ni, s);
+      else if (hv.qpc == 2) launch_lb<float2, 2, 1, 2, 12>(bd, a, ni, s);
+      else if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
       else if (rr == 2) launch_lb<float2, 2, 2>(bd, a, ni, s);
       else if (hv.minb == 1) launch_lb<float2, 1, 1>(bd, a, ni, s);
       else launch_lb<float2, 2, 1>(bd, a, ni, s);
     } else {
-      if (rr == 3) launch_lb<__nv_bfloat162, 4, 3>(bd, a, ni, s);
+      if (hv.qpc == 2 && hv.maxr == 6) launch_lb<__nv_bfloat162, 5, 1, 2, 6>(bd, a, ni, s);
+      else if (hv.qpc == 2) launch_lb<__nv_bfloat162, 2, 1, 2, 12>(bd, a, ni, s);
+      else if (rr == 3) launch_lb<__nv_bfloat162, 4, 3>(bd, a, ni, s);
       else if (rr == 2) launch_lb<__nv_bfloat162, 3, 2>(bd, a, ni, s);
       else if (hv.minb == 1) launch_lb<__nv_bfloat162, 1, 1>(bd, a, ni, s);
       else launch_lb<__nv_bfloat162, 2, 1>(bd, a, ni, s);
@@ -1079,6 +1152,7 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
   HopArgs a = a0;
   a.err = c->d_err;
   a.clov_inv = (c->clover_active && prec == DD_F64) ? c->d_clovi : nullptr;
+  a.lb_fault = c->debug_wait_fault ? 1 : 0;
   int p = a.p_out;
   if (b.nitems[p] == 0) return DD_OK;
   const long long nblk = (long long)b.nitems[p] * b.nrhs;
@@ -1268,10 +1342,14 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.r < 0)
+        if (h.r < 0 && h.qpc == 4 && h.maxr == 12)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);
+        else if (h.r < 0)
+          snprintf(names[k][u], sizeof names[k][u],
+                   "k_hop_lb<%s,%d,%d,%d,%d>: bulk-copied links, %d sites and up to %d rhs per CTA",
+                   ty[k], h.minb, -h.r, h.qpc, h.maxr, 32 * h.qpc, h.maxr);
         else if (h.r == 0)
           snprintf(names[k][u], sizeof names[k][u], "k_hop_split<%s,%d,%s>: forward/backward split",
                    ty[k], h.minb, h.persist ? "persistent" : "grid");
@@ -1288,6 +1366,12 @@ dd_status dd_set_hop_variant(dd_ctx* c, dd_prec prec, int v) {
   if (!c || (prec != DD_F64 && prec != DD_F32 && prec != DD_BF16)) return DD_EINVAL;
   if (v < -1 || v >= dd::hop_variant_count(prec)) return dd::fail(c, DD_EINVAL, "variant out of range");
   c->forced_variant[prec == DD_F64 ? 0 : (prec == DD_F32 ? 1 : 2)] = v;
+  return DD_OK;
+}
+
+dd_status dd_debug_wait_fault(dd_ctx* c, int on) {
+  if (!c) return DD_EINVAL;
+  c->debug_wait_fault = on != 0;
   return DD_OK;
 }
 

@@ -114,6 +114,9 @@ def lib():
                                     C.POINTER(SolveParams), vp],
             "dd_mb_force": [vp, C.c_int, dp, vp, vp, C.POINTER(SolveParams), vp],
             "dd_set_clover": [vp, C.c_double],
+            "dd_debug_wait_fault": [vp, C.c_int],
+            "dd_logdet_force": [vp, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
+            "dd_fp64_fma_rate": [dp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -133,7 +136,8 @@ def exported_symbols():
             "dd_last_solve_stats", "dd_net_create", "dd_net_destroy", "dd_net_weights",
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
-            "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover"]
+            "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover",
+            "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate"]
 
 
 def hop_variant_name(prec, v):
@@ -154,8 +158,10 @@ def _ptr(x):
 
 
 def _stream(stream):
+    """A CUDA stream handle: an int, a torch stream (its handle), or None for
+    torch's current stream (the legacy default stream without torch)."""
     if stream is not None:
-        return C.c_void_p(stream)
+        return C.c_void_p(getattr(stream, "cuda_stream", stream))
     try:
         import torch
         if torch.cuda.is_available() and torch.cuda.is_initialized():
@@ -182,6 +188,15 @@ def roots(N, c):
     if st:
         raise DDError(st, lib().dd_strerror(st).decode())
     return out[0::2] + 1j * out[1::2]
+
+
+def fp64_fma_rate():
+    """Measured FP64 FMA rate of the current device (TFLOP/s)."""
+    t = C.c_double(0)
+    st = lib().dd_fp64_fma_rate(C.byref(t))
+    if st:
+        raise DDError(st, "dd_fp64_fma_rate failed")
+    return t.value
 
 
 def launch_count():
@@ -350,6 +365,16 @@ class Context:
             C.byref(prm or params()), _stream(stream)))
         return out, st
 
+    def logdet_force(self, n_noise, eta, G=None, prm=None, stream=None):
+        """Noise estimate of d ln|det D_Omega0^a| / d eps on the active links:
+        G[x0,x1,x2,x3,mu,t], zero off the active links.  eta: n_noise noise vectors
+        per framed block in the layout of solve_blocks on all blocks.  G: optional
+        device tensor of V*4*8 doubles.  Returns (G, status)."""
+        out = G if G is not None else np.zeros(self.L + (4, 8))
+        st = self._check(lib().dd_logdet_force(self._h, n_noise, _ptr(eta), _ptr(out),
+                                               C.byref(prm or params()), _stream(stream)))
+        return out, st
+
     def reweight_samples(self, N, c, eta, r_eta=None, prm=None, stream=None):
         """Samples s = |eta|^2 - |M eta|^2, M = 1 - R_{N+1}(W_1), one per source of eta
         (layout of apply_w); mean(exp(s)) estimates |W_N|^-2 (Eq. rw).  Returns
@@ -395,6 +420,10 @@ class Context:
     def set_hop_variant(self, prec, v):
         p = PREC[prec] if isinstance(prec, str) else prec
         self._check(lib().dd_set_hop_variant(self._h, p, v))
+
+    def debug_wait_fault(self, on):
+        """Test hook: the bundle-form stencil's bounded wait gives up (DD_ETIMEOUT)."""
+        self._check(lib().dd_debug_wait_fault(self._h, 1 if on else 0))
 
     def last_solve_stats(self):
         st = SolveStats()

@@ -50,3 +50,36 @@ def test_invalid_geometry_and_sizes():
     info = ctx.set_geometry(uniform_cores(L, 3, 1))
     with pytest.raises(dd4d.DDError):
         ctx.solve_blocks("omega", [0], 70000, np.zeros(24), np.zeros(24), dd4d.params())
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """The bundle stencil's bounded mbarrier wait, made to give up through the test
+    hook dd_debug_wait_fault (one CTA arms a barrier without issuing its copy, so
+    nothing is in flight, and waits about 64 us), comes back as DD_ETIMEOUT; with
+    the hook off, the same context computes the stencil (checked against the
+    oracle) and solves to 1e-10."""
+    from oracle.lattice import apply_D_restricted
+    from gpu_common import from_field, relerr, to_field
+    L = (8,) * 4
+    U, ctx, info, geo = make_case(L, 0.13, 0.3, 1, uniform_cores(L, 3, 1))
+    v = next(k for k in range(64) if (dd4d.hop_variant_name("f32", k) or "").startswith("k_hop_lb"))
+    ctx.set_hop_variant("f32", v)
+    ids = list(range(info["nblocks"]))
+    sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
+    psi = synth.complex_gaussian(3, synth.TAG_RHS, (len(ids), 2, len(sites[0]), 12))
+    out = np.zeros_like(psi)
+    ctx.debug_wait_fault(True)
+    with pytest.raises(dd4d.DDError) as e:
+        ctx.apply_D_block("omega", ids, 2, psi, out, "f32")       # host buffers: synchronising
+    assert e.value.status == dd4d.DD_ETIMEOUT
+    ctx.debug_wait_fault(False)
+    out[:] = 0
+    ctx.apply_D_block("omega", ids, 2, psi, out, "f32")
+    for b in ids:
+        for r in range(2):
+            f = to_field(L, sites[b], psi[b, r])
+            want = from_field(L, sites[b], apply_D_restricted(U, f, 0.13, geo.omega_mask[b]))
+            assert relerr(out[b, r], want) < 2e-6
+    x = np.zeros_like(psi)
+    st = ctx.solve_blocks("omega", ids, 2, psi, x, dd4d.params(1e-10, inner_prec="f32"))
+    assert st["status"] == 0 and st["max_relres"] <= 1e-10

@@ -69,3 +69,30 @@ def test_device_output_matches_host_output():
     _, st = ctx.mb_force(u, torch.from_numpy(vec.view(np.float64)).cuda(), F=dF, prm=prm)
     assert st == 0
     assert np.array_equal(dF.cpu().numpy(), Fh)
+
+
+@pytest.mark.parametrize("name", ["1D 8x4x4x2", "8^4"])
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_logdet_force_matches_oracle(name, inner):
+    """Noise estimate of d ln|det D_Omega0^a| / d eps (Eq. SFeffN) with the same noise
+    vectors on both sides (passed in): every entry within 1e-8 (FP64) / 1e-7 (FP32 inner)
+    of the largest value, exactly zero off the active links; the oracle's estimator is
+    pinned against the dense trace (test_oracle_dd)."""
+    U, ctx, info, geo = CASES[name]()
+    n = 4
+    ids = list(range(info["nblocks"]))
+    sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
+    V = int(np.prod(geo.L))
+    fields = [[synth.complex_gaussian(13, 700 + 50 * b + k, geo.L + (4, 3)) * geo.omega_mask[b][..., None, None]
+               for k in range(n)] for b in ids]
+    eta = np.stack([np.stack([f.reshape(V, 12)[sites[b]] for f in fields[b]]) for b in ids])
+    tol = 1e-12 if inner == "f64" else 1e-11
+    G, st = ctx.logdet_force(n, eta, prm=dd4d.params(tol, inner_prec=inner))
+    assert st == 0
+    o = Oracle(U, 0.13, geo)
+    ref, _ = o.logdet_force_stochastic(fields)
+    act = _active(o, geo)
+    assert np.all(G[~act] == 0)
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert np.abs(G - ref).max() <= (1e-8 if inner == "f64" else 1e-7) * scale

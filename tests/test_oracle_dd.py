@@ -598,3 +598,31 @@ def test_effective_force_matches_finite_differences_of_the_effective_action():
         x, mu = o.active_links(a)[n]
         fd = _fd_links(U, seff, x, mu, t)
         assert abs(fd - F[x + (mu, t)]) < 1e-6 * max(1.0, abs(fd)), (a, x, mu, t, fd, F[x + (mu, t)])
+
+
+def test_logdet_force_noise_estimate_matches_the_exact_trace():
+    """The noise estimate of d ln|det D_Omega0^a| / d eps (complex Gaussian noise,
+    E[eta eta^dag] = 1) lies within 5 standard errors of the dense trace on every
+    active link and generator; a planted mistake (z = D_Omega^{-1} eta instead of
+    the adjoint solve) is far outside."""
+    L, cores = (8, 4, 4, 2), [[(0, 1), (4, 5)], [], [], []]
+    U = synth.gauge_field(L, 0.4, 3)
+    g = Decomposition(L, cores)
+    o = Oracle(U, 0.13, g)
+    exact = o.logdet_force()
+    n = 96
+    etas = [[synth.complex_gaussian(11, 500 + 100 * a + k, L + (4, 3)) * g.omega_mask[a][..., None, None]
+             for k in range(n)] for a in range(g.nblocks)]
+    G, SD = o.logdet_force_stochastic(etas)
+    act = SD > 0
+    assert act.sum() > 100
+    z = (G[act] - exact[act]) / (SD[act] / math.sqrt(n))
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    assert np.all(G[~act] == 0)
+    # planted mistake: the forward solve in place of the adjoint one
+    bad = Oracle(U, 0.13, g)
+    bad.omega_solver(0).solve_adjoint_field = bad.omega_solver(0).solve_field
+    bad.omega_solver(1).solve_adjoint_field = bad.omega_solver(1).solve_field
+    Gb, _ = bad.logdet_force_stochastic(etas)
+    zb = (Gb[act] - exact[act]) / (SD[act] / math.sqrt(n))
+    assert np.abs(zb).max() > 6.0
