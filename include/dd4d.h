@@ -261,6 +261,30 @@ dd_status dd_last_solve_stats(const dd_ctx* ctx, dd_solve_stats* stats);
 dd_status dd_apply_w(dd_ctx* ctx, int n_f, const double* chi, double* w_chi,
                      const dd_solve_params* params, void* stream);
 
+/* ---- w in stages, for a subset of blocks (paper Sec. 5: blocks on separate
+ * nodes or GPUs) ------------------------------------------------------------
+ * The three stages of dd_apply_w as separate calls, so that ranks owning
+ * disjoint subsets of the blocks can each compute their part and combine the
+ * results with sums across ranks:
+ *   DD_W_FRAME_Q  in = chi; writes on every dPi1 entry of out the share of Q chi
+ *                 of the listed blocks, sum over b in ids of P_{dPi1} D_{Phi1^b}^{-1}
+ *                 D_{Phi1^b, dLambda0^b} chi (zero where none of their frame pieces
+ *                 reaches); the sum over the ranks of these arrays is Q chi.
+ *   DD_W_BLOCKS   in = chi' = chi - Q chi; writes (w chi)_{dLambda0^a} =
+ *                 -P_{dLambda0^a} D_{Omega0^a}^{-1} D_{Omega0^a, ext} chi' on the
+ *                 dLambda0^a entries of the listed blocks.
+ *   DD_W_FRAME    in = chi (ids ignored); writes -P_{dPi1} D_{Lambda1}^{-1}
+ *                 D_{Lambda1, dLambda0} chi on the dPi1 entries; adding Q chi gives
+ *                 (w chi)_{dPi1}.
+ * in, out: n_f fields in the layout of dd_apply_w, device or host; entries of
+ * out that the stage does not write are left as they were.  ids: distinct
+ * block ids.  Solves to params->tol.  Synchronises. */
+#define DD_W_FRAME_Q 0
+#define DD_W_BLOCKS 1
+#define DD_W_FRAME 2
+dd_status dd_apply_w_part(dd_ctx* ctx, int part, int n_f, const int* ids, int nblk, const double* in,
+                          double* out, const dd_solve_params* params, void* stream);
+
 /* ---- multi-boson action (paper Sec. 4, Eqs. MBaction, localMB, globalMB)
  * S = sum_k |(u_k - w) chi_k|^2 = sum_a S^a + S^r with
  * S^a = sum_k |P_{dLambda0^a}(u_k - w)chi_k|^2, S^r = sum_k |P_{dPi1}(...)|^2.

@@ -140,13 +140,15 @@ __global__ void k_inject_frame(const int* __restrict__ l1_glob, int n_l1,
   for (int c = 0; c < 12; ++c) out[c] = make_double2(-a.kappa * acc[c].x, -a.kappa * acc[c].y);
 }
 
-// Sources of the frame pieces: t(x) = D_{Phi1^j, dLambda0^j} chi for x in
-// Phi1^j, the hops into x from the boundary sites of its own core j (the batch
-// holds Phi1^0 .. Phi1^{nb-1} at positions 0 .. nb-1).
+// Sources of the frame pieces: t(x) = D_{Phi1^b, dLambda0^b} chi for x in
+// Phi1^b, the hops into x from the boundary sites of its own core b (batch
+// position j holds Phi1^b, b = blk_of_pos[j], or b = j without the map).
 // grid: (ceil(max_sites/128), n_f, nb)
-__global__ void k_inject_phi(BatchDev bd, InjectArgs a, const int* __restrict__ dpi_kind) {
+__global__ void k_inject_phi(BatchDev bd, InjectArgs a, const int* __restrict__ dpi_kind,
+                             const int* __restrict__ blk_of_pos) {
   const int f = blockIdx.y, j = blockIdx.z;
   const int sys = j * a.n_f + f;
+  const int blk = blk_of_pos ? blk_of_pos[j] : j;
   const DomInst* d = bd.inst_tab + bd.inst[j];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d->nsites) return;
@@ -162,7 +164,7 @@ __global__ void k_inject_phi(BatchDev bd, InjectArgs a, const int* __restrict__ 
     gy[mu] = (g[mu] + step + a.L[mu]) % a.L[mu];
     const int y = glob_index(gy, a.L);
     const int q = a.dpi_pos[y];
-    if (q < 0 || dpi_kind[q] != j) continue;          // not a boundary site of core j
+    if (q < 0 || dpi_kind[q] != blk) continue;        // not a boundary site of this core
     add_exterior_hop(acc, dir, gx, y, a, f);
   }
   double2* out = a.src + bd.uoff[sys] + 12LL * d->fmap[k];
@@ -179,7 +181,8 @@ __global__ void k_frame_q(const int* __restrict__ q_beg, const int* __restrict__
                           const int* __restrict__ c_dpi, int nC, int n_f, int n_dpi, int frame_pos,
                           const long long* __restrict__ uoff, const double2* __restrict__ sol,
                           const double2* __restrict__ chi, double2* __restrict__ chi_p,
-                          double2* __restrict__ w) {
+                          double2* __restrict__ w, const int* __restrict__ pos_of_blk,
+                          double2* __restrict__ q_out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (k >= nC) return;
@@ -187,11 +190,18 @@ __global__ void k_frame_q(const int* __restrict__ q_beg, const int* __restrict__
 #pragma unroll
   for (int c = 0; c < 12; ++c) q[c] = make_double2(0.0, 0.0);
   for (int e = q_beg[k]; e < q_beg[k + 1]; ++e) {
-    const double2* s = sol + uoff[(long long)q_blk[e] * n_f + f] + q_loc[e];
+    const int pos = pos_of_blk ? pos_of_blk[q_blk[e]] : q_blk[e];
+    if (pos < 0) continue;                     // a frame piece outside this batch
+    const double2* s = sol + uoff[(long long)pos * n_f + f] + q_loc[e];
 #pragma unroll
     for (int c = 0; c < 12; ++c) q[c] = make_double2(q[c].x + s[c].x, q[c].y + s[c].y);
   }
   const long long o = ((long long)f * n_dpi + c_dpi[k]) * 12;
+  if (q_out) {                                 // Q chi of the batch's frame pieces only
+#pragma unroll
+    for (int c = 0; c < 12; ++c) q_out[o + c] = q[c];
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < 12; ++c) chi_p[o + c] = make_double2(chi[o + c].x - q[c].x, chi[o + c].y - q[c].y);
   if (w) {
@@ -208,11 +218,15 @@ __global__ void k_frame_q(const int* __restrict__ q_beg, const int* __restrict__
 __global__ void k_extract(const int* __restrict__ sys_blk, int blk_fixed, const long long* __restrict__ loc,
                           const int* __restrict__ dpi_idx, int n, int n_f, int n_dpi,
                           const long long* __restrict__ uoff, const double2* __restrict__ sol,
-                          double2* __restrict__ w) {
+                          double2* __restrict__ w, const int* __restrict__ pos_of_blk) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (k >= n) return;
-  const int blk = sys_blk ? sys_blk[k] : blk_fixed;
+  int blk = sys_blk ? sys_blk[k] : blk_fixed;
+  if (sys_blk && pos_of_blk) {
+    blk = pos_of_blk[blk];
+    if (blk < 0) return;                       // a block outside this batch
+  }
   const double2* s = sol + uoff[(long long)blk * n_f + f] + loc[k];
   double2* o = w + ((long long)f * n_dpi + dpi_idx[k]) * 12;
 #pragma unroll
@@ -614,7 +628,7 @@ static dd_status frame_stage(dd_ctx* c, WPlan& P, int n_f, const double* chi, do
   a.src = (double2*)src_a;
   BatchDev bd = batch_view(c, *ab);
   dim3 g1((P.max_phi + 127) / 128, n_f, nb);
-  DD_COUNT_LAUNCH(), k_inject_phi<<<g1, 128, 0, s>>>(bd, a, c->d_dpi_kind);
+  DD_COUNT_LAUNCH(), k_inject_phi<<<g1, 128, 0, s>>>(bd, a, c->d_dpi_kind, nullptr);
   if (with_frame) {
     long long phi_user = 0;
     for (int b = 0; b < nb; ++b) phi_user += 12LL * c->inst[c->phi0 + b].d.nsites * n_f;
@@ -633,7 +647,7 @@ static dd_status frame_stage(dd_ctx* c, WPlan& P, int n_f, const double* chi, do
     DD_COUNT_LAUNCH(), k_frame_q<<<g, 128, 0, s>>>(P.d_q_beg, P.d_q_blk, P.d_q_loc, P.d_c_loc, P.d_c_dpi, nC, n_f,
                                                    c->info.n_dpi, nb, ab->d_uoff, (const double2*)sol_a,
                                                    (const double2*)chi, (double2*)chi_p,
-                                                   with_frame ? (double2*)wchi : nullptr);
+                                                   with_frame ? (double2*)wchi : nullptr, nullptr, nullptr);
     DD_CUDA(c, cudaGetLastError());
   }
   return r;
@@ -745,10 +759,98 @@ static dd_status apply_w_dev(dd_ctx* c, int n_f, const double* chi, double* wchi
     dim3 g((nB + 127) / 128, n_f);
     DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(P.d_b_blk, 0, P.d_b_loc, P.d_b_dpi, nB, n_f,
                                                    c->info.n_dpi, ob->d_uoff, (const double2*)sol_o,
-                                                   (double2*)wchi);
+                                                   (double2*)wchi, nullptr);
   }
   DD_CUDA(c, cudaGetLastError());
   if (noconv) return fail(c, DD_ENOCONV, "a block, frame-piece or frame solve missed its tolerance");
+  return DD_OK;
+}
+
+// One stage of w for a subset of blocks (dd_apply_w_part): the pieces a rank
+// that owns some of the blocks computes.  Writes only the entries of its stage.
+static dd_status apply_w_part_dev(dd_ctx* c, int part, int n_f, const int* ids, int nblk, const double* in,
+                                  double* out, const dd_solve_params* prm, cudaStream_t s) {
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  const int nb = (int)c->blocks.size();
+  dd_status e;
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  std::vector<int> pos(nb, -1), blk;
+  if (part != DD_W_FRAME) {
+    if (!ids || nblk < 1 || nblk > nb) return fail(c, DD_EINVAL, "block list required");
+    for (int k = 0; k < nblk; ++k) {
+      if (ids[k] < 0 || ids[k] >= nb || pos[ids[k]] >= 0) return fail(c, DD_EINVAL, "bad or repeated block id");
+      pos[ids[k]] = k;
+      blk.push_back(ids[k]);
+    }
+  }
+  InjectArgs a;
+  a.U = c->d_U;
+  a.chi = (const double2*)in;
+  a.dpi_pos = c->d_dpi_pos;
+  for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
+  a.n_dpi = c->info.n_dpi;
+  a.n_f = n_f;
+  a.kappa = c->kappa;
+  std::vector<int> insts;
+  if (part == DD_W_FRAME_Q) {
+    if ((e = build_q_plan(c, P)) != DD_OK) return e;
+    for (int b : blk) insts.push_back(c->phi0 + b);
+  } else if (part == DD_W_BLOCKS) {
+    for (int b : blk) insts.push_back(c->omega0 + b);
+  } else if (part == DD_W_FRAME) {
+    insts.push_back(c->lambda1);
+  } else {
+    return fail(c, DD_EINVAL, "unknown stage of w");
+  }
+  Batch* bt;
+  if ((e = get_batch_insts(c, insts, n_f, &bt)) != DD_OK) return e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  void *src, *sol, *dmap;
+  if ((e = workspace(c, 36, 16ULL * bt->user_tot, &src)) || (e = workspace(c, 37, 16ULL * bt->user_tot, &sol)) ||
+      (e = workspace(c, 43, sizeof(int) * (2 * nb + 2), &dmap)))
+    return e;
+  int* d_pos = (int*)dmap;
+  int* d_blk = d_pos + nb + 1;
+  if (part != DD_W_FRAME) {
+    DD_CUDA(c, cudaMemcpyAsync(d_pos, pos.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    DD_CUDA(c, cudaMemcpyAsync(d_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice, s));
+  }
+  a.src = (double2*)src;
+  BatchDev bd = batch_view(c, *bt);
+  if (part == DD_W_FRAME_Q) {
+    dim3 g1((P.max_phi + 127) / 128, n_f, nblk);
+    DD_COUNT_LAUNCH(), k_inject_phi<<<g1, 128, 0, s>>>(bd, a, c->d_dpi_kind, d_blk);
+  } else if (part == DD_W_BLOCKS) {
+    dim3 g1((c->info.max_omega + 127) / 128, n_f, nblk);
+    DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
+  } else {
+    dim3 g2((P.n_l1 + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_inject_frame<<<g2, 128, 0, s>>>(P.d_l1_glob, P.n_l1, P.d_in_l1, a);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  dd_solve_stats st{};
+  dd_status r = solve_batch(c, *bt, (const double*)src, (double*)sol, prm, &st, s, true);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  const int nB = c->info.n_B, nC = c->info.n_C;
+  if (part == DD_W_FRAME_Q && nC) {
+    dim3 g((nC + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_frame_q<<<g, 128, 0, s>>>(P.d_q_beg, P.d_q_blk, P.d_q_loc, P.d_c_loc, P.d_c_dpi, nC, n_f,
+                                                   c->info.n_dpi, -1, bt->d_uoff, (const double2*)sol, nullptr,
+                                                   nullptr, nullptr, d_pos, (double2*)out);
+  } else if (part == DD_W_BLOCKS && nB) {
+    dim3 g((nB + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(P.d_b_blk, 0, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
+                                                   bt->d_uoff, (const double2*)sol, (double2*)out, d_pos);
+  } else if (part == DD_W_FRAME && nC) {
+    dim3 g((nC + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_extract<<<g, 128, 0, s>>>(nullptr, 0, P.d_c_loc, P.d_c_dpi, nC, n_f, c->info.n_dpi,
+                                                   bt->d_uoff, (const double2*)sol, (double2*)out, nullptr);
+  }
+  DD_CUDA(c, cudaGetLastError());
+  if (r == DD_ENOCONV) return fail(c, DD_ENOCONV, "a solve of this stage missed its tolerance");
   return DD_OK;
 }
 
@@ -1014,6 +1116,36 @@ dd_status dd_apply_w(dd_ctx* c, int n_f, const double* chi, double* w_chi,
   dd_status r = apply_w_dev(c, n_f, din, dout, prm, s);
   if (r != DD_OK && r != DD_ENOCONV) return r;
   if (hout) DD_CUDA(c, cudaMemcpyAsync(w_chi, dout, bytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  return r;
+}
+
+dd_status dd_apply_w_part(dd_ctx* c, int part, int n_f, const int* ids, int nblk, const double* in,
+                          double* out, const dd_solve_params* prm, void* stream) {
+  if (!c || !in || !out || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (n_f > 65535) return fail(c, DD_EINVAL, "n_f must be <= 65535");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
+  const double* din = in;
+  double* dout = out;
+  const bool hin = !is_device_ptr(in), hout = !is_device_ptr(out);
+  dd_status e;
+  if (hin) {
+    void* p;
+    if ((e = workspace(c, 44, bytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, in, bytes, cudaMemcpyHostToDevice, s));
+    din = (const double*)p;
+  }
+  if (hout) {          // the entries the stage does not write are kept
+    void* p;
+    if ((e = workspace(c, 45, bytes, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, out, bytes, cudaMemcpyHostToDevice, s));
+    dout = (double*)p;
+  }
+  dd_status r = apply_w_part_dev(c, part, n_f, ids, nblk, din, dout, prm, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  if (hout) DD_CUDA(c, cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
   return r;
 }

@@ -117,6 +117,7 @@ def lib():
             "dd_debug_wait_fault": [vp, C.c_int],
             "dd_logdet_force": [vp, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
             "dd_fp64_fma_rate": [dp],
+            "dd_apply_w_part": [vp, C.c_int, C.c_int, ip, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -137,7 +138,7 @@ def exported_symbols():
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover",
-            "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate"]
+            "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate", "dd_apply_w_part"]
 
 
 def hop_variant_name(prec, v):
@@ -336,6 +337,16 @@ class Context:
         st = self._check(lib().dd_apply_w(self._h, n_f, _ptr(chi), _ptr(w_chi), C.byref(prm),
                                           _stream(stream)))
         return st
+
+    W_PARTS = {"frame_q": 0, "blocks": 1, "frame": 2}
+
+    def apply_w_part(self, part, n_f, ids, inp, out, prm=None, stream=None):
+        """One stage of w for the blocks ids (None for the frame stage): see dd_apply_w_part."""
+        ids = list(ids) if ids is not None else [0]
+        idarr = (C.c_int * len(ids))(*ids)
+        p = self.W_PARTS[part] if isinstance(part, str) else part
+        return self._check(lib().dd_apply_w_part(self._h, p, n_f, idarr, len(ids), _ptr(inp), _ptr(out),
+                                                 C.byref(prm or params()), _stream(stream)))
 
     def multiboson_heatbath(self, u, eta, chi, tol=1e-10, maxiter=200, prm=None, stream=None):
         """chi_k = W_{u_k}^{-1} eta_k for the fields of eta (layout of apply_w); stats dict."""
