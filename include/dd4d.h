@@ -410,7 +410,12 @@ dd_status dd_logdet_check(dd_ctx* ctx, const dd_solve_params* params, double* lo
  * weights complex, [layer][d = 0, +0..+3, -0..-3][c_out][c_in], complex128
  * (re, im) on the host.  Supported layers 4->16, 16->16, 16->4 (input and
  * output: the 4 spin components of a spinor).  FP32 master weights (Adam),
- * BF16-rounded weights in the kernels, FP32 activations and accumulation. */
+ * BF16-rounded weights in the kernels.  The forward and backward-data layers
+ * run on the tensor cores (tcgen05.mma, BF16 operands: the weights and the
+ * parallel-transported activations, FP32 accumulation in tensor memory) by
+ * default, or on the FP32 CUDA cores (FP32 activations and accumulation)
+ * after dd_net_tensor_cores(net, 0); the weight gradients run on the CUDA
+ * cores (FP32) in both cases. */
 typedef struct dd_net dd_net;
 typedef struct {
   int steps;          /* full-batch Adam steps */
@@ -450,6 +455,9 @@ dd_status dd_net_loss_grad(dd_ctx* ctx, dd_net* net, const int* ids, int nblk, i
 dd_status dd_net_train(dd_ctx* ctx, dd_net* net, const int* ids, int nblk, int nrhs,
                        const double* b, const dd_train_params* params, dd_train_stats* stats,
                        void* stream);
+/* Layers of the network on the tensor cores (on != 0, the default) or on the
+ * FP32 CUDA cores (on = 0).  Host-only. */
+dd_status dd_net_tensor_cores(dd_net* net, int on);
 /* Network used by DD_SOLVE_NET_GUESS on this context (NULL to clear; not owned). */
 dd_status dd_set_net(dd_ctx* ctx, dd_net* net);
 

@@ -37,6 +37,7 @@ struct dd_net {
   float* d_wadj = nullptr;       // adjoint weights: [d'][cin][cout] = conj(W[d][cout][cin]), d' = flip(d)
   std::vector<long long> woff;   // offset (complex) of layer l in d_w / d_wadj
   bool dirty = true;
+  bool tc = true;                // layers on the tensor cores (BF16 operands), else FP32 CUDA cores
 };
 
 namespace dd {
@@ -123,6 +124,247 @@ __global__ void __launch_bounds__(NT) k_ptconv(BatchDev bd, int p, const float2*
   for (int c = 0; c < COUT; ++c)
 #pragma unroll
     for (int a = 0; a < 3; ++a) o[cidx(c * 3 + a, n_out, i)] = acc[c][a];
+}
+
+// ---- tensor-core form of the layer (tcgen05, BF16 operands, FP32 in TMEM) ----
+// The channel mixing is a GEMM per 32-site quarter of a work item: rows are
+// (colour slot a, site s) = 32 a + s, 128 rows with slot 3 zero; for tap d the
+// columns are the transported input channels, real and imaginary parts
+// interleaved (k = 2 c' + {0, 1}); the output columns n < COUT hold Re y_n and
+// COUT <= n < 2 COUT hold Im y_{n - COUT}:
+//   D[row][n] = sum_d sum_k A_d[row][k] B_d[n][k],
+//   B_d[c][2c'] = Re W, B_d[c][2c'+1] = -Im W, B_d[COUT+c][2c'] = Im W, B_d[COUT+c][2c'+1] = Re W.
+// SIMT threads build A_d (parallel transport of the neighbour's colour vectors,
+// rounded to BF16) in one of two shared-memory buffers while the previous tap's
+// MMAs run; one thread issues the MMAs (K = 16 per instruction, M = 128) and
+// commits them to the buffer's mbarrier.  Operands are K-major without swizzle:
+// 8 x 16-byte core matrices, k-groups 128 B apart, 8-row groups SBO apart.
+namespace tc {
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ int koff(int r, int k, int sbo) {
+  return (r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity, unsigned limit) {
+  for (unsigned k = 0; k < limit; ++k) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, P;\n}"
+                 : "=r"(done)
+                 : "r"(saddr(bar)), "r"(parity)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t ta, float (&v)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t ta, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t ta, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int CIN, int COUT>
+struct Shape {
+  static constexpr int KT = 2 * CIN < 16 ? 16 : 2 * CIN;       // real columns per tap (>= 16)
+  static constexpr int N = 2 * COUT < 16 ? 16 : 2 * COUT;      // real output columns
+  static constexpr int SBO_A = 128 * (KT / 8);
+  static constexpr int SBO_B = 128 * (KT / 8);
+  static constexpr int A_BYTES = 16 * SBO_A;                    // 128 rows
+  static constexpr int B_TAP = (N / 8) * SBO_B;
+  static constexpr int SMEM = 2 * A_BYTES + 9 * B_TAP + 64;
+};
+
+constexpr unsigned WAIT_LIMIT = 1u << 22;
+
+}  // namespace tc
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128, 4) k_ptconv_tc(BatchDev bd, int p, const float2* __restrict__ in0,
+                                                   const float2* __restrict__ in1, float2* __restrict__ out,
+                                                   const float2* __restrict__ W, int* err) {
+  typedef tc::Shape<CIN, COUT> SH;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* abuf = smem;                                   // two A buffers
+  unsigned char* bmat = smem + 2 * SH::A_BYTES;                 // B of the 9 taps
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(bmat + 9 * SH::B_TAP);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bar + 2);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int item = blockIdx.x / bd.nrhs, r = blockIdx.x - item * bd.nrhs;
+  const int4 it = (p ? bd.items[1] : bd.items[0])[item];
+  const int sys = it.x * bd.nrhs + r;
+  const DomInst* dp = bd.inst_tab + bd.inst[it.x];
+  const int n0 = dp->n[0];
+  const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
+  const long long off_p = (p ? bd.off[1] : bd.off[0])[sys];
+  const long long off_q = (p ? bd.off[0] : bd.off[1])[sys];
+  const float2* inp = (p ? in1 : in0) + off_p / 4 * CIN;
+  const float2* inq = (p ? in0 : in1) + off_q / 4 * CIN;
+  // B of every tap (BF16 of the BF16-rounded weights: exact), A buffers zeroed
+  for (int e = t; e < 9 * SH::N * SH::KT; e += 128) {
+    const int d = e / (SH::N * SH::KT), rem = e - d * SH::N * SH::KT;
+    const int n = rem / SH::KT, k = rem - n * SH::KT;
+    const int j = k >> 1, part = k & 1;
+    float v = 0.f;
+    if (j < CIN && n < 2 * COUT) {
+      const int c = n < COUT ? n : n - COUT;
+      const float2 w = W[(d * COUT + c) * CIN + j];
+      v = n < COUT ? (part ? -w.y : w.x) : (part ? w.x : w.y);
+    }
+    *reinterpret_cast<__nv_bfloat16*>(bmat + d * SH::B_TAP + tc::koff(n, k, SH::SBO_B)) = __float2bfloat16(v);
+  }
+  for (int e = t; e < 2 * SH::A_BYTES / 16; e += 128) reinterpret_cast<uint4*>(abuf)[e] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(tc::saddr(tbase)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tbase;
+  const int* nbr = dp->nbr + (p ? 8LL * n0 : 0);
+  const float2* lk = dp->link32;
+  unsigned ncommit[2] = {0, 0};          // commits issued on each buffer's barrier (uniform)
+  bool ok = true;
+  const int nq = (it.z + 31) / 32;
+  for (int q = 0; q < nq; ++q) {
+    const int s = lane;                  // the site of this thread in the quarter
+    const int li = q * 32 + s;
+    const bool live = li < it.z;
+    const int i = it.y + (live ? li : 0);
+    for (int d = 0; d < 9; ++d) {
+      const int b = d & 1;
+      // the buffer is free once the MMAs of its previous tap have completed
+      if (ncommit[b] > 0 && !tc::bar_wait(&bar[b], (ncommit[b] - 1) & 1, tc::WAIT_LIMIT)) ok = false;
+      unsigned char* A = abuf + b * SH::A_BYTES;
+      int j = -1;
+      float2 U[9];
+      if (live) {
+        if (d == 0) {
+          j = i;
+        } else {
+          const int dir = d - 1;
+          j = nbr[dir * n_out + i];
+          if (j >= 0) {
+            const int mu = dir & 3;
+            if (dir < 4) ld_link(lk + link_block(p, mu, n0, n_out), n_out, i, U);
+            else ld_link(lk + link_block(1 - p, mu, n0, n_in), n_in, j, U);
+          }
+        }
+      }
+      for (int cp = warp; cp < CIN; cp += 4) {
+        float2 tv[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (j >= 0) {
+          float2 v[3];
+          const float2* src = d == 0 ? inp : inq;
+          const int nn = d == 0 ? n_out : n_in;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) v[a] = src[cidx(cp * 3 + a, nn, j)];
+          if (d == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) tv[a] = v[a];
+          } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b2 = 0; b2 < 3; ++b2) {
+                if (d <= 4) cfma(tv[a], U[a * 3 + b2], v[b2]);
+                else cfmac(tv[a], U[b2 * 3 + a], v[b2]);
+              }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(tv[a].x, tv[a].y);
+          *reinterpret_cast<__nv_bfloat162*>(A + tc::koff(a * 32 + s, 2 * cp, SH::SBO_A)) = h;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (t == 0) {
+        constexpr uint32_t id = tc::idesc_bf16(128, SH::N);
+#pragma unroll
+        for (int ks = 0; ks < SH::KT / 16; ++ks) {
+          const uint64_t da = tc::smem_desc(tc::saddr(A) + ks * 256, 128, SH::SBO_A);
+          const uint64_t db = tc::smem_desc(tc::saddr(bmat + d * SH::B_TAP) + ks * 256, 128, SH::SBO_B);
+          const uint32_t acc = (d > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(id), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            tc::saddr(&bar[b])));
+      }
+      ++ncommit[b];
+    }
+    // the quarter's accumulator: wait for the last tap (its commit covers every earlier MMA)
+    if (!tc::bar_wait(&bar[0], (ncommit[0] - 1) & 1, tc::WAIT_LIMIT)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp < 3 && ok) {
+      float v[SH::N];
+      tc::tmem_ld<SH::N>(tmem + ((uint32_t)(32 * warp) << 16), v);
+      if (live) {
+        float2* o = out + off_p / 4 * COUT;
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) o[cidx(c * 3 + warp, n_out, i)] = make_float2(v[c], v[COUT + c]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok) {
+    if (t == 0) atomicExch(err, 1);
+    // before the accumulator is released, every MMA this CTA issued has to be done
+    tc::bar_wait(&bar[0], (ncommit[0] - 1) & 1, tc::WAIT_LIMIT);
+    if (ncommit[1]) tc::bar_wait(&bar[1], (ncommit[1] - 1) & 1, tc::WAIT_LIMIT);
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
 }
 
 // weight gradient partials: one CTA per (item, rhs) work unit of parity p;
@@ -332,10 +574,30 @@ static dd_status upload_weights(dd_ctx* c, dd_net* n) {
   return DD_OK;
 }
 
+template <int CIN, int COUT>
+static void launch_tc(unsigned grid, const BatchDev& bd, int p, const float2* in0, const float2* in1, float2* out,
+                      const float2* W, int* err, cudaStream_t s) {
+  constexpr int smem = tc::Shape<CIN, COUT>::SMEM;
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaFuncSetAttribute(k_ptconv_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr[dev] = true;
+  }
+  DD_COUNT_LAUNCH(), k_ptconv_tc<CIN, COUT><<<grid, 128, smem, s>>>(bd, p, in0, in1, out, W, err);
+}
+
 static void launch_layer(const Batch& b, const BatchDev& bd, int p, int cin, int cout, const float2* in0,
-                         const float2* in1, float2* out, const float2* W, cudaStream_t s) {
+                         const float2* in1, float2* out, const float2* W, cudaStream_t s, int* err = nullptr) {
   const unsigned grid = (unsigned)((long long)b.nitems[p] * b.nrhs);
   if (!grid) return;
+  if (err) {                       // tensor cores (tcgen05), BF16 operands
+    if (cin == 4 && cout == 16) launch_tc<4, 16>(grid, bd, p, in0, in1, out, W, err, s);
+    else if (cin == 16 && cout == 16) launch_tc<16, 16>(grid, bd, p, in0, in1, out, W, err, s);
+    else launch_tc<16, 4>(grid, bd, p, in0, in1, out, W, err, s);
+    return;
+  }
   if (cin == 4 && cout == 16) DD_COUNT_LAUNCH(), k_ptconv<4, 16><<<grid, NT, 0, s>>>(bd, p, in0, in1, out, W);
   else if (cin == 16 && cout == 16) DD_COUNT_LAUNCH(), k_ptconv<16, 16><<<grid, NT, 0, s>>>(bd, p, in0, in1, out, W);
   else DD_COUNT_LAUNCH(), k_ptconv<16, 4><<<grid, NT, 0, s>>>(bd, p, in0, in1, out, W);
@@ -386,7 +648,8 @@ static dd_status net_forward(dd_ctx* c, dd_net* n, const Batch& b, const Acts& A
   for (int l = 0; l < n->nl; ++l) {
     const float2* W = (const float2*)n->d_w + n->woff[l];
     for (int p = 0; p < 2; ++p)
-      launch_layer(b, bd, p, n->ch[l], n->ch[l + 1], A.a[l][0], A.a[l][1], A.a[l + 1][p], W, s);
+      launch_layer(b, bd, p, n->ch[l], n->ch[l + 1], A.a[l][0], A.a[l][1], A.a[l + 1][p], W, s,
+                   n->tc ? c->d_err : nullptr);
   }
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
@@ -443,7 +706,8 @@ static dd_status net_loss_grad(dd_ctx* c, dd_net* n, const Batch& b, const Acts&
     if (l > 0) {
       const float2* Wa = (const float2*)n->d_wadj + n->woff[l];
       for (int p = 0; p < 2; ++p)
-        launch_layer(b, bd, p, cout, cin, Gr.a[l + 1][0], Gr.a[l + 1][1], Gr.a[l][p], Wa, s);
+        launch_layer(b, bd, p, cout, cin, Gr.a[l + 1][0], Gr.a[l + 1][1], Gr.a[l][p], Wa, s,
+                     n->tc ? c->d_err : nullptr);
     }
   }
   DD_CUDA(c, cudaGetLastError());
@@ -742,6 +1006,12 @@ dd_status dd_net_train(dd_ctx* c, dd_net* n, const int* ids, int nblk, int nrhs,
     ts->pairs = b->nb * b->nrhs;
   }
   (void)last;
+  return DD_OK;
+}
+
+dd_status dd_net_tensor_cores(dd_net* n, int on) {
+  if (!n) return DD_EINVAL;
+  n->tc = on != 0;
   return DD_OK;
 }
 

@@ -118,6 +118,7 @@ def lib():
             "dd_logdet_force": [vp, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
             "dd_fp64_fma_rate": [dp],
             "dd_apply_w_part": [vp, C.c_int, C.c_int, ip, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
+            "dd_net_tensor_cores": [vp, C.c_int],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -138,7 +139,8 @@ def exported_symbols():
             "dd_net_apply", "dd_net_loss_grad", "dd_net_train", "dd_set_net", "dd_net_save", "dd_net_load", "dd_multiboson_heatbath",
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover",
-            "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate", "dd_apply_w_part"]
+            "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate", "dd_apply_w_part",
+            "dd_net_tensor_cores"]
 
 
 def hop_variant_name(prec, v):
@@ -515,6 +517,12 @@ class Net:
         w = np.zeros(2 * n)
         lib().dd_net_weights(self._h, w.ctypes.data_as(C.POINTER(C.c_double)))
         return self._split(w.view(np.complex128))
+
+    def tensor_cores(self, on=True):
+        """Layers on the tensor cores (BF16 operands, the default) or the FP32 CUDA cores."""
+        st = lib().dd_net_tensor_cores(self._h, 1 if on else 0)
+        if st:
+            raise DDError(st, "dd_net_tensor_cores failed")
 
     def apply(self, ids, nrhs, inp, out, stream=None):
         idarr = (C.c_int * len(ids))(*ids)

@@ -1,9 +1,12 @@
 """GPU parallel-transport network: forward and gradients vs the FP64 oracle,
 training on solver-generated pairs, and its use as the block-solve initial guess.
 
-The oracle evaluates the same (BF16-rounded) weights in FP64; the GPU keeps
-FP32 activations, so forward outputs agree to ~1e-6 and gradients to ~1e-5
-relative (tolerances 2e-5 and 2e-4, norm-wise).
+The oracle evaluates the same (BF16-rounded) weights in FP64.  On the FP32
+CUDA cores the GPU keeps FP32 activations, so forward outputs agree to ~1e-6 and
+gradients to ~1e-5 relative (tolerances 2e-5 and 2e-4, norm-wise).  On the
+tensor cores (tcgen05, the default) the parallel-transported activations enter
+each layer's contraction rounded to BF16 (unit roundoff 2^-9 = 2e-3) with FP32
+accumulation: four layers give at most ~4 x 2e-3 relative, tolerance 2e-2.
 """
 
 import numpy as np
@@ -43,6 +46,7 @@ def test_forward_matches_oracle(case):
     torch = pytest.importorskip("torch")
     U, ctx, info, geo, Ws = case
     net = dd4d.Net(ctx, Ws)
+    net.tensor_cores(False)
     ids, nrhs = [0, 9], 2
     n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
     b = synth.complex_gaussian(4, synth.TAG_RHS, (len(ids), nrhs, n, 12))
@@ -58,10 +62,42 @@ def test_forward_matches_oracle(case):
             assert relerr(y[k, r].ravel(), ref) < 2e-5
 
 
+@pytest.mark.parametrize("ids", [[0, 9], [5]])
+def test_tensor_core_forward_matches_oracle(case, ids):
+    """The tcgen05 layers (BF16 operands, FP32 accumulation in tensor memory) against
+    the FP64 oracle and against the FP32 CUDA-core layers, on every site of two
+    framed blocks (5^4 sites: work items with a ragged last quarter)."""
+    torch = pytest.importorskip("torch")
+    U, ctx, info, geo, Ws = case
+    net = dd4d.Net(ctx, Ws)
+    nrhs = 3
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    b = synth.complex_gaussian(7, synth.TAG_RHS, (len(ids), nrhs, n, 12))
+    db = torch.from_numpy(b.view(np.float64).copy()).cuda()
+    dy = torch.full_like(db, float("nan"))
+    net.apply(ids, nrhs, db, dy)
+    net.tensor_cores(False)
+    dz = torch.zeros_like(db)
+    net.apply(ids, nrhs, db, dz)
+    y = dy.cpu().numpy().view(np.complex128)
+    z = dz.cpu().numpy().view(np.complex128)
+    assert np.all(np.isfinite(y))
+    Wr = [bf16(w) for w in Ws]
+    for k, blk in enumerate(ids):
+        Ub, side = _block(ctx, U, blk)
+        for r in range(nrhs):
+            ref, _ = onet.forward(Ub, Wr, b[k, r].ravel(), side)
+            e = relerr(y[k, r].ravel(), ref)
+            assert 1e-7 < e < 2e-2, e            # BF16 operands: close, but not the FP32 result
+            assert relerr(z[k, r].ravel(), ref) < 2e-5
+    assert relerr(y, z) < 2e-2
+
+
 def test_gradients_match_oracle(case):
     torch = pytest.importorskip("torch")
     U, ctx, info, geo, Ws = case
     net = dd4d.Net(ctx, Ws)
+    net.tensor_cores(False)
     ids, nrhs = [2, 13], 2
     n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
     b = synth.complex_gaussian(5, synth.TAG_RHS, (len(ids), nrhs, n, 12))
