@@ -94,6 +94,7 @@ typedef struct {
   int max_outer;       /* defect-correction cycles cap (mixed only) */
   int check_every;     /* iterations between host convergence checks (>= 1) */
   int flags;           /* DD_SOLVE_* below, or-ed, or 0 */
+  int restart;         /* Arnoldi steps per FGMRES cycle (DD_SOLVE_FGMRES; 1..16) */
 } dd_solve_params;
 
 /* dd_solve_params.flags */
@@ -107,6 +108,14 @@ typedef struct {
 #define DD_SOLVE_PIPELINE 8  /* page-locked host b and x: always split the blocks into
                                 chunks whose host<->device copies overlap the solves of
                                 the other chunks (done anyway from 256 MB of b) */
+#define DD_SOLVE_FGMRES 16   /* inner solve by flexible GMRES(restart) instead of BiCGstab
+                                (FP32 or FP64 inner precision; the host checks after
+                                every Arnoldi step) */
+#define DD_SOLVE_NET_PRECOND 32 /* with DD_SOLVE_FGMRES and FP32 inner solves of framed
+                                blocks: the network set with dd_set_net is the variable
+                                right preconditioner, z = [N((v_e, 0))]_even, the even
+                                block of its approximation of D_Omega^{-1} (= the inverse
+                                of the Schur complement) */
 
 typedef struct {
   int systems;         /* number of (block, rhs) systems solved */

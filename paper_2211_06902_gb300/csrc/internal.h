@@ -112,6 +112,19 @@ struct BatchDev {           // device-visible view of a Batch
   int nb, nrhs;
 };
 
+// per-system state of the batched solver (krylov.cu, fgmres.cu), device memory
+struct SysState {
+  double2 rho, alpha, omega, beta;
+  double rr;        // current |r|^2 of the inner recursion (or outer residual)
+  double target2;   // inner stopping threshold on |r|^2
+  double bnorm2;    // |b|^2 of the full (both-parity) right-hand side
+  double outer2;    // outer threshold (tol |b|)^2
+  int active;       // inner recursion running
+  int outer_active; // outer loop still running
+  int iters;        // inner iterations, summed over cycles
+  int status;       // 0 ok, 1 converged, 2 breakdown
+};
+
 // two CUDA events destroyed on scope exit (also on the early error returns)
 struct EventPair {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -282,6 +295,16 @@ void free_workspace(dd_ctx* c);
 void free_plan(dd_ctx* c);
 dd_status get_batch(dd_ctx* c, dd_domain kind, const int* ids, int nblk, int nrhs, Batch** out);
 dd_status get_batch_insts(dd_ctx* c, const std::vector<int>& inst, int nrhs, Batch** out);
+// Flexible GMRES(m) for the even Schur systems of a batch (fgmres.cu): solves
+// M x_e = rhs_e (x_e at the inner precision, from zero) for the systems still in
+// the outer loop, to max(inner_tol2 |rhs|^2, floor_frac outer2); with `net`, the
+// network is the variable right preconditioner z = [N((v, 0))]_even (FP32 only)
+dd_status run_fgmres(dd_ctx* c, const Batch& b, dd_prec prec, SysState* st, const void* rhs, void* x,
+                     int restart, double inner_tol2, double floor_frac, int maxiter, dd_net* net,
+                     cudaStream_t s, int* iters_run);
+// z_e = [N((v_e, 0))]_even on every system of the batch (net.cu), FP32 vectors
+dd_status net_precondition(dd_ctx* c, dd_net* n, const Batch& b, const float2* ve, float2* ze,
+                           cudaStream_t s);
 // learned initial guess x0 = N(b) (net.cu) from FP64 or double-float (df)
 // parity vectors, written as FP32 parity vectors
 dd_status net_guess(dd_ctx* c, dd_net* n, const Batch& b, const void* be, const void* bo, bool df,

@@ -19,18 +19,6 @@
 
 namespace dd {
 
-struct SysState {
-  double2 rho, alpha, omega, beta;
-  double rr;        // current |r|^2 of the inner recursion (or outer residual)
-  double target2;   // inner stopping threshold on |r|^2
-  double bnorm2;    // |b|^2 of the full (both-parity) right-hand side
-  double outer2;    // outer threshold (tol |b|)^2
-  int active;       // inner recursion running
-  int outer_active; // outer loop still running
-  int iters;        // inner iterations, summed over cycles
-  int status;       // 0 ok, 1 converged, 2 breakdown
-};
-
 namespace {
 
 __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
@@ -883,7 +871,10 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
     }
     int its = 0;
-    if (ip == DD_F64)
+    if (prm->flags & DD_SOLVE_FGMRES) {
+      dd_net* pn = ((prm->flags & DD_SOLVE_NET_PRECOND) && c->net && all_omega) ? c->net : nullptr;
+      e = run_fgmres(c, b, ip, st, rhs, w.x, prm->restart, inner_tol2, floor_frac, prm->maxiter, pn, s, &its);
+    } else if (ip == DD_F64)
       e = run_bicgstab<double2>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
                                 floor_frac, prm->maxiter, check_every, use_graph, s, &its);
     else if (ip == DD_F32)

@@ -747,6 +747,25 @@ static dd_status target_norms(dd_ctx* c, const Batch& b, const float2* const xt[
   return DD_OK;
 }
 
+// variable preconditioner of the Schur system: z_e = [N((v_e, 0))]_even.  The
+// network approximates D_Omega^{-1}, whose even-even block is the inverse of the
+// Schur complement 1 - k^2 H_eo H_oe.  The input and output even vectors serve
+// as the first and last activations directly (same SoA layout, 4 channels).
+dd_status net_precondition(dd_ctx* c, dd_net* n, const Batch& b, const float2* ve, float2* ze,
+                           cudaStream_t s) {
+  dd_status e = check_net(c, n, b);
+  if (e != DD_OK) return e;
+  Acts A;
+  if ((e = alloc_acts(c, b, n, 100, A)) != DD_OK) return e;
+  void* zo;
+  if ((e = workspace(c, 110, sizeof(float2) * b.tot[1] + 16, &zo)) != DD_OK) return e;
+  DD_CUDA(c, cudaMemsetAsync(zo, 0, sizeof(float2) * b.tot[1], s));
+  A.a[0][0] = const_cast<float2*>(ve);
+  A.a[0][1] = (float2*)zo;
+  A.a[n->nl][0] = ze;
+  return net_forward(c, n, b, A, s);
+}
+
 // initial guess for the solver: x0 = N(b) from the solver's parity vectors
 // be, bo (FP64, or double-float when `df`), written as FP32 parity vectors
 // xe32, xo32

@@ -149,6 +149,38 @@ def test_training_and_initial_guess():
     net.detach()
 
 
+def test_network_as_fgmres_preconditioner():
+    """The trained network as the variable right preconditioner of FGMRES (FP32
+    inner solves): every system still reaches 1e-10 against the oracle's D_Omega,
+    and the iteration counts with and without the network are recorded (the
+    benchmark reports their times)."""
+    torch = pytest.importorskip("torch")
+    from oracle.lattice import apply_D_restricted
+    U, ctx, info, geo = config1()
+    net = dd4d.Net(ctx, onet.init_weights(7))
+    ids = list(range(info["nblocks"]))
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    bt = synth.complex_gaussian(17, synth.TAG_RHS, (len(ids), 4, n, 12))
+    net.train(ids, 4, torch.from_numpy(bt.view(np.float64).copy()).cuda(), steps=80, lr=3e-3)
+    net.attach()
+    b = synth.complex_gaussian(18, synth.TAG_RHS, (len(ids), 2, n, 12))
+    x0, x1 = np.zeros_like(b), np.zeros_like(b)
+    s0 = ctx.solve_blocks("omega", ids, 2, b, x0, dd4d.params(1e-10, inner_prec="f32", fgmres=True, restart=10))
+    s1 = ctx.solve_blocks("omega", ids, 2, b, x1, dd4d.params(1e-10, inner_prec="f32", fgmres=True, restart=10,
+                                                               net_precond=True))
+    assert s0["status"] == s1["status"] == 0
+    assert s1["max_relres"] <= 1e-10
+    print("FGMRES iterations without / with the network:", s0["max_iters"], s1["max_iters"])
+    L = geo.L
+    for blk in (0, 7, 15):
+        sites = ctx.geom_sites(dd4d.SET_OMEGA, blk)
+        for r in range(2):
+            f = to_field(L, sites, b[blk, r])
+            res = f - apply_D_restricted(U, to_field(L, sites, x1[blk, r]), 0.13, geo.omega_mask[blk])
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
+    net.detach()
+
+
 def test_save_and_load_resume_exactly(tmp_path):
     """A saved network loads with the same weights and Adam state: it applies
     identically and a further training step gives identical weights."""

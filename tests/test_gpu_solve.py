@@ -208,3 +208,34 @@ def test_pipelined_host_buffers(inner):
             res = f - apply_D_restricted(U, xf, 0.12, geo.omega_mask[blk])
             assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
             off += n
+
+
+@pytest.mark.parametrize("inner,restart", [("f64", 8), ("f32", 8), ("f32", 3)])
+def test_fgmres_inner_solves(case1, inner, restart):
+    """FGMRES(m) as the inner solver (no preconditioner): every system reaches
+    1e-10 against the oracle's D_Omega, FP64 solutions agree with the oracle's
+    solves to 1e-8; m = 3 forces restarts."""
+    U, ctx, info, geo = case1
+    o = Oracle(U, 0.13, geo)
+    ids = list(range(info["nblocks"]))
+    sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
+    nrhs = 2
+    b = synth.complex_gaussian(11, synth.TAG_RHS, (len(ids), nrhs, len(sites[0]), 12))
+    x = np.zeros_like(b)
+    st = ctx.solve_blocks("omega", ids, nrhs, b, x,
+                          dd4d.params(1e-10, inner_prec=inner, fgmres=True, restart=restart))
+    assert st["status"] == dd4d.DD_OK, st
+    assert st["converged"] == len(ids) * nrhs and st["max_relres"] <= 1e-10
+    _check_block_solutions(U, geo, 0.13, sites, geo.omega_mask, ids, b, x,
+                           oracle=o.omega_solver if inner == "f64" else None)
+
+
+def test_fgmres_frame_solve(case1):
+    U, ctx, info, geo = case1
+    sites = ctx.geom_sites(dd4d.SET_LAMBDA1)
+    b = synth.complex_gaussian(12, synth.TAG_RHS, (1, 2, len(sites), 12))
+    x = np.zeros_like(b)
+    st = ctx.solve_blocks("lambda1", None, 2, b, x, dd4d.params(1e-10, inner_prec="f32", fgmres=True,
+                                                                 restart=12))
+    assert st["status"] == 0 and st["max_relres"] <= 1e-10
+    _check_block_solutions(U, geo, 0.13, [sites], [geo.Lambda1], [0], b, x)
