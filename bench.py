@@ -357,6 +357,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
 
+    # the same mixed solve with each inner solve as one graph launch (device-side loop)
+    loop_prm = dd4d.params(TOL, inner_prec="f32", inner_tol=args.inner_tol, autotune=True, graph_loop=True)
+    step(loop_prm)
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    la = dd4d.launch_count()
+    l0.record(stream)
+    lst = step(loop_prm)
+    l1.record(stream)
+    torch.cuda.synchronize()
+    device_loop = {"ms_per_step": l0.elapsed_time(l1), "max_iters": lst["max_iters"],
+                   "max_relres": lst["max_relres"], "kernel_launches_per_step": dd4d.launch_count() - la,
+                   "host_polls_per_inner_solve": 0}
+
     # BF16-storage inner solve of the same batch (FP32 arithmetic, double-float residuals)
     bf16 = None
     if rank == 0:
@@ -380,6 +394,10 @@ def run_ours(args):
     if rank == 0 and not args.no_learned:
         learned = learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms)
         learned["max_iters_without"] = stats["max_iters"]
+        # the learned mixed-precision forms against the plain FP64 GPU form of the same batch
+        learned["speedup_vs_plain_f64"] = {
+            "bicgstab_net_guess": plain_ms / learned["ms_per_step_with_net"],
+            "fgmres10_net_preconditioned": plain_ms / learned["fgmres10_net_preconditioned"]["ms_per_step"]}
 
     # end to end through the C ABI with pinned host buffers
     bh = torch.from_numpy(b_h.view(np.float64)).pin_memory()
@@ -476,6 +494,7 @@ def run_ours(args):
         "solver": {"max_relres": stats["max_relres"], "max_iters": stats["max_iters"],
                    "outer_cycles": stats["outer_cycles"], "hop_variant": stats["hop_variant"]},
         "bf16_inner": bf16,
+        "device_loop_graph": device_loop,
         "plain_f64": {"value": world * units / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                       "max_iters": pst["max_iters"], "speedup_of_mixed": plain_ms / ms,
                       "residual_hop_ms_in_mixed_step": hop64_ms / args.steps},
@@ -536,23 +555,48 @@ def learned_ab(dd4d, synth, torch, ctx, ids, b, x, units, ms_plain_guess):
                       "seconds": st["seconds"], "pairs": st["pairs"]})
         c.close()
     net.attach(ctx)
-    prm = dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, net_guess=True, autotune=True)
-    ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    st = ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+
+    def timed(prm):
+        ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = ctx.solve_blocks("omega", ids, NRHS, b, x, prm)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st
+    ms, st = timed(dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, net_guess=True, autotune=True))
+    # FGMRES(10) inner solves, without and with the network as right preconditioner
+    fg0_ms, fg0 = timed(dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, autotune=True, fgmres=True, restart=10))
+    fg1_ms, fg1 = timed(dd4d.params(TOL, inner_prec="f32", inner_tol=3e-6, autotune=True, fgmres=True, restart=10,
+                                    net_precond=True))
+    # one application of the network to the whole batch (tensor cores), and on the CUDA cores
+    y = torch.empty_like(b)
+    app = {}
+    for tcm in (True, False):
+        net.tensor_cores(tcm)
+        net.apply(ids, NRHS, b, y)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.apply(ids, NRHS, b, y)
+        e1.record()
+        torch.cuda.synchronize()
+        app["tensor_cores" if tcm else "fp32_cuda_cores"] = e0.elapsed_time(e1)
+    net.tensor_cores(True)
+    del y
     net.detach(ctx)
     net.close()
     return {"workload": "network trained on 3 x 16^4 lattices (eps 0.4/0.5/0.6, 64 pairs each), "
-                        "4 layers 4-16-16-16-4, BF16 weights, used as initial guess on the "
-                        "held-out bench lattice (seed 2)",
+                        "4 layers 4-16-16-16-4, BF16 weights, applied on the held-out bench lattice (seed 2)",
             "training": train, "ms_per_step_with_net": ms, "ms_per_step_without": ms_plain_guess,
             "value_with_net": units / (ms * 1e-3), "max_iters_with_net": st["max_iters"],
-            "max_relres_with_net": st["max_relres"], "status": st["status"]}
+            "max_relres_with_net": st["max_relres"], "status": st["status"],
+            "fgmres10_plain": {"ms_per_step": fg0_ms, "max_iters": fg0["max_iters"],
+                               "max_relres": fg0["max_relres"], "status": fg0["status"]},
+            "fgmres10_net_preconditioned": {"ms_per_step": fg1_ms, "max_iters": fg1["max_iters"],
+                                            "max_relres": fg1["max_relres"], "status": fg1["status"]},
+            "net_application_ms": app}
 
 
 def stencil_rates(dd4d, synth, torch, ctx, ids, b12, n_om):
@@ -755,6 +799,27 @@ def config5_action_rate(dd4d, synth, torch, group=8):
         relres = max(relres, c.last_solve_stats()["max_relres"])
     dt = time.perf_counter() - t0
     site_rhs = len(u) * (info["nblocks"] * info["max_omega"] + info["n_lambda1"])
+    # the first group of fields in three forms: FP32 inner (as above), plain FP64
+    # inner solves (the reference form) and BF16-storage inner solves; each one's
+    # time and the relative difference of its S^r and S^a to the FP64 form's
+    forms = {}
+    for name, fprm in (("f32_inner", prm),
+                       ("plain_f64", dd4d.params(TOL, inner_prec="f64")),
+                       ("bf16_inner", dd4d.params(TOL, inner_prec="bf16", inner_tol=1e-3, autotune=True))):
+        c.multiboson_action(groups[0], chis[0], fprm)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        Sg, Sb, Sr, _ = c.multiboson_action(groups[0], chis[0], fprm)
+        forms[name] = {"seconds": time.perf_counter() - t1, "S": Sg, "S_r": Sr, "S_blocks": np.asarray(Sb),
+                       "max_relres": c.last_solve_stats()["max_relres"]}
+    ref = forms["plain_f64"]
+    out_forms = {}
+    for name, f in forms.items():
+        out_forms[name] = {"seconds_first_group": f["seconds"], "max_relres": f["max_relres"],
+                           "rel_diff_S_vs_f64": abs(f["S"] - ref["S"]) / ref["S"],
+                           "rel_diff_S_r_vs_f64": abs(f["S_r"] - ref["S_r"]) / ref["S_r"],
+                           "max_rel_diff_S_block_vs_f64": float(np.max(np.abs(f["S_blocks"] - ref["S_blocks"])
+                                                                       / ref["S_blocks"]))}
     c.close()
     return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s",
             "workload": "48^4, kappa 0.1365, eps 0.6 (links drawn on the device, seed 5), 1296 framed blocks "
@@ -762,7 +827,9 @@ def config5_action_rate(dd4d, synth, torch, group=8):
                         "device generator), FP32 inner + double-float defect correction to 1e-10, fields in "
                         "groups of %d" % group,
             "seconds_per_eval": dt, "block_and_frame_site_rhs_per_eval": site_rhs,
-            "site_rhs_per_s": site_rhs / dt, "S": S, "max_relres": relres}
+            "site_rhs_per_s": site_rhs / dt, "S": S, "max_relres": relres,
+            "first_group_forms": out_forms,
+            "mixed_speedup_vs_plain_f64": forms["plain_f64"]["seconds"] / forms["f32_inner"]["seconds"]}
 
 
 def uneven_action_rate(dd4d, synth, torch, evals=2):

@@ -86,7 +86,10 @@ typedef struct {
 } dd_geom_info;
 
 typedef struct {
-  double tol;          /* stop when |b - D x| <= tol |b| per system (e.g. 1e-10) */
+  double tol;          /* stop when |b - D x| <= tol |b| per system (e.g. 1e-10); with the
+                          clover term on (dd_set_clover) the test is on the left-preconditioned
+                          residual, |A^{-1}(b - D x)| <= tol |A^{-1} b|, so the true relative
+                          residual is bounded by tol times the condition number of A */
   int maxiter;         /* Krylov iterations cap per system (inner ones for mixed) */
   dd_prec inner_prec;  /* DD_F64: plain FP64 BiCGstab; DD_F32 / DD_BF16: inner
                           solve at that precision with FP64 defect correction */
@@ -108,6 +111,11 @@ typedef struct {
 #define DD_SOLVE_PIPELINE 8  /* page-locked host b and x: always split the blocks into
                                 chunks whose host<->device copies overlap the solves of
                                 the other chunks (done anyway from 256 MB of b) */
+#define DD_SOLVE_GRAPH_LOOP 64 /* each inner BiCGstab solve as ONE captured CUDA graph: a
+                                conditional WHILE node repeats the iteration, and a
+                                one-thread kernel sets its condition from the device-side
+                                count of running systems (no host polls inside the inner
+                                solve; ignored while kernel timing is on) */
 #define DD_SOLVE_FGMRES 16   /* inner solve by flexible GMRES(restart) instead of BiCGstab
                                 (FP32 or FP64 inner precision; the host checks after
                                 every Arnoldi step) */

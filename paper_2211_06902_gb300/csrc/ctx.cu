@@ -636,8 +636,8 @@ dd_status dd_create(dd_ctx** out, const int L[4], int time_bc, double kappa) {
   c->kappa = kappa;
   cudaGetDevice(&c->device);
   dd_status st = dalloc(c, (void**)&c->d_U, sizeof(double2) * 36ULL * V);
-  if (st == DD_OK && (st = dalloc(c, (void**)&c->d_err, sizeof(int))) == DD_OK &&
-      cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
+  if (st == DD_OK && (st = dalloc(c, (void**)&c->d_err, 2 * sizeof(int))) == DD_OK &&
+      cudaMemset(c->d_err, 0, 2 * sizeof(int)) != cudaSuccess)
     st = DD_ECUDA;
   if (st != DD_OK) {
     dfree(c->d_U);

@@ -96,6 +96,7 @@ struct Batch {
   mutable int hop_variant[3] = {0, 0, 0};
   mutable bool tuned[3] = {false, false, false};
   mutable std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
+  mutable std::map<std::string, long long> graph_kernels;   // kernel nodes per replay (launch count)
   ~Batch();
 };
 
@@ -191,7 +192,8 @@ struct dd_ctx {
   double2* d_clovi = nullptr;
   bool clover_ready = false;
   bool clover_active = false;     // inside a solve: FP64 hops apply A^{-1} (clov_inv)
-  int* d_err = nullptr;           // device error word, set by kernels whose bounded waits give up
+  int* d_err = nullptr;           // [0]: device error word, set by kernels whose bounded waits give up;
+                                  // [1]: work-queue counter of the persistent stencil
   // work space (krylov.cu) and cached batches
   void* scratch = nullptr;
   std::map<std::string, std::unique_ptr<dd::Batch>> batches;
@@ -258,6 +260,7 @@ struct HopArgs {
                             // hop sum at the output site (left-preconditioned solves)
   int lb_fault;             // test hook of the bundle form (dd_debug_wait_fault): CTA 0 leaves
                             // one quarter's bulk copy unissued and waits a few microseconds
+  int* queue;               // work-queue counter of the persistent bundle form
 };
 dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a, cudaStream_t s);
 int hop_variant_count(dd_prec prec);

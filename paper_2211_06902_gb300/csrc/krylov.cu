@@ -450,11 +450,19 @@ struct InnerVecs {
   void *r, *rhat, *p, *v, *s, *t, *x, *tmp;
 };
 
+// condition of the device-side inner loop (DD_SOLVE_GRAPH_LOOP): one more
+// iteration while some system runs and the cap is not reached
+__global__ void k_loop_cond(const int* count, int* iter, int maxiter, cudaGraphConditionalHandle h) {
+  const int it = *iter + 1;
+  *iter = it;
+  cudaGraphSetConditional(h, (*count > 0 && it < maxiter) ? 1u : 0u);
+}
+
 template <class S>
 dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs& w, SysState* st,
                        double* partial, int* d_count, int* h_count, const void* rhs,
                        double inner_tol2, double floor_frac, int maxiter, int check_every,
-                       bool use_graph, cudaStream_t s, int* iters_run) {
+                       bool use_graph, cudaStream_t s, int* iters_run, bool device_loop = false) {
   BatchDev bd = batch_view(c, b);
   const int nsys = b.nb * b.nrhs;
   const long long stride = (long long)b.nitems[0] * b.nrhs;
@@ -514,7 +522,75 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
   };
   int it = 0;
   bool done = false;
-  if (use_graph && check_every <= maxiter) {
+  if (device_loop) {
+    // the whole inner solve as one graph: a memset node zeroes the iteration
+    // counter, then a conditional WHILE node repeats {iteration, condition}
+    // until no system runs or maxiter iterations have started
+    int* d_iter = d_count + 1;
+    char key[256];
+    snprintf(key, sizeof key, "loop:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%d:%a:%d%d%d", (int)prec, w.r, w.rhat,
+             w.p, w.v, w.s, w.t, w.x, w.tmp, (void*)st, (void*)partial, (void*)d_count, maxiter, c->kappa,
+             b.hop_variant[0], b.hop_variant[1], b.hop_variant[2]);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : b.graphs)
+      if (g.first == key) exec = g.second;
+    if (!exec) {
+      if (!c->capture_stream)
+        DD_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+      cudaStream_t cs = c->capture_stream;
+      cudaGraph_t graph = nullptr;
+      DD_CUDA(c, cudaGraphCreate(&graph, 0));
+      struct GraphGuard {
+        cudaGraph_t g;
+        ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+      } guard{graph};
+      cudaMemsetParams mp{};
+      mp.dst = d_iter;
+      mp.value = 0;
+      mp.elementSize = sizeof(int);
+      mp.width = 1;
+      mp.height = 1;
+      cudaGraphNode_t n0 = nullptr, n1 = nullptr;
+      DD_CUDA(c, cudaGraphAddMemsetNode(&n0, graph, nullptr, 0, &mp));
+      cudaGraphConditionalHandle h;
+      DD_CUDA(c, cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      DD_CUDA(c, cudaGraphAddNode(&n1, graph, &n0, nullptr, 1, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      DD_CUDA(c, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      const long long l0 = g_launches.load();
+      dd_status e = iteration(true, cs);
+      if (e == DD_OK) DD_COUNT_LAUNCH(), k_loop_cond<<<1, 1, 0, cs>>>(d_count, d_iter, maxiter, h);
+      // captured launches are not executions: the replays count them
+      const long long nk = g_launches.load() - l0;
+      g_launches.fetch_sub(nk);
+      b.graph_kernels[key] = nk;
+      cudaGraph_t body_out = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(cs, &body_out);
+      if (e != DD_OK) return e;
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture (inner loop body)");
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaGraphInstantiate (inner loop)");
+      if (b.graphs.size() >= 8) {
+        cudaGraphExecDestroy(b.graphs.front().second);
+        b.graphs.erase(b.graphs.begin());
+      }
+      b.graphs.push_back({std::string(key), exec});
+    }
+    DD_CUDA(c, cudaGraphLaunch(exec, s));
+    int hv[2] = {0, 0};
+    DD_CUDA(c, cudaMemcpyAsync(hv, d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(c, cudaStreamSynchronize(s));
+    *h_count = hv[0];
+    it = hv[1];
+    g_launches.fetch_add(b.graph_kernels[key] * it);
+    done = true;
+  }
+  if (!done && use_graph && check_every <= maxiter) {
     // the check_every iterations between two polls, captured once per batch,
     // precision, buffers and launch variant, then replayed
     char key[256];
@@ -531,8 +607,12 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
         DD_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
       cudaStream_t cs = c->capture_stream;
       DD_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      const long long l0 = g_launches.load();
       dd_status e = DD_OK;
       for (int i = 0; i < check_every && e == DD_OK; ++i) e = iteration(i == check_every - 1, cs);
+      const long long nk = g_launches.load() - l0;
+      g_launches.fetch_sub(nk);
+      b.graph_kernels[key] = nk;
       cudaGraph_t graph = nullptr;
       cudaError_t ce = cudaStreamEndCapture(cs, &graph);
       if (e != DD_OK) {
@@ -549,8 +629,10 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
       }
       b.graphs.push_back({std::string(key), exec});
     }
+    const long long nk = b.graph_kernels[key];
     while (it + check_every <= maxiter) {
       DD_CUDA(c, cudaGraphLaunch(exec, s));
+      g_launches.fetch_add(nk);
       it += check_every;
       dd_status e = poll();
       if (e != DD_OK) return e;
@@ -799,6 +881,8 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   // CUDA graphs replay the inner iterations between polls (not while the
   // per-launch kernel timing is on: its events are host-side records)
   const bool use_graph = (prm->flags & DD_SOLVE_GRAPH) && !c->timing;
+  // each inner solve as one graph launch with its loop on the device
+  const bool device_loop = (prm->flags & DD_SOLVE_GRAPH_LOOP) && !c->timing;
   void* tune64 = nullptr;
   if ((prm->flags & DD_SOLVE_AUTOTUNE) &&
       (e = ws_get(c, 27, std::max(ne, no) * c64, &tune64)) != DD_OK)
@@ -876,13 +960,13 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       e = run_fgmres(c, b, ip, st, rhs, w.x, prm->restart, inner_tol2, floor_frac, prm->maxiter, pn, s, &its);
     } else if (ip == DD_F64)
       e = run_bicgstab<double2>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
-                                floor_frac, prm->maxiter, check_every, use_graph, s, &its);
+                                floor_frac, prm->maxiter, check_every, use_graph, s, &its, device_loop);
     else if (ip == DD_F32)
       e = run_bicgstab<float2>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
-                               floor_frac, prm->maxiter, check_every, use_graph, s, &its);
+                               floor_frac, prm->maxiter, check_every, use_graph, s, &its, device_loop);
     else
       e = run_bicgstab<__nv_bfloat162>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
-                                       floor_frac, prm->maxiter, check_every, use_graph, s, &its);
+                                       floor_frac, prm->maxiter, check_every, use_graph, s, &its, device_loop);
     if (e != DD_OK) return e;
     // e_o = r_o + k H_oe e_e
     {

@@ -652,15 +652,15 @@ __device__ __forceinline__ bool mbar_try_wait_hint(unsigned long long* bar, unsi
 // test-hook limit: 64 polls of at most ~1 us
 constexpr unsigned LB_FAULT_POLLS = 64;
 constexpr unsigned LB_FAULT_POLL_NS = 1000;
-// bounded wait for phase 0 of a once-used barrier (short: the test hook's CTA)
-__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, bool short_wait = false) {
+// bounded wait for the phase of parity `par` (short: the test hook's CTA)
+__device__ __forceinline__ bool mbar_waitp(unsigned long long* bar, unsigned par, bool short_wait) {
   if (short_wait) {
     for (unsigned k = 0; k < LB_FAULT_POLLS; ++k)
-      if (mbar_try_wait_hint(bar, 0, LB_FAULT_POLL_NS)) return true;
+      if (mbar_try_wait_hint(bar, par, LB_FAULT_POLL_NS)) return true;
     return false;
   }
   for (unsigned k = 0; k < LB_WAIT_LIMIT; ++k)
-    if (mbar_try_wait(bar, 0)) return true;
+    if (mbar_try_wait(bar, par)) return true;
   return false;
 }
 
@@ -727,9 +727,14 @@ constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64;
 // QPC: quarters of the item per CTA (4: the whole item; 2: half of it, so two
 // CTAs share an item and add their inner-product partials atomically onto
 // zeroed slots); MAXR: most rhs per CTA.
-template <class S, int MINB, int RR, int QPC, int MAXR>
-__global__ void __launch_bounds__(32 * MAXR / RR, MINB)
-    k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
+// One work unit (item, rhs group, part of the item) of the bundle form; the
+// barriers of the QPC quarter slots are initialised by the caller, and slot q
+// waits for the phase parity (ph >> q) & 1.  Returns the number of slots it used
+// (0 when the unit had nothing to do); every CTA-wide barrier inside is reached
+// by all threads or by none.
+template <class S, int RR, int QPC, int MAXR>
+__device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, long long unit,
+                                       unsigned ph, bool fault) {
   typedef typename StoreTraits<S>::C C;
   typedef typename StoreTraits<S>::T T;
   constexpr int QB = lb_quarter_bytes<S>();
@@ -737,14 +742,14 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
   extern __shared__ __align__(128) unsigned char lb_smem[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + QPC * QB);
   const int p = a.p_out;
-  const int item = (int)(blockIdx.x / (ngroups * NH));
-  const int rem = (int)(blockIdx.x - (long long)item * ngroups * NH);
+  const int item = (int)(unit / (ngroups * NH));
+  const int rem = (int)(unit - (long long)item * ngroups * NH);
   const int hh = NH == 1 ? 0 : rem / ngroups;
   const int g = rem - hh * ngroups;
   const int4 it = (p ? bd.items[1] : bd.items[0])[item];
   const int q0 = hh * QPC;
   const int nq = min(QPC, (it.z + LB_LANES - 1) / LB_LANES - q0);   // quarters of this CTA
-  if (nq <= 0) return;                         // the item is shorter than this part (uniform)
+  if (nq <= 0) return 0;                       // the item is shorter than this part (uniform)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   bool actk[RR];
   int sysk[RR];
@@ -763,22 +768,19 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
 #pragma unroll
   for (int k = 0; k < RR; ++k) nact_rhs += actk[k] ? 1 : 0;
   const int cta_rhs = __syncthreads_count(lane < nact_rhs);   // lanes 0 .. nact_rhs-1 of each warp
-  if (cta_rhs == 0) return;                    // every rhs of the group has converged
+  if (cta_rhs == 0) return 0;                  // every rhs of the group has converged
   const DomInst* dp = bd.inst_tab + bd.inst[it.x];
   const int n0 = dp->n[0];
-  // test hook: CTA 0 arms the barrier of its last quarter without issuing the
-  // copy, so that wait gives up (nothing is in flight for it) after a short limit
-  const bool fault = a.lb_fault && blockIdx.x == 0;
+  // test hook: the first unit of CTA 0 arms the barrier of its last quarter
+  // without issuing the copy, so that wait gives up (nothing is in flight for it)
+  // after a short limit
   const int fq = fault ? nq - 1 : -1;
   if (threadIdx.x == 0) {
-    for (int q = 0; q < nq; ++q) mbar_init(&bar[q], 1);
-    mbar_fence_init();
-    // one atomic per CTA for the algorithmic-byte accounting (timing only)
+    // one atomic per unit for the algorithmic-byte accounting (timing only)
     if (a.work_bytes)
       atomicAdd(a.work_bytes, a.site_bytes * min(it.z - q0 * LB_LANES, nq * LB_LANES) * cta_rhs);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+    // the bulk copies below overwrite shared memory an earlier unit of this CTA read
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const unsigned char* src = bundle_of<S>(*dp) +
         (lb_quarter_base(p, n0) + (long long)LB_QUARTERS * (it.y / LB_CHUNK) + q0) * QB;
     for (int q = 0; q < nq; ++q) {
@@ -793,11 +795,11 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     // idle warp of a busy CTA: thread 0 still sees its copies land before leaving
     if (threadIdx.x == 0)
       for (int q = 0; q < nq; ++q)
-        if (!mbar_wait0(&bar[q], fault)) {
+        if (!mbar_waitp(&bar[q], (ph >> q) & 1u, fault)) {
           atomicExch(a.err, 1);
-          if (q != fq) mbar_wait0(&bar[q]);
+          if (q != fq) mbar_waitp(&bar[q], (ph >> q) & 1u, false);
         }
-    return;
+    return nq;
   }
   const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
   const long long* off_in = p ? bd.off[0] : bd.off[1];
@@ -818,9 +820,9 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     tqs[k][0] = tqs[k][1] = 0;
   }
   for (int q = 0; q < nq; ++q) {
-    if (!mbar_wait0(&bar[q], fault)) {
+    if (!mbar_waitp(&bar[q], (ph >> q) & 1u, fault)) {
       if (lane == 0) atomicExch(a.err, 1);
-      if (threadIdx.x == 0 && q != fq) mbar_wait0(&bar[q]);
+      if (threadIdx.x == 0 && q != fq) mbar_waitp(&bar[q], (ph >> q) & 1u, false);
       continue;
     }
     const int li = (q0 + q) * LB_LANES + lane;
@@ -976,6 +978,51 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
       }
     }
   }
+  return nq;
+}
+
+template <class S, int MINB, int RR, int QPC, int MAXR>
+__global__ void __launch_bounds__(32 * MAXR / RR, MINB)
+    k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
+  extern __shared__ __align__(128) unsigned char lb_smem[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + QPC * lb_quarter_bytes<S>());
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < QPC; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  lb_unit<S, RR, QPC, MAXR>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
+}
+
+// Persistent form with a work queue: a grid of (SMs x resident CTAs) CTAs pulls
+// units (item, rhs group, part) from a device counter (a.queue, zeroed before
+// the launch), so blocks of uneven sizes and converged systems are balanced at
+// run time; the quarter barriers are initialised once and reused phase by phase.
+template <class S, int MINB, int RR, int QPC, int MAXR>
+__global__ void __launch_bounds__(32 * MAXR / RR, MINB)
+    k_hop_lbq(BatchDev bd, HopArgs a, int ngroups, int rb, int nunits) {
+  extern __shared__ __align__(128) unsigned char lb_smem[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(lb_smem + QPC * lb_quarter_bytes<S>());
+  __shared__ int next_unit;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < QPC; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  unsigned ph = 0;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) next_unit = atomicAdd(a.queue, 1);
+    __syncthreads();                       // also: every thread is done with the previous unit
+    const int u = next_unit;
+    // a wait that gave up (here or in another CTA) stops the queue: a barrier
+    // whose phase did not complete cannot serve another unit
+    const bool stop = *(volatile const int*)a.err != 0;
+    __syncthreads();                       // next_unit is rewritten only after all have read it
+    if (u >= nunits || stop) break;
+    const int used = lb_unit<S, RR, QPC, MAXR>(bd, a, ngroups, rb, u, ph, a.lb_fault && blockIdx.x == 0 && first);
+    ph ^= (1u << used) - 1u;
+    first = false;
+  }
 }
 
 template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS>
@@ -999,6 +1046,30 @@ static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, 
       <<<(unsigned)(nitems_p * ngroups * NH), nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb);
 }
 
+// the work-queue form: (SMs x MINB) CTAs pull the units from a zeroed counter
+template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS>
+static void launch_lbq(const BatchDev& bd, const HopArgs& a, long long nitems_p, int nsm, cudaStream_t s) {
+  const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
+  const int rb = (bd.nrhs + ngroups - 1) / ngroups;
+  const int nthreads = 32 * ((rb + RR - 1) / RR);
+  constexpr int NH = LB_QUARTERS / QPC;
+  if (NH > 1 && a.partial) {
+    const long long stride = nitems_p * bd.nrhs;
+    auto zero = [&](int slot) { cudaMemsetAsync(a.partial + 2 * slot * stride, 0, 16 * stride, s); };
+    if (a.dotq) zero(0);
+    if (a.dots) {
+      zero(a.dotq ? 1 : 0);
+      zero(a.dotq ? 2 : 1);
+    }
+    if (a.dotqs) zero(3);
+  }
+  const long long nunits = nitems_p * ngroups * NH;
+  cudaMemsetAsync(a.queue, 0, sizeof(int), s);
+  const long long grid = std::min<long long>(nunits, (long long)nsm * MINB);
+  DD_COUNT_LAUNCH(), k_hop_lbq<S, MINB, RR, QPC, MAXR>
+      <<<(unsigned)grid, nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb, (int)nunits);
+}
+
 void hop_bundle_prepare() {
   static bool done[64] = {false};
   int dev = 0;
@@ -1020,6 +1091,9 @@ void hop_bundle_prepare() {
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 4, 3, 4, 12>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 2, 12>, at, h16);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 5, 1, 2, 6>, at, h16);
+  cudaFuncSetAttribute(k_hop_lbq<float2, 2, 1, 4, 12>, at, b32);
+  cudaFuncSetAttribute(k_hop_lbq<float2, 4, 1, 2, 6>, at, h32);
+  cudaFuncSetAttribute(k_hop_lbq<__nv_bfloat162, 2, 1, 4, 12>, at, b16);
   done[dev] = true;
 }
 
@@ -1039,13 +1113,13 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
                                          {2, false, -3}, {2, false, -1, 2, 12}, {5, false, -1, 2, 6},
-                                         {4, false, -1, 2, 6}};
+                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
                                          {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
-                                         {2, false, -1, 2, 12}, {5, false, -1, 2, 6}};
+                                         {2, false, -1, 2, 12}, {5, false, -1, 2, 6}, {2, true, -1}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 20 : 14); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 22 : 15); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1084,6 +1158,12 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
   const HopVariant& hv = variant_of(prec, v);
   if (hv.r < 0) {
     const int rr = -hv.r;
+    if (hv.persist) {
+      if (prec == DD_F32 && hv.qpc == 2) launch_lbq<float2, 4, 1, 2, 6>(bd, a, ni, nsm, s);
+      else if (prec == DD_F32) launch_lbq<float2, 2, 1>(bd, a, ni, nsm, s);
+      else launch_lbq<__nv_bfloat162, 2, 1>(bd, a, ni, nsm, s);
+      return;
+    }
     if (prec == DD_F32) {
       if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2 && hv.maxr == 6) launch_lb<float2, 4, 1, 2, 6>(bd, a, ni, s);
@@ -1153,6 +1233,7 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
   a.err = c->d_err;
   a.clov_inv = (c->clover_active && prec == DD_F64) ? c->d_clovi : nullptr;
   a.lb_fault = c->debug_wait_fault ? 1 : 0;
+  a.queue = c->d_err + 1;
   int p = a.p_out;
   if (b.nitems[p] == 0) return DD_OK;
   const long long nblk = (long long)b.nitems[p] * b.nrhs;
@@ -1342,10 +1423,14 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.r < 0 && h.qpc == 4 && h.maxr == 12)
+        if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);
+        else if (h.r < 0 && h.persist)
+          snprintf(names[k][u], sizeof names[k][u],
+                   "k_hop_lbq<%s,%d,%d,%d,%d>: work-queue persistent bundle form, %d sites and up to %d rhs per unit",
+                   ty[k], h.minb, -h.r, h.qpc, h.maxr, 32 * h.qpc, h.maxr);
         else if (h.r < 0)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d,%d,%d>: bulk-copied links, %d sites and up to %d rhs per CTA",

@@ -1,11 +1,15 @@
-"""One batched block solve on a chosen lattice, for profiling the kernels.
+"""One batched block solve (or network application) on a chosen lattice, the
+small cases that the ncu summaries under profiles/ were taken on.
 
     python -m paper_2211_06902_gb300.profile_case --L 24 --core 7 --nrhs 12 --inner f32 --variant 13
+    python -m paper_2211_06902_gb300.profile_case --L 24 --nrhs 12 --net
 
 Builds the lattice (links exp(i eps H)), the framed blocks of `core`^4 cores
 with a one-site frame, Gaussian right-hand sides on every block, and runs
-`--repeat` solves to 1e-10 with the requested inner precision.  Prints the
-solver statistics; exits non-zero if a system misses the tolerance.
+`--repeat` solves to 1e-10 with the requested inner precision (or, with
+--net, `--repeat` applications of the 4-layer network with tensor-core
+layers).  Prints the solver statistics; exits non-zero if a system misses the
+tolerance.
 """
 
 import argparse
@@ -33,6 +37,7 @@ def main():
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--variant", type=int, default=-1,
                     help="stencil launch variant of the inner precision (-1: default)")
+    ap.add_argument("--net", action="store_true", help="apply the network instead of solving")
     a = ap.parse_args()
     import torch
     torch.cuda.init()
@@ -46,6 +51,16 @@ def main():
     b = synth.complex_gaussian(2, synth.TAG_RHS, (len(ids), a.nrhs, info["max_omega"], 12))
     bd = torch.from_numpy(b.view(np.float64)).cuda()
     xd = torch.zeros_like(bd)
+    if a.net:
+        net = dd4d.Net(ctx, synth.net_init_weights(11))
+        y = torch.zeros_like(bd)
+        for _ in range(a.repeat):
+            net.apply(ids, a.nrhs, bd, y)
+        torch.cuda.synchronize()
+        print("network applied", a.repeat, "times, |y| =", float(y.norm()))
+        net.close()
+        ctx.close()
+        return 0
     if a.variant >= 0:
         ctx.set_hop_variant(a.inner, a.variant)
     prm = dd4d.params(1e-10, inner_prec=a.inner)

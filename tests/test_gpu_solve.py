@@ -239,3 +239,26 @@ def test_fgmres_frame_solve(case1):
                                                                  restart=12))
     assert st["status"] == 0 and st["max_relres"] <= 1e-10
     _check_block_solutions(U, geo, 0.13, [sites], [geo.Lambda1], [0], b, x)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_device_loop_graph_is_bit_identical(inner):
+    """DD_SOLVE_GRAPH_LOOP: each inner solve is one graph launch whose WHILE node
+    repeats the iteration until the device-side count of running systems is zero.
+    The same kernels run in the same order (after convergence every kernel skips
+    the finished systems), so the solutions equal the host-polled ones bit for
+    bit; uneven blocks in one batch, two solves (the second replays the graph)."""
+    L = (12, 8, 8, 10)
+    cores = [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]]
+    U, ctx, info, geo = make_case(L, 0.12, 0.5, 7, cores)
+    ids = list(range(info["nblocks"]))
+    tot = sum(len(ctx.geom_sites(dd4d.SET_OMEGA, b)) for b in ids)
+    b = synth.complex_gaussian(13, synth.TAG_RHS, (2 * tot, 12))
+    x0, x1, x2 = np.zeros_like(b), np.zeros_like(b), np.zeros_like(b)
+    s0 = ctx.solve_blocks("omega", ids, 2, b, x0, dd4d.params(1e-10, inner_prec=inner))
+    s1 = ctx.solve_blocks("omega", ids, 2, b, x1, dd4d.params(1e-10, inner_prec=inner, graph_loop=True))
+    s2 = ctx.solve_blocks("omega", ids, 2, b, x2, dd4d.params(1e-10, inner_prec=inner, graph_loop=True))
+    assert s0["status"] == s1["status"] == s2["status"] == 0
+    assert s1["max_relres"] <= 1e-10
+    assert np.array_equal(x0, x1) and np.array_equal(x1, x2)
+    assert s0["max_iters"] == s1["max_iters"]
