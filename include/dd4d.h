@@ -157,11 +157,17 @@ dd_status dd_set_kappa(dd_ctx* ctx, double kappa);
  * (DD_F64 only); dd_solve_blocks and everything built on it (dd_apply_w, the
  * action, the heat-bath, the reweighting samples, dd_logdet_check) solve
  * (1 - kappa A^{-1} H) x = A^{-1} b with the even-odd Schur form
- * 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe, FP64 inner solves only
- * (inner_prec DD_F64, else DD_EINVAL), so the tolerance applies to the
- * residual A^{-1}(b - D x) relative to A^{-1} b.  dd_mb_force and
- * dd_apply_D_block_noalloc return DD_EINVAL with the term on.  c_sw = 0 turns
- * it off (the default). */
+ * 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe, so the tolerance applies to the
+ * residual A^{-1}(b - D x) relative to A^{-1} b.  Every hop of a solve applies
+ * A^{-1} of its output site at its own precision: FP64 for DD_F64 solves; for
+ * DD_F32 and DD_BF16 inner solves an FP32 copy of A^{-1} (each hermitian block
+ * packed to its diagonal and upper triangle, 288 B per site), and for their
+ * double-float residual a double-float copy (576 B per site); A^{-1} b is
+ * formed once in FP64.  The two copies (1.5 times the FP64 table) are built
+ * at the first mixed solve after A changes.  dd_mb_force, dd_apply_D_block at
+ * DD_F32 / DD_BF16, dd_apply_D_block_noalloc and the learned network
+ * (DD_SOLVE_NET_GUESS, DD_SOLVE_NET_PRECOND) return DD_EINVAL with the term
+ * on.  c_sw = 0 turns it off (the default). */
 dd_status dd_set_clover(dd_ctx* ctx, double c_sw);
 
 /* Gauge links U_mu(x) in SU(3) (paper Sec. 1).  Host buffer, layout

@@ -255,10 +255,90 @@ __global__ void k_clover_apply(BatchDev bd, int p, double2* v, const double2* __
   st_site<12>(base, n, i, w);
 }
 
+// one thread per (site, chirality block): the hermitian-packed FP32 and
+// double-float copies of A^{-1} (diagonal real parts, then the entries above
+// the diagonal row by row)
+__global__ void k_clover_pack(const double2* __restrict__ Ai, float4* __restrict__ t32,
+                              float4* __restrict__ tdf, long long V) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 2 * V) return;
+  const double2* a = Ai + k * 36;
+  float f[36];
+  float4* o = tdf + k * 18;
+  for (int q = 0; q < 3; ++q) {
+    const float2 d0 = split_d(a[(2 * q) * 7].x), d1 = split_d(a[(2 * q + 1) * 7].x);
+    o[q] = make_float4(d0.x, d0.y, d1.x, d1.y);
+  }
+  for (int r = 0; r < 6; ++r) f[r] = (float)a[r * 7].x;
+  int z = 6, zq = 3;
+  for (int r = 0; r < 6; ++r)
+    for (int c = r + 1; c < 6; ++c, z += 2, ++zq) {
+      const double2 m = a[r * 6 + c];
+      f[z] = (float)m.x;
+      f[z + 1] = (float)m.y;
+      const float2 re = split_d(m.x), im = split_d(m.y);
+      o[zq] = make_float4(re.x, im.x, re.y, im.y);
+    }
+  float4* o32 = t32 + k * 9;
+  for (int q = 0; q < 9; ++q) o32[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+}
+
+// v <- A^{-1}(x) v on one parity of a batch of double-float vectors, in FP64
+// from the full table (once per solve: the preconditioned right-hand side)
+__global__ void k_clover_apply_df(BatchDev bd, int p, df2s* v, const double2* __restrict__ M) {
+  const int4 it = (p ? bd.items[1] : bd.items[0])[blockIdx.x];
+  const int r = blockIdx.y;
+  const int sys = it.x * bd.nrhs + r;
+  const DomInst* d = bd.inst_tab + bd.inst[it.x];
+  const int n0 = d->n[0];
+  const int n = p ? d->n[1] : n0;
+  if ((int)threadIdx.x >= it.z) return;
+  const int i = it.y + threadIdx.x;
+  df2s* base = v + (p ? bd.off[1] : bd.off[0])[sys];
+  dfc u[12];
+  ld_site<12>(base, n, i, u);
+  double2 w[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) w[k] = to_d2(u[k]);
+  clover_mul(M + 72LL * d->glob[(p ? n0 : 0) + i], w);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) u[k] = cmk<dfc>(w[k].x, w[k].y);
+  st_site<12>(base, n, i, u);
+}
+
 }  // namespace
+
+dd_status clover_mixed_tables(dd_ctx* c) {
+  if (!c->clover_ready) return fail(c, DD_EINVAL, "clover term not built");
+  if (c->clover_mixed_ready) return DD_OK;
+  dd_status e;
+  if (!c->d_clovi32 && (e = dalloc(c, (void**)&c->d_clovi32, sizeof(float4) * 18ULL * c->V)) != DD_OK) return e;
+  if (!c->d_clovi_df && (e = dalloc(c, (void**)&c->d_clovi_df, sizeof(float4) * 36ULL * c->V)) != DD_OK)
+    return e;
+  DD_COUNT_LAUNCH(), k_clover_pack<<<(unsigned)((2LL * c->V + 127) / 128), 128>>>(c->d_clovi, c->d_clovi32,
+                                                                                  c->d_clovi_df, (long long)c->V);
+  DD_CUDA(c, cudaGetLastError());
+  DD_CUDA(c, cudaDeviceSynchronize());
+  c->clover_mixed_ready = true;
+  return DD_OK;
+}
+
+dd_status clover_apply_inv_df(dd_ctx* c, const Batch& b, void* ve, void* vo, cudaStream_t s) {
+  if (!c->clover_ready) return fail(c, DD_EINVAL, "clover term not built");
+  dd_status e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  BatchDev bd = batch_view(c, b);
+  if (b.nitems[0] > 0)
+    DD_COUNT_LAUNCH(), k_clover_apply_df<<<dim3(b.nitems[0], b.nrhs), 128, 0, s>>>(bd, 0, (df2s*)ve, c->d_clovi);
+  if (b.nitems[1] > 0)
+    DD_COUNT_LAUNCH(), k_clover_apply_df<<<dim3(b.nitems[1], b.nrhs), 128, 0, s>>>(bd, 1, (df2s*)vo, c->d_clovi);
+  DD_CUDA(c, cudaGetLastError());
+  return DD_OK;
+}
 
 dd_status clover_build(dd_ctx* c) {
   c->clover_ready = false;
+  c->clover_mixed_ready = false;
   if (c->csw == 0.0 || !c->gauge_ready) return DD_OK;
   SigmaBlocks sig;
   if (!sigma_blocks(sig)) return fail(c, DD_EINVAL, "sigma_mu_nu is not chirally block-diagonal");

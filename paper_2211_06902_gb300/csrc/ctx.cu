@@ -670,6 +670,8 @@ dd_status dd_destroy(dd_ctx* c) {
   dfree(c->d_err);
   dfree(c->d_clov);
   dfree(c->d_clovi);
+  dfree(c->d_clovi32);
+  dfree(c->d_clovi_df);
   free_workspace(c);
   free_plan(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);

@@ -141,4 +141,35 @@ __device__ __forceinline__ void axpy(dfc& o, float2 s, dfc v) {
 }
 __device__ __forceinline__ float nrm2f(dfc a) { return fmaf(a.h.x, a.h.x, a.h.y * a.h.y); }
 
+// Hermitian clover block times a double-float vector, from a double-float
+// packed table: per chirality block the 6 real diagonal entries as (h, l)
+// pairs (3 float4), then the 15 entries above the diagonal row by row as
+// (re_h, im_h, re_l, im_l) (15 float4): 18 float4 (288 B), 36 per site.
+constexpr int CLOV_HDF_F4 = 36;
+__device__ __forceinline__ void clover_mul_h(const float4* __restrict__ M, dfc (&v)[12]) {
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    const float4* m = M + ch * 18;
+    dfc w[6];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 d = __ldg(m + q);
+      w[2 * q] = scale(v[ch * 6 + 2 * q], make_float2(d.x, d.y));
+      w[2 * q + 1] = scale(v[ch * 6 + 2 * q + 1], make_float2(d.z, d.w));
+    }
+    int z = 3;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r + 1; c < 6; ++c, ++z) {
+        const float4 t = __ldg(m + z);
+        const dfc e{make_float2(t.x, t.y), make_float2(t.z, t.w)};
+        cfma(w[r], e, v[ch * 6 + c]);          // w_r += m v_c
+        cfmac(w[c], e, v[ch * 6 + r]);         // w_c += conj(m) v_r
+      }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) v[ch * 6 + r] = w[r];
+  }
+}
+
 }  // namespace dd

@@ -190,8 +190,11 @@ struct dd_ctx {
   double csw = 0.0;
   double2* d_clov = nullptr;
   double2* d_clovi = nullptr;
+  float4* d_clovi32 = nullptr;    // A^{-1} hermitian-packed, FP32 [V][18] float4
+  float4* d_clovi_df = nullptr;   // A^{-1} hermitian-packed, double-float [V][36] float4
   bool clover_ready = false;
-  bool clover_active = false;     // inside a solve: FP64 hops apply A^{-1} (clov_inv)
+  bool clover_mixed_ready = false;   // the two packed tables match A^{-1}
+  bool clover_active = false;     // inside a solve: every hop applies A^{-1} (clov_inv)
   int* d_err = nullptr;           // [0]: device error word, set by kernels whose bounded waits give up;
                                   // [1]: work-queue counter of the persistent stencil
   // work space (krylov.cu) and cached batches
@@ -256,8 +259,11 @@ struct HopArgs {
   double* work_bytes;       // timing only: algorithmic bytes of the CTAs that ran
   double site_bytes;        // algorithmic bytes per output (site, rhs)
   int* err;                 // device error word (bounded waits that gave up)
-  const double2* clov_inv;  // FP64 only: A^{-1} [V][72] of the clover term applied to the
-                            // hop sum at the output site (left-preconditioned solves)
+  const void* clov_inv;     // A^{-1} of the clover term, applied to the hop sum at the output
+                            // site (left-preconditioned solves): FP64 [V][72] complex for
+                            // FP64 hops; hermitian-packed FP32 [V][72] floats for FP32 and
+                            // BF16-storage hops; hermitian-packed double-float [V][36]
+                            // float4 for the double-float residual hops
   int lb_fault;             // test hook of the bundle form (dd_debug_wait_fault): CTA 0 leaves
                             // one quarter's bulk copy unissued and waits a few microseconds
   int* queue;               // work-queue counter of the persistent bundle form
@@ -274,6 +280,8 @@ dd_status gauge_finish(dd_ctx* c);
 // v <- A v or A^{-1} v on both parity vectors of a batch (FP64)
 dd_status clover_build(dd_ctx* c);
 dd_status clover_apply(dd_ctx* c, const Batch& b, void* ve, void* vo, bool inverse, cudaStream_t s);
+dd_status clover_mixed_tables(dd_ctx* c);
+dd_status clover_apply_inv_df(dd_ctx* c, const Batch& b, void* ve, void* vo, cudaStream_t s);
 
 // layout conversions (stencil.cu)
 // b -> b, r = b (outer precision F64 or double-float), x = 0, in caller field order

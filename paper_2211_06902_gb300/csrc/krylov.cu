@@ -770,12 +770,14 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   const int nsys = b.nb * b.nrhs;
   const dd_prec ip = prm->inner_prec;
   const size_t c64 = 16, cin = prec_bytes(ip);
-  // clover term: left preconditioning by A^{-1} (clover.cu), FP64 solves only
+  // clover term: left preconditioning by A^{-1} (clover.cu); every hop of the
+  // solve applies A^{-1} of its output site, at the hop's own precision
   const bool clov = c->csw != 0.0;
   if (clov) {
-    if (ip != DD_F64) return fail(c, DD_EINVAL, "the clover term needs inner_prec f64");
-    if (prm->flags & DD_SOLVE_NET_GUESS) return fail(c, DD_EINVAL, "no learned guess with the clover term");
+    if (prm->flags & (DD_SOLVE_NET_GUESS | DD_SOLVE_NET_PRECOND))
+      return fail(c, DD_EINVAL, "the learned network does not include the clover term");
     if (!c->clover_ready && (e = clover_build(c)) != DD_OK) return e;
+    if (ip != DD_F64 && (e = clover_mixed_tables(c)) != DD_OK) return e;
   }
   struct ActiveGuard {
     dd_ctx* c;
@@ -838,7 +840,8 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   if ((e = launch_pack_init(c, b, b_user, be, bo, re, ro, xe, xo, op, s)) != DD_OK) return e;
   if (clov) {
     // solve (1 - kappa A^{-1} H) x = A^{-1} b: b and r = b preconditioned once
-    if ((e = clover_apply(c, b, be, bo, true, s)) != DD_OK) return e;
+    // (in FP64 arithmetic also for the double-float vectors of the mixed forms)
+    if ((e = dfo ? clover_apply_inv_df(c, b, be, bo, s) : clover_apply(c, b, be, bo, true, s)) != DD_OK) return e;
     DD_CUDA(c, cudaMemcpyAsync(re, be, ne * c64, cudaMemcpyDeviceToDevice, s));
     if (no > 0) DD_CUDA(c, cudaMemcpyAsync(ro, bo, no * c64, cudaMemcpyDeviceToDevice, s));
   }

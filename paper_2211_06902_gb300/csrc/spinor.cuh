@@ -258,6 +258,45 @@ __device__ __forceinline__ void clover_mul(const double2* __restrict__ M, double
   }
 }
 
+// The clover blocks are hermitian (A = 1 + i kappa c_sw sigma.F with i sigma.F
+// hermitian, and so its inverse), so the mixed-precision tables keep half of
+// each 6x6 block.  FP32 packing per chirality block: the 6 real diagonal
+// entries, then the 15 entries above the diagonal (row by row) as complex:
+// 36 floats (144 B), 72 floats per site.
+constexpr int CLOV_H32_FLOATS = 72;
+// (v_ch <- M_ch v_ch for both blocks) from an FP32 packed table
+__device__ __forceinline__ void clover_mul_h(const float4* __restrict__ M, float2 (&v)[12]) {
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    float f[36];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const float4 t = __ldg(M + ch * 9 + q);
+      f[4 * q] = t.x;
+      f[4 * q + 1] = t.y;
+      f[4 * q + 2] = t.z;
+      f[4 * q + 3] = t.w;
+    }
+    float2 w[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) w[r] = make_float2(f[r] * v[ch * 6 + r].x, f[r] * v[ch * 6 + r].y);
+    int z = 6;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r + 1; c < 6; ++c, z += 2) {
+        const float2 m = make_float2(f[z], f[z + 1]), x = v[ch * 6 + c], y = v[ch * 6 + r];
+        // w_r += m v_c ; w_c += conj(m) v_r
+        w[r].x = fmaf(m.x, x.x, fmaf(-m.y, x.y, w[r].x));
+        w[r].y = fmaf(m.x, x.y, fmaf(m.y, x.x, w[r].y));
+        w[c].x = fmaf(m.x, y.x, fmaf(m.y, y.y, w[c].x));
+        w[c].y = fmaf(m.x, y.y, fmaf(-m.y, y.x, w[c].y));
+      }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) v[ch * 6 + r] = w[r];
+  }
+}
+
 // ---- scalar helpers of the stencil epilogue (overloaded for double-float) ---------
 template <class C> struct ScalOf;
 template <> struct ScalOf<float2> { typedef float type; };

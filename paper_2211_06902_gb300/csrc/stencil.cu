@@ -30,6 +30,18 @@ __device__ __forceinline__ const __nv_bfloat162* links_of<__nv_bfloat162>(const 
 template <>
 __device__ __forceinline__ const df2s* links_of<df2s>(const DomInst& d) { return d.linkdf; }
 
+// A^{-1} of the clover term on the hop sum of output site g: FP64 from the full
+// table, FP32 and double-float from the hermitian-packed tables
+__device__ __forceinline__ void clover_epilogue(const void* t, long long g, double2 (&acc)[12]) {
+  clover_mul((const double2*)t + 72LL * g, acc);
+}
+__device__ __forceinline__ void clover_epilogue(const void* t, long long g, float2 (&acc)[12]) {
+  clover_mul_h((const float4*)t + (CLOV_H32_FLOATS / 4) * g, acc);
+}
+__device__ __forceinline__ void clover_epilogue(const void* t, long long g, dfc (&acc)[12]) {
+  clover_mul_h((const float4*)t + CLOV_HDF_F4 * g, acc);
+}
+
 template <int DIR, class S, class C>
 __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int n_out,
                                         int n_in, int j, const S* __restrict__ in_sys,
@@ -48,7 +60,7 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
 // grid: nitems[p] * nrhs CTAs, rhs fastest (the CTAs that share a site chunk,
 // and so its links, run together and hit L2); one output site per thread.
 // One CTA work unit t = item * nrhs + rhs of the hop launch.
-template <class S>
+template <class S, bool CLOV>
 __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, long long t,
                                          double* red) {
   typedef typename StoreTraits<S>::C C;
@@ -85,9 +97,10 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     hop_one<5, S>(acc, n0, p, i, n_out, n_in, jn[5], in_sys, lk);
     hop_one<6, S>(acc, n0, p, i, n_out, n_in, jn[6], in_sys, lk);
     hop_one<7, S>(acc, n0, p, i, n_out, n_in, jn[7], in_sys, lk);
-    if constexpr (std::is_same<C, double2>::value) {
-      // clover term: the hop sum times A^{-1} of the output site
-      if (a.clov_inv) clover_mul(a.clov_inv + 72LL * dp->glob[(p ? n0 : 0) + i], acc);
+    // clover term: the hop sum times A^{-1} of the output site (compiled into
+    // the FP64 forms and the clover instantiations only)
+    if constexpr (CLOV) {
+      if (a.clov_inv) clover_epilogue(a.clov_inv, dp->glob[(p ? n0 : 0) + i], acc);
     }
     const auto b = mkscal<C>(a.b);
 #pragma unroll
@@ -579,16 +592,16 @@ __global__ void __launch_bounds__(2 * HOP_THREADS, MINB) k_hop_split(BatchDev bd
 // of the register allocator; PERSIST = a grid of (SMs x MINB) CTAs that walks
 // the work units with a stride (one launch of persistent CTAs over blocks of
 // any size) instead of one CTA per unit.
-template <class S, int MINB, bool PERSIST, int R>
+template <class S, int MINB, bool PERSIST, int R, bool CLOV = std::is_same<S, double2>::value>
 __global__ void __launch_bounds__(HOP_THREADS, MINB) k_hop(BatchDev bd, HopArgs a, long long nunits) {
   __shared__ double red[32 * 4];
   if (PERSIST) {
     for (long long t = blockIdx.x; t < nunits; t += gridDim.x) {
-      if constexpr (R == 1) hop_unit<S>(bd, a, t, red);
+      if constexpr (R == 1) hop_unit<S, CLOV>(bd, a, t, red);
       else hop_unit_r<S, R>(bd, a, t, red);
     }
   } else {
-    if constexpr (R == 1) hop_unit<S>(bd, a, blockIdx.x, red);
+    if constexpr (R == 1) hop_unit<S, CLOV>(bd, a, blockIdx.x, red);
     else hop_unit_r<S, R>(bd, a, blockIdx.x, red);
   }
 }
@@ -732,7 +745,7 @@ constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64;
 // waits for the phase parity (ph >> q) & 1.  Returns the number of slots it used
 // (0 when the unit had nothing to do); every CTA-wide barrier inside is reached
 // by all threads or by none.
-template <class S, int RR, int QPC, int MAXR>
+template <class S, int RR, int QPC, int MAXR, bool CLOV>
 __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, long long unit,
                                        unsigned ph, bool fault) {
   typedef typename StoreTraits<S>::C C;
@@ -847,6 +860,13 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
     hop_lb_dir<5, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
     hop_lb_dir<0, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
     hop_lb_dir<4, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    if constexpr (CLOV) {
+      // clover term: the hop sums times A^{-1} of the output site
+      const long long gs = dp->glob[(p ? n0 : 0) + i];
+#pragma unroll
+      for (int k = 0; k < RR; ++k)
+        if (actk[k]) clover_epilogue(a.clov_inv, gs, acc[k]);
+    }
 #pragma unroll
     for (int k = 0; k < RR; ++k) {
       if (!actk[k]) continue;
@@ -981,7 +1001,7 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
   return nq;
 }
 
-template <class S, int MINB, int RR, int QPC, int MAXR>
+template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false>
 __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
   extern __shared__ __align__(128) unsigned char lb_smem[];
@@ -991,7 +1011,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     mbar_fence_init();
   }
   __syncthreads();
-  lb_unit<S, RR, QPC, MAXR>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
+  lb_unit<S, RR, QPC, MAXR, CLOV>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
 }
 
 // Persistent form with a work queue: a grid of (SMs x resident CTAs) CTAs pulls
@@ -1019,13 +1039,13 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     const bool stop = *(volatile const int*)a.err != 0;
     __syncthreads();                       // next_unit is rewritten only after all have read it
     if (u >= nunits || stop) break;
-    const int used = lb_unit<S, RR, QPC, MAXR>(bd, a, ngroups, rb, u, ph, a.lb_fault && blockIdx.x == 0 && first);
+    const int used = lb_unit<S, RR, QPC, MAXR, false>(bd, a, ngroups, rb, u, ph, a.lb_fault && blockIdx.x == 0 && first);
     ph ^= (1u << used) - 1u;
     first = false;
   }
 }
 
-template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS>
+template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
   const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
   const int rb = (bd.nrhs + ngroups - 1) / ngroups;
@@ -1042,7 +1062,7 @@ static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, 
     }
     if (a.dotqs) zero(3);
   }
-  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR>
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV>
       <<<(unsigned)(nitems_p * ngroups * NH), nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb);
 }
 
@@ -1079,6 +1099,8 @@ void hop_bundle_prepare() {
   const int h32 = 2 * lb_quarter_bytes<float2>() + 64, h16 = 2 * lb_quarter_bytes<__nv_bfloat162>() + 64;
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, true>, at, b32);
+  cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 4, 12, true>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<float2, 1, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 2, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 3, 4, 12>, at, b32);
@@ -1127,13 +1149,13 @@ static const HopVariant& variant_of(dd_prec prec, int v) {
   return t[v];
 }
 
-template <class S, int MINB, bool PERSIST, int R>
+template <class S, int MINB, bool PERSIST, int R, bool CLOV = std::is_same<S, double2>::value>
 static void launch_variant(const BatchDev& bd, const HopArgs& a, long long nitems_p, int nsm,
                            cudaStream_t s) {
   const long long nunits = nitems_p * ((bd.nrhs + R - 1) / R);
   long long grid = nunits;
   if (PERSIST) grid = std::min<long long>(nunits, (long long)nsm * MINB);
-  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST, R><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
+  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST, R, CLOV><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
 }
 
 template <class S, int MINB, bool PERSIST>
@@ -1148,11 +1170,19 @@ static void launch_split(const BatchDev& bd, const HopArgs& a, long long nitems_
 static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs& a, long long ni,
                          int nsm, cudaStream_t s) {
   if (prec == DD_DF64) {
-    launch_variant<df2s, 4, false, 1>(bd, a, ni, nsm, s);
+    if (a.clov_inv) launch_variant<df2s, 4, false, 1, true>(bd, a, ni, nsm, s);
+    else launch_variant<df2s, 4, false, 1>(bd, a, ni, nsm, s);
     return;
   }
   if (prec == DD_F64 && a.clov_inv) {      // the clover epilogue lives in the plain form
     launch_variant<double2, 3, false, 1>(bd, a, ni, nsm, s);
+    return;
+  }
+  if (a.clov_inv) {
+    // FP32 / BF16 storage with the clover term: the bundle form with the
+    // epilogue compiled in (no launch-form tuning)
+    if (prec == DD_F32) launch_lb<float2, 2, 1, LB_QUARTERS, LB_MAX_RHS, true>(bd, a, ni, s);
+    else launch_lb<__nv_bfloat162, 2, 1, LB_QUARTERS, LB_MAX_RHS, true>(bd, a, ni, s);
     return;
   }
   const HopVariant& hv = variant_of(prec, v);
@@ -1231,7 +1261,10 @@ dd_status launch_hop(dd_ctx* c, const Batch& b, dd_prec prec, const HopArgs& a0,
   BatchDev bd = batch_view(c, b);
   HopArgs a = a0;
   a.err = c->d_err;
-  a.clov_inv = (c->clover_active && prec == DD_F64) ? c->d_clovi : nullptr;
+  a.clov_inv = nullptr;
+  if (c->clover_active)
+    a.clov_inv = prec == DD_F64 ? (const void*)c->d_clovi
+                                : (prec == DD_DF64 ? (const void*)c->d_clovi_df : (const void*)c->d_clovi32);
   a.lb_fault = c->debug_wait_fault ? 1 : 0;
   a.queue = c->d_err + 1;
   int p = a.p_out;

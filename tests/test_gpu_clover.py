@@ -1,9 +1,11 @@
 """GPU clover term (the site-local term the paper admits in D, Sec. 1) against the
 oracle: D_X = A - kappa H restricted (FP64 stencil, 1e-12), block and frame
-solves (left-preconditioned by A^{-1}, FP64 to 1e-11: the oracle's own residual
-|b - D_X x| <= 1e-9 |b| and the oracle's solution to 1e-8), w and the multi-boson
-action (1e-8 / 1e-9), the dense check of Eq. (detD) with the clover term, the
-rebuild of A on a new gauge field and kappa, and the calls that refuse the term."""
+solves (left-preconditioned by A^{-1} to 1e-11, FP64 and the mixed forms with
+FP32 or BF16-storage inner solves and a double-float residual: the oracle's own
+residual |b - D_X x| <= 1e-9 |b| and the oracle's solution to 1e-8), w and the
+multi-boson action (1e-8 / 1e-9, FP64 and FP32 inner), the dense check of
+Eq. (detD) with the clover term, the rebuild of A on a new gauge field and
+kappa, and the calls that refuse the term."""
 
 import numpy as np
 import pytest
@@ -55,8 +57,9 @@ def test_stencil(name):
                 assert relerr(out[b, r], ref) < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_block_and_frame_solves(name):
+def test_block_and_frame_solves(name, prec):
     U, ctx, info, geo = _clover_case(name)
     o = Oracle(U, 0.13, geo, csw=CSW)
     L = geo.L
@@ -64,7 +67,9 @@ def test_block_and_frame_solves(name):
     sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
     b = synth.complex_gaussian(3, synth.TAG_RHS, (len(ids), 2, len(sites[0]), 12))
     x = np.zeros_like(b)
-    st = ctx.solve_blocks("omega", ids, 2, b, x, dd4d.params(1e-11, inner_prec="f64"))
+    prm = dd4d.params(1e-11, inner_prec=prec, inner_tol=1e-3 if prec == "bf16" else 3e-6,
+                      autotune=prec != "f64")
+    st = ctx.solve_blocks("omega", ids, 2, b, x, prm)
     assert st["status"] == dd4d.DD_OK, st
     for k in ids[:4]:
         for r in range(2):
@@ -76,13 +81,14 @@ def test_block_and_frame_solves(name):
     fs = ctx.geom_sites(dd4d.SET_LAMBDA1)
     bf = synth.complex_gaussian(4, synth.TAG_RHS, (1, 1, len(fs), 12))
     xf = np.zeros_like(bf)
-    assert ctx.solve_blocks("lambda1", None, 1, bf, xf, dd4d.params(1e-11))["status"] == 0
+    assert ctx.solve_blocks("lambda1", None, 1, bf, xf, prm)["status"] == 0
     f = to_field(L, fs, bf[0, 0])
     assert relerr(xf[0, 0], from_field(L, fs, o.frame_solver().solve_field(f))) < 1e-8
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_w_and_action(name):
+def test_w_and_action(name, prec):
     U, ctx, info, geo = _clover_case(name)
     o = Oracle(U, 0.13, geo, csw=CSW)
     dpi = ctx.geom_sites(dd4d.SET_DPI)
@@ -91,7 +97,7 @@ def test_w_and_action(name):
             for k in range(2)]
     vec = np.stack([c.reshape(V, 12)[dpi] for c in chis])
     out = np.zeros_like(vec)
-    prm = dd4d.params(1e-11, inner_prec="f64")
+    prm = dd4d.params(1e-11, inner_prec=prec)
     assert ctx.apply_w(2, vec, out, prm) == 0
     for k in range(2):
         assert relerr(out[k], o.apply_w(chis[k]).reshape(V, 12)[dpi]) < 1e-8
@@ -145,8 +151,27 @@ def test_refusals():
     n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
     b = synth.complex_gaussian(8, synth.TAG_RHS, (len(ids), 1, n, 12))
     with pytest.raises(dd4d.DDError):
-        ctx.solve_blocks("omega", ids, 1, b, np.zeros_like(b), dd4d.params(1e-10, inner_prec="f32"))
+        ctx.solve_blocks("omega", ids, 1, b, np.zeros_like(b), dd4d.params(1e-10, inner_prec="f32",
+                                                                            net_guess=True))
     dpi = ctx.geom_sites(dd4d.SET_DPI)
     chi = synth.complex_gaussian(8, synth.TAG_CHI, (1, len(dpi), 12))
     with pytest.raises(dd4d.DDError):
         ctx.mb_force([0.5 + 0.5j], chi)
+
+
+def test_mixed_matches_f64_and_rebuilds_tables():
+    """The mixed solve with the clover term agrees with the FP64 one (both to
+    1e-11, so within 1e-8), also after A changes with a new kappa (the packed
+    tables follow the FP64 one)."""
+    U, ctx, info, geo = _clover_case("8^4")
+    ids = list(range(info["nblocks"]))
+    n = len(ctx.geom_sites(dd4d.SET_OMEGA, 0))
+    b = synth.complex_gaussian(9, synth.TAG_RHS, (len(ids), 3, n, 12))
+    for kappa in (0.13, 0.125):
+        ctx.set_kappa(kappa)
+        x64 = np.zeros_like(b)
+        x32 = np.zeros_like(b)
+        assert ctx.solve_blocks("omega", ids, 3, b, x64, dd4d.params(1e-11, inner_prec="f64"))["status"] == 0
+        st = ctx.solve_blocks("omega", ids, 3, b, x32, dd4d.params(1e-11, inner_prec="f32"))
+        assert st["status"] == 0 and st["max_relres"] <= 1e-11
+        assert relerr(x32, x64) < 1e-8
