@@ -22,10 +22,17 @@ factorization of the fermion determinant", Lattice 2022):
                  factors of Eq. (detD), the stochastic samples of the
                  reweighting factor of Eq. (rw) and the force of the
                  factorized multi-boson action on the active links.
+* ``md``       - block-local molecular dynamics of the active links (Sec. 4,
+                 Eq. SFeffN; Sec. 5): pseudofermions for the block
+                 determinants, their force, the SU(3) link update and the
+                 leapfrog integrator.
 
 Parity status: every function is pinned by a CPU test against closed forms,
 identities of the paper or brute force.  W_1 is assembled from the blocks the
 paper prints (Sec. 3); it is fixed by the printed upper-right block of Eq.
 (offdiagW1), the gamma_5-hermiticity of diag(D^d, D^_{dPi1}) W_1 and the Schur
-complement of Eq. (Dtilde), and it satisfies Eqs. (detD) and (WW).
+complement of Eq. (Dtilde), and it satisfies Eqs. (detD) and (WW).  The
+molecular dynamics is pinned by the pseudofermion heat-bath identity, finite
+differences of its action, SU(3) closure, time reversibility and the dt^2
+scaling of the energy violation.
 """

@@ -41,6 +41,7 @@ TAG_RHS = 2
 TAG_CHI = 3
 TAG_PERTURB = 4
 TAG_NET = 5
+TAG_MOMENTA = 6
 
 
 def _mix64(z):
@@ -123,6 +124,14 @@ def complex_gaussian(seed, tag, shape):
     n = int(np.prod(shape))
     g = normals(seed, tag, 2 * n).reshape(n, 2) * np.sqrt(0.5)
     return (g[:, 0] + 1j * g[:, 1]).reshape(shape)
+
+
+def momenta(L, seed):
+    """Gaussian momenta P_t(x, mu) ~ N(0, 1), layout [L0,L1,L2,L3,4,8] float64
+    (the link momenta of a molecular-dynamics trajectory)."""
+    L = tuple(int(v) for v in L)
+    V = int(np.prod(L))
+    return normals(seed, TAG_MOMENTA, V * 32).reshape(L + (4, 8))
 
 
 def gauge_transform(seed, L):
