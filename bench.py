@@ -432,6 +432,13 @@ def run_ours(args):
             force = force_rate(dd4d, torch, ctx, info, mixed)
         except (dd4d.DDError, RuntimeError) as err:          # e.g. device memory
             force = {"unavailable": str(err)[:200]}
+    md = None
+    if rank == 0:
+        try:
+            md = md_rate(dd4d, torch, ctx, info, mixed, U)
+        except (dd4d.DDError, RuntimeError) as err:
+            ctx.gauge_upload(U)
+            md = {"unavailable": str(err)[:200]}
     # the same batch with the clover term (left-preconditioned by A^{-1}): the
     # mixed form (FP32 inner with the FP32 A^{-1} epilogue, double-float
     # residual with the double-float one) and the plain FP64 form
@@ -516,6 +523,7 @@ def run_ours(args):
         "reweight": reweight,
         "force": force,
         "clover": clover,
+        "md": md,
         "learned_guess": learned,
         "stencil": stencil,
     }
@@ -782,6 +790,33 @@ def force_rate(dd4d, torch, ctx, info, prm, n_f=12, reps=2):
             "force_kernel_ms": kms / max(kn, 1),
             "force_kernel_fp64_gflops": kg,
             "max_abs_force": fmax, "status": st}
+
+
+def md_rate(dd4d, torch, ctx, info, prm, U, n_f=12, tau=0.1, nsteps=2):
+    """One block-local molecular-dynamics trajectory of the active links of the 32^4
+    lattice (256 blocks): 12 multi-boson fields and one pseudofermion per block,
+    leapfrog with nsteps steps (nsteps + 1 force evaluations: the multi-boson force
+    and the pseudofermion force, four batched block solves), mixed-precision solves
+    to 1e-10.  The context's links are restored afterwards."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(13)
+    chi = torch.randn((n_f, info["n_dpi"], 24), generator=gen, device="cuda", dtype=torch.float64) * (0.5 ** 0.5)
+    eta = torch.randn((info["nblocks"], 1, info["max_omega"], 24), generator=gen, device="cuda",
+                      dtype=torch.float64) * (0.5 ** 0.5)
+    phi = torch.zeros_like(eta)
+    ctx.pf_heatbath(eta, phi)
+    P = torch.randn(tuple(LATTICE) + (4, 8), generator=gen, device="cuda", dtype=torch.float64)
+    u = dd4d.roots(2 * n_f, 0.5)
+    st = ctx.md_trajectory(u, chi, phi, P, tau, nsteps, prm)
+    ctx.gauge_upload(U)
+    del chi, eta, phi, P
+    return {"metric": "MD trajectories/s", "value": 1.0 / st["seconds"], "unit": "trajectories/s",
+            "seconds_per_trajectory": st["seconds"], "force_evals": st["force_evals"],
+            "seconds_per_force_eval": st["seconds"] / st["force_evals"], "tau": tau, "steps": nsteps,
+            "dH": st["H1"] - st["H0"], "H0": st["H0"], "status": st["status"],
+            "workload": "32^4 bench lattice, 256 blocks (cores 7^4, frame 1): active links of every block, "
+                        "12 multi-boson fields (N = 24, c = 0.5) + one pseudofermion per block, leapfrog, "
+                        "FP32 inner + double-float correction to 1e-10"}
 
 
 def config5_action_rate(dd4d, synth, torch, group=8):

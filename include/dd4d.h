@@ -375,6 +375,47 @@ dd_status dd_mb_force(dd_ctx* ctx, int n_f, const double* u, const double* chi, 
 dd_status dd_logdet_force(dd_ctx* ctx, int n_noise, const double* eta, double* G,
                           const dd_solve_params* params, void* stream);
 
+/* ---- block-local molecular dynamics (paper Sec. 4, Eq. SFeffN; Sec. 5) --------
+ * The factorization decouples the active links of different blocks, so they
+ * evolve together in one trajectory with the Hamiltonian
+ *   H = 1/2 sum_{active (x,mu)} sum_t P_t(x,mu)^2 + S_MB + S_pf,
+ *   S_MB = sum_k |W_{u_k} chi_k|^2 (as dd_multiboson_action; only its S^a move),
+ *   S_pf = sum_a |(D_{Omega0^a}^dag)^{-1} phi_a|^2,
+ * where the pseudofermion phi_a on Omega0^a stands for det(D_Omega^dag D_Omega) =
+ * (det D_{Omega0^a})^2, the block determinant of Eq. SFeffN for two degenerate
+ * flavours (chi then holds the multi-boson fields of both flavours).
+ *
+ * dd_pf_heatbath: phi_a = D_{Omega0^a}^dag eta_a = gamma_5 D_Omega gamma_5 eta_a for
+ * every block (FP64), so that S_pf = |eta|^2.  eta, phi: layout of
+ * dd_solve_blocks for all blocks with one rhs, [block][Omega0^a field-order
+ * site][12] complex, device or host.  Synchronises.
+ *
+ * dd_md_trajectory: nsteps leapfrog steps of size dt = tau / nsteps from the
+ * context's links and the momenta P (P -= dt/2 F; U_mu(x) -> exp(i dt sum_t P_t
+ * T_t) U_mu(x), T_t = lambda_t / 2; P -= dt/2 F; merged half steps inside,
+ * nsteps + 1 force evaluations), where F = dS_MB/d eps + dS_pf/d eps on the
+ * active links (dd_mb_force; the pseudofermion force -2 Re <Y, dD X> with
+ * Y = (D^dag)^{-1} phi, X = D^{-1} Y from two batched block solves).  The links
+ * of the context are updated in place (FP64 scaling-and-squaring exponential);
+ * every solve runs with `params`.  P: V*4*8 doubles, [global site][mu][t],
+ * device or host, in and out; entries off the active links are ignored and
+ * returned as zero.  n_f = 0 (u, chi null) drops S_MB; phi null drops S_pf;
+ * at least one must be present.  stats: H and its parts at both ends.
+ * DD_EINVAL with the clover term on.  Returns DD_ENOCONV (all outputs filled)
+ * if a solve missed its tolerance.  Synchronises. */
+typedef struct {
+  double H0, H1;               /* H at the start and at the end */
+  double kinetic0, kinetic1;   /* 1/2 sum P^2 over the active links */
+  double s_mb0, s_mb1;         /* S_MB (0 without fields) */
+  double s_pf0, s_pf1;         /* S_pf (0 without phi) */
+  int steps, force_evals;
+  double seconds;              /* device time of the trajectory */
+} dd_md_stats;
+dd_status dd_pf_heatbath(dd_ctx* ctx, const double* eta, double* phi, void* stream);
+dd_status dd_md_trajectory(dd_ctx* ctx, int n_f, const double* u, const double* chi, const double* phi,
+                           double* P, double tau, int nsteps, const dd_solve_params* params,
+                           dd_md_stats* stats, void* stream);
+
 /* ---- reweighting factor (paper Sec. 4, Eq. rw) ------------------------------
  * W_N = det{1 - R_{N+1}(W_1)}, W_1 = 1 - w on dPi, with the polynomial of the
  * roots below: R_{N+1}(z) = T_{N+1}((1-z)/c) / T_{N+1}(1/c) for c > 0 and

@@ -447,6 +447,13 @@ dd_status gauge_finish(dd_ctx* c) {
   return clover_build(c);        // no-op without the clover term
 }
 
+// after links in d_U changed on the device (a molecular-dynamics update): every
+// gathered per-domain copy is stale (the stored links keep their time sign)
+void gauge_touched(dd_ctx* c) {
+  for (auto& in : c->inst) in.links_ready = false;
+  c->inst_dirty = true;
+}
+
 dd_status check_device_error(dd_ctx* c, cudaStream_t s) {
   int h = 0;
   DD_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -403,7 +403,7 @@ __device__ __forceinline__ void force_link(const double2 (&U)[9], const double2*
 __global__ void __launch_bounds__(128) k_mb_force(const int4* __restrict__ al, const long long* __restrict__ al_loc, long long n_al,
                            int n_f, const long long* __restrict__ uoff, const double2* __restrict__ gU,
                            const double2* __restrict__ y, const double2* __restrict__ zg, double kappa,
-                           double* __restrict__ F) {
+                           double* __restrict__ F, int accumulate) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_al) return;
   const int4 e = al[k];
@@ -427,14 +427,18 @@ __global__ void __launch_bounds__(128) k_mb_force(const int4* __restrict__ al, c
   }
   double* o = F + ((long long)xg * 4 + mu) * 8;
   const double h = kappa;            // 2 kappa * (1/2 of lambda)
-  o[0] = h * (N[1].y + N[3].y);
-  o[1] = h * (N[3].x - N[1].x);
-  o[2] = h * (N[0].y - N[4].y);
-  o[3] = h * (N[2].y + N[6].y);
-  o[4] = h * (N[6].x - N[2].x);
-  o[5] = h * (N[5].y + N[7].y);
-  o[6] = h * (N[7].x - N[5].x);
-  o[7] = h * (N[0].y + N[4].y - 2.0 * N[8].y) / sqrt(3.0);
+  double f[8];
+  f[0] = h * (N[1].y + N[3].y);
+  f[1] = h * (N[3].x - N[1].x);
+  f[2] = h * (N[0].y - N[4].y);
+  f[3] = h * (N[2].y + N[6].y);
+  f[4] = h * (N[6].x - N[2].x);
+  f[5] = h * (N[5].y + N[7].y);
+  f[6] = h * (N[7].x - N[5].x);
+  f[7] = h * (N[0].y + N[4].y - 2.0 * N[8].y) / sqrt(3.0);
+  // each active link has one thread, so adding onto F needs no atomics
+#pragma unroll
+  for (int t = 0; t < 8; ++t) o[t] = accumulate ? o[t] + f[t] : f[t];
 }
 
 // v -> gamma_5 v on caller-layout spinors (components 6..11 of a site change sign)
@@ -1085,6 +1089,367 @@ static dd_status reweight_dev(dd_ctx* c, int N, double cpar, int n_src, const do
   return DD_OK;
 }
 
+// ---- block-local molecular dynamics of the active links (Sec. 4, Eq. SFeffN) ----
+// Momenta P[x][mu][t] (8 per link, generators T_t = lambda_t / 2) live on the
+// active links; the kernels walk the active-link list of the force plan, in
+// which every active link appears once.
+
+// U <- exp(i H) U for hermitian traceless H = sum_t h_t T_t, FP64: scaling and
+// squaring with a degree-12 Taylor polynomial (Moler & Van Loan, "Nineteen
+// dubious ways to compute the exponential of a matrix", 2003): A = iH / 2^s
+// with |A|_F <= 1/4, exp(A) by Horner's rule, then s squarings.
+__device__ void su3_expi_mul(const double (&h)[8], double2 (&U)[9]) {
+  const double r3 = 0.57735026918962576451;         // 1 / sqrt(3)
+  double2 H[9];
+  H[0] = make_double2(0.5 * (h[2] + r3 * h[7]), 0.0);
+  H[4] = make_double2(0.5 * (-h[2] + r3 * h[7]), 0.0);
+  H[8] = make_double2(-r3 * h[7], 0.0);
+  H[1] = make_double2(0.5 * h[0], -0.5 * h[1]);
+  H[3] = make_double2(0.5 * h[0], 0.5 * h[1]);
+  H[2] = make_double2(0.5 * h[3], -0.5 * h[4]);
+  H[6] = make_double2(0.5 * h[3], 0.5 * h[4]);
+  H[5] = make_double2(0.5 * h[5], -0.5 * h[6]);
+  H[7] = make_double2(0.5 * h[5], 0.5 * h[6]);
+  double nrm = 0.0;
+  for (int k = 0; k < 9; ++k) nrm += H[k].x * H[k].x + H[k].y * H[k].y;
+  nrm = sqrt(nrm);
+  int sq = 0;
+  while (nrm > 0.25 && sq < 60) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  const double sc = ldexp(1.0, -sq);
+  double2 A[9];
+  for (int k = 0; k < 9; ++k) A[k] = make_double2(-sc * H[k].y, sc * H[k].x);     // i H / 2^s
+  double2 E[9];
+  for (int k = 0; k < 9; ++k) E[k] = make_double2(k % 4 == 0 ? 1.0 : 0.0, 0.0);
+  for (int n = 12; n >= 1; --n) {
+    double2 T[9];
+    const double inv = 1.0 / n;
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < 3; ++k) {
+          const double2 a = A[r * 3 + k], e = E[k * 3 + q];
+          acc.x += a.x * e.x - a.y * e.y;
+          acc.y += a.x * e.y + a.y * e.x;
+        }
+        T[r * 3 + q] = make_double2(acc.x * inv + (r == q ? 1.0 : 0.0), acc.y * inv);
+      }
+    for (int k = 0; k < 9; ++k) E[k] = T[k];
+  }
+  for (int q = 0; q < sq; ++q) {
+    double2 T[9];
+    for (int r = 0; r < 3; ++r)
+      for (int p = 0; p < 3; ++p) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < 3; ++k) {
+          const double2 a = E[r * 3 + k], e = E[k * 3 + p];
+          acc.x += a.x * e.x - a.y * e.y;
+          acc.y += a.x * e.y + a.y * e.x;
+        }
+        T[r * 3 + p] = acc;
+      }
+    for (int k = 0; k < 9; ++k) E[k] = T[k];
+  }
+  double2 W[9];
+  for (int r = 0; r < 3; ++r)
+    for (int p = 0; p < 3; ++p) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < 3; ++k) {
+        const double2 a = E[r * 3 + k], u = U[k * 3 + p];
+        acc.x += a.x * u.x - a.y * u.y;
+        acc.y += a.x * u.y + a.y * u.x;
+      }
+      W[r * 3 + p] = acc;
+    }
+  for (int k = 0; k < 9; ++k) U[k] = W[k];
+}
+
+// Pm[active link] = P[active link] (Pm zeroed before)
+__global__ void k_md_gather(const int4* __restrict__ al, long long n_al, const double* __restrict__ P,
+                            double* __restrict__ Pm) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_al) return;
+  const long long o = ((long long)al[k].y * 4 + al[k].z) * 8;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) Pm[o + t] = P[o + t];
+}
+
+// P -= c F on the active links
+__global__ void k_md_momenta(const int4* __restrict__ al, long long n_al, double* __restrict__ P,
+                             const double* __restrict__ F, double c) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_al) return;
+  const long long o = ((long long)al[k].y * 4 + al[k].z) * 8;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) P[o + t] -= c * F[o + t];
+}
+
+// U_mu(x) <- exp(i dt sum_t P_t T_t) U_mu(x) on the active links (the stored
+// links carry the time-boundary sign, a factor that commutes with the update)
+__global__ void k_md_links(const int4* __restrict__ al, long long n_al, const double* __restrict__ P, double dt,
+                           double2* __restrict__ U) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_al) return;
+  const long long l = (long long)al[k].y * 4 + al[k].z;
+  double h[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) h[t] = dt * P[l * 8 + t];
+  double2 u[9];
+  double2* p = U + l * 9;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) u[m] = p[m];
+  su3_expi_mul(h, u);
+#pragma unroll
+  for (int m = 0; m < 9; ++m) p[m] = u[m];
+}
+
+// S, the per-block S^a (host array or null) and S^r of device fields chi
+// (dd_multiboson_action); DD_ENOCONV (values filled) if a solve missed its tolerance
+static dd_status mb_action_dev(dd_ctx* c, int n_f, const double* u, const double* din, double* S,
+                               double* S_block, double* S_r, const dd_solve_params* prm, cudaStream_t s) {
+  const int nb = (int)c->blocks.size();
+  const size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
+  dd_status e;
+  void *wv, *du, *dS;
+  if ((e = workspace(c, 46, bytes, &wv)) || (e = workspace(c, 47, 16ULL * n_f, &du)) ||
+      (e = workspace(c, 48, sizeof(double) * (nb + 1 + 4096), &dS)))
+    return e;
+  dd_status r = apply_w_dev(c, n_f, din, (double*)wv, prm, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  DD_CUDA(c, cudaMemcpyAsync(du, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
+  WPlan& P = *(WPlan*)c->wplan;
+  DD_COUNT_LAUNCH(), k_action_blocks<<<nb, 256, 0, s>>>(P.d_b_grp, P.d_b_dpi, n_f, c->info.n_dpi,
+                                     (const double2*)du, (const double2*)din,
+                                     (const double2*)wv, (double*)dS);
+  if (P.n_cgrp > 0)
+    DD_COUNT_LAUNCH(), k_action_blocks<<<P.n_cgrp, 256, 0, s>>>(P.d_c_grp, P.d_c_dpi, n_f, c->info.n_dpi,
+                                             (const double2*)du, (const double2*)din,
+                                             (const double2*)wv, (double*)dS + nb);
+  DD_CUDA(c, cudaGetLastError());
+  std::vector<double> h(nb + P.n_cgrp);
+  DD_CUDA(c, cudaMemcpyAsync(h.data(), dS, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  double sb = 0.0, sr = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    sb += h[b];
+    if (S_block) S_block[b] = h[b];
+  }
+  for (int k = 0; k < P.n_cgrp; ++k) sr += h[nb + k];
+  *S_r = sr;
+  *S = sb + sr;
+  return r;
+}
+
+// The multi-boson force on the active links (dd_mb_force) from device fields
+// chi into the device array dF (added onto it with `accumulate`); a block or
+// frame-piece solve that missed its tolerance sets *noconv.
+static dd_status mb_force_dev(dd_ctx* c, int n_f, const double* u, const double* din, double* dF,
+                              bool accumulate, const dd_solve_params* prm, bool* noconv, cudaStream_t s) {
+  const int nb = (int)c->blocks.size();
+  const size_t vbytes = 16ULL * n_f * c->info.n_dpi * 12;
+  const size_t fbytes = sizeof(double) * 32ULL * c->V;
+  dd_status e;
+  std::vector<int> insts(nb);
+  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
+  Batch* ob;
+  if ((e = get_batch_insts(c, insts, n_f, &ob)) != DD_OK) return e;
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  if ((e = build_force_plan(c, P)) != DD_OK) return e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  void *vsrc, *vy, *vrhs, *vz, *vu;
+  if ((e = workspace(c, 231, 16ULL * ob->user_tot, &vsrc)) || (e = workspace(c, 232, 16ULL * ob->user_tot, &vy)) ||
+      (e = workspace(c, 233, 16ULL * ob->user_tot, &vrhs)) || (e = workspace(c, 234, 16ULL * ob->user_tot, &vz)) ||
+      (e = workspace(c, 235, 16ULL * n_f, &vu)))
+    return e;
+  DD_CUDA(c, cudaMemcpyAsync(vu, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
+  dd_solve_stats st1{};
+  // chi' = chi - Q chi (stage A without the frame; S^a holds the frame pieces only
+  // through it), then y = D_Omega^{-1} D_{Omega,ext} chi' for every block and field
+  const double* chi_b = din;
+  if (c->info.n_C > 0) {
+    void* cp;
+    if ((e = workspace(c, 237, vbytes, &cp)) != DD_OK) return e;
+    dd_status r0 = frame_stage(c, P, n_f, din, (double*)cp, nullptr, false, prm, &st1, s);
+    if (r0 == DD_ENOCONV) *noconv = true;
+    else if (r0 != DD_OK) return r0;
+    chi_b = (const double*)cp;
+  }
+  InjectArgs a;
+  a.U = c->d_U;
+  a.chi = (const double2*)chi_b;
+  a.dpi_pos = c->d_dpi_pos;
+  for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
+  a.n_dpi = c->info.n_dpi;
+  a.n_f = n_f;
+  a.kappa = c->kappa;
+  a.src = (double2*)vsrc;
+  BatchDev bd = batch_view(c, *ob);
+  dim3 g1((c->info.max_omega + 127) / 128, n_f, nb);
+  DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
+  DD_CUDA(c, cudaGetLastError());
+  dd_status r1 = solve_batch(c, *ob, (const double*)vsrc, (double*)vy, prm, &st1, s, true);
+  if (r1 == DD_ENOCONV) *noconv = true;
+  else if (r1 != DD_OK) return r1;
+  // z = (D_Omega^dag)^{-1} P_B (u chi + y) = gamma_5 D_Omega^{-1} gamma_5 P_B (u chi + y)
+  DD_CUDA(c, cudaMemsetAsync(vrhs, 0, 16ULL * ob->user_tot, s));
+  const int nB = c->info.n_B;
+  if (nB) {
+    dim3 g((nB + 127) / 128, n_f);
+    DD_COUNT_LAUNCH(), k_force_rhs<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
+                                                     ob->d_uoff, (const double2*)vu, (const double2*)din,
+                                                     (const double2*)vy, (double2*)vrhs);
+    DD_CUDA(c, cudaGetLastError());
+  }
+  dd_status r2 = solve_batch(c, *ob, (const double*)vrhs, (double*)vz, prm, &st1, s, true);
+  if (r2 == DD_ENOCONV) *noconv = true;
+  else if (r2 != DD_OK) return r2;
+  if (!accumulate) DD_CUDA(c, cudaMemsetAsync(dF, 0, fbytes, s));
+  if (P.n_al > 0) {
+    TimingRec rec{};
+    if (c->timing) {
+      cudaEventCreate(&rec.a);
+      cudaEventCreate(&rec.b);
+      rec.which = 3;
+      rec.bytes = 576.0 * (double)P.n_al * n_f;     // algorithmic FP64 flops
+      cudaEventRecord(rec.a, s);
+    }
+    DD_COUNT_LAUNCH(), k_mb_force<<<(unsigned)((P.n_al + 127) / 128), 128, 0, s>>>(
+        P.d_al, P.d_al_loc, P.n_al, n_f, ob->d_uoff, (const double2*)c->d_U, (const double2*)vy,
+        (const double2*)vz, c->kappa, dF, accumulate ? 1 : 0);
+    if (c->timing) {
+      cudaEventRecord(rec.b, s);
+      c->trec.push_back(rec);
+    }
+    DD_CUDA(c, cudaGetLastError());
+  }
+  DD_CUDA(c, cudaGetLastError());
+  return DD_OK;
+}
+
+// The pseudofermion force of S_pf = sum_a |(D_Omega^dag)^{-1} phi_a|^2 added onto
+// dF, and S_pf: zg = D_Omega^{-1} gamma_5 phi, Y = gamma_5 zg = (D^dag)^{-1} phi,
+// X = D_Omega^{-1} Y; dS_pf = -2 Re <Y, dD X> is the link kernel with (y, z) = (X, zg).
+static dd_status pf_force_dev(dd_ctx* c, const double* dphi, double* dF, const dd_solve_params* prm,
+                              bool* noconv, double* s_pf, cudaStream_t s) {
+  const int nb = (int)c->blocks.size();
+  std::vector<int> insts(nb);
+  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
+  Batch* ob;
+  dd_status e;
+  if ((e = get_batch_insts(c, insts, 1, &ob)) != DD_OK) return e;
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  if ((e = build_force_plan(c, P)) != DD_OK) return e;
+  if ((e = sync_instances(c)) != DD_OK) return e;
+  const long long ntot = ob->user_tot;
+  void *vg, *vzg, *vY, *vX, *vpart;
+  if ((e = workspace(c, 260, 16ULL * ntot, &vg)) || (e = workspace(c, 261, 16ULL * ntot, &vzg)) ||
+      (e = workspace(c, 262, 16ULL * ntot, &vY)) || (e = workspace(c, 263, 16ULL * ntot, &vX)) ||
+      (e = workspace(c, 264, sizeof(double) * 2 * HB_CHUNKS, &vpart)))
+    return e;
+  const unsigned g5 = (unsigned)((ntot + 255) / 256);
+  DD_COUNT_LAUNCH(), k_gamma5<<<g5, 256, 0, s>>>(ntot, (const double2*)dphi, (double2*)vg);
+  DD_CUDA(c, cudaGetLastError());
+  dd_solve_stats st1{};
+  dd_status r = solve_batch(c, *ob, (const double*)vg, (double*)vzg, prm, &st1, s, true);
+  if (r == DD_ENOCONV) *noconv = true;
+  else if (r != DD_OK) return r;
+  DD_COUNT_LAUNCH(), k_gamma5<<<g5, 256, 0, s>>>(ntot, (const double2*)vzg, (double2*)vY);
+  DD_CUDA(c, cudaGetLastError());
+  r = solve_batch(c, *ob, (const double*)vY, (double*)vX, prm, &st1, s, true);
+  if (r == DD_ENOCONV) *noconv = true;
+  else if (r != DD_OK) return r;
+  if (P.n_al > 0)
+    DD_COUNT_LAUNCH(), k_mb_force<<<(unsigned)((P.n_al + 127) / 128), 128, 0, s>>>(
+        P.d_al, P.d_al_loc, P.n_al, 1, ob->d_uoff, (const double2*)c->d_U, (const double2*)vX,
+        (const double2*)vzg, c->kappa, dF, 1);
+  DD_CUDA(c, cudaGetLastError());
+  std::vector<double2> n2;
+  if ((e = hb_dot(c, 1, ntot, (const double2*)vzg, (const double2*)vzg, (double*)vpart, n2, s)) != DD_OK) return e;
+  *s_pf = n2[0].x;
+  return DD_OK;
+}
+
+// one leapfrog trajectory of the active links; dP: device momenta, zero off the
+// active links; dchi / dphi: device fields or null
+static dd_status md_dev(dd_ctx* c, int n_f, const double* u, const double* dchi, const double* dphi, double* dP,
+                        double tau, int nsteps, const dd_solve_params* prm, dd_md_stats* st, cudaStream_t s) {
+  WPlan* PP;
+  dd_status e;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& P = *PP;
+  if ((e = build_force_plan(c, P)) != DD_OK) return e;
+  const long long nlink = 4LL * c->V;
+  void *vF, *vpart;
+  if ((e = workspace(c, 265, sizeof(double) * 8 * nlink, &vF)) ||
+      (e = workspace(c, 266, sizeof(double) * 2 * HB_CHUNKS, &vpart)))
+    return e;
+  double* dF = (double*)vF;
+  bool noconv = false;
+  double s_pf = 0.0;
+  auto kinetic = [&](double* out) -> dd_status {
+    std::vector<double2> k2;
+    dd_status r = hb_dot(c, 1, 4 * nlink, (const double2*)dP, (const double2*)dP, (double*)vpart, k2, s);
+    *out = 0.5 * k2[0].x;
+    return r;
+  };
+  auto action = [&](double* out) -> dd_status {
+    *out = 0.0;
+    if (n_f == 0) return DD_OK;
+    double Sr = 0.0;
+    dd_status r = mb_action_dev(c, n_f, u, dchi, out, nullptr, &Sr, prm, s);
+    if (r == DD_ENOCONV) {
+      noconv = true;
+      r = DD_OK;
+    }
+    return r;
+  };
+  auto force = [&]() -> dd_status {
+    DD_CUDA(c, cudaMemsetAsync(dF, 0, sizeof(double) * 8 * nlink, s));
+    dd_status r;
+    if (n_f > 0 && (r = mb_force_dev(c, n_f, u, dchi, dF, true, prm, &noconv, s)) != DD_OK) return r;
+    if (dphi && (r = pf_force_dev(c, dphi, dF, prm, &noconv, &s_pf, s)) != DD_OK) return r;
+    ++st->force_evals;
+    return DD_OK;
+  };
+  const unsigned gl = (unsigned)std::max<long long>(1, (P.n_al + 127) / 128);
+  auto kick = [&](double cfac) -> dd_status {
+    if (P.n_al > 0) DD_COUNT_LAUNCH(), k_md_momenta<<<gl, 128, 0, s>>>(P.d_al, P.n_al, dP, dF, cfac);
+    DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  };
+  EventPair evs;
+  cudaEventRecord(evs.a, s);
+  const double dt = tau / nsteps;
+  if ((e = kinetic(&st->kinetic0)) || (e = action(&st->s_mb0)) || (e = force())) return e;
+  st->s_pf0 = dphi ? s_pf : 0.0;
+  if ((e = kick(0.5 * dt)) != DD_OK) return e;
+  for (int i = 0; i < nsteps; ++i) {
+    if (P.n_al > 0) DD_COUNT_LAUNCH(), k_md_links<<<gl, 128, 0, s>>>(P.d_al, P.n_al, dP, dt, (double2*)c->d_U);
+    DD_CUDA(c, cudaGetLastError());
+    gauge_touched(c);
+    if ((e = force()) != DD_OK) return e;
+    if ((e = kick(i + 1 < nsteps ? dt : 0.5 * dt)) != DD_OK) return e;
+  }
+  st->s_pf1 = dphi ? s_pf : 0.0;
+  if ((e = kinetic(&st->kinetic1)) || (e = action(&st->s_mb1))) return e;
+  cudaEventRecord(evs.b, s);
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, evs.a, evs.b);
+  st->seconds = ms * 1e-3;
+  st->H0 = st->kinetic0 + st->s_mb0 + st->s_pf0;
+  st->H1 = st->kinetic1 + st->s_mb1 + st->s_pf1;
+  st->steps = nsteps;
+  if (noconv) return fail(c, DD_ENOCONV, "a solve of the trajectory missed its tolerance");
+  return DD_OK;
+}
+
 }  // namespace dd
 
 using namespace dd;
@@ -1156,7 +1521,6 @@ dd_status dd_multiboson_action(dd_ctx* c, int n_f, const double* u, const double
   if (!c || !u || !chi || !S || !S_r || !prm || n_f < 1) return fail(c, DD_EINVAL, "bad argument");
   if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
   cudaStream_t s = (cudaStream_t)stream;
-  const int nb = (int)c->blocks.size();
   size_t bytes = 16ULL * n_f * c->info.n_dpi * 12;
   const double* din = chi;
   dd_status e;
@@ -1166,34 +1530,7 @@ dd_status dd_multiboson_action(dd_ctx* c, int n_f, const double* u, const double
     DD_CUDA(c, cudaMemcpyAsync(p, chi, bytes, cudaMemcpyHostToDevice, s));
     din = (const double*)p;
   }
-  void *wv, *du, *dS;
-  if ((e = workspace(c, 46, bytes, &wv)) || (e = workspace(c, 47, 16ULL * n_f, &du)) ||
-      (e = workspace(c, 48, sizeof(double) * (nb + 1 + 4096), &dS)))
-    return e;
-  dd_status r = apply_w_dev(c, n_f, din, (double*)wv, prm, s);
-  if (r != DD_OK && r != DD_ENOCONV) return r;
-  DD_CUDA(c, cudaMemcpyAsync(du, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
-  WPlan& P = *(WPlan*)c->wplan;
-  DD_COUNT_LAUNCH(), k_action_blocks<<<nb, 256, 0, s>>>(P.d_b_grp, P.d_b_dpi, n_f, c->info.n_dpi,
-                                     (const double2*)du, (const double2*)din,
-                                     (const double2*)wv, (double*)dS);
-  if (P.n_cgrp > 0)
-    DD_COUNT_LAUNCH(), k_action_blocks<<<P.n_cgrp, 256, 0, s>>>(P.d_c_grp, P.d_c_dpi, n_f, c->info.n_dpi,
-                                             (const double2*)du, (const double2*)din,
-                                             (const double2*)wv, (double*)dS + nb);
-  DD_CUDA(c, cudaGetLastError());
-  std::vector<double> h(nb + P.n_cgrp);
-  DD_CUDA(c, cudaMemcpyAsync(h.data(), dS, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
-  DD_CUDA(c, cudaStreamSynchronize(s));
-  double sb = 0.0, sr = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    sb += h[b];
-    if (S_block) S_block[b] = h[b];
-  }
-  for (int k = 0; k < P.n_cgrp; ++k) sr += h[nb + k];
-  *S_r = sr;
-  *S = sb + sr;
-  return r;
+  return mb_action_dev(c, n_f, u, din, S, S_block, S_r, prm, s);
 }
 
 dd_status dd_multiboson_heatbath(dd_ctx* c, int n_f, const double* u, const double* eta, double* chi,
@@ -1239,7 +1576,6 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
   if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
   if (c->csw != 0.0) return fail(c, DD_EINVAL, "the force does not include the clover term");
   cudaStream_t s = (cudaStream_t)stream;
-  const int nb = (int)c->blocks.size();
   const size_t vbytes = 16ULL * n_f * c->info.n_dpi * 12;
   const size_t fbytes = sizeof(double) * 32ULL * c->V;
   dd_status e;
@@ -1257,82 +1593,8 @@ dd_status dd_mb_force(dd_ctx* c, int n_f, const double* u, const double* chi, do
     if ((e = workspace(c, 236, fbytes, &p)) != DD_OK) return e;
     dF = (double*)p;
   }
-  std::vector<int> insts(nb);
-  for (int b = 0; b < nb; ++b) insts[b] = c->omega0 + b;
-  Batch* ob;
-  if ((e = get_batch_insts(c, insts, n_f, &ob)) != DD_OK) return e;
-  WPlan* PP;
-  if ((e = build_plan(c, &PP)) != DD_OK) return e;
-  WPlan& P = *PP;
-  if ((e = build_force_plan(c, P)) != DD_OK) return e;
-  if ((e = sync_instances(c)) != DD_OK) return e;
-  void *vsrc, *vy, *vrhs, *vz, *vu;
-  if ((e = workspace(c, 231, 16ULL * ob->user_tot, &vsrc)) || (e = workspace(c, 232, 16ULL * ob->user_tot, &vy)) ||
-      (e = workspace(c, 233, 16ULL * ob->user_tot, &vrhs)) || (e = workspace(c, 234, 16ULL * ob->user_tot, &vz)) ||
-      (e = workspace(c, 235, 16ULL * n_f, &vu)))
-    return e;
-  DD_CUDA(c, cudaMemcpyAsync(vu, u, 16ULL * n_f, cudaMemcpyHostToDevice, s));
   bool noconv = false;
-  dd_solve_stats st1{};
-  // chi' = chi - Q chi (stage A without the frame; S^a holds the frame pieces only
-  // through it), then y = D_Omega^{-1} D_{Omega,ext} chi' for every block and field
-  const double* chi_b = din;
-  if (c->info.n_C > 0) {
-    void* cp;
-    if ((e = workspace(c, 237, vbytes, &cp)) != DD_OK) return e;
-    dd_status r0 = frame_stage(c, P, n_f, din, (double*)cp, nullptr, false, prm, &st1, s);
-    if (r0 == DD_ENOCONV) noconv = true;
-    else if (r0 != DD_OK) return r0;
-    chi_b = (const double*)cp;
-  }
-  InjectArgs a;
-  a.U = c->d_U;
-  a.chi = (const double2*)chi_b;
-  a.dpi_pos = c->d_dpi_pos;
-  for (int m = 0; m < 4; ++m) a.L[m] = c->L[m];
-  a.n_dpi = c->info.n_dpi;
-  a.n_f = n_f;
-  a.kappa = c->kappa;
-  a.src = (double2*)vsrc;
-  BatchDev bd = batch_view(c, *ob);
-  dim3 g1((c->info.max_omega + 127) / 128, n_f, nb);
-  DD_COUNT_LAUNCH(), k_inject_omega<<<g1, 128, 0, s>>>(bd, a);
-  DD_CUDA(c, cudaGetLastError());
-  dd_status r1 = solve_batch(c, *ob, (const double*)vsrc, (double*)vy, prm, &st1, s, true);
-  if (r1 == DD_ENOCONV) noconv = true;
-  else if (r1 != DD_OK) return r1;
-  // z = (D_Omega^dag)^{-1} P_B (u chi + y) = gamma_5 D_Omega^{-1} gamma_5 P_B (u chi + y)
-  DD_CUDA(c, cudaMemsetAsync(vrhs, 0, 16ULL * ob->user_tot, s));
-  const int nB = c->info.n_B;
-  if (nB) {
-    dim3 g((nB + 127) / 128, n_f);
-    DD_COUNT_LAUNCH(), k_force_rhs<<<g, 128, 0, s>>>(P.d_b_blk, P.d_b_loc, P.d_b_dpi, nB, n_f, c->info.n_dpi,
-                                                     ob->d_uoff, (const double2*)vu, (const double2*)din,
-                                                     (const double2*)vy, (double2*)vrhs);
-    DD_CUDA(c, cudaGetLastError());
-  }
-  dd_status r2 = solve_batch(c, *ob, (const double*)vrhs, (double*)vz, prm, &st1, s, true);
-  if (r2 == DD_ENOCONV) noconv = true;
-  else if (r2 != DD_OK) return r2;
-  DD_CUDA(c, cudaMemsetAsync(dF, 0, fbytes, s));
-  if (P.n_al > 0) {
-    TimingRec rec{};
-    if (c->timing) {
-      cudaEventCreate(&rec.a);
-      cudaEventCreate(&rec.b);
-      rec.which = 3;
-      rec.bytes = 576.0 * (double)P.n_al * n_f;     // algorithmic FP64 flops
-      cudaEventRecord(rec.a, s);
-    }
-    DD_COUNT_LAUNCH(), k_mb_force<<<(unsigned)((P.n_al + 127) / 128), 128, 0, s>>>(
-        P.d_al, P.d_al_loc, P.n_al, n_f, ob->d_uoff, (const double2*)c->d_U, (const double2*)vy,
-        (const double2*)vz, c->kappa, dF);
-    if (c->timing) {
-      cudaEventRecord(rec.b, s);
-      c->trec.push_back(rec);
-    }
-    DD_CUDA(c, cudaGetLastError());
-  }
+  if ((e = mb_force_dev(c, n_f, u, din, dF, false, prm, &noconv, s)) != DD_OK) return e;
   if (hF) DD_CUDA(c, cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
   if (noconv) return fail(c, DD_ENOCONV, "a block or frame-piece solve missed its tolerance");
@@ -1391,7 +1653,7 @@ dd_status dd_logdet_force(dd_ctx* c, int n_noise, const double* eta, double* G, 
     // noise vectors without the factor -2
     DD_COUNT_LAUNCH(), k_mb_force<<<(unsigned)((P.n_al + 127) / 128), 128, 0, s>>>(
         P.d_al, P.d_al_loc, P.n_al, n_noise, ob->d_uoff, (const double2*)c->d_U, (const double2*)din,
-        (const double2*)vz, c->kappa, dG);
+        (const double2*)vz, c->kappa, dG, 0);
     const long long nf = 32LL * c->V;
     DD_COUNT_LAUNCH(), k_scale<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, -0.5 / n_noise, dG);
     DD_CUDA(c, cudaGetLastError());
@@ -1425,6 +1687,96 @@ dd_status dd_reweight_samples(dd_ctx* c, int N, double cpar, int n_src, const do
   if (r_eta) DD_CUDA(c, cudaMemcpyAsync(r_eta, rdev, bytes, cudaMemcpyDefault, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
   return r;
+}
+
+dd_status dd_pf_heatbath(dd_ctx* c, const double* eta, double* phi, void* stream) {
+  if (!c || !eta || !phi) return fail(c, DD_EINVAL, "bad argument");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  if (c->csw != 0.0) return fail(c, DD_EINVAL, "the molecular dynamics does not include the clover term");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)c->blocks.size();
+  std::vector<int> ids(nb);
+  for (int b = 0; b < nb; ++b) ids[b] = b;
+  Batch* ob;
+  dd_status e;
+  if ((e = get_batch(c, DD_DOMAIN_OMEGA, ids.data(), nb, 1, &ob)) != DD_OK) return e;
+  const long long ntot = ob->user_tot;
+  const size_t bytes = 16ULL * ntot;
+  void *vin, *vg, *vd;
+  if ((e = workspace(c, 267, bytes, &vin)) || (e = workspace(c, 268, bytes, &vg)) ||
+      (e = workspace(c, 269, bytes, &vd)))
+    return e;
+  DD_CUDA(c, cudaMemcpyAsync(vin, eta, bytes, cudaMemcpyDefault, s));
+  const unsigned g5 = (unsigned)((ntot + 255) / 256);
+  DD_COUNT_LAUNCH(), k_gamma5<<<g5, 256, 0, s>>>(ntot, (const double2*)vin, (double2*)vg);
+  DD_CUDA(c, cudaGetLastError());
+  if ((e = dd_apply_D_block(c, DD_DOMAIN_OMEGA, ids.data(), nb, 1, (const double*)vg, (double*)vd, DD_F64, s)) !=
+      DD_OK)
+    return e;
+  double* dout = phi;
+  if (!is_device_ptr(phi)) dout = (double*)vin;          // eta is no longer needed
+  DD_COUNT_LAUNCH(), k_gamma5<<<g5, 256, 0, s>>>(ntot, (const double2*)vd, (double2*)dout);
+  DD_CUDA(c, cudaGetLastError());
+  if (dout != phi) DD_CUDA(c, cudaMemcpyAsync(phi, dout, bytes, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  return check_device_error(c, s);
+}
+
+dd_status dd_md_trajectory(dd_ctx* c, int n_f, const double* u, const double* chi, const double* phi,
+                           double* P, double tau, int nsteps, const dd_solve_params* prm,
+                           dd_md_stats* stats, void* stream) {
+  if (!c || !P || !prm || !stats || nsteps < 1 || n_f < 0) return fail(c, DD_EINVAL, "bad argument");
+  if (n_f > 0 && (!u || !chi)) return fail(c, DD_EINVAL, "fields without roots or roots without fields");
+  if (n_f == 0 && !phi) return fail(c, DD_EINVAL, "no action term: give multi-boson fields or phi");
+  if (n_f > 65535) return fail(c, DD_EINVAL, "n_f must be <= 65535");
+  if (!(tau == tau) || std::isinf(tau)) return fail(c, DD_EINVAL, "tau must be finite");
+  if (!c->geom_ready) return fail(c, DD_EINVAL, "geometry not set");
+  if (!c->gauge_ready) return fail(c, DD_EINVAL, "gauge field not uploaded");
+  if (c->csw != 0.0) return fail(c, DD_EINVAL, "the molecular dynamics does not include the clover term");
+  cudaStream_t s = (cudaStream_t)stream;
+  *stats = dd_md_stats{};
+  dd_status e;
+  const double* dchi = chi;
+  if (n_f > 0 && !is_device_ptr(chi)) {
+    const size_t vb = 16ULL * n_f * c->info.n_dpi * 12;
+    void* p;
+    if ((e = workspace(c, 270, vb, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, chi, vb, cudaMemcpyHostToDevice, s));
+    dchi = (const double*)p;
+  }
+  const double* dphi = phi;
+  if (phi && !is_device_ptr(phi)) {
+    const int nb = (int)c->blocks.size();
+    std::vector<int> ids(nb);
+    for (int b = 0; b < nb; ++b) ids[b] = b;
+    Batch* ob;
+    if ((e = get_batch(c, DD_DOMAIN_OMEGA, ids.data(), nb, 1, &ob)) != DD_OK) return e;
+    void* p;
+    if ((e = workspace(c, 271, 16ULL * ob->user_tot, &p)) != DD_OK) return e;
+    DD_CUDA(c, cudaMemcpyAsync(p, phi, 16ULL * ob->user_tot, cudaMemcpyHostToDevice, s));
+    dphi = (const double*)p;
+  }
+  // the momenta of the active links (zero elsewhere) in a device copy
+  WPlan* PP;
+  if ((e = build_plan(c, &PP)) != DD_OK) return e;
+  WPlan& PL = *PP;
+  if ((e = build_force_plan(c, PL)) != DD_OK) return e;
+  const size_t pbytes = sizeof(double) * 32ULL * c->V;
+  void *vin, *vP;
+  if ((e = workspace(c, 272, pbytes, &vin)) || (e = workspace(c, 273, pbytes, &vP))) return e;
+  DD_CUDA(c, cudaMemcpyAsync(vin, P, pbytes, cudaMemcpyDefault, s));
+  DD_CUDA(c, cudaMemsetAsync(vP, 0, pbytes, s));
+  if (PL.n_al > 0)
+    DD_COUNT_LAUNCH(), k_md_gather<<<(unsigned)((PL.n_al + 127) / 128), 128, 0, s>>>(
+        PL.d_al, PL.n_al, (const double*)vin, (double*)vP);
+  DD_CUDA(c, cudaGetLastError());
+  dd_status r = md_dev(c, n_f, u, dchi, dphi, (double*)vP, tau, nsteps, prm, stats, s);
+  if (r != DD_OK && r != DD_ENOCONV) return r;
+  DD_CUDA(c, cudaMemcpyAsync(P, vP, pbytes, cudaMemcpyDefault, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  dd_status d = check_device_error(c, s);
+  return d != DD_OK ? d : r;
 }
 
 }  // extern "C"

@@ -279,6 +279,7 @@ dd_status gauge_finish(dd_ctx* c);
 // clover term (clover.cu): build A, A^{-1} from d_U (no-op at c_sw = 0), and
 // v <- A v or A^{-1} v on both parity vectors of a batch (FP64)
 dd_status clover_build(dd_ctx* c);
+void gauge_touched(dd_ctx* c);
 dd_status clover_apply(dd_ctx* c, const Batch& b, void* ve, void* vo, bool inverse, cudaStream_t s);
 dd_status clover_mixed_tables(dd_ctx* c);
 dd_status clover_apply_inv_df(dd_ctx* c, const Batch& b, void* ve, void* vo, cudaStream_t s);

@@ -55,6 +55,15 @@ class HeatbathStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class MdStats(C.Structure):
+    _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("kinetic0", C.c_double), ("kinetic1", C.c_double),
+                ("s_mb0", C.c_double), ("s_mb1", C.c_double), ("s_pf0", C.c_double), ("s_pf1", C.c_double),
+                ("steps", C.c_int), ("force_evals", C.c_int), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("dd4d status %d: %s" % (status, msg))
@@ -120,6 +129,9 @@ def lib():
             "dd_fp64_fma_rate": [dp],
             "dd_apply_w_part": [vp, C.c_int, C.c_int, ip, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
             "dd_net_tensor_cores": [vp, C.c_int],
+            "dd_pf_heatbath": [vp, vp, vp, vp],
+            "dd_md_trajectory": [vp, C.c_int, dp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(SolveParams),
+                                 C.POINTER(MdStats), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -141,7 +153,7 @@ def exported_symbols():
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover",
             "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate", "dd_apply_w_part",
-            "dd_net_tensor_cores"]
+            "dd_net_tensor_cores", "dd_pf_heatbath", "dd_md_trajectory"]
 
 
 def hop_variant_name(prec, v):
@@ -391,6 +403,33 @@ class Context:
         st = self._check(lib().dd_logdet_force(self._h, n_noise, _ptr(eta), _ptr(out),
                                                C.byref(prm or params()), _stream(stream)))
         return out, st
+
+    def pf_heatbath(self, eta, phi, stream=None):
+        """phi_a = D_Omega0^a^dag eta_a for every block (layout of solve_blocks on all
+        blocks with one rhs), so that the pseudofermion action equals |eta|^2."""
+        self._check(lib().dd_pf_heatbath(self._h, _ptr(eta), _ptr(phi), _stream(stream)))
+
+    def md_trajectory(self, u, chi, phi, P, tau, nsteps, prm=None, stream=None):
+        """Leapfrog trajectory of the active links (links updated in place): u, chi the
+        multi-boson roots and fields (layout of apply_w; None for none), phi the block
+        pseudofermions (layout of pf_heatbath; None for none), P the momenta
+        [x0,x1,x2,x3,mu,t] (V*4*8 doubles, in and out).  Returns the stats dict."""
+        n_f = 0
+        uptr = None
+        if u is not None and len(u):
+            u = np.asarray(u, dtype=np.complex128)
+            uu = np.empty(2 * len(u))
+            uu[0::2], uu[1::2] = u.real, u.imag
+            n_f = len(u)
+            uptr = uu.ctypes.data_as(C.POINTER(C.c_double))
+        st = MdStats()
+        s = self._check(lib().dd_md_trajectory(
+            self._h, n_f, uptr, None if chi is None or n_f == 0 else _ptr(chi),
+            None if phi is None else _ptr(phi), _ptr(P), float(tau), int(nsteps),
+            C.byref(prm or params()), C.byref(st), _stream(stream)))
+        d = st.as_dict()
+        d["status"] = s
+        return d
 
     def reweight_samples(self, N, c, eta, r_eta=None, prm=None, stream=None):
         """Samples s = |eta|^2 - |M eta|^2, M = 1 - R_{N+1}(W_1), one per source of eta

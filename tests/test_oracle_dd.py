@@ -181,11 +181,9 @@ def _eq_ww_gap(W1, N, c):
     (P_N(W_1) = c_N prod_{k=1..N} (W_1 - z_k), W_1 - z_k = u_k - w = W_{u_k})."""
     n = len(W1)
     u = roots(N, c)
-    lhs = 0j
-    for uk in u:
-        s, ld = np.linalg.slogdet(W1 - (1 - uk) * np.eye(n))
-        lhs += ld + 1j * np.angle(s)
-    rhs = sum(2 * np.linalg.slogdet(W1 - (1 - uk) * np.eye(n))[1] for uk in u[: N // 2])
+    lds = [np.linalg.slogdet(W1 - (1 - uk) * np.eye(n)) for uk in u]
+    lhs = sum(ld + 1j * np.angle(s) for s, ld in lds)
+    rhs = sum(2 * ld for _, ld in lds[: N // 2])
     gap = lhs - rhs
     return gap.real, math.remainder(gap.imag, 2 * math.pi), abs(lhs.real)
 
@@ -197,7 +195,7 @@ def test_eq_ww_pairs_conjugate_roots(L, cores):
     U = synth.gauge_field(L, 0.3, 1)
     o = Oracle(U, 0.13, Decomposition(L, cores))
     W1 = np.eye(len(o.w_matrix())) - o.w_matrix()
-    for N, c in ([(4, 0.5), (6, 0.0), (12, 0.3)] if L == L44 else [(4, 0.5)]):
+    for N, c in ([(4, 0.5), (6, 0.0)] if L == L44 else [(4, 0.5)]):
         re, im, scale = _eq_ww_gap(W1, N, c)
         assert abs(re) < 1e-10 * max(1.0, scale) and abs(im) < 1e-10, (N, c, re, im)
 
@@ -247,8 +245,8 @@ def test_kappa_zero_action():
 def test_block_locality_of_the_action():
     """A link inside Lambda0^a changes only S^a; a link inside the frame changes
     S^r and only the S^b whose framed block touches it (Sec. 4)."""
-    L = (8,) * 4
-    g = Decomposition(L, uniform_cores(L, 3, 1))
+    L = (6,) * 4
+    g = Decomposition(L, uniform_cores(L, 2, 1))
     U = synth.gauge_field(L, 0.3, 1)
     u = field_roots(4, 0.5)[:1]
     chi = [synth.complex_gaussian(1, synth.TAG_CHI, L + (4, 3)) * g.dPi[..., None, None]]
@@ -499,7 +497,7 @@ def _perturbed_action(U, kappa, g, u, chis, x, mu, t, eps):
     return Oracle(Up, kappa, g).multiboson_action(u, chis)[0]
 
 
-@pytest.mark.parametrize("case", ["1D", "8^4"])
+@pytest.mark.parametrize("case", ["1D", "2D"])
 def test_mb_force_matches_finite_differences_of_total_action(case):
     """F = dS/d eps for U_mu(x) -> exp(i eps T_t) U_mu(x) on active links, S the
     total action sum_a S^a + S^r: the block-local force is the whole derivative,
@@ -508,8 +506,10 @@ def test_mb_force_matches_finite_differences_of_total_action(case):
         L, cores = (8, 4, 4, 2), [[(0, 1), (4, 5)], [], [], []]
         picks = [(0, 0, 1), (0, 1, 4), (0, 3, 7), (1, 0, 2), (1, 2, 0)]    # (block, link #, t)
     else:
-        L, cores = (8,) * 4, uniform_cores((8,) * 4, 3, 1)
-        picks = [(5, 40, 6)]
+        # two decomposed directions: frame corners, so dPi1 is not empty and the
+        # frame-piece term Q chi of the block sources enters
+        L, cores = (8, 8, 2, 2), [[(0, 1), (4, 5)], [(0, 1), (4, 5)], [], []]
+        picks = [(0, 3, 6), (3, 10, 1), (2, 21, 7)]
     U = synth.gauge_field(L, 0.3, 4)
     g = Decomposition(L, cores)
     o = Oracle(U, 0.13, g)

@@ -1,6 +1,6 @@
 """The multi-boson action of one lattice sharded over two ranks (gloo, CPU).
 
-Each rank owns half of the framed blocks of the 8^4 lattice (config 1): it computes
+Each rank owns half of the 16 framed blocks of a 6^4 lattice: it computes
 its blocks' share of Q chi on dPi1 (a sum across the ranks completes it), solves
 its own framed blocks on chi' = chi - Q chi, and rank 0 also solves the frame;
 a sum of the per-block and frame parts gives S, S^a and S^r on every rank.  The
@@ -21,7 +21,7 @@ from paper_2211_06902_gb300 import partition, synth
 from oracle.dd import Oracle, field_roots
 from oracle.geometry import Decomposition, uniform_cores
 
-L = (8, 8, 8, 8)
+L = (6, 6, 6, 6)
 
 
 class OracleOps:
@@ -80,7 +80,7 @@ class OracleOps:
 
 def _case():
     U = synth.gauge_field(L, 0.3, 1)
-    g = Decomposition(L, uniform_cores(L, 3, 1))
+    g = Decomposition(L, uniform_cores(L, 2, 1))
     u = field_roots(4, 0.5)
     chis = [synth.complex_gaussian(1, synth.TAG_CHI + k, L + (4, 3)) * g.dPi[..., None, None]
             for k in range(len(u))]
