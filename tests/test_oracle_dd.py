@@ -65,12 +65,24 @@ def test_det_factorization_identity(L, cores):
     assert abs(f["D"][0].imag) < 1e-12                  # det D real (gamma_5-hermiticity)
 
 
+_W_CACHE = {}
+
+
+def _w_case(L, cores, seed=1):
+    """(U, geometry, oracle, dense w) of one lattice; the dense w is assembled once
+    per case and shared by the tests that read it (none of them modifies it)."""
+    key = (tuple(L), repr(cores), seed)
+    if key not in _W_CACHE:
+        U = synth.gauge_field(L, 0.3, seed)
+        g = Decomposition(L, cores)
+        o = Oracle(U, 0.13, g)
+        _W_CACHE[key] = (U, g, o, o.w_matrix())
+    return _W_CACHE[key]
+
+
 def test_det_identity_fails_for_a_wrong_w():
     """A plausible mistake (dropping the frame solve) breaks Eq. (detD)."""
-    U = synth.gauge_field(L44, 0.3, 1)
-    g = Decomposition(L44, uniform_cores(L44, 1, 1))
-    o = Oracle(U, 0.13, g)
-    w = o.w_matrix()
+    U, g, o, w = _w_case(L44, uniform_cores(L44, 1, 1))
     dpi = g.sites(g.dPi)
     isC = np.repeat(g.C.ravel()[dpi], 12)
     w_bad = w.copy()
@@ -127,15 +139,13 @@ def test_w1_is_fixed_by_the_printed_blocks(L, cores):
     D_{Phi,dL0a} and D^_{dPi1} = D_{dPi1} - D_{dPi1,E} D_E^-1 D_{E,dPi1}; (iii) the Schur
     complement of M onto dLambda0 is Eq. (Dtilde)'s D~ = D_{dL0} - D_{dL0,L0bar} D_{L0bar}^-1
     D_{L0bar,dL0} - D_{dL0,Lambda1} D_{Lambda1}^-1 D_{Lambda1,dL0}."""
-    U = synth.gauge_field(L, 0.3, 1)
-    g = Decomposition(L, cores)
-    o = Oracle(U, 0.13, g)
+    U, g, o, w = _w_case(L, cores)
     d = _Dense(U, 0.13, g)
     dpi = g.sites(g.dPi)
     pos = np.full(int(np.prod(L)), -1)
     pos[dpi] = np.arange(len(dpi))
     r = lambda sites: d.idx(pos[np.asarray(sites)])            # rows of W_1 (dPi order)
-    W1 = np.eye(12 * len(dpi)) - o.w_matrix()
+    W1 = np.eye(12 * len(dpi)) - w
     Bs, Cs, Es = g.sites(g.B), g.sites(g.C), g.sites(g.E)
     Diag = np.zeros_like(W1)
     for a in range(g.nblocks):
@@ -192,9 +202,8 @@ def _eq_ww_gap(W1, N, c):
 def test_eq_ww_pairs_conjugate_roots(L, cores):
     """Eq. (WW) holds exactly: the roots k and N+1-k are complex conjugates and
     det(W_1 - conj z) = conj det(W_1 - z) (the characteristic polynomial of W_1 is real)."""
-    U = synth.gauge_field(L, 0.3, 1)
-    o = Oracle(U, 0.13, Decomposition(L, cores))
-    W1 = np.eye(len(o.w_matrix())) - o.w_matrix()
+    U, g, o, w = _w_case(L, cores)
+    W1 = np.eye(len(w)) - w
     for N, c in ([(4, 0.5), (6, 0.0)] if L == L44 else [(4, 0.5)]):
         re, im, scale = _eq_ww_gap(W1, N, c)
         assert abs(re) < 1e-10 * max(1.0, scale) and abs(im) < 1e-10, (N, c, re, im)
@@ -205,9 +214,7 @@ def test_dirichlet_completion_keeps_det_but_breaks_eq_ww():
     extension (rows dLambda0^a: P D_Omega^-1 D_{Omega,ext}; rows dPi1:
     P D_Lambda1^-1 D_{Lambda1,dL0}) gives the same det W_1 (Eq. detD) but a
     characteristic polynomial that is not real, so Eq. (WW) fails."""
-    U = synth.gauge_field(L44, 0.3, 1)
-    g = Decomposition(L44, uniform_cores(L44, 1, 1))
-    o = Oracle(U, 0.13, g)
+    U, g, o, w = _w_case(L44, uniform_cores(L44, 1, 1))
     d = _Dense(U, 0.13, g)
     dpi = g.sites(g.dPi)
     pos = np.full(int(np.prod(L44)), -1)
@@ -221,7 +228,7 @@ def test_dirichlet_completion_keeps_det_but_breaks_eq_ww():
     l1, Bs, Cs = g.sites(g.Lambda1), g.sites(g.B), g.sites(g.C)
     G = d.inv(l1) @ d(l1, Bs)
     Wd[np.ix_(r(Cs), r(Bs))] += G[d.idx(np.searchsorted(l1, Cs))]
-    W1 = np.eye(len(Wd)) - o.w_matrix()
+    W1 = np.eye(len(Wd)) - w
     assert abs(np.linalg.slogdet(Wd)[1] - np.linalg.slogdet(W1)[1]) < 1e-10
     re, im, _ = _eq_ww_gap(Wd, 4, 0.5)
     assert abs(re) > 1e-4
