@@ -458,6 +458,7 @@ def run_ours(args):
                 c1.record(stream)
                 torch.cuda.synchronize()
                 return c0.elapsed_time(c1), cst
+            c_A = ctx.clover_cond()
             mms, mst = clover_time(mixed)
             cms, cst = clover_time(plain)
             ctx.set_clover(0.0)
@@ -467,6 +468,8 @@ def run_ours(args):
                       "plain_f64": {"value": units / (cms * 1e-3), "ms_per_step": cms,
                                     "max_iters": cst["max_iters"], "max_relres": cst["max_relres"]},
                       "mixed_speedup_vs_plain_f64": cms / mms,
+                      "cond_bound_c_A": c_A,
+                      "tol_preconditioned": TOL / c_A,
                       "mixed_ms_without_clover": ms,
                       "table_build_s": build_s,
                       "workload": "the bench batch (256 framed blocks of 9^4 x 12 rhs, 32^4) with "

@@ -87,9 +87,10 @@ typedef struct {
 
 typedef struct {
   double tol;          /* stop when |b - D x| <= tol |b| per system (e.g. 1e-10); with the
-                          clover term on (dd_set_clover) the test is on the left-preconditioned
-                          residual, |A^{-1}(b - D x)| <= tol |A^{-1} b|, so the true relative
-                          residual is bounded by tol times the condition number of A */
+                          clover term on (dd_set_clover) the solver tests the left-preconditioned
+                          residual, |A^{-1}(b - D x)| <= (tol / c_A) |A^{-1} b| with
+                          c_A = max_x |A_x|_inf max_x |A_x^{-1}|_inf >= cond_2(A), which keeps
+                          the true residual |b - D x| <= tol |b| */
   int maxiter;         /* Krylov iterations cap per system (inner ones for mixed) */
   dd_prec inner_prec;  /* DD_F64: plain FP64 BiCGstab; DD_F32 / DD_BF16: inner
                           solve at that precision with FP64 defect correction */
@@ -157,8 +158,10 @@ dd_status dd_set_kappa(dd_ctx* ctx, double kappa);
  * (DD_F64 only); dd_solve_blocks and everything built on it (dd_apply_w, the
  * action, the heat-bath, the reweighting samples, dd_logdet_check) solve
  * (1 - kappa A^{-1} H) x = A^{-1} b with the even-odd Schur form
- * 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe, so the tolerance applies to the
- * residual A^{-1}(b - D x) relative to A^{-1} b.  Every hop of a solve applies
+ * 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe, to tol / c_A on the residual
+ * A^{-1}(b - D x) relative to A^{-1} b (c_A: the bound of cond_2(A) from the
+ * row-sum norms of the hermitian blocks of A and A^{-1}, computed with the
+ * tables), so the true residual stays within tol.  Every hop of a solve applies
  * A^{-1} of its output site at its own precision: FP64 for DD_F64 solves; for
  * DD_F32 and DD_BF16 inner solves an FP32 copy of A^{-1} (each hermitian block
  * packed to its diagonal and upper triangle, 288 B per site), and for their
@@ -169,6 +172,9 @@ dd_status dd_set_kappa(dd_ctx* ctx, double kappa);
  * (DD_SOLVE_NET_GUESS, DD_SOLVE_NET_PRECOND) return DD_EINVAL with the term
  * on.  c_sw = 0 turns it off (the default). */
 dd_status dd_set_clover(dd_ctx* ctx, double c_sw);
+/* c_A = max_x |A_x|_inf * max_x |A_x^{-1}|_inf, the bound of cond_2(A) the solves
+ * divide their tolerance by (1 without the term). */
+dd_status dd_clover_cond(dd_ctx* ctx, double* c_A);
 
 /* Gauge links U_mu(x) in SU(3) (paper Sec. 1).  Host buffer, layout
  * [site (global index)][mu 0..3][3][3] complex128 (row-major 3x3).  The

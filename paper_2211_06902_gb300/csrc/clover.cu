@@ -16,6 +16,7 @@
 // the right-hand side is multiplied by A^{-1} once.  The even-odd Schur form of
 // that operator is 1 - kappa^2 A_ee^{-1} H_eo A_oo^{-1} H_oe.
 #include <cmath>
+#include <cstring>
 #include <complex>
 #include <vector>
 
@@ -255,6 +256,26 @@ __global__ void k_clover_apply(BatchDev bd, int p, double2* v, const double2* __
   st_site<12>(base, n, i, w);
 }
 
+// one thread per (site, chirality block): the largest absolute row sum of the
+// 6x6 block of A (m = 0) and of A^{-1} (m = 1), folded into out[m] by an atomic
+// max on the bit pattern (non-negative doubles order like their bits).  For a
+// hermitian matrix the row-sum norm bounds the spectral norm.
+__global__ void k_clover_rownorm(const double2* __restrict__ A, const double2* __restrict__ Ai, long long V,
+                                 unsigned long long* out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 2 * V) return;
+  for (int m = 0; m < 2; ++m) {
+    const double2* a = (m ? Ai : A) + k * 36;
+    double best = 0.0;
+    for (int r = 0; r < 6; ++r) {
+      double sum = 0.0;
+      for (int c = 0; c < 6; ++c) sum += hypot(a[r * 6 + c].x, a[r * 6 + c].y);
+      best = fmax(best, sum);
+    }
+    atomicMax(out + m, (unsigned long long)__double_as_longlong(best));
+  }
+}
+
 // one thread per (site, chirality block): the hermitian-packed FP32 and
 // double-float copies of A^{-1} (diagonal real parts, then the entries above
 // the diagonal row by row)
@@ -355,7 +376,22 @@ dd_status clover_build(dd_ctx* c) {
   DD_COUNT_LAUNCH(), k_clover_invert<<<(unsigned)((2LL * c->V + 127) / 128), 128>>>(c->d_clov, c->d_clovi,
                                                                                     (long long)c->V);
   DD_CUDA(c, cudaGetLastError());
-  DD_CUDA(c, cudaDeviceSynchronize());
+  // cond_2(A) <= max_x |A_x|_inf * max_x |A_x^{-1}|_inf (hermitian chiral blocks)
+  unsigned long long* dn = nullptr;
+  if ((e = dalloc(c, (void**)&dn, 2 * sizeof(unsigned long long))) != DD_OK) return e;
+  DD_CUDA(c, cudaMemset(dn, 0, 2 * sizeof(unsigned long long)));
+  DD_COUNT_LAUNCH(), k_clover_rownorm<<<(unsigned)((2LL * c->V + 127) / 128), 128>>>(c->d_clov, c->d_clovi,
+                                                                                     (long long)c->V, dn);
+  DD_CUDA(c, cudaGetLastError());
+  unsigned long long hn[2] = {0, 0};
+  DD_CUDA(c, cudaMemcpy(hn, dn, sizeof hn, cudaMemcpyDeviceToHost));
+  dfree(dn);
+  double na, ni;
+  memcpy(&na, &hn[0], sizeof na);
+  memcpy(&ni, &hn[1], sizeof ni);
+  c->clover_cond = na * ni;
+  if (!(c->clover_cond >= 1.0) || std::isinf(c->clover_cond))
+    return fail(c, DD_EINVAL, "the clover term A is singular or ill-conditioned");
   c->clover_ready = true;
   return DD_OK;
 }
@@ -379,6 +415,16 @@ dd_status clover_apply(dd_ctx* c, const Batch& b, void* ve, void* vo, bool inver
 using namespace dd;
 
 extern "C" {
+
+dd_status dd_clover_cond(dd_ctx* c, double* c_A) {
+  if (!c || !c_A) return DD_EINVAL;
+  if (c->csw != 0.0 && !c->clover_ready) {
+    dd_status e = clover_build(c);
+    if (e != DD_OK) return e;
+  }
+  *c_A = c->csw != 0.0 ? c->clover_cond : 1.0;
+  return DD_OK;
+}
 
 dd_status dd_set_clover(dd_ctx* c, double csw) {
   if (!c) return DD_EINVAL;

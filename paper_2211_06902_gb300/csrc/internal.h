@@ -193,6 +193,7 @@ struct dd_ctx {
   float4* d_clovi32 = nullptr;    // A^{-1} hermitian-packed, FP32 [V][18] float4
   float4* d_clovi_df = nullptr;   // A^{-1} hermitian-packed, double-float [V][36] float4
   bool clover_ready = false;
+  double clover_cond = 1.0;          // max |A_x|_inf * max |A_x^{-1}|_inf >= cond_2(A)
   bool clover_mixed_ready = false;   // the two packed tables match A^{-1}
   bool clover_active = false;     // inside a solve: every hop applies A^{-1} (clov_inv)
   int* d_err = nullptr;           // [0]: device error word, set by kernels whose bounded waits give up;

@@ -779,6 +779,15 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     if (!c->clover_ready && (e = clover_build(c)) != DD_OK) return e;
     if (ip != DD_F64 && (e = clover_mixed_tables(c)) != DD_OK) return e;
   }
+  // The solve stops on the preconditioned residual A^{-1}(b - D x) relative to
+  // A^{-1} b; running it to tol / c_A with c_A >= |A| |A^{-1}| keeps the true
+  // residual |b - D x| <= tol |b|.
+  dd_solve_params prm_clov;
+  if (clov) {
+    prm_clov = *prm;
+    prm_clov.tol = prm->tol / c->clover_cond;
+    prm = &prm_clov;
+  }
   struct ActiveGuard {
     dd_ctx* c;
     ActiveGuard(dd_ctx* cc, bool on) : c(cc) { c->clover_active = on; }

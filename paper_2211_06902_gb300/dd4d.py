@@ -130,6 +130,7 @@ def lib():
             "dd_apply_w_part": [vp, C.c_int, C.c_int, ip, C.c_int, vp, vp, C.POINTER(SolveParams), vp],
             "dd_net_tensor_cores": [vp, C.c_int],
             "dd_pf_heatbath": [vp, vp, vp, vp],
+            "dd_clover_cond": [vp, dp],
             "dd_md_trajectory": [vp, C.c_int, dp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(SolveParams),
                                  C.POINTER(MdStats), vp],
         }
@@ -153,7 +154,7 @@ def exported_symbols():
             "dd_set_hop_variant", "dd_hop_variants", "dd_hop_variant_name",
             "dd_apply_D_block_noalloc", "dd_reweight_samples", "dd_mb_force", "dd_set_clover",
             "dd_debug_wait_fault", "dd_logdet_force", "dd_fp64_fma_rate", "dd_apply_w_part",
-            "dd_net_tensor_cores", "dd_pf_heatbath", "dd_md_trajectory"]
+            "dd_net_tensor_cores", "dd_pf_heatbath", "dd_md_trajectory", "dd_clover_cond"]
 
 
 def hop_variant_name(prec, v):
@@ -281,6 +282,12 @@ class Context:
     def set_clover(self, csw):
         """Clover term c_sw (0 = off): A(x) = 1 + i kappa c_sw sum sigma F in D."""
         self._check(lib().dd_set_clover(self._h, float(csw)))
+
+    def clover_cond(self):
+        """The bound c_A >= cond_2(A) the solves divide their tolerance by (1 without the term)."""
+        v = C.c_double(0)
+        self._check(lib().dd_clover_cond(self._h, C.byref(v)))
+        return v.value
 
     def gauge_upload(self, U):
         U = np.ascontiguousarray(U, dtype=np.complex128)
