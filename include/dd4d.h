@@ -117,6 +117,14 @@ typedef struct {
                                 one-thread kernel sets its condition from the device-side
                                 count of running systems (no host polls inside the inner
                                 solve; ignored while kernel timing is on) */
+#define DD_SOLVE_GRAPH_SOLVE 128 /* the whole mixed-precision solve (FP32 or BF16 inner BiCGstab)
+                                as ONE CUDA graph launch after b is packed: conditional WHILE
+                                and IF nodes run the defect-correction cycles, their inner
+                                solves, the verification of an updated residual and the
+                                choice between a true and an updated residual, each decided
+                                by a one-thread kernel from device-side counts (no host poll
+                                in the solve); taken once the launch form is tuned, and not
+                                with FGMRES or while kernel timing is on */
 #define DD_SOLVE_FGMRES 16   /* inner solve by flexible GMRES(restart) instead of BiCGstab
                                 (FP32 or FP64 inner precision; the host checks after
                                 every Arnoldi step) */

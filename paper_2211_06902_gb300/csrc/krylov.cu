@@ -10,6 +10,7 @@
 // products.  All per-system scalars live on the device; the host only polls
 // the number of unconverged systems every `check_every` iterations.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -302,9 +303,11 @@ __global__ void k_sc_bnorm(ScalarArgs a, const double* partial_o, const int* ib_
 // largest relative residual (as ordered bits of a non-negative double)
 __global__ void k_sc_outer(ScalarArgs a, const double* partial_o, const int* ib_o,
                            long long stride_o, double margin2, int* count,
-                           unsigned long long* maxrel, double* relres) {
+                           unsigned long long* maxrel, double* relres, const int* last_true = nullptr) {
   int sys = blockIdx.x * blockDim.x + threadIdx.x;
   if (sys >= a.nsys) return;
+  // inside the whole-solve graph the margin follows the device-side flag
+  if (last_true) margin2 = *last_true ? 1.0 : 0.25;
   int j = sys / a.nrhs, r = sys % a.nrhs;
   SysState& s = a.st[sys];
   double re = sum_slot(a.partial, 0, a.stride, a.item_begin[j], a.item_begin[j + 1], a.nrhs, r).x;
@@ -458,33 +461,102 @@ __global__ void k_loop_cond(const int* count, int* iter, int maxiter, cudaGraphC
   cudaGraphSetConditional(h, (*count > 0 && it < maxiter) ? 1u : 0u);
 }
 
+// The launches of the inner BiCGstab on one batch (van der Vorst 1992), shared
+// by the host-driven loop and the captured graphs.
+// Device-side state of the outer defect-correction loop of the whole-solve graph
+struct OuterState {
+  int cyc;         // correction cycles run
+  int last_true;   // the current residual is a true one (b - D x)
+  int tr;          // this cycle ends with a true residual
+  int osteps;      // outer-loop passes (bounded)
+  int iters;       // inner iterations started, all cycles
+  int n_verify;    // verification passes
+  int n_tr;        // cycles that ended with a true residual
+  int pad;
+};
+
+__global__ void k_outer_init(OuterState* o) {
+  o->cyc = 0;
+  o->last_true = 1;
+  o->tr = 1;
+  o->osteps = 0;
+  o->iters = 0;
+  o->n_verify = 0;
+  o->n_tr = 0;
+}
+
+// After the outer check (k_sc_outer): verify (all stopped on an updated
+// residual), run a cycle (systems left and cycles left), or stop; the loop
+// also stops after max_outer + 3 passes whatever the flags say.
+__global__ void k_outer_decide(OuterState* o, const int* count, const unsigned long long* maxrel_bits,
+                               int max_outer, int f32, double theta, double inner_tol, double tol,
+                               cudaGraphConditionalHandle h_verify, cudaGraphConditionalHandle h_cycle,
+                               cudaGraphConditionalHandle h_outer) {
+  const int n = count[0];
+  const double maxrel = __longlong_as_double((long long)maxrel_bits[0]);
+  const int verify = (n == 0 && !o->last_true) ? 1 : 0;
+  const int cycle = (n > 0 && o->cyc < max_outer) ? 1 : 0;
+  o->tr = (!f32 || o->cyc == 0 || maxrel > theta || inner_tol * maxrel <= 0.25 * tol) ? 1 : 0;
+  o->osteps += 1;
+  cudaGraphSetConditional(h_verify, verify);
+  cudaGraphSetConditional(h_cycle, cycle);
+  cudaGraphSetConditional(h_outer, ((verify || cycle) && o->osteps < max_outer + 3) ? 1u : 0u);
+}
+
+__global__ void k_outer_verified(OuterState* o) {
+  o->last_true = 1;
+  o->n_verify += 1;
+}
+
+__global__ void k_outer_cycle_end(OuterState* o, const int* d_iter) {
+  o->last_true = o->tr;
+  o->n_tr += o->tr;
+  o->cyc += 1;
+  o->iters += *d_iter;
+}
+
+__global__ void k_cond_set(const int* flag, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, (!flag || *flag) ? 1u : 0u);
+}
+
 template <class S>
-dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs& w, SysState* st,
-                       double* partial, int* d_count, int* h_count, const void* rhs,
-                       double inner_tol2, double floor_frac, int maxiter, int check_every,
-                       bool use_graph, cudaStream_t s, int* iters_run, bool device_loop = false) {
-  BatchDev bd = batch_view(c, b);
-  const int nsys = b.nb * b.nrhs;
-  const long long stride = (long long)b.nitems[0] * b.nrhs;
-  ScalarArgs sa{st, partial, b.d_item_begin[0], stride, nsys, b.nrhs};
-  const int sth = 128, sbl = (nsys + sth - 1) / sth;
-  dim3 eg(b.nitems[0], b.nrhs);
-  const double k2 = c->kappa * c->kappa;
+struct BicgOps {
+  dd_ctx* c;
+  const Batch& b;
+  dd_prec prec;
+  InnerVecs w;
+  SysState* st;
+  double* partial;
+  BatchDev bd;
+  int nsys;
+  ScalarArgs sa;
+  int sth = 128, sbl;
+  dim3 eg;
+  double k2;
   // seed of the generated shadow vector r^ (any nonzero constant)
-  const unsigned rseed = 0x2211u;
-  DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, (const S*)rhs, (S*)w.r, (S*)w.p, (S*)w.x, rseed,
-                                                        partial);
-  DD_COUNT_LAUNCH(), k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
-  DD_CUDA(c, cudaGetLastError());
-  const int* act = (const int*)((const char*)st + offsetof(SysState, active));
-  const int act_stride = (int)(sizeof(SysState) / sizeof(int));
-  // one BiCGstab iteration for every active system (van der Vorst 1992),
-  // enqueued on stream s (captured into a graph when s is the capture stream).
-  // p enters the iteration already updated (by the previous k_xrp_update, or
-  // p = r at the start), so an iteration is: check, v = M p with (r^, v),
-  // alpha, s, t = M s with (r^, t), (t, s), |t|^2, (r^, s), omega and beta,
-  // and the fused x, r, p update.
-  auto iteration = [&](bool check, cudaStream_t s) -> dd_status {
+  static constexpr unsigned rseed = 0x2211u;
+  const int* act;
+  int act_stride;
+  BicgOps(dd_ctx* cc, const Batch& bb, dd_prec pp, const InnerVecs& ww, SysState* ss, double* part)
+      : c(cc), b(bb), prec(pp), w(ww), st(ss), partial(part), bd(batch_view(cc, bb)), nsys(bb.nb * bb.nrhs),
+        sa{ss, part, bb.d_item_begin[0], (long long)bb.nitems[0] * bb.nrhs, bb.nb * bb.nrhs, bb.nrhs},
+        sbl((bb.nb * bb.nrhs + 127) / 128), eg(bb.nitems[0], bb.nrhs), k2(cc->kappa * cc->kappa),
+        act((const int*)((const char*)ss + offsetof(SysState, active))),
+        act_stride((int)(sizeof(SysState) / sizeof(int))) {}
+  // r = p = rhs, x = 0, rho = (r^, r), the per-system inner targets
+  dd_status init(const void* rhs, double inner_tol2, double floor_frac, cudaStream_t s) {
+    DD_COUNT_LAUNCH(), k_inner_init<S><<<eg, 128, 0, s>>>(bd, (const S*)rhs, (S*)w.r, (S*)w.p, (S*)w.x, rseed,
+                                                          partial);
+    DD_COUNT_LAUNCH(), k_sc_inner_init<<<sbl, sth, 0, s>>>(sa, inner_tol2, floor_frac);
+    DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  }
+  // one BiCGstab iteration for every active system, enqueued on stream s
+  // (captured into a graph when s is capturing).  p enters the iteration
+  // already updated (by the previous k_xrp_update, or p = r at the start), so
+  // an iteration is: check, v = M p with (r^, v), alpha, s, t = M s with
+  // (r^, t), (t, s), |t|^2, (r^, s), omega and beta, and the fused x, r, p update.
+  dd_status iteration(int* d_count, bool check, cudaStream_t s) {
     if (check) DD_CUDA(c, cudaMemsetAsync(d_count, 0, sizeof(int), s));
     DD_COUNT_LAUNCH(), k_sc_check<<<sbl, sth, 0, s>>>(sa, check ? d_count : nullptr);
     // v = M p = p - k^2 H_eo H_oe p ; partial (rhat, v)
@@ -514,7 +586,20 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
                                                           (const S*)w.t, (const S*)w.v, partial);
     DD_CUDA(c, cudaGetLastError());
     return DD_OK;
-  };
+  }
+  // marks the systems that converged in the last iteration
+  void final_check(cudaStream_t s) { DD_COUNT_LAUNCH(), k_sc_check<<<sbl, sth, 0, s>>>(sa, nullptr); }
+};
+
+template <class S>
+dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs& w, SysState* st,
+                       double* partial, int* d_count, int* h_count, const void* rhs,
+                       double inner_tol2, double floor_frac, int maxiter, int check_every,
+                       bool use_graph, cudaStream_t s, int* iters_run, bool device_loop = false) {
+  BicgOps<S> ops(c, b, prec, w, st, partial);
+  dd_status e0 = ops.init(rhs, inner_tol2, floor_frac, s);
+  if (e0 != DD_OK) return e0;
+  auto iteration = [&](bool check, cudaStream_t s) -> dd_status { return ops.iteration(d_count, check, s); };
   auto poll = [&]() -> dd_status {
     DD_CUDA(c, cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
     DD_CUDA(c, cudaStreamSynchronize(s));
@@ -528,9 +613,11 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     // until no system runs or maxiter iterations have started
     int* d_iter = d_count + 1;
     char key[256];
-    snprintf(key, sizeof key, "loop:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%d:%a:%d%d%d", (int)prec, w.r, w.rhat,
+    // (the instance table's address is part of the key: a reallocation of it
+    // must not leave a replay reading the old one)
+    snprintf(key, sizeof key, "loop:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%d:%a:%d%d%d:%p", (int)prec, w.r, w.rhat,
              w.p, w.v, w.s, w.t, w.x, w.tmp, (void*)st, (void*)partial, (void*)d_count, maxiter, c->kappa,
-             b.hop_variant[0], b.hop_variant[1], b.hop_variant[2]);
+             b.hop_variant[0], b.hop_variant[1], b.hop_variant[2], (void*)c->d_inst);
     cudaGraphExec_t exec = nullptr;
     for (auto& g : b.graphs)
       if (g.first == key) exec = g.second;
@@ -594,9 +681,9 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     // the check_every iterations between two polls, captured once per batch,
     // precision, buffers and launch variant, then replayed
     char key[256];
-    snprintf(key, sizeof key, "%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%d:%a:%d%d%d", (int)prec, w.r,
+    snprintf(key, sizeof key, "%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%d:%a:%d%d%d:%p", (int)prec, w.r,
              w.rhat, w.p, w.v, w.s, w.t, w.x, w.tmp, (void*)st, (void*)partial, (void*)d_count,
-             check_every, c->kappa, b.hop_variant[0], b.hop_variant[1], b.hop_variant[2]);
+             check_every, c->kappa, b.hop_variant[0], b.hop_variant[1], b.hop_variant[2], (void*)c->d_inst);
     cudaGraphExec_t exec = nullptr;
     for (auto& g : b.graphs)
       if (g.first == key) exec = g.second;
@@ -655,7 +742,7 @@ dd_status run_bicgstab(dd_ctx* c, const Batch& b, dd_prec prec, const InnerVecs&
     }
   }
   // a final check marks the systems that converged in the last iteration
-  DD_COUNT_LAUNCH(), k_sc_check<<<sbl, sth, 0, s>>>(sa, nullptr);
+  ops.final_check(s);
   *iters_run = it;
   DD_CUDA(c, cudaGetLastError());
   return DD_OK;
@@ -759,6 +846,225 @@ dd_status true_residual_pass(dd_ctx* c, const Batch& b, dd_prec op, bool dfo, co
   dd_status e;
   if ((e = launch_hop(c, b, op, h, s)) != DD_OK) return e;
   return launch_hop(c, b, op, g, s);
+}
+
+// Sequential construction of a CUDA graph from captured segments and
+// conditional nodes: each segment is captured onto the current leaves, each
+// conditional node depends on them and becomes the only leaf.
+struct GraphSeq {
+  dd_ctx* c;
+  cudaGraph_t g;
+  cudaStream_t cs;
+  std::vector<cudaGraphNode_t> deps;
+  long long kernels = 0;   // kernel launches captured by the last segment
+  dd_status capture(const std::function<dd_status(cudaStream_t)>& fn) {
+    DD_CUDA(c, cudaStreamBeginCaptureToGraph(cs, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                             cudaStreamCaptureModeThreadLocal));
+    const long long l0 = g_launches.load();
+    dd_status e = fn(cs);
+    // captured launches are not executions: the replays count them
+    kernels = g_launches.load() - l0;
+    g_launches.fetch_sub(kernels);
+    cudaStreamCaptureStatus stt;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    cudaError_t ci = cudaStreamGetCaptureInfo(cs, &stt, nullptr, nullptr, &d, nullptr, &nd);
+    std::vector<cudaGraphNode_t> leaves(d, d + (ci == cudaSuccess ? nd : 0));
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &out);
+    if (e != DD_OK) return e;
+    if (ci != cudaSuccess) return cuda_fail(c, ci, "cudaStreamGetCaptureInfo");
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture (solve graph)");
+    deps = leaves;
+    return DD_OK;
+  }
+  dd_status cond(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, unsigned size,
+                 cudaGraph_t* bodies) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = size;
+    cudaGraphNode_t n = nullptr;
+    DD_CUDA(c, cudaGraphAddNode(&n, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
+    for (unsigned k = 0; k < size; ++k) bodies[k] = cp.conditional.phGraph_out[k];
+    deps.assign(1, n);
+    return DD_OK;
+  }
+};
+
+// The whole mixed-precision solve after the right-hand side is packed, as one
+// graph launch:
+//   OuterState init; WHILE (outer) {
+//     outer check (k_sc_outer) and decision (k_outer_decide);
+//     IF (verify) { r = b - D x };
+//     IF (cycle)  { residual to the inner precision; Schur right-hand side;
+//                   inner BiCGstab: init, WHILE (inner) { iteration }, final check;
+//                   x += e; IF (true residual) { r = b - D x } ELSE { r -= D e };
+//                   cycle bookkeeping } }
+// Every decision of the host-driven loop is taken by a one-thread kernel from
+// the same device-side counts; the outer loop is capped at max_outer + 3
+// passes and the inner one at maxiter iterations.
+template <class S>
+dd_status whole_solve(dd_ctx* c, const Batch& b, dd_prec ip, const InnerVecs& w, SysState* st, double* partial,
+                      double* partial_o, int* d_count, unsigned long long* d_maxrel, double* vrel, const void* rhs,
+                      double inner_tol2, double floor_frac, double theta, const dd_solve_params* prm,
+                      int max_outer, const std::function<dd_status(cudaStream_t)>& to_inner,
+                      const std::function<dd_status(cudaStream_t)>& schur_rhs,
+                      const std::function<dd_status(cudaStream_t)>& correct_x,
+                      const std::function<dd_status(cudaStream_t)>& true_res,
+                      const std::function<dd_status(cudaStream_t)>& update_res, const std::string& keyx,
+                      cudaStream_t s, int* cycles_out) {
+  dd_status e;
+  void* vos;
+  if ((e = ws_get(c, 39, sizeof(OuterState), &vos)) != DD_OK) return e;
+  OuterState* os = (OuterState*)vos;
+  int* d_iter = d_count + 1;
+  const int nsys = b.nb * b.nrhs;
+  const long long stride = (long long)b.nitems[0] * b.nrhs;
+  const long long stride_o = (long long)b.nitems[1] * b.nrhs;
+  ScalarArgs sa{st, partial, b.d_item_begin[0], stride, nsys, b.nrhs};
+  const int sth = 128, sbl = (nsys + sth - 1) / sth;
+  BicgOps<S> ops(c, b, ip, w, st, partial);
+  char kb[512];
+  snprintf(kb, sizeof kb,
+           "solve:%d:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%p:%a:%a:%a:%a:%d:%d:%d%d%d:%d:%p:%p:%p:%p",
+           (int)ip, w.r, w.rhat, w.p, w.v, w.s, w.t, w.x, w.tmp, (void*)st, (void*)partial, (void*)partial_o,
+           (void*)d_count, (void*)vrel, rhs, c->kappa, prm->tol, prm->inner_tol, floor_frac, max_outer,
+           prm->maxiter, b.hop_variant[0], b.hop_variant[1], b.hop_variant[2], c->clover_active ? 1 : 0,
+           (void*)c->d_clovi32, (void*)c->d_clovi_df, (void*)c->d_inst, vos);
+  const std::string key = std::string(kb) + keyx;
+  // kernels per pass of each part (for the launch count)
+  struct Counts {
+    long long init, check, verify, pre, inner, post, tres, upd, end;
+  };
+  static thread_local std::map<std::string, Counts> counts;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : b.graphs)
+    if (g.first == key) exec = g.second;
+  if (!exec) {
+    if (!c->capture_stream) DD_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    DD_CUDA(c, cudaGraphCreate(&graph, 0));
+    struct GraphGuard {
+      cudaGraph_t g;
+      ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+    } guard{graph};
+    Counts n{};
+    const int f32 = ip == DD_F32 ? 1 : 0;
+    GraphSeq top{c, graph, c->capture_stream, {}};
+    cudaGraphConditionalHandle h_outer;
+    DD_CUDA(c, cudaGraphConditionalHandleCreate(&h_outer, graph, 1, cudaGraphCondAssignDefault));
+    if ((e = top.capture([&](cudaStream_t q) {
+           DD_COUNT_LAUNCH(), k_outer_init<<<1, 1, 0, q>>>(os);
+           return DD_OK;
+         })) != DD_OK)
+      return e;
+    n.init = top.kernels;
+    cudaGraph_t body_outer;
+    if ((e = top.cond(h_outer, cudaGraphCondTypeWhile, 1, &body_outer)) != DD_OK) return e;
+    GraphSeq ob{c, body_outer, c->capture_stream, {}};
+    cudaGraphConditionalHandle h_verify, h_cycle;
+    DD_CUDA(c, cudaGraphConditionalHandleCreate(&h_verify, body_outer, 0, 0));
+    DD_CUDA(c, cudaGraphConditionalHandleCreate(&h_cycle, body_outer, 0, 0));
+    if ((e = ob.capture([&](cudaStream_t q) {
+           DD_CUDA(c, cudaMemsetAsync(d_count, 0, 64, q));
+           DD_COUNT_LAUNCH(), k_sc_outer<<<sbl, sth, 0, q>>>(sa, partial_o, b.d_item_begin[1], stride_o, 1.0,
+                                                            d_count, d_maxrel, vrel, &os->last_true);
+           DD_COUNT_LAUNCH(), k_outer_decide<<<1, 1, 0, q>>>(os, d_count, d_maxrel, max_outer, f32, theta,
+                                                            prm->inner_tol, prm->tol, h_verify, h_cycle, h_outer);
+           DD_CUDA(c, cudaGetLastError());
+           return DD_OK;
+         })) != DD_OK)
+      return e;
+    n.check = ob.kernels;
+    cudaGraph_t body_verify;
+    if ((e = ob.cond(h_verify, cudaGraphCondTypeIf, 1, &body_verify)) != DD_OK) return e;
+    GraphSeq vb{c, body_verify, c->capture_stream, {}};
+    if ((e = vb.capture([&](cudaStream_t q) {
+           dd_status r = true_res(q);
+           DD_COUNT_LAUNCH(), k_outer_verified<<<1, 1, 0, q>>>(os);
+           return r;
+         })) != DD_OK)
+      return e;
+    n.verify = vb.kernels;
+    cudaGraph_t body_cycle;
+    if ((e = ob.cond(h_cycle, cudaGraphCondTypeIf, 1, &body_cycle)) != DD_OK) return e;
+    GraphSeq cb{c, body_cycle, c->capture_stream, {}};
+    cudaGraphConditionalHandle h_inner, h_true;
+    DD_CUDA(c, cudaGraphConditionalHandleCreate(&h_inner, body_cycle, 1, 0));
+    DD_CUDA(c, cudaGraphConditionalHandleCreate(&h_true, body_cycle, 1, 0));
+    if ((e = cb.capture([&](cudaStream_t q) {
+           dd_status r;
+           if ((r = to_inner(q)) != DD_OK || (r = schur_rhs(q)) != DD_OK ||
+               (r = ops.init(rhs, inner_tol2, floor_frac, q)) != DD_OK)
+             return r;
+           DD_CUDA(c, cudaMemsetAsync(d_iter, 0, sizeof(int), q));
+           // the inner loop's condition starts at 1 on every pass of the outer loop
+           DD_COUNT_LAUNCH(), k_cond_set<<<1, 1, 0, q>>>(nullptr, h_inner);
+           DD_CUDA(c, cudaGetLastError());
+           return DD_OK;
+         })) != DD_OK)
+      return e;
+    n.pre = cb.kernels;
+    cudaGraph_t body_inner;
+    if ((e = cb.cond(h_inner, cudaGraphCondTypeWhile, 1, &body_inner)) != DD_OK) return e;
+    GraphSeq ib{c, body_inner, c->capture_stream, {}};
+    if ((e = ib.capture([&](cudaStream_t q) {
+           dd_status r = ops.iteration(d_count, true, q);
+           if (r != DD_OK) return r;
+           DD_COUNT_LAUNCH(), k_loop_cond<<<1, 1, 0, q>>>(d_count, d_iter, prm->maxiter, h_inner);
+           DD_CUDA(c, cudaGetLastError());
+           return DD_OK;
+         })) != DD_OK)
+      return e;
+    n.inner = ib.kernels;
+    if ((e = cb.capture([&](cudaStream_t q) {
+           ops.final_check(q);
+           dd_status r = correct_x(q);
+           DD_COUNT_LAUNCH(), k_cond_set<<<1, 1, 0, q>>>(&os->tr, h_true);
+           DD_CUDA(c, cudaGetLastError());
+           return r;
+         })) != DD_OK)
+      return e;
+    n.post = cb.kernels;
+    cudaGraph_t body_tr[2];
+    if ((e = cb.cond(h_true, cudaGraphCondTypeIf, 2, body_tr)) != DD_OK) return e;
+    GraphSeq tb{c, body_tr[0], c->capture_stream, {}};
+    if ((e = tb.capture(true_res)) != DD_OK) return e;
+    n.tres = tb.kernels;
+    GraphSeq ub{c, body_tr[1], c->capture_stream, {}};
+    if ((e = ub.capture(update_res)) != DD_OK) return e;
+    n.upd = ub.kernels;
+    if ((e = cb.capture([&](cudaStream_t q) {
+           DD_COUNT_LAUNCH(), k_outer_cycle_end<<<1, 1, 0, q>>>(os, d_iter);
+           DD_CUDA(c, cudaGetLastError());
+           return DD_OK;
+         })) != DD_OK)
+      return e;
+    n.end = cb.kernels;
+    cudaError_t ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaGraphInstantiate (solve graph)");
+    if (b.graphs.size() >= 8) {
+      cudaGraphExecDestroy(b.graphs.front().second);
+      b.graphs.erase(b.graphs.begin());
+    }
+    b.graphs.push_back({key, exec});
+    counts[key] = n;
+  }
+  DD_CUDA(c, cudaGraphLaunch(exec, s));
+  OuterState ho{};
+  DD_CUDA(c, cudaMemcpyAsync(&ho, os, sizeof ho, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(c, cudaStreamSynchronize(s));
+  auto it = counts.find(key);
+  if (it != counts.end()) {
+    const Counts& n = it->second;
+    g_launches.fetch_add(n.init + n.check * ho.osteps + n.verify * ho.n_verify +
+                         (n.pre + n.post + n.end) * ho.cyc + n.inner * ho.iters + n.tres * ho.n_tr +
+                         n.upd * (ho.cyc - ho.n_tr));
+  }
+  *cycles_out = ho.cyc;
+  return DD_OK;
 }
 
 }  // namespace
@@ -910,10 +1216,74 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
   // to keep a margin.  BF16 links round at 2^-9, so BF16 inner solves always
   // recompute the residual in FP64.
   const double theta = prm->tol * 1e5;
+  // the launches of one correction cycle, shared by the host-driven loop and
+  // the whole-solve graph
+  const void* rin_e = ip != DD_F64 ? w.s : re;   // residual at the inner precision
+  const void* rin_o = ip != DD_F64 ? rso : ro;
+  auto to_inner = [&](cudaStream_t q) -> dd_status {
+    if (ip != DD_F64) {
+      convert_outer(dfo, ip, bd, eg, 0, w.s, re, st, q);
+      if (has_odd) convert_outer(dfo, ip, bd, og, 1, rso, ro, st, q);
+    }
+    DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  };
+  // Schur right-hand side r^_e = r_e + k H_eo r_o
+  auto schur_rhs = [&](cudaStream_t q) -> dd_status {
+    HopArgs h{};
+    h.p_out = 0; h.in = rin_o; h.out = rhs; h.s1 = rin_e; h.a1 = 1.0; h.b = kap;
+    return launch_hop(c, b, ip, h, q);
+  };
+  // e_o = r_o + k H_oe e_e, then x += e
+  auto correct_x = [&](cudaStream_t q) -> dd_status {
+    HopArgs h{};
+    h.p_out = 1; h.in = w.x; h.out = eo; h.s1 = rin_o; h.a1 = 1.0; h.b = kap;
+    dd_status r = launch_hop(c, b, ip, h, q);
+    if (r != DD_OK) return r;
+    axpy_outer(dfo, bd, eg, 0, xe, w.x, ip, 1.0, st, q);
+    if (has_odd) axpy_outer(dfo, bd, og, 1, xo, eo, ip, 1.0, st, q);
+    DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  };
+  auto true_res = [&](cudaStream_t q) -> dd_status {
+    return true_residual_pass(c, b, op, dfo, xe, xo, be, bo, re, ro, partial, partial_o, q);
+  };
+  // r -= D e with D e at the inner precision (and the |r|^2 partials)
+  auto update_res = [&](cudaStream_t q) -> dd_status {
+    HopArgs h{};
+    h.p_out = 0; h.in = eo; h.out = w.t; h.s1 = w.x; h.a1 = 1.0; h.b = -kap;
+    dd_status r = launch_hop(c, b, ip, h, q);
+    if (r != DD_OK) return r;
+    HopArgs g{};
+    g.p_out = 1; g.in = w.x; g.out = w.tmp; g.s1 = eo; g.a1 = 1.0; g.b = -kap;
+    if ((r = launch_hop(c, b, ip, g, q)) != DD_OK) return r;
+    axpy_outer(dfo, bd, eg, 0, re, w.t, ip, -1.0, st, q, partial);
+    if (has_odd) axpy_outer(dfo, bd, og, 1, ro, w.tmp, ip, -1.0, st, q, partial_o);
+    DD_CUDA(c, cudaGetLastError());
+    return DD_OK;
+  };
   int cycles = 0;
+  // The whole solve as one graph launch (mixed forms with BiCGstab inner
+  // solves, once the launch form is tuned): the outer checks and their
+  // decisions run on the device (whole_solve below).
+  const int pi_in = ip == DD_F32 ? 1 : 2;
+  const bool graph_solve = (prm->flags & DD_SOLVE_GRAPH_SOLVE) && !c->timing && dfo &&
+                           !(prm->flags & (DD_SOLVE_FGMRES | DD_SOLVE_NET_PRECOND)) &&
+                           (!(prm->flags & DD_SOLVE_AUTOTUNE) || b.tuned[pi_in]);
+  if (graph_solve) {
+    auto run = [&](auto tag) -> dd_status {
+      using S = decltype(tag);
+      char kx[256];
+      snprintf(kx, sizeof kx, ":%p:%p:%p:%p:%p:%p:%p:%p", be, bo, xe, xo, re, ro, rso, eo);
+      return whole_solve<S>(c, b, ip, w, st, partial, partial_o, (int*)vcnt, d_maxrel, (double*)vrel, rhs,
+                            inner_tol2, floor_frac, theta, prm, max_outer, to_inner, schur_rhs, correct_x,
+                            true_res, update_res, std::string(kx), s, &cycles);
+    };
+    if ((e = ip == DD_F32 ? run(float2{}) : run(__nv_bfloat162{})) != DD_OK) return e;
+  }
   bool last_true = true;
   double maxrel = 1.0;
-  for (int cyc = 0;; ++cyc) {
+  for (int cyc = 0; !graph_solve; ++cyc) {
     // |r|^2 of both parities -> convergence
     if (!norms_ready) {
       norm2_outer(dfo, bd, eg, 0, re, partial, s);
@@ -934,8 +1304,7 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     // verified: r = b - D x once more at the outer precision, and the check
     // repeats on it, so the residuals a solve reports are true residuals.
     if (h_count == 0 && !last_true) {
-      if ((e = true_residual_pass(c, b, op, dfo, xe, xo, be, bo, re, ro, partial, partial_o, s)) != DD_OK)
-        return e;
+      if ((e = true_res(s)) != DD_OK) return e;
       last_true = true;
       norms_ready = dfo;
       continue;
@@ -947,25 +1316,13 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
     // solve: its residual is computed as b - D x straight away
     const bool last_cycle = prm->inner_tol * maxrel <= 0.25 * prm->tol;
     const bool true_residual = (ip != DD_F32) || cyc == 0 || maxrel > theta || last_cycle;
-    // residual at the inner precision
-    const void *rin_e = re, *rin_o = ro;
-    if (ip != DD_F64) {
-      convert_outer(dfo, ip, bd, eg, 0, w.s, re, st, s);
-      if (has_odd) convert_outer(dfo, ip, bd, og, 1, rso, ro, st, s);
-      rin_e = w.s;
-      rin_o = rso;
-    }
+    if ((e = to_inner(s)) != DD_OK) return e;
     if ((prm->flags & DD_SOLVE_AUTOTUNE) && cyc == 0) {
       const int pi = ip == DD_F64 ? 0 : (ip == DD_F32 ? 1 : 2);
       if (!b.tuned[pi] && (e = tune_hop(c, b, ip, rin_e, ip == DD_F64 ? tune64 : w.tmp, s)) != DD_OK)
         return e;
     }
-    // Schur right-hand side r^_e = r_e + k H_eo r_o
-    {
-      HopArgs h{};
-      h.p_out = 0; h.in = rin_o; h.out = rhs; h.s1 = rin_e; h.a1 = 1.0; h.b = kap;
-      if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
-    }
+    if ((e = schur_rhs(s)) != DD_OK) return e;
     int its = 0;
     if (prm->flags & DD_SOLVE_FGMRES) {
       dd_net* pn = ((prm->flags & DD_SOLVE_NET_PRECOND) && c->net && all_omega) ? c->net : nullptr;
@@ -980,29 +1337,12 @@ dd_status solve_batch(dd_ctx* c, const Batch& b, const double* b_user, double* x
       e = run_bicgstab<__nv_bfloat162>(c, b, ip, w, st, partial, d_count, &h_count, rhs, inner_tol2,
                                        floor_frac, prm->maxiter, check_every, use_graph, s, &its, device_loop);
     if (e != DD_OK) return e;
-    // e_o = r_o + k H_oe e_e
-    {
-      HopArgs h{};
-      h.p_out = 1; h.in = w.x; h.out = eo; h.s1 = rin_o; h.a1 = 1.0; h.b = kap;
-      if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
-    }
-    // x += e
-    axpy_outer(dfo, bd, eg, 0, xe, w.x, ip, 1.0, st, s);
-    if (has_odd) axpy_outer(dfo, bd, og, 1, xo, eo, ip, 1.0, st, s);
+    if ((e = correct_x(s)) != DD_OK) return e;
     if (true_residual) {
-      if ((e = true_residual_pass(c, b, op, dfo, xe, xo, be, bo, re, ro, partial, partial_o, s)) != DD_OK)
-        return e;
+      if ((e = true_res(s)) != DD_OK) return e;
       norms_ready = dfo;
     } else {
-      // r -= D e with D e at the inner precision
-      HopArgs h{};
-      h.p_out = 0; h.in = eo; h.out = w.t; h.s1 = w.x; h.a1 = 1.0; h.b = -kap;
-      if ((e = launch_hop(c, b, ip, h, s)) != DD_OK) return e;
-      HopArgs g{};
-      g.p_out = 1; g.in = w.x; g.out = w.tmp; g.s1 = eo; g.a1 = 1.0; g.b = -kap;
-      if ((e = launch_hop(c, b, ip, g, s)) != DD_OK) return e;
-      axpy_outer(dfo, bd, eg, 0, re, w.t, ip, -1.0, st, s, partial);
-      if (has_odd) axpy_outer(dfo, bd, og, 1, ro, w.tmp, ip, -1.0, st, s, partial_o);
+      if ((e = update_res(s)) != DD_OK) return e;
       norms_ready = true;
     }
     last_true = true_residual;

@@ -29,7 +29,7 @@ class GeomInfo(C.Structure):
 
 
 SOLVE_GRAPH, SOLVE_AUTOTUNE, SOLVE_NET_GUESS, SOLVE_PIPELINE = 1, 2, 4, 8
-SOLVE_FGMRES, SOLVE_NET_PRECOND, SOLVE_GRAPH_LOOP = 16, 32, 64
+SOLVE_FGMRES, SOLVE_NET_PRECOND, SOLVE_GRAPH_LOOP, SOLVE_GRAPH_SOLVE = 16, 32, 64, 128
 
 
 class SolveParams(C.Structure):
@@ -190,14 +190,14 @@ def _stream(stream):
 
 def params(tol=1e-10, maxiter=2000, inner_prec="f64", inner_tol=3e-6, max_outer=None,
            check_every=8, graph=False, autotune=False, net_guess=False, pipeline=False,
-           fgmres=False, restart=8, net_precond=False, graph_loop=False):
+           fgmres=False, restart=8, net_precond=False, graph_loop=False, graph_solve=False):
     ip = PREC[inner_prec] if isinstance(inner_prec, str) else inner_prec
     if max_outer is None:
         max_outer = 4 if ip == F64 else 30
     flags = ((SOLVE_GRAPH if graph else 0) | (SOLVE_AUTOTUNE if autotune else 0)
              | (SOLVE_NET_GUESS if net_guess else 0) | (SOLVE_PIPELINE if pipeline else 0)
              | (SOLVE_FGMRES if fgmres else 0) | (SOLVE_NET_PRECOND if net_precond else 0)
-             | (SOLVE_GRAPH_LOOP if graph_loop else 0))
+             | (SOLVE_GRAPH_LOOP if graph_loop else 0) | (SOLVE_GRAPH_SOLVE if graph_solve else 0))
     return SolveParams(tol, maxiter, ip, inner_tol, max_outer, check_every, flags, restart)
 
 

@@ -262,3 +262,33 @@ def test_device_loop_graph_is_bit_identical(inner):
     assert s1["max_relres"] <= 1e-10
     assert np.array_equal(x0, x1) and np.array_equal(x1, x2)
     assert s0["max_iters"] == s1["max_iters"]
+
+
+@pytest.mark.parametrize("inner,itol,csw", [("f32", 3e-6, 0.0), ("f32", 1e-3, 0.0), ("f32", 3e-3, 0.0),
+                                            ("bf16", 1e-3, 0.0), ("f32", 1e-3, 1.0)])
+def test_whole_solve_graph_is_bit_identical(inner, itol, csw):
+    """DD_SOLVE_GRAPH_SOLVE: the whole mixed solve is one graph launch whose WHILE and
+    IF nodes take the host loop's decisions on the device (run a cycle, verify an
+    updated residual, true or updated residual after a cycle).  The kernels are the
+    same and run in the same order, so the solutions, cycle counts and iteration
+    counts equal the host-driven ones bit for bit; several inner tolerances reach
+    the updated-residual and verification branches; BF16 inner and the clover term;
+    uneven blocks; the second solve replays the graph."""
+    L = (12, 8, 8, 10)
+    cores = [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]]
+    U, ctx, info, geo = make_case(L, 0.12, 0.5, 7, cores)
+    if csw:
+        ctx.set_clover(csw)
+    ids = list(range(info["nblocks"]))
+    tot = sum(len(ctx.geom_sites(dd4d.SET_OMEGA, b)) for b in ids)
+    b = synth.complex_gaussian(13, synth.TAG_RHS, (2 * tot, 12))
+    x0, x1, x2 = np.zeros_like(b), np.zeros_like(b), np.zeros_like(b)
+    s0 = ctx.solve_blocks("omega", ids, 2, b, x0, dd4d.params(1e-10, inner_prec=inner, inner_tol=itol))
+    prm = dd4d.params(1e-10, inner_prec=inner, inner_tol=itol, graph_solve=True)
+    s1 = ctx.solve_blocks("omega", ids, 2, b, x1, prm)
+    s2 = ctx.solve_blocks("omega", ids, 2, b, x2, prm)
+    assert s0["status"] == s1["status"] == s2["status"] == 0
+    assert s1["max_relres"] <= 1e-10
+    assert np.array_equal(x0, x1) and np.array_equal(x1, x2)
+    assert s0["outer_cycles"] == s1["outer_cycles"] == s2["outer_cycles"]
+    assert s0["max_iters"] == s1["max_iters"]
