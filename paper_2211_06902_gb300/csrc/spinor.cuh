@@ -193,6 +193,25 @@ __device__ __forceinline__ void hop_project(const C (&psi)[12], C (&h)[2][3]) {
     }
   }
 }
+// row a of (U h) for both half-spinor components, rebuilt into all four spins of acc
+template <int MU, bool FWD, class C>
+__device__ __forceinline__ void hop_accum_row(C (&acc)[12], int a, C u0, C u1) {
+  acc[a] = cadd(acc[a], u0);
+  acc[3 + a] = cadd(acc[3 + a], u1);
+  if (MU == 0) {
+    acc[6 + a] = FWD ? cadd(acc[6 + a], u0) : csub(acc[6 + a], u0);
+    acc[9 + a] = FWD ? cadd(acc[9 + a], u1) : csub(acc[9 + a], u1);
+  } else if (MU == 1) {
+    acc[6 + a] = FWD ? csubi(acc[6 + a], u1) : caddi(acc[6 + a], u1);
+    acc[9 + a] = FWD ? csubi(acc[9 + a], u0) : caddi(acc[9 + a], u0);
+  } else if (MU == 2) {
+    acc[6 + a] = FWD ? csub(acc[6 + a], u1) : cadd(acc[6 + a], u1);
+    acc[9 + a] = FWD ? cadd(acc[9 + a], u0) : csub(acc[9 + a], u0);
+  } else {
+    acc[6 + a] = FWD ? csubi(acc[6 + a], u0) : caddi(acc[6 + a], u0);
+    acc[9 + a] = FWD ? caddi(acc[9 + a], u1) : csubi(acc[9 + a], u1);
+  }
+}
 // U (forward) or U^+ (backward) times the half spinor, rebuilt into all four spins of acc
 template <int MU, bool FWD, class C>
 __device__ __forceinline__ void hop_apply(C (&acc)[12], const C (&h)[2][3], const C (&U)[9]) {
@@ -211,23 +230,7 @@ __device__ __forceinline__ void hop_apply(C (&acc)[12], const C (&h)[2][3], cons
     }
   }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    acc[a] = cadd(acc[a], uh[0][a]);
-    acc[3 + a] = cadd(acc[3 + a], uh[1][a]);
-    if (MU == 0) {
-      acc[6 + a] = FWD ? cadd(acc[6 + a], uh[0][a]) : csub(acc[6 + a], uh[0][a]);
-      acc[9 + a] = FWD ? cadd(acc[9 + a], uh[1][a]) : csub(acc[9 + a], uh[1][a]);
-    } else if (MU == 1) {
-      acc[6 + a] = FWD ? csubi(acc[6 + a], uh[1][a]) : caddi(acc[6 + a], uh[1][a]);
-      acc[9 + a] = FWD ? csubi(acc[9 + a], uh[0][a]) : caddi(acc[9 + a], uh[0][a]);
-    } else if (MU == 2) {
-      acc[6 + a] = FWD ? csub(acc[6 + a], uh[1][a]) : cadd(acc[6 + a], uh[1][a]);
-      acc[9 + a] = FWD ? cadd(acc[9 + a], uh[0][a]) : csub(acc[9 + a], uh[0][a]);
-    } else {
-      acc[6 + a] = FWD ? csubi(acc[6 + a], uh[0][a]) : caddi(acc[6 + a], uh[0][a]);
-      acc[9 + a] = FWD ? caddi(acc[9 + a], uh[1][a]) : csubi(acc[9 + a], uh[1][a]);
-    }
-  }
+  for (int a = 0; a < 3; ++a) hop_accum_row<MU, FWD>(acc, a, uh[0][a], uh[1][a]);
 }
 template <int MU, bool FWD, class C>
 __device__ __forceinline__ void hop_dir(C (&acc)[12], const C (&psi)[12], const C (&U)[9]) {

@@ -8,8 +8,8 @@ Builds the lattice (links exp(i eps H)), the framed blocks of `core`^4 cores
 with a one-site frame, Gaussian right-hand sides on every block, and runs
 `--repeat` solves to 1e-10 with the requested inner precision (or, with
 --net, `--repeat` applications of the 4-layer network with tensor-core
-layers).  Prints the solver statistics; exits non-zero if a system misses the
-tolerance.
+layers); --csw adds the clover term to the solves.  Prints the solver
+statistics; exits non-zero if a system misses the tolerance.
 """
 
 import argparse
@@ -38,6 +38,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="stencil launch variant of the inner precision (-1: default)")
     ap.add_argument("--net", action="store_true", help="apply the network instead of solving")
+    ap.add_argument("--csw", type=float, default=0.0, help="clover coefficient (0: no clover term)")
     a = ap.parse_args()
     import torch
     torch.cuda.init()
@@ -61,6 +62,8 @@ def main():
         net.close()
         ctx.close()
         return 0
+    if a.csw:
+        ctx.set_clover(a.csw)
     if a.variant >= 0:
         ctx.set_hop_variant(a.inner, a.variant)
     prm = dd4d.params(1e-10, inner_prec=a.inner)
