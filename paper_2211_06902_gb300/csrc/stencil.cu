@@ -701,40 +701,9 @@ __device__ __forceinline__ void lds_link(const S* dirblk, int lane, C (&U)[9]) {
   U[8] = lds_c(dirblk + (4 * LB_LANES + lane) * 2);
 }
 
-// entry k (row-major a*3+b) of a link in a shared-memory bundle (lane's column)
-template <class S>
-__device__ __forceinline__ float2 lds_entry(const S* dirblk, int lane, int k) {
-  return lds_c(dirblk + ((k >> 1) * LB_LANES + lane) * 2 + (k & 1));
-}
-// one direction with the link streamed from shared memory: each row of U (or
-// column, for U^+) is read where it is used, so only 3 link entries are live
-// at a time instead of 9 (a smaller register set for forms with more CTAs per SM)
-template <int MU, bool FWD, class S, class C>
-__device__ __forceinline__ void hop_dir_lds(C (&acc)[12], const C (&psi)[12], const S* dirblk, int lane) {
-  C h[2][3];
-  hop_project<MU, FWD>(psi, h);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    C u0 = cmk<C>(0.0, 0.0), u1 = cmk<C>(0.0, 0.0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const C e = lds_entry(dirblk, lane, FWD ? a * 3 + b : b * 3 + a);
-      if (FWD) {
-        cfma(u0, e, h[0][b]);
-        cfma(u1, e, h[1][b]);
-      } else {
-        cfmac(u0, e, h[0][b]);
-        cfmac(u1, e, h[1][b]);
-      }
-    }
-    hop_accum_row<MU, FWD>(acc, a, u0, u1);
-  }
-}
-
 // one direction of the hop for the RR rhs of a thread: the link is read from
 // the shared-memory bundle once and applied to each rhs's neighbour spinor
-// (STREAM, one rhs per thread: read row by row where it is used)
-template <int DIR, class S, class C, int RR, bool STREAM = false>
+template <int DIR, class S, class C, int RR>
 __device__ __forceinline__ void hop_lb_dir(C (&acc)[RR][12], const int* qi, const S* ql, int lane,
                                            int n_in, const void* in, const long long* off_in,
                                            const int (&sysk)[RR], const bool (&actk)[RR]) {
@@ -742,13 +711,6 @@ __device__ __forceinline__ void hop_lb_dir(C (&acc)[RR][12], const int* qi, cons
   constexpr bool FWD = DIR < 4;
   const int j = qi[DIR * LB_LANES + lane];
   if (j < 0) return;
-  if constexpr (STREAM && RR == 1) {
-    if (!actk[0]) return;
-    C psi[12];
-    ld_site<12>((const S*)in + off_in[sysk[0]], n_in, j, psi);
-    hop_dir_lds<MU, FWD>(acc[0], psi, ql + DIR * 5 * LB_LANES * 2, lane);
-    return;
-  }
   C U[9];
   lds_link(ql + DIR * 5 * LB_LANES * 2, lane, U);
 #pragma unroll
@@ -783,7 +745,7 @@ constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64;
 // waits for the phase parity (ph >> q) & 1.  Returns the number of slots it used
 // (0 when the unit had nothing to do); every CTA-wide barrier inside is reached
 // by all threads or by none.
-template <class S, int RR, int QPC, int MAXR, bool CLOV, bool STREAM = false>
+template <class S, int RR, int QPC, int MAXR, bool CLOV>
 __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, long long unit,
                                        unsigned ph, bool fault) {
   typedef typename StoreTraits<S>::C C;
@@ -890,14 +852,14 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
     // forward and backward hop of a direction back to back: along x3 and x2
     // the two neighbour sets of a warp's 32 sites nearly coincide, so the
     // second load finds the first one's lines in L1
-    hop_lb_dir<3, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<7, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<2, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<6, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<1, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<5, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<0, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<4, S, C, RR, STREAM>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<3, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<7, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<2, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<6, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<1, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<5, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<0, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<4, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
     if constexpr (CLOV) {
       // clover term: the hop sums times A^{-1} of the output site
       const long long gs = dp->glob[(p ? n0 : 0) + i];
@@ -1039,7 +1001,7 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
   return nq;
 }
 
-template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false, bool STREAM = false>
+template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false>
 __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
   extern __shared__ __align__(128) unsigned char lb_smem[];
@@ -1049,7 +1011,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     mbar_fence_init();
   }
   __syncthreads();
-  lb_unit<S, RR, QPC, MAXR, CLOV, STREAM>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
+  lb_unit<S, RR, QPC, MAXR, CLOV>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
 }
 
 // Persistent form with a work queue: a grid of (SMs x resident CTAs) CTAs pulls
@@ -1083,8 +1045,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
   }
 }
 
-template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false,
-          bool STREAM = false>
+template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
   const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
   const int rb = (bd.nrhs + ngroups - 1) / ngroups;
@@ -1101,7 +1062,7 @@ static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, 
     }
     if (a.dotqs) zero(3);
   }
-  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV, STREAM>
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV>
       <<<(unsigned)(nitems_p * ngroups * NH), nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb);
 }
 
@@ -1139,9 +1100,6 @@ void hop_bundle_prepare() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, true>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, false, true>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 3, 1, 2, 12, false, true>, at, h32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 5, 1, 2, 6, false, true>, at, h32);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 4, 12, true>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<float2, 1, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 2, 4, 12>, at, b32);
@@ -1168,7 +1126,6 @@ struct HopVariant {
                   // with k rhs per thread)
   int qpc = 4;    // bundle form: link quarters of the 128-site item per CTA
   int maxr = 12;  // bundle form: most rhs per CTA
-  bool stream = false;   // bundle form: links read row by row from shared memory
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -1178,15 +1135,13 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
                                          {2, false, -3}, {2, false, -1, 2, 12}, {5, false, -1, 2, 6},
-                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6},
-                                         {2, false, -1, 4, 12, true}, {3, false, -1, 2, 12, true},
-                                         {5, false, -1, 2, 6, true}};
+                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
                                          {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
                                          {2, false, -1, 2, 12}, {5, false, -1, 2, 6}, {2, true, -1}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 25 : 15); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 22 : 15); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1240,10 +1195,7 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
       return;
     }
     if (prec == DD_F32) {
-      if (hv.stream && hv.qpc == 2 && hv.maxr == 6) launch_lb<float2, 5, 1, 2, 6, false, true>(bd, a, ni, s);
-      else if (hv.stream && hv.qpc == 2) launch_lb<float2, 3, 1, 2, 12, false, true>(bd, a, ni, s);
-      else if (hv.stream) launch_lb<float2, 2, 1, 4, 12, false, true>(bd, a, ni, s);
-      else if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
+      if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2 && hv.maxr == 6) launch_lb<float2, 4, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2) launch_lb<float2, 2, 1, 2, 12>(bd, a, ni, s);
       else if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
@@ -1504,11 +1456,7 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.r < 0 && h.stream)
-          snprintf(names[k][u], sizeof names[k][u],
-                   "k_hop_lb<%s,%d,%d,%d,%d,rows>: bulk-copied links read row by row, %d sites and up to %d rhs per CTA",
-                   ty[k], h.minb, -h.r, h.qpc, h.maxr, 32 * h.qpc, h.maxr);
-        else if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
+        if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);
