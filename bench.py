@@ -935,8 +935,16 @@ def uneven_action_rate(dd4d, synth, torch, evals=2):
     dt = (time.perf_counter() - t0) / evals
     stats = c.last_solve_stats()
     sizes = sorted({len(c.geom_sites(dd4d.SET_OMEGA, b)) for b in range(0, info["nblocks"], 7)})
+    # the error of the mixed form against the plain FP64 form of the same action
+    # (the FP64 form is the one the oracle pins, on smaller uneven lattices)
+    t1 = time.perf_counter()
+    S64, Sb64, Sr64, _ = c.multiboson_action(u, d, dd4d.params(TOL, inner_prec="f64"))
+    f64_s = time.perf_counter() - t1
     c.close()
-    return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s",
+    err = {"rel_diff_S_vs_f64": abs(S - S64) / abs(S64), "rel_diff_S_r_vs_f64": abs(Sr - Sr64) / abs(Sr64),
+           "max_rel_diff_S_block_vs_f64": max(abs(a - b) / abs(b) for a, b in zip(Sb, Sb64)),
+           "plain_f64_seconds_per_eval": f64_s, "mixed_speedup_vs_plain_f64": f64_s / dt}
+    return {"metric": "action evals/s", "value": 1.0 / dt, "unit": "evals/s", "error_vs_f64": err,
             "workload": "64x32^3, kappa 0.136, eps 0.6, seed 3: 512 uneven framed blocks "
                         "(cores 6/8 per direction, frame 1) + frame Lambda1 (%d sites), "
                         "12 fields (N = 24, c = 0.5), FP32 inner + FP64 defect correction "
