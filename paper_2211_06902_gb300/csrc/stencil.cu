@@ -703,24 +703,12 @@ __device__ __forceinline__ void lds_link(const S* dirblk, int lane, C (&U)[9]) {
 
 // one direction of the hop for the RR rhs of a thread: the link is read from
 // the shared-memory bundle once and applied to each rhs's neighbour spinor
-// PF >= 0: first ask L2 for the neighbour spinor of direction PF (a later one
-// in the visiting order) with prefetch instructions, which keep more lines in
-// flight without holding registers
-template <int DIR, class S, class C, int RR, int PF = -1>
+template <int DIR, class S, class C, int RR>
 __device__ __forceinline__ void hop_lb_dir(C (&acc)[RR][12], const int* qi, const S* ql, int lane,
                                            int n_in, const void* in, const long long* off_in,
                                            const int (&sysk)[RR], const bool (&actk)[RR]) {
   constexpr int MU = DIR & 3;
   constexpr bool FWD = DIR < 4;
-  if constexpr (PF >= 0 && RR == 1) {
-    const int jp = qi[PF * LB_LANES + lane];
-    if (jp >= 0 && actk[0]) {
-      const S* base = (const S*)in + off_in[sysk[0]];
-#pragma unroll
-      for (int q = 0; q < 6; ++q)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((long long)q * n_in + jp) * 2));
-    }
-  }
   const int j = qi[DIR * LB_LANES + lane];
   if (j < 0) return;
   C U[9];
@@ -757,12 +745,7 @@ constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64;
 // waits for the phase parity (ph >> q) & 1.  Returns the number of slots it used
 // (0 when the unit had nothing to do); every CTA-wide barrier inside is reached
 // by all threads or by none.
-// the visiting order of the directions in the bundle form, and the direction
-// AHEAD places later (-1 past the end or with AHEAD = 0)
-constexpr int lb_order(int k) { return k == 0 ? 3 : k == 1 ? 7 : k == 2 ? 2 : k == 3 ? 6 : k == 4 ? 1 : k == 5 ? 5 : k == 6 ? 0 : 4; }
-constexpr int lb_ahead(int k, int ahead) { return (ahead > 0 && k + ahead < 8) ? lb_order(k + ahead) : -1; }
-
-template <class S, int RR, int QPC, int MAXR, bool CLOV, int AHEAD = 0>
+template <class S, int RR, int QPC, int MAXR, bool CLOV>
 __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, long long unit,
                                        unsigned ph, bool fault) {
   typedef typename StoreTraits<S>::C C;
@@ -879,14 +862,14 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
     // forward and backward hop of a direction back to back: along x3 and x2
     // the two neighbour sets of a warp's 32 sites nearly coincide, so the
     // second load finds the first one's lines in L1
-    hop_lb_dir<3, S, C, RR, lb_ahead(0, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<7, S, C, RR, lb_ahead(1, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<2, S, C, RR, lb_ahead(2, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<6, S, C, RR, lb_ahead(3, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<1, S, C, RR, lb_ahead(4, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<5, S, C, RR, lb_ahead(5, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<0, S, C, RR, lb_ahead(6, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
-    hop_lb_dir<4, S, C, RR, lb_ahead(7, AHEAD)>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<3, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<7, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<2, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<6, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<1, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<5, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<0, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
+    hop_lb_dir<4, S, C, RR>(acc, qi, ql, lane, n_in, a.in, off_in, sysk, actk);
     if constexpr (CLOV) {
       // clover term: the hop sums times A^{-1} of the output site
       const long long gs = dp->glob[(p ? n0 : 0) + i];
@@ -1028,7 +1011,7 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
   return nq;
 }
 
-template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false, int AHEAD = 0>
+template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false>
 __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
   extern __shared__ __align__(128) unsigned char lb_smem[];
@@ -1038,7 +1021,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     mbar_fence_init();
   }
   __syncthreads();
-  lb_unit<S, RR, QPC, MAXR, CLOV, AHEAD>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
+  lb_unit<S, RR, QPC, MAXR, CLOV>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
 }
 
 // Persistent form with a work queue: a grid of (SMs x resident CTAs) CTAs pulls
@@ -1072,8 +1055,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
   }
 }
 
-template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false,
-          int AHEAD = 0>
+template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
   const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
   const int rb = (bd.nrhs + ngroups - 1) / ngroups;
@@ -1090,7 +1072,7 @@ static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, 
     }
     if (a.dotqs) zero(3);
   }
-  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV, AHEAD>
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV>
       <<<(unsigned)(nitems_p * ngroups * NH), nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb);
 }
 
@@ -1128,9 +1110,6 @@ void hop_bundle_prepare() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, true>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, false, 1>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, false, 2>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 2, 12, false, 1>, at, h32);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 4, 12, true>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<float2, 1, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 2, 4, 12>, at, b32);
@@ -1157,7 +1136,6 @@ struct HopVariant {
                   // with k rhs per thread)
   int qpc = 4;    // bundle form: link quarters of the 128-site item per CTA
   int maxr = 12;  // bundle form: most rhs per CTA
-  int ahead = 0;  // bundle form: L2 prefetch of the neighbours this many directions ahead
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -1167,15 +1145,13 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
                                          {2, false, -3}, {2, false, -1, 2, 12}, {5, false, -1, 2, 6},
-                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6},
-                                         {2, false, -1, 4, 12, 1}, {2, false, -1, 4, 12, 2},
-                                         {2, false, -1, 2, 12, 1}};
+                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
                                          {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
                                          {2, false, -1, 2, 12}, {5, false, -1, 2, 6}, {2, true, -1}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 25 : 15); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 22 : 15); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1229,10 +1205,7 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
       return;
     }
     if (prec == DD_F32) {
-      if (hv.ahead && hv.qpc == 2) launch_lb<float2, 2, 1, 2, 12, false, 1>(bd, a, ni, s);
-      else if (hv.ahead == 2) launch_lb<float2, 2, 1, 4, 12, false, 2>(bd, a, ni, s);
-      else if (hv.ahead == 1) launch_lb<float2, 2, 1, 4, 12, false, 1>(bd, a, ni, s);
-      else if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
+      if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2 && hv.maxr == 6) launch_lb<float2, 4, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2) launch_lb<float2, 2, 1, 2, 12>(bd, a, ni, s);
       else if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
@@ -1493,11 +1466,7 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.r < 0 && h.ahead)
-          snprintf(names[k][u], sizeof names[k][u],
-                   "k_hop_lb<%s,%d,%d,%d,%d,l2+%d>: bulk-copied links, %d sites per CTA, L2 prefetch %d directions ahead",
-                   ty[k], h.minb, -h.r, h.qpc, h.maxr, h.ahead, 32 * h.qpc, h.ahead);
-        else if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
+        if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);
