@@ -668,9 +668,17 @@ def stencil_rates(dd4d, synth, torch, ctx, ids, b12, n_om):
                     best = (gbs, ms / n, v)
             ctx.set_hop_variant(prec, -1)
             del o
-            out["%s_%drhs" % (prec, nrhs)] = {
-                "GB_s": best[0], "frac_of_hbm": best[0] / peak if peak else None,
-                "ms_per_launch": best[1], "variant": dd4d.hop_variant_name(prec, best[2])}
+            entry = {"GB_s": best[0], "frac_of_hbm": best[0] / peak if peak else None,
+                     "ms_per_launch": best[1], "variant": dd4d.hop_variant_name(prec, best[2])}
+            if prec == "f64":
+                # the FP64 form is bound by the FP64 pipes: 1320 flops per output (site, rhs)
+                # for the hop and 48 for the self term, against the measured FP64 FMA rate
+                units = len(ids) * n_om * nrhs / 2.0
+                tf = units * 1368.0 / (best[1] * 1e-3) / 1e12
+                fma = dd4d.fp64_fma_rate()
+                entry.update({"fp64_tflops": tf, "fp64_fma_peak_tflops": fma, "frac_of_fp64_fma": tf / fma,
+                              "bound": "alu (FP64)"})
+            out["%s_%drhs" % (prec, nrhs)] = entry
     return out
 
 
