@@ -103,3 +103,23 @@ def test_action_deterministic():
     a = ctx.multiboson_action(u, vec, dd4d.params(1e-10))
     b = ctx.multiboson_action(u, vec, dd4d.params(1e-10))
     assert a[0] == b[0] and a[2] == b[2] and np.array_equal(a[1], b[1])
+
+
+def test_whole_solve_graph_in_w_and_action():
+    """w and the action with every batched solve (uneven framed blocks, frame
+    pieces and the frame Lambda1 in one batch) run as one graph launch each:
+    bit-identical to the host-driven solves, and equal to the oracle."""
+    U, ctx, info, geo = CASES["uneven 12x8x8x10"]()
+    u = field_roots(6, 0.5)
+    chis, vec, dpi = _chis(geo, ctx, 3, 12)
+    w0, w1 = np.zeros_like(vec), np.zeros_like(vec)
+    assert ctx.apply_w(3, vec, w0, dd4d.params(1e-10, inner_prec="f32")) == 0
+    g = dd4d.params(1e-10, inner_prec="f32", graph_solve=True)
+    for _ in range(2):                          # the second call replays the graphs
+        assert ctx.apply_w(3, vec, w1, g) == 0
+        assert np.array_equal(w0, w1)
+    a = ctx.multiboson_action(u, vec, dd4d.params(1e-10, inner_prec="f32"))
+    b = ctx.multiboson_action(u, vec, g)
+    assert a[3] == b[3] == 0 and a[0] == b[0] and np.array_equal(a[1], b[1])
+    S0, Sb0, Sr0 = Oracle(U, 0.13, geo).multiboson_action(u, chis)
+    assert abs(b[0] - S0) <= 1e-9 * S0
