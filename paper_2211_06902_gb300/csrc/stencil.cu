@@ -42,7 +42,10 @@ __device__ __forceinline__ void clover_epilogue(const void* t, long long g, dfc 
   clover_mul_h((const float4*)t + CLOV_HDF_F4 * g, acc);
 }
 
-template <int DIR, class S, class C>
+// ROWS: the link is read one row (U) or column (U^+) at a time after the spin
+// projection, so 3 of its entries are live instead of 9 (the double-float form,
+// whose 12-number accumulator and neighbour spinor fill the register budget)
+template <int DIR, class S, class C, bool ROWS = false>
 __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int n_out,
                                         int n_in, int j, const S* __restrict__ in_sys,
                                         const S* __restrict__ lk) {
@@ -51,6 +54,29 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
   if (j < 0) return;
   C psi[12];
   ld_site<12>(in_sys, n_in, j, psi);
+  if constexpr (ROWS) {
+    C h[2][3];
+    hop_project<MU, FWD>(psi, h);
+    const S* blk = FWD ? lk + link_block(p, MU, n0, n_out) : lk + link_block(1 - p, MU, n0, n_in);
+    const long long nn = FWD ? n_out : n_in, site = FWD ? i : j;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      C u0 = cmk<C>(0.0, 0.0), u1 = cmk<C>(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const C e = ldc(blk + cidx(FWD ? a * 3 + b : b * 3 + a, nn, site));
+        if (FWD) {
+          cfma(u0, e, h[0][b]);
+          cfma(u1, e, h[1][b]);
+        } else {
+          cfmac(u0, e, h[0][b]);
+          cfmac(u1, e, h[1][b]);
+        }
+      }
+      hop_accum_row<MU, FWD>(acc, a, u0, u1);
+    }
+    return;
+  }
   C U[9];
   if (FWD) ld_link(lk + link_block(p, MU, n0, n_out), n_out, i, U);
   else ld_link(lk + link_block(1 - p, MU, n0, n_in), n_in, j, U);
@@ -60,7 +86,7 @@ __device__ __forceinline__ void hop_one(C (&acc)[12], int n0, int p, int i, int 
 // grid: nitems[p] * nrhs CTAs, rhs fastest (the CTAs that share a site chunk,
 // and so its links, run together and hit L2); one output site per thread.
 // One CTA work unit t = item * nrhs + rhs of the hop launch.
-template <class S, bool CLOV>
+template <class S, bool CLOV, bool ROWS = false>
 __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, long long t,
                                          double* red) {
   typedef typename StoreTraits<S>::C C;
@@ -89,14 +115,14 @@ __device__ __forceinline__ void hop_unit(const BatchDev& bd, const HopArgs& a, l
     int jn[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) jn[d] = __ldg(nbr + d * n_out + i);
-    hop_one<0, S>(acc, n0, p, i, n_out, n_in, jn[0], in_sys, lk);
-    hop_one<1, S>(acc, n0, p, i, n_out, n_in, jn[1], in_sys, lk);
-    hop_one<2, S>(acc, n0, p, i, n_out, n_in, jn[2], in_sys, lk);
-    hop_one<3, S>(acc, n0, p, i, n_out, n_in, jn[3], in_sys, lk);
-    hop_one<4, S>(acc, n0, p, i, n_out, n_in, jn[4], in_sys, lk);
-    hop_one<5, S>(acc, n0, p, i, n_out, n_in, jn[5], in_sys, lk);
-    hop_one<6, S>(acc, n0, p, i, n_out, n_in, jn[6], in_sys, lk);
-    hop_one<7, S>(acc, n0, p, i, n_out, n_in, jn[7], in_sys, lk);
+    hop_one<0, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[0], in_sys, lk);
+    hop_one<1, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[1], in_sys, lk);
+    hop_one<2, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[2], in_sys, lk);
+    hop_one<3, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[3], in_sys, lk);
+    hop_one<4, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[4], in_sys, lk);
+    hop_one<5, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[5], in_sys, lk);
+    hop_one<6, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[6], in_sys, lk);
+    hop_one<7, S, C, ROWS>(acc, n0, p, i, n_out, n_in, jn[7], in_sys, lk);
     // clover term: the hop sum times A^{-1} of the output site (compiled into
     // the FP64 forms and the clover instantiations only)
     if constexpr (CLOV) {
@@ -592,16 +618,17 @@ __global__ void __launch_bounds__(2 * HOP_THREADS, MINB) k_hop_split(BatchDev bd
 // of the register allocator; PERSIST = a grid of (SMs x MINB) CTAs that walks
 // the work units with a stride (one launch of persistent CTAs over blocks of
 // any size) instead of one CTA per unit.
-template <class S, int MINB, bool PERSIST, int R, bool CLOV = std::is_same<S, double2>::value>
+template <class S, int MINB, bool PERSIST, int R, bool CLOV = std::is_same<S, double2>::value,
+          bool ROWS = false>
 __global__ void __launch_bounds__(HOP_THREADS, MINB) k_hop(BatchDev bd, HopArgs a, long long nunits) {
   __shared__ double red[32 * 4];
   if (PERSIST) {
     for (long long t = blockIdx.x; t < nunits; t += gridDim.x) {
-      if constexpr (R == 1) hop_unit<S, CLOV>(bd, a, t, red);
+      if constexpr (R == 1) hop_unit<S, CLOV, ROWS>(bd, a, t, red);
       else hop_unit_r<S, R>(bd, a, t, red);
     }
   } else {
-    if constexpr (R == 1) hop_unit<S, CLOV>(bd, a, blockIdx.x, red);
+    if constexpr (R == 1) hop_unit<S, CLOV, ROWS>(bd, a, blockIdx.x, red);
     else hop_unit_r<S, R>(bd, a, blockIdx.x, red);
   }
 }
@@ -1159,13 +1186,14 @@ static const HopVariant& variant_of(dd_prec prec, int v) {
   return t[v];
 }
 
-template <class S, int MINB, bool PERSIST, int R, bool CLOV = std::is_same<S, double2>::value>
+template <class S, int MINB, bool PERSIST, int R, bool CLOV = std::is_same<S, double2>::value,
+          bool ROWS = false>
 static void launch_variant(const BatchDev& bd, const HopArgs& a, long long nitems_p, int nsm,
                            cudaStream_t s) {
   const long long nunits = nitems_p * ((bd.nrhs + R - 1) / R);
   long long grid = nunits;
   if (PERSIST) grid = std::min<long long>(nunits, (long long)nsm * MINB);
-  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST, R, CLOV><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
+  DD_COUNT_LAUNCH(), k_hop<S, MINB, PERSIST, R, CLOV, ROWS><<<(unsigned)grid, HOP_THREADS, 0, s>>>(bd, a, nunits);
 }
 
 template <class S, int MINB, bool PERSIST>
@@ -1181,7 +1209,7 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
                          int nsm, cudaStream_t s) {
   if (prec == DD_DF64) {
     if (a.clov_inv) launch_variant<df2s, 4, false, 1, true>(bd, a, ni, nsm, s);
-    else launch_variant<df2s, 4, false, 1>(bd, a, ni, nsm, s);
+    else launch_variant<df2s, 4, false, 1, false, true>(bd, a, ni, nsm, s);
     return;
   }
   if (prec == DD_F64 && a.clov_inv) {      // the clover epilogue lives in the plain form
