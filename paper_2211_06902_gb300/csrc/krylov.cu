@@ -934,11 +934,13 @@ dd_status whole_solve(dd_ctx* c, const Batch& b, dd_prec ip, const InnerVecs& w,
            prm->maxiter, b.hop_variant[0], b.hop_variant[1], b.hop_variant[2], c->clover_active ? 1 : 0,
            (void*)c->d_clovi32, (void*)c->d_clovi_df, (void*)c->d_inst, vos);
   const std::string key = std::string(kb) + keyx;
-  // kernels per pass of each part (for the launch count)
+  // kernels per pass of each part (for the launch count), kept with the batch's
+  // graphs under the graph's key and a suffix per part
   struct Counts {
     long long init, check, verify, pre, inner, post, tres, upd, end;
   };
-  static thread_local std::map<std::string, Counts> counts;
+  static const char* const parts[9] = {":init", ":check", ":verify", ":pre", ":inner", ":post", ":tres", ":upd",
+                                       ":end"};
   cudaGraphExec_t exec = nullptr;
   for (auto& g : b.graphs)
     if (g.first == key) exec = g.second;
@@ -1050,19 +1052,18 @@ dd_status whole_solve(dd_ctx* c, const Batch& b, dd_prec ip, const InnerVecs& w,
       b.graphs.erase(b.graphs.begin());
     }
     b.graphs.push_back({key, exec});
-    counts[key] = n;
+    const long long nv[9] = {n.init, n.check, n.verify, n.pre, n.inner, n.post, n.tres, n.upd, n.end};
+    for (int k = 0; k < 9; ++k) b.graph_kernels[key + parts[k]] = nv[k];
   }
   DD_CUDA(c, cudaGraphLaunch(exec, s));
   OuterState ho{};
   DD_CUDA(c, cudaMemcpyAsync(&ho, os, sizeof ho, cudaMemcpyDeviceToHost, s));
   DD_CUDA(c, cudaStreamSynchronize(s));
-  auto it = counts.find(key);
-  if (it != counts.end()) {
-    const Counts& n = it->second;
-    g_launches.fetch_add(n.init + n.check * ho.osteps + n.verify * ho.n_verify +
-                         (n.pre + n.post + n.end) * ho.cyc + n.inner * ho.iters + n.tres * ho.n_tr +
-                         n.upd * (ho.cyc - ho.n_tr));
-  }
+  long long nv[9];
+  for (int k = 0; k < 9; ++k) nv[k] = b.graph_kernels[key + parts[k]];
+  const Counts n{nv[0], nv[1], nv[2], nv[3], nv[4], nv[5], nv[6], nv[7], nv[8]};
+  g_launches.fetch_add(n.init + n.check * ho.osteps + n.verify * ho.n_verify + (n.pre + n.post + n.end) * ho.cyc +
+                       n.inner * ho.iters + n.tres * ho.n_tr + n.upd * (ho.cyc - ho.n_tr));
   *cycles_out = ho.cyc;
   return DD_OK;
 }
