@@ -292,3 +292,59 @@ def test_whole_solve_graph_is_bit_identical(inner, itol, csw):
     assert np.array_equal(x0, x1) and np.array_equal(x1, x2)
     assert s0["outer_cycles"] == s1["outer_cycles"] == s2["outer_cycles"]
     assert s0["max_iters"] == s1["max_iters"]
+
+
+def test_config5_sampled_blocks_against_the_oracle():
+    """The 48^4 lattice of the largest workload (kappa 0.1365, links exp(i 0.6 H) drawn on
+    the device with seed 5, 1296 framed blocks of 9^4): all blocks x 2 rhs solved with the
+    mixed form to 1e-10 in one batch, and for sampled blocks the true residual recomputed
+    with the oracle's own restricted operator D_Omega (assembled on a box cut around the
+    block from the downloaded links) must be <= 1e-10 |b|."""
+    import torch
+    from oracle.dd import DomainSolver
+    L = (48,) * 4
+    ctx = dd4d.Context(L, 0.1365)
+    ctx.gauge_random(0.6, 5)
+    info = ctx.set_geometry([[(8 * i, 8 * i + 6) for i in range(6)]] * 4)
+    assert info["nblocks"] == 1296
+    ids = list(range(info["nblocks"]))
+    n = info["max_omega"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    b = torch.randn((len(ids), 2, n, 24), generator=gen, device="cuda", dtype=torch.float64) * (0.5 ** 0.5)
+    x = torch.zeros_like(b)
+    st = ctx.solve_blocks("omega", ids, 2, b, x, dd4d.params(1e-10, inner_prec="f32", autotune=True))
+    assert st["status"] == 0 and st["max_relres"] <= 1e-10 and st["systems"] == 2592
+    U = ctx.gauge_download()
+    side = 9
+    for blk in (0, 431, 862, 1295):
+        sites = ctx.geom_sites(dd4d.SET_OMEGA, blk)
+        xs = np.stack(np.unravel_index(sites, L), axis=1)
+        # a box one site larger than the block (the spare layer holds identity links);
+        # blocks that wrap around the lattice are shifted into the box coordinates
+        org = np.array([(c.min() if c.max() - c.min() < side else (c[c >= L[0] // 2].min()))
+                        for c in xs.T])
+        loc = (xs - org) % np.array(L)
+        assert loc.max() < side
+        box = np.zeros((side + 1,) * 4 + (4, 3, 3), dtype=np.complex128)
+        box[...] = np.eye(3)
+        gl = tuple(((org[m] + np.arange(side)) % L[m]) for m in range(4))
+        box[:side, :side, :side, :side] = U[np.ix_(*gl)]
+        # the antiperiodic sign of links crossing x0 = L0-1 -> 0 inside the box
+        t_last = np.flatnonzero(gl[0] == L[0] - 1)
+        if len(t_last) and t_last[0] < side - 1:
+            box[t_last[0], :side, :side, :side, 0] *= -1.0
+        mask = np.zeros(box.shape[:4], dtype=bool)
+        mask[:side, :side, :side, :side] = True
+        sol = DomainSolver(box, 0.1365, mask, time_bc=1)
+        pos = np.ravel_multi_index(tuple(loc.T), (side + 1,) * 4)
+        order = np.searchsorted(sol.sites, pos)
+        bb = b[blk].cpu().numpy().view(np.complex128)
+        xb = x[blk].cpu().numpy().view(np.complex128)
+        for r in range(2):
+            bv = np.zeros((len(sol.sites), 12), dtype=np.complex128)
+            xv = np.zeros_like(bv)
+            bv[order] = bb[r, :len(sites)]
+            xv[order] = xb[r, :len(sites)]
+            res = bv.ravel() - sol.M @ xv.ravel()
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(bv), (blk, r)
