@@ -772,23 +772,7 @@ constexpr int lb_smem_bytes() { return LB_QUARTERS * lb_quarter_bytes<S>() + 64;
 // waits for the phase parity (ph >> q) & 1.  Returns the number of slots it used
 // (0 when the unit had nothing to do); every CTA-wide barrier inside is reached
 // by all threads or by none.
-// Shared state of the compacted bundle form: the active rhs of the CTA and the
-// per-(rhs, quarter) inner-product partials, summed over the quarters in order
-struct LbCompact {
-  int flag[LB_MAX_RHS];
-  int list[LB_MAX_RHS];
-  int na;
-  double part[LB_MAX_RHS][LB_QUARTERS][7];
-};
-__device__ __forceinline__ LbCompact& lb_compact_smem() {
-  __shared__ LbCompact sc;
-  return sc;
-}
-
-// CMP (one rhs per thread, whole items, non-persistent): the CTA's
-// (active rhs, quarter) pairs are spread over all its warps, so the warps of
-// rhs that have converged take quarters of the rhs still running
-template <class S, int RR, int QPC, int MAXR, bool CLOV, bool CMP = false>
+template <class S, int RR, int QPC, int MAXR, bool CLOV>
 __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, long long unit,
                                        unsigned ph, bool fault) {
   typedef typename StoreTraits<S>::C C;
@@ -847,7 +831,7 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
   // Thread 0 waits on every quarter on each path.  If a wait on an issued copy
   // gives up, thread 0 at once waits for that copy once more (bounded), so the
   // CTA's shared memory outlives every copy it started.
-  if (!CMP && !act) {
+  if (!act) {
     // idle warp of a busy CTA: thread 0 still sees its copies land before leaving
     if (threadIdx.x == 0)
       for (int q = 0; q < nq; ++q)
@@ -875,16 +859,14 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
     ts[k][0] = ts[k][1] = ts[k][2] = 0;
     tqs[k][0] = tqs[k][1] = 0;
   }
-  // one quarter of the item for the thread's rhs (the wait on its bundle copy
-  // is taken here, or by the caller when `waited`)
-  auto quarter = [&](int q, bool waited) {
-    if (!waited && !mbar_waitp(&bar[q], (ph >> q) & 1u, fault)) {
+  for (int q = 0; q < nq; ++q) {
+    if (!mbar_waitp(&bar[q], (ph >> q) & 1u, fault)) {
       if (lane == 0) atomicExch(a.err, 1);
       if (threadIdx.x == 0 && q != fq) mbar_waitp(&bar[q], (ph >> q) & 1u, false);
-      return;
+      continue;
     }
     const int li = (q0 + q) * LB_LANES + lane;
-    if (li >= it.z) return;
+    if (li >= it.z) continue;
     const int i = it.y + li;
     if constexpr (CLOV) {
       // the site's A^{-1} rows (288 B) into L1 while the eight directions run;
@@ -1005,79 +987,6 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
         }
       }
     }
-  };
-  if constexpr (!CMP) {
-    for (int q = 0; q < nq; ++q) quarter(q, false);
-  } else {
-    LbCompact& sc = lb_compact_smem();
-    const int nw = blockDim.x >> 5;
-    for (int e = threadIdx.x; e < LB_MAX_RHS * LB_QUARTERS * 7; e += blockDim.x) (&sc.part[0][0][0])[e] = 0.0;
-    if (lane == 0) sc.flag[w] = actk[0] ? 1 : 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int n = 0;
-      for (int v = 0; v < nw; ++v)
-        if (sc.flag[v]) sc.list[n++] = v;
-      sc.na = n;
-    }
-    __syncthreads();
-    const int na = sc.na;
-    for (int kk = w; kk < na * nq; kk += nw) {
-      const int q = kk / na, rr = sc.list[kk % na];
-      sysk[0] = it.x * bd.nrhs + g * rb + rr;
-      actk[0] = true;
-      tq[0][0] = tq[0][1] = 0;
-      ts[0][0] = ts[0][1] = ts[0][2] = 0;
-      tqs[0][0] = tqs[0][1] = 0;
-      // the wait is taken by the whole warp, and a warp whose wait gave up skips
-      // the pair as a whole (the partials keep their zero; the error word is set)
-      const bool okw = mbar_waitp(&bar[q], (ph >> q) & 1u, fault);
-      if (!__all_sync(0xffffffffu, okw)) {
-        if (lane == 0) atomicExch(a.err, 1);
-        continue;
-      }
-      quarter(q, true);
-      T v[7] = {tq[0][0], tq[0][1], ts[0][0], ts[0][1], ts[0][2], tqs[0][0], tqs[0][1]};
-#pragma unroll
-      for (int e = 0; e < 7; ++e)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[e] += __shfl_down_sync(0xffffffffu, v[e], o);
-      if (lane == 0)
-#pragma unroll
-        for (int e = 0; e < 7; ++e) sc.part[rr][q][e] = (double)v[e];
-    }
-    __syncthreads();
-    // thread 0 has not necessarily waited on every quarter: every copy has
-    // landed before the CTA leaves (bounded; a wait that gave up was flagged)
-    if (threadIdx.x == 0)
-      for (int q = 0; q < nq; ++q)
-        if (q != fq && !mbar_waitp(&bar[q], (ph >> q) & 1u, false)) atomicExch(a.err, 1);
-    // per-system partials: the quarters summed in order (deterministic)
-    const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
-    if ((int)threadIdx.x < na) {
-      const int rr = sc.list[threadIdx.x];
-      const long long my = (long long)item * bd.nrhs + g * rb + rr;
-      double v[7] = {0, 0, 0, 0, 0, 0, 0};
-      for (int q = 0; q < nq; ++q)
-#pragma unroll
-        for (int e = 0; e < 7; ++e) v[e] += sc.part[rr][q][e];
-      if (a.dotq) {
-        a.partial[2 * my] = v[0];
-        a.partial[2 * my + 1] = v[1];
-      }
-      if (a.dots) {
-        double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
-        P[2 * my] = v[2];
-        P[2 * my + 1] = v[3];
-        P[2 * (slot_stride + my)] = v[4];
-        P[2 * (slot_stride + my) + 1] = 0.0;
-      }
-      if (a.dotqs) {
-        a.partial[2 * (3 * slot_stride + my)] = v[5];
-        a.partial[2 * (3 * slot_stride + my) + 1] = v[6];
-      }
-    }
-    return nq;
   }
   // per-(warp, k) = per-system partial sums of the chunk
   const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
@@ -1129,7 +1038,7 @@ __device__ __forceinline__ int lb_unit(const BatchDev& bd, const HopArgs& a, int
   return nq;
 }
 
-template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false, bool CMP = false>
+template <class S, int MINB, int RR, int QPC, int MAXR, bool CLOV = false>
 __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     k_hop_lb(BatchDev bd, HopArgs a, int ngroups, int rb) {
   extern __shared__ __align__(128) unsigned char lb_smem[];
@@ -1139,7 +1048,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
     mbar_fence_init();
   }
   __syncthreads();
-  lb_unit<S, RR, QPC, MAXR, CLOV, CMP>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
+  lb_unit<S, RR, QPC, MAXR, CLOV>(bd, a, ngroups, rb, blockIdx.x, 0u, a.lb_fault && blockIdx.x == 0);
 }
 
 // Persistent form with a work queue: a grid of (SMs x resident CTAs) CTAs pulls
@@ -1173,8 +1082,7 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
   }
 }
 
-template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false,
-          bool CMP = false>
+template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
   const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
   const int rb = (bd.nrhs + ngroups - 1) / ngroups;
@@ -1191,7 +1099,7 @@ static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, 
     }
     if (a.dotqs) zero(3);
   }
-  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV, CMP>
+  DD_COUNT_LAUNCH(), k_hop_lb<S, MINB, RR, QPC, MAXR, CLOV>
       <<<(unsigned)(nitems_p * ngroups * NH), nthreads, QPC * lb_quarter_bytes<S>() + 64, s>>>(bd, a, ngroups, rb);
 }
 
@@ -1229,7 +1137,6 @@ void hop_bundle_prepare() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, true>, at, b32);
-  cudaFuncSetAttribute(k_hop_lb<float2, 2, 1, 4, 12, false, true>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<__nv_bfloat162, 2, 1, 4, 12, true>, at, b16);
   cudaFuncSetAttribute(k_hop_lb<float2, 1, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lb<float2, 2, 2, 4, 12>, at, b32);
@@ -1256,7 +1163,6 @@ struct HopVariant {
                   // with k rhs per thread)
   int qpc = 4;    // bundle form: link quarters of the 128-site item per CTA
   int maxr = 12;  // bundle form: most rhs per CTA
-  bool cmp = false;  // bundle form: the warps of converged rhs take quarters of the running ones
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -1266,14 +1172,13 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
                                          {2, false, -3}, {2, false, -1, 2, 12}, {5, false, -1, 2, 6},
-                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6},
-                                         {2, false, -1, 4, 12, true}};
+                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
                                          {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
                                          {2, false, -1, 2, 12}, {5, false, -1, 2, 6}, {2, true, -1}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 23 : 15); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 22 : 15); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1328,8 +1233,7 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
       return;
     }
     if (prec == DD_F32) {
-      if (hv.cmp) launch_lb<float2, 2, 1, LB_QUARTERS, LB_MAX_RHS, false, true>(bd, a, ni, s);
-      else if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
+      if (hv.qpc == 2 && hv.maxr == 6 && hv.minb == 5) launch_lb<float2, 5, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2 && hv.maxr == 6) launch_lb<float2, 4, 1, 2, 6>(bd, a, ni, s);
       else if (hv.qpc == 2) launch_lb<float2, 2, 1, 2, 12>(bd, a, ni, s);
       else if (rr == 3) launch_lb<float2, 2, 3>(bd, a, ni, s);
@@ -1590,11 +1494,7 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.r < 0 && h.cmp)
-          snprintf(names[k][u], sizeof names[k][u],
-                   "k_hop_lb<%s,%d,%d,cmp>: bundle form, the warps of converged rhs take quarters of running ones",
-                   ty[k], h.minb, -h.r);
-        else if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
+        if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);
