@@ -1082,562 +1082,6 @@ __global__ void __launch_bounds__(32 * MAXR / RR, MINB)
   }
 }
 
-// The output of one site for one rhs: out = b*acc + a1*s1 + a2*s2 stored at the
-// site, and the lane's partials of the fused inner products (see HopArgs);
-// oo is the system's offset in the output vector.
-template <class S, class C, class T, class SC>
-__device__ __forceinline__ void lb_site_out(const HopArgs& a, const C (&acc)[12], long long oo, int n_out, int i,
-                                            int sys, bool end_mode, bool dots_in_s1, SC bsc, SC a1, SC a2,
-                                            T (&tq)[2], T (&ts)[3], T (&tqs)[2]) {
-  if (end_mode) {
-    // t = s - k^2 H tmp with (r^, t), (t, s), |t|^2 and (r^, s): one pass over
-    // the component pairs reads s and r^ once each
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const long long e = oo + ((long long)q * n_out + i) * 2;
-      C sv[2], rv[2], ov[2];
-      ld_pair((const S*)a.s1 + e, sv[0], sv[1]);
-      ld_rhat_pair(a.rhat_seed, sys, (const S*)a.dotq + oo, n_out, i, q, rv[0], rv[1]);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        ov[h] = scale(acc[2 * q + h], bsc);
-        axpy(ov[h], a1, sv[h]);
-        const C o = ov[h], w = rv[h], z = sv[h];
-        ts[0] = fma(o.x, z.x, fma(o.y, z.y, ts[0]));
-        ts[1] = fma(o.x, z.y, fma(-o.y, z.x, ts[1]));
-        ts[2] = fma(o.x, o.x, fma(o.y, o.y, ts[2]));
-        tq[0] = fma(w.x, o.x, fma(w.y, o.y, tq[0]));
-        tq[1] = fma(w.x, o.y, fma(-w.y, o.x, tq[1]));
-        tqs[0] = fma(w.x, z.x, fma(w.y, z.y, tqs[0]));
-        tqs[1] = fma(w.x, z.y, fma(-w.y, z.x, tqs[1]));
-      }
-      st_pair((S*)a.out + e, ov[0], ov[1]);
-    }
-    return;
-  }
-  C out[12];
-#pragma unroll
-  for (int c = 0; c < 12; ++c) out[c] = scale(acc[c], bsc);
-  if (a.s1) {
-    C v[12];
-    ld_site<12>((const S*)a.s1 + oo, n_out, i, v);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      axpy(out[c], a1, v[c]);
-      if (dots_in_s1) {
-        ts[0] = fma(out[c].x, v[c].x, fma(out[c].y, v[c].y, ts[0]));
-        ts[1] = fma(out[c].x, v[c].y, fma(-out[c].y, v[c].x, ts[1]));
-        ts[2] = fma(out[c].x, out[c].x, fma(out[c].y, out[c].y, ts[2]));
-      }
-    }
-  }
-  if (a.s2) {
-    C v[12];
-    ld_site<12>((const S*)a.s2 + oo, n_out, i, v);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) axpy(out[c], a2, v[c]);
-  }
-  st_site<12>((S*)a.out + oo, n_out, i, out);
-  if (a.dotq) {
-    C wv[12];
-    ld_rhat(a.rhat_seed, sys, (const S*)a.dotq + oo, n_out, i, wv);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      tq[0] = fma(wv[c].x, out[c].x, fma(wv[c].y, out[c].y, tq[0]));
-      tq[1] = fma(wv[c].x, out[c].y, fma(-wv[c].y, out[c].x, tq[1]));
-    }
-    if (a.dotqs) {
-      // (dotq, s1): the self term is re-read (it was loaded moments ago)
-      C sv[12];
-      ld_site<12>((const S*)a.s1 + oo, n_out, i, sv);
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        tqs[0] = fma(wv[c].x, sv[c].x, fma(wv[c].y, sv[c].y, tqs[0]));
-        tqs[1] = fma(wv[c].x, sv[c].y, fma(-wv[c].y, sv[c].x, tqs[1]));
-      }
-    }
-  }
-  if (a.dots && !dots_in_s1) {
-    C wv[12];
-    ld_site<12>((const S*)a.dots + oo, n_out, i, wv);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      ts[0] = fma(out[c].x, wv[c].x, fma(out[c].y, wv[c].y, ts[0]));
-      ts[1] = fma(out[c].x, wv[c].y, fma(-out[c].y, wv[c].x, ts[1]));
-      ts[2] = fma(out[c].x, out[c].x, fma(out[c].y, out[c].y, ts[2]));
-    }
-  }
-}
-
-// Warp sums of the lane partials of one system, stored (STORE: one CTA per item
-// and system) or added onto zeroed slots (parts of an item) at slot index my;
-// every lane of the warp takes part.
-template <bool STORE, class T>
-__device__ __forceinline__ void lb_put_partials(const HopArgs& a, long long slot_stride, long long my, int lane,
-                                                T (&tq)[2], T (&ts)[3], T (&tqs)[2]) {
-  // parts add onto the zeroed slot (two addends onto zero: order-independent)
-  auto put = [&](double* dst, double v) {
-    if (STORE) *dst = v;
-    else atomicAdd(dst, v);
-  };
-  if (a.dotq) {
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) tq[e] += __shfl_down_sync(0xffffffffu, tq[e], o);
-    if (lane == 0) {
-      put(&a.partial[2 * my], (double)tq[0]);
-      put(&a.partial[2 * my + 1], (double)tq[1]);
-    }
-  }
-  if (a.dots) {
-#pragma unroll
-    for (int e = 0; e < 3; ++e)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ts[e] += __shfl_down_sync(0xffffffffu, ts[e], o);
-    if (lane == 0) {
-      double* P = a.partial + (a.dotq ? 2 * slot_stride : 0);
-      put(&P[2 * my], (double)ts[0]);
-      put(&P[2 * my + 1], (double)ts[1]);
-      put(&P[2 * (slot_stride + my)], (double)ts[2]);
-      if (STORE) P[2 * (slot_stride + my) + 1] = 0.0;
-    }
-  }
-  if (a.dotqs) {
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) tqs[e] += __shfl_down_sync(0xffffffffu, tqs[e], o);
-    if (lane == 0) {
-      put(&a.partial[2 * (3 * slot_stride + my)], (double)tqs[0]);
-      put(&a.partial[2 * (3 * slot_stride + my) + 1], (double)tqs[1]);
-    }
-  }
-}
-
-// ---- neighbour-tile form of the FP32 bundle hop -------------------------------
-// One persistent CTA per SM, one warp per rhs (up to 12).  The link bundles of
-// the CTA's quarters (32 output sites each) pass through a ring of four
-// shared-memory slots: quarter-use t of the CTA's stream lands in slot t & 3,
-// and the last warp to release slot t & 3 issues the bulk copy of quarter-use
-// t + 4, so the next unit's bundles load while the current one computes.  Each
-// warp brings its own rhs's neighbour spinors in by bulk copy too: the
-// neighbours of 32 consecutive output sites in one direction form a run of at
-// most 32 consecutive sites of the input parity (x3-fastest order within the
-// block), the forward and backward runs along x3 and x2 overlap into one run of
-// at most 33 / 41 sites, so a quarter needs about six runs, copied plane by
-// plane (6 pair planes x 16 B per site) into a two-stage ring of the warp.  No
-// thread holds registers or issues loads for a neighbour while it is in flight.
-// A direction whose run would not fit a stage (other geometries) and a system
-// vector that is not 16-byte aligned fall back to per-thread loads.
-constexpr int LBT_WARPS = 12;
-constexpr int LBT_CAP = 48;                       // sites per stage
-constexpr int LBT_STAGE = 6 * LBT_CAP * 16;       // bytes per stage (FP32 pair planes)
-constexpr int LBT_NONE = -1;                      // no neighbour of the quarter in this direction
-constexpr int LBT_DIRECT = -2;                    // neighbours by per-thread loads
-struct LbtPlan {                                  // one quarter of one warp, in shared memory
-  const float4* src;                              // pair plane 0 of the warp's input system
-  int n_in;                                       // sites per plane
-  int nr;                                         // runs
-  unsigned merged;                                // bit mu: directions mu, mu + 4 share one run
-  int jm[8];                                      // per direction: first site of its run, or a marker
-  int rj[8], rs[8];                               // per run: first site, sites
-  int pad[3];
-};
-static_assert(sizeof(LbtPlan) == 128, "plan slot size");
-constexpr int LBT_PLANS = 4;                      // plan ring per warp
-constexpr int LBT_OFF_STAGE = LB_QUARTERS * lb_quarter_bytes<float2>();
-constexpr int LBT_OFF_PLAN = LBT_OFF_STAGE + LBT_WARPS * 2 * LBT_STAGE;
-constexpr int LBT_OFF_BAR = LBT_OFF_PLAN + LBT_WARPS * LBT_PLANS * (int)sizeof(LbtPlan);
-constexpr int LBT_SMEM = LBT_OFF_BAR + (LB_QUARTERS + 2 * LBT_WARPS) * 8 + LB_QUARTERS * 4;
-static_assert(LBT_SMEM <= 227 * 1024, "shared memory of the tile form");
-static_assert(LBT_OFF_STAGE % 128 == 0 && LBT_STAGE % 128 == 0, "stage alignment");
-
-// a work unit (item, rhs group) of the CTA's stream and which of its rhs run
-struct LbtUnit {
-  int u;             // unit index; nunits: past the end
-  int item, g, nq;   // item, rhs group, quarters
-  int4 it;           // (block, first site, sites, -) of the item
-  unsigned act;      // bit r: rhs g * rb + r is active
-};
-
-// the first unit at or after u (stride: the grid) with an active rhs; every
-// lane of the warp takes part and all get the same answer
-__device__ __forceinline__ LbtUnit lbt_find(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, int u,
-                                           int nunits, int lane) {
-  LbtUnit U;
-  for (; u < nunits; u += gridDim.x) {
-    U.item = u / ngroups;
-    U.g = u - U.item * ngroups;
-    U.it = (a.p_out ? bd.items[1] : bd.items[0])[U.item];
-    U.nq = min(LB_QUARTERS, (U.it.z + LB_LANES - 1) / LB_LANES);
-    const int r = U.g * rb + lane;
-    const bool on = lane < rb && r < bd.nrhs &&
-                    (!a.active || a.active[((long long)U.it.x * bd.nrhs + r) * a.active_stride]);
-    U.act = __ballot_sync(0xffffffffu, on);
-    if (U.act && U.nq > 0) {
-      U.u = u;
-      return U;
-    }
-  }
-  U.u = nunits;
-  U.act = 0;
-  U.nq = 0;
-  return U;
-}
-
-// bounded wait of the tile form: the full limit while no wait anywhere has
-// given up, a short one after that, so that a failed wait ends the kernel soon
-__device__ __forceinline__ bool lbt_wait(unsigned long long* bar, unsigned par, const int* err) {
-  if (mbar_try_wait(bar, par)) return true;
-  return mbar_waitp(bar, par, *(volatile const int*)err != 0);
-}
-
-// the quarter-use after (U, q): the next quarter of the unit or quarter 0 of
-// the next unit with work
-__device__ __forceinline__ void lbt_step(const BatchDev& bd, const HopArgs& a, int ngroups, int rb, int nunits,
-                                         int lane, LbtUnit& U, int& q) {
-  if (++q < U.nq) return;
-  q = 0;
-  U = lbt_find(bd, a, ngroups, rb, U.u + gridDim.x, nunits, lane);
-}
-
-// bulk copy of quarter q of unit U's link bundle into ring slot `slot` (one thread)
-__device__ __forceinline__ void lbt_issue_bundle(const BatchDev& bd, int p, const LbtUnit& U, int q,
-                                                 unsigned char* smem, unsigned long long* bar, int slot) {
-  constexpr int QB = lb_quarter_bytes<float2>();
-  const DomInst* dp = bd.inst_tab + bd.inst[U.it.x];
-  const unsigned char* src = bundle_of<float2>(*dp) +
-      (lb_quarter_base(p, dp->n[0]) + (long long)LB_QUARTERS * (U.it.y / LB_CHUNK) + q) * QB;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(&bar[slot], QB);
-  bulk_copy_g2s(smem + slot * QB, src, QB, &bar[slot]);
-}
-
-// The runs of one quarter from its neighbour table qi (all lanes take part;
-// lane m < 4 plans the direction pair mu = 3 - m, the pairs' runs in that
-// order).  src = the warp's input system, or null: no runs (idle).
-__device__ __forceinline__ void lbt_plan(LbtPlan* P, const int* qi, const float4* src, int n_in, int lane) {
-  int lo[8], hi[8];
-#pragma unroll
-  for (int d = 0; d < 8; ++d) {
-    const int j = src ? qi[d * LB_LANES + lane] : -1;
-    lo[d] = __reduce_min_sync(0xffffffffu, j >= 0 ? j : 0x7fffffff);
-    hi[d] = __reduce_max_sync(0xffffffffu, j);
-  }
-  const int m = lane & 3, mu = 3 - m;
-  int lf = lo[0], hf = hi[0], lb = lo[4], hb = hi[4];
-#pragma unroll
-  for (int k = 1; k < 4; ++k)
-    if (mu == k) {
-      lf = lo[k];
-      hf = hi[k];
-      lb = lo[k + 4];
-      hb = hi[k + 4];
-    }
-  const bool tiles = src && ((reinterpret_cast<unsigned long long>(src) & 15ull) == 0);
-  const bool vf = hf >= 0, vb = hb >= 0;
-  const int ulo = min(lf, lb), uhi = max(hf, hb);
-  const bool merged = tiles && vf && vb && uhi - ulo + 1 <= LBT_CAP;
-  const bool tf = !merged && tiles && vf && hf - lf + 1 <= LBT_CAP;
-  const bool tb = !merged && tiles && vb && hb - lb + 1 <= LBT_CAP;
-  const int c = merged ? 1 : (tf ? 1 : 0) + (tb ? 1 : 0);
-  // exclusive prefix of the run counts over lanes 0..3
-  int incl = c;
-#pragma unroll
-  for (int o = 1; o < 4; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o, 4);
-    if (m >= o) incl += v;
-  }
-  const int first = incl - c;
-  const int nr = __shfl_sync(0xffffffffu, incl, 3);
-  const unsigned mb = __ballot_sync(0xffffffffu, lane < 4 && merged);
-  if (lane < 4) {
-    if (merged) {
-      P->rj[first] = ulo;
-      P->rs[first] = uhi - ulo + 1;
-      P->jm[mu] = P->jm[mu + 4] = ulo;
-    } else {
-      int k = first;
-      if (tf) {
-        P->rj[k] = lf;
-        P->rs[k] = hf - lf + 1;
-        ++k;
-      }
-      if (tb) {
-        P->rj[k] = lb;
-        P->rs[k] = hb - lb + 1;
-      }
-      P->jm[mu] = tf ? lf : (vf ? LBT_DIRECT : LBT_NONE);
-      P->jm[mu + 4] = tb ? lb : (vb ? LBT_DIRECT : LBT_NONE);
-    }
-  }
-  if (lane == 0) {
-    P->src = src;
-    P->n_in = n_in;
-    P->nr = src ? nr : 0;
-    // ballot bit m is pair mu = 3 - m
-    P->merged = ((mb & 1u) << 3) | ((mb & 2u) << 1) | ((mb & 4u) >> 1) | ((mb & 8u) >> 3);
-  }
-  __syncwarp();
-}
-
-// one direction of the tile form: the link from the bundle slot, the
-// neighbour spinor from the warp's stage (a run starting at site jm)
-template <int DIR>
-__device__ __forceinline__ void hop_lbt_dir(float2 (&acc)[12], const int* qi, const float2* ql, int lane,
-                                            const float4* st, int jm) {
-  constexpr int MU = DIR & 3;
-  constexpr bool FWD = DIR < 4;
-  const int j = qi[DIR * LB_LANES + lane];
-  if (j < 0) return;
-  float2 U[9];
-  lds_link(ql + DIR * 5 * LB_LANES * 2, lane, U);
-  float2 psi[12];
-  const float4* s = st + (j - jm);
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const float4 v = s[q * LBT_CAP];
-    psi[2 * q] = make_float2(v.x, v.y);
-    psi[2 * q + 1] = make_float2(v.z, v.w);
-  }
-  hop_dir<MU, FWD>(acc, psi, U);
-}
-
-// The neighbour runs of one warp: a two-stage ring filled by bulk copies (lane
-// 0 issues, the stage's barrier counts the bytes) from the warp's plan ring;
-// the producer keeps two runs ahead of the consumer.  All lanes keep the same
-// counters.
-struct LbtRuns {
-  unsigned long long* bar;   // the warp's two stage barriers
-  unsigned char* base;       // the warp's two stages
-  LbtPlan* plans;            // the warp's plan ring
-  int ki, kc;                // runs issued, consumed
-  int pt, pr;                // producer: quarter-use and run within it
-  int tplan;                 // last quarter-use with a plan
-
-  __device__ __forceinline__ void top_up(int lane) {
-    while (ki < kc + 2 && pt <= tplan) {
-      const LbtPlan* P = plans + (pt & (LBT_PLANS - 1));
-      const int nr = P->nr;
-      if (pr >= nr) {
-        ++pt;
-        pr = 0;
-        continue;
-      }
-      // lane 0 arms the stage's barrier, lanes 0..5 copy one pair plane each;
-      // the stage was read by the warp's run ki - 2 (its lanes met at __syncwarp)
-      const int s = ki & 1;
-      const unsigned ns = P->rs[pr];
-      if (lane == 0) mbar_expect_tx(&bar[s], 6u * ns * 16u);
-      __syncwarp();
-      if (lane < 6) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_copy_g2s(base + s * LBT_STAGE + lane * LBT_CAP * 16, P->src + (long long)lane * P->n_in + P->rj[pr],
-                      ns * 16u, &bar[s]);
-      }
-      ++ki;
-      if (++pr >= nr) {
-        ++pt;
-        pr = 0;
-      }
-    }
-  }
-  // the stage of the next run to consume, once its copies have landed (bounded)
-  __device__ __forceinline__ const float4* wait(int lane, int* err) {
-    const int s = kc & 1;
-    const unsigned par = (kc >> 1) & 1;
-    if (!lbt_wait(&bar[s], par, err) && lane == 0) {
-      atomicExch(err, 1);
-      lbt_wait(&bar[s], par, err);
-    }
-    return reinterpret_cast<const float4*>(base + s * LBT_STAGE);
-  }
-  __device__ __forceinline__ void done(int lane) {
-    __syncwarp();
-    ++kc;
-    top_up(lane);
-  }
-};
-
-// the directions mu and mu + 4 of one quarter, in the order of the plan's runs
-template <int MU>
-__device__ __forceinline__ void lbt_pair(float2 (&acc)[1][12], const LbtPlan* P, LbtRuns& R, const int* qi,
-                                         const float2* ql, int lane, int n_in, const void* in,
-                                         const long long* off_in, const int (&sysk)[1], const bool (&actk)[1],
-                                         int* err) {
-  const int jf = P->jm[MU], jb = P->jm[MU + 4];
-  if ((P->merged >> MU) & 1u) {
-    const float4* st = R.wait(lane, err);
-    hop_lbt_dir<MU>(acc[0], qi, ql, lane, st, jf);
-    hop_lbt_dir<MU + 4>(acc[0], qi, ql, lane, st, jb);
-    R.done(lane);
-    return;
-  }
-  if (jf >= 0) {
-    const float4* st = R.wait(lane, err);
-    hop_lbt_dir<MU>(acc[0], qi, ql, lane, st, jf);
-    R.done(lane);
-  } else if (jf == LBT_DIRECT) {
-    hop_lb_dir<MU, float2, float2, 1>(acc, qi, ql, lane, n_in, in, off_in, sysk, actk);
-  }
-  if (jb >= 0) {
-    const float4* st = R.wait(lane, err);
-    hop_lbt_dir<MU + 4>(acc[0], qi, ql, lane, st, jb);
-    R.done(lane);
-  } else if (jb == LBT_DIRECT) {
-    hop_lb_dir<MU + 4, float2, float2, 1>(acc, qi, ql, lane, n_in, in, off_in, sysk, actk);
-  }
-}
-
-// grid: min(units, SMs) persistent CTAs of 32 * rb threads (rb <= 12 rhs of
-// a group, one warp each); CTA b takes the units b, b + grid, ... that have an
-// active rhs, in order.  Same arithmetic per site and the same direction order
-// as the bundle form.
-__global__ void __launch_bounds__(32 * LBT_WARPS, 1)
-    k_hop_lbt(BatchDev bd, HopArgs a, int ngroups, int rb, int nunits) {
-  typedef float2 S;
-  typedef float2 C;
-  typedef float T;
-  constexpr int QB = lb_quarter_bytes<S>();
-  extern __shared__ __align__(128) unsigned char lb_smem[];
-  unsigned long long* qbar = reinterpret_cast<unsigned long long*>(lb_smem + LBT_OFF_BAR);
-  int* rel = reinterpret_cast<int*>(qbar + LB_QUARTERS + 2 * LBT_WARPS);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < LB_QUARTERS + 2 * nw; ++k) mbar_init(&qbar[k], 1);
-    for (int q = 0; q < LB_QUARTERS; ++q) rel[q] = 0;
-    mbar_fence_init();
-  }
-  __syncthreads();
-  const int p = a.p_out;
-  auto qi_of = [&](int slot) { return reinterpret_cast<const int*>(lb_smem + slot * QB + lb_link_bytes<S>()); };
-  // the warp's input system in unit V (null: its rhs is idle there)
-  const long long* off_in = p ? bd.off[0] : bd.off[1];
-  const long long* off_out = p ? bd.off[1] : bd.off[0];
-  auto sys_src = [&](const LbtUnit& V, int& nin) -> const float4* {
-    if (!((V.act >> w) & 1u)) return nullptr;
-    const DomInst* dv = bd.inst_tab + bd.inst[V.it.x];
-    nin = p ? dv->n[0] : dv->n[1];
-    const long long sys = (long long)V.it.x * bd.nrhs + V.g * rb + w;
-    return reinterpret_cast<const float4*>((const S*)a.in + off_in[sys]);
-  };
-  auto wait_slot = [&](int slot, unsigned par) {
-    if (!lbt_wait(&qbar[slot], par, a.err) && lane == 0) {
-      atomicExch(a.err, 1);
-      lbt_wait(&qbar[slot], par, a.err);
-    }
-  };
-  LbtUnit U = lbt_find(bd, a, ngroups, rb, blockIdx.x, nunits, lane);
-  // ahead cursor: quarter-use t + 4, whose bundle the last warp to release
-  // slot t & 3 issues; the first four are issued here
-  LbtUnit A = U;
-  int qa = 0;
-  for (int k = 0; k < LB_QUARTERS; ++k)
-    if (A.u < nunits) {
-      if (threadIdx.x == 0) lbt_issue_bundle(bd, p, A, qa, lb_smem, qbar, k);
-      lbt_step(bd, a, ngroups, rb, nunits, lane, A, qa);
-    }
-  LbtRuns R;
-  R.bar = qbar + LB_QUARTERS + 2 * w;
-  R.base = lb_smem + LBT_OFF_STAGE + w * 2 * LBT_STAGE;
-  R.plans = reinterpret_cast<LbtPlan*>(lb_smem + LBT_OFF_PLAN) + w * LBT_PLANS;
-  R.ki = R.kc = R.pt = R.pr = 0;
-  R.tplan = -1;
-  if (U.u < nunits) {
-    int nin = 0;
-    const float4* src = sys_src(U, nin);
-    if (src) wait_slot(0, 0);
-    lbt_plan(R.plans, qi_of(0), src, nin, lane);
-    R.tplan = 0;
-    R.top_up(lane);
-  }
-  const auto bsc = mkscal<C>(a.b);
-  const auto a1 = mkscal<C>(a.a1);
-  const auto a2 = mkscal<C>(a.a2);
-  const bool dots_in_s1 = a.dots && a.dots == a.s1 && !a.s2;
-  const bool end_mode = dots_in_s1 && a.dotq && a.dotqs;
-  const long long slot_stride = (long long)(p ? bd.nitems[1] : bd.nitems[0]) * bd.nrhs;
-  T tq[2] = {0, 0}, ts[3] = {0, 0, 0}, tqs[2] = {0, 0};
-  int q = 0, t = 0;
-  while (U.u < nunits) {
-    const int slot = t & 3;
-    const bool act = (U.act >> w) & 1u;
-    const DomInst* dp = bd.inst_tab + bd.inst[U.it.x];
-    const int n0 = dp->n[0];
-    const int n_out = p ? dp->n[1] : n0, n_in = p ? n0 : dp->n[1];
-    const int r = U.g * rb + w;
-    const int sysk[1] = {U.it.x * bd.nrhs + r};
-    const bool actk[1] = {act};
-    if (q == 0 && threadIdx.x == 0 && a.work_bytes)
-      atomicAdd(a.work_bytes, a.site_bytes * U.it.z * __popc(U.act));
-    // every warp waits for the slot, busy or idle: its release below must not
-    // be counted before the slot's copy was issued
-    wait_slot(slot, (t >> 2) & 1);
-    // the next quarter-use and its plan, so that its first runs are in flight
-    // while this quarter computes
-    LbtUnit N = U;
-    int qn = q;
-    lbt_step(bd, a, ngroups, rb, nunits, lane, N, qn);
-    if (N.u < nunits) {
-      int nin = 0;
-      const float4* src = sys_src(N, nin);
-      const int sn = (t + 1) & 3;
-      if (src) wait_slot(sn, ((t + 1) >> 2) & 1);
-      lbt_plan(R.plans + ((t + 1) & (LBT_PLANS - 1)), qi_of(sn), src, nin, lane);
-      R.tplan = t + 1;
-      R.top_up(lane);
-    }
-    if (act) {
-      const unsigned char* qb = lb_smem + slot * QB;
-      const float2* ql = reinterpret_cast<const float2*>(qb);
-      const int* qi = reinterpret_cast<const int*>(qb + lb_link_bytes<S>());
-      const LbtPlan* P = R.plans + (t & (LBT_PLANS - 1));
-      C acc[1][12];
-#pragma unroll
-      for (int c = 0; c < 12; ++c) acc[0][c] = make_float2(0.f, 0.f);
-      lbt_pair<3>(acc, P, R, qi, ql, lane, n_in, a.in, off_in, sysk, actk, a.err);
-      lbt_pair<2>(acc, P, R, qi, ql, lane, n_in, a.in, off_in, sysk, actk, a.err);
-      lbt_pair<1>(acc, P, R, qi, ql, lane, n_in, a.in, off_in, sysk, actk, a.err);
-      lbt_pair<0>(acc, P, R, qi, ql, lane, n_in, a.in, off_in, sysk, actk, a.err);
-      const int li = q * LB_LANES + lane;
-      if (li < U.it.z)
-        lb_site_out<S, C, T>(a, acc[0], off_out[sysk[0]], n_out, U.it.y + li, sysk[0], end_mode, dots_in_s1,
-                             bsc, a1, a2, tq, ts, tqs);
-      if (q == U.nq - 1) {
-        lb_put_partials<true>(a, slot_stride, (long long)U.item * bd.nrhs + r, lane, tq, ts, tqs);
-        tq[0] = tq[1] = 0;
-        ts[0] = ts[1] = ts[2] = 0;
-        tqs[0] = tqs[1] = 0;
-      }
-    }
-    // release the slot; the last warp issues the bundle of quarter-use t + 4
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) {
-      __threadfence_block();
-      last = atomicAdd(&rel[slot], 1) == nw - 1;
-      if (last) rel[slot] = 0;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (A.u < nunits) {
-      if (last && lane == 0) lbt_issue_bundle(bd, p, A, qa, lb_smem, qbar, slot);
-      lbt_step(bd, a, ngroups, rb, nunits, lane, A, qa);
-    }
-    U = N;
-    q = qn;
-    ++t;
-  }
-}
-
-static void launch_lbt(const BatchDev& bd, const HopArgs& a, long long nitems_p, int nsm, cudaStream_t s) {
-  const int ngroups = (bd.nrhs + LBT_WARPS - 1) / LBT_WARPS;
-  const int rb = (bd.nrhs + ngroups - 1) / ngroups;
-  const long long nunits = nitems_p * ngroups;
-  const long long grid = std::min<long long>(nunits, nsm);
-  DD_COUNT_LAUNCH(), k_hop_lbt<<<(unsigned)grid, 32 * rb, LBT_SMEM, s>>>(bd, a, ngroups, rb, (int)nunits);
-}
-
 template <class S, int MINB, int RR, int QPC = LB_QUARTERS, int MAXR = LB_MAX_RHS, bool CLOV = false>
 static void launch_lb(const BatchDev& bd, const HopArgs& a, long long nitems_p, cudaStream_t s) {
   const int ngroups = (bd.nrhs + MAXR - 1) / MAXR;
@@ -1709,7 +1153,6 @@ void hop_bundle_prepare() {
   cudaFuncSetAttribute(k_hop_lbq<float2, 2, 1, 4, 12>, at, b32);
   cudaFuncSetAttribute(k_hop_lbq<float2, 4, 1, 2, 6>, at, h32);
   cudaFuncSetAttribute(k_hop_lbq<__nv_bfloat162, 2, 1, 4, 12>, at, b16);
-  cudaFuncSetAttribute(k_hop_lbt, at, LBT_SMEM);
   done[dev] = true;
 }
 
@@ -1720,7 +1163,6 @@ struct HopVariant {
                   // with k rhs per thread)
   int qpc = 4;    // bundle form: link quarters of the 128-site item per CTA
   int maxr = 12;  // bundle form: most rhs per CTA
-  bool tiles = false;  // bundle form with the neighbour spinors by bulk copy (FP32)
 };
 // per storage precision; index 0 is the default before tuning
 static const HopVariant kVariants64[] = {{3, false, 1}, {2, false, 1}, {3, true, 1}, {2, false, 2},
@@ -1730,14 +1172,13 @@ static const HopVariant kVariants32[] = {{6, false, 1}, {4, false, 1}, {8, false
                                          {3, false, 3}, {3, false, 4}, {3, false, 0}, {4, false, 0},
                                          {3, true, 0}, {2, false, -1}, {1, false, -1}, {2, false, -2},
                                          {2, false, -3}, {2, false, -1, 2, 12}, {5, false, -1, 2, 6},
-                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6},
-                                         {1, true, -1, 4, 12, true}};
+                                         {4, false, -1, 2, 6}, {2, true, -1}, {4, true, -1, 2, 6}};
 static const HopVariant kVariants16[] = {{5, false, 1}, {4, false, 1}, {8, false, 1}, {5, true, 1},
                                          {4, false, 2}, {3, false, 3}, {3, false, 0}, {4, false, 0},
                                          {2, false, -1}, {1, false, -1}, {3, false, -2}, {4, false, -3},
                                          {2, false, -1, 2, 12}, {5, false, -1, 2, 6}, {2, true, -1}};
 
-int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 23 : 15); }
+int hop_variant_count(dd_prec prec) { return prec == DD_F64 ? 5 : (prec == DD_F32 ? 22 : 15); }
 
 static const HopVariant& variant_of(dd_prec prec, int v) {
   const HopVariant* t = prec == DD_F64 ? kVariants64 : (prec == DD_F32 ? kVariants32 : kVariants16);
@@ -1783,10 +1224,6 @@ static void dispatch_hop(dd_prec prec, int v, const BatchDev& bd, const HopArgs&
     return;
   }
   const HopVariant& hv = variant_of(prec, v);
-  if (hv.tiles && prec == DD_F32) {
-    launch_lbt(bd, a, ni, nsm, s);
-    return;
-  }
   if (hv.r < 0) {
     const int rr = -hv.r;
     if (hv.persist) {
@@ -2057,10 +1494,7 @@ const char* dd_hop_variant_name(dd_prec prec, int v) {
     for (int k = 0; k < 3; ++k)
       for (int u = 0; u < dd::hop_variant_count(ps[k]) && u < 32; ++u) {
         const dd::HopVariant& h = dd::variant_of(ps[k], u);
-        if (h.tiles)
-          snprintf(names[k][u], sizeof names[k][u],
-                   "k_hop_lbt<%s>: persistent bundle form, neighbour runs by bulk copy, up to 12 rhs per CTA", ty[k]);
-        else if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
+        if (h.r < 0 && h.qpc == 4 && h.maxr == 12 && !h.persist)
           snprintf(names[k][u], sizeof names[k][u],
                    "k_hop_lb<%s,%d,%d>: links by bulk copy into shared memory, up to 12 rhs per CTA, %d per thread",
                    ty[k], h.minb, -h.r, -h.r);

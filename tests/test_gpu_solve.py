@@ -348,48 +348,3 @@ def test_config5_sampled_blocks_against_the_oracle():
             xv[order] = xb[r, :len(sites)]
             res = bv.ravel() - sol.M @ xv.ravel()
             assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(bv), (blk, r)
-
-
-def test_neighbour_tile_form_in_solves():
-    """The FP32 hop form that copies each warp's neighbour runs into shared
-    memory (k_hop_lbt: persistent CTAs, link bundles through a ring of four
-    quarter slots) against the plain bundle form: the same stencil on 9^4
-    framed blocks and on uneven blocks, and mixed solves whose launches carry
-    the fused inner products and skip converged systems, with 13 rhs (two
-    groups of 7 and 6 warps) and 3 rhs; every solution re-checked with the
-    oracle's operator."""
-    names = [dd4d.hop_variant_name("f32", k) or "" for k in range(64)]
-    vt = next(k for k, n in enumerate(names) if n.startswith("k_hop_lbt"))
-    vb = next(k for k, n in enumerate(names) if n.startswith("k_hop_lb<"))
-    cases = [((16, 16, 16, 16), uniform_cores((16,) * 4, 7, 1), 0.135, 13),
-             ((12, 8, 8, 10), [[(0, 3), (6, 8)], [(1, 2), (5, 6)], [(0, 4), (6, 6)], [(0, 2), (4, 7)]],
-              0.12, 3)]
-    for L, cores, kappa, nrhs in cases:
-        U, ctx, info, geo = make_case(L, kappa, 0.5, 7, cores)
-        ids = list(range(info["nblocks"]))
-        sites = [ctx.geom_sites(dd4d.SET_OMEGA, b) for b in ids]
-        tot = sum(len(s) for s in sites)
-        b = synth.complex_gaussian(9, synth.TAG_RHS, (nrhs * tot, 12))
-        outs, xs = [], []
-        for v in (vb, vt):
-            ctx.set_hop_variant("f32", v)
-            out = np.zeros_like(b)
-            ctx.apply_D_block("omega", ids, nrhs, b, out, "f32")
-            x = np.zeros_like(b)
-            st = ctx.solve_blocks("omega", ids, nrhs, b, x, dd4d.params(1e-10, inner_prec="f32"))
-            assert st["status"] == 0 and st["max_relres"] <= 1e-10, (v, st)
-            outs.append(out)
-            xs.append(x)
-        ctx.set_hop_variant("f32", -1)
-        assert relerr(outs[1], outs[0]) < 1e-6
-        assert relerr(xs[1], xs[0]) < 1e-8
-        off = 0
-        for k, blk in enumerate(ids):
-            n = len(sites[k])
-            for r in range(nrhs):
-                if (k + r) % 5 == 0:
-                    f = to_field(L, sites[k], b[off:off + n])
-                    xf = to_field(L, sites[k], xs[1][off:off + n])
-                    res = f - apply_D_restricted(U, xf, kappa, geo.omega_mask[blk])
-                    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(f) * 1.0000001
-                off += n
