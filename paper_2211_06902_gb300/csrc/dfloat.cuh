@@ -52,6 +52,73 @@ __device__ __forceinline__ void df_renorm(float& h, float& l) {
   l = t;
 }
 
+// ---- packed pairs: two FP32 lanes in one 64-bit register --------------------------
+// The f32x2 forms of add, sub, mul and fma (round to nearest on each lane) run
+// the real and imaginary parts of a complex double-float through one
+// instruction stream: every lane performs the same operations in the same
+// order as the scalar primitives above, so the results are theirs.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk(float x, float y) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ f2p pk(float2 v) { return pk(v.x, v.y); }
+__device__ __forceinline__ float2 upk(f2p r) {
+  float x, y;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+  return make_float2(x, y);
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+  f2p r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+  f2p r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+  f2p r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// df_add on both lanes
+__device__ __forceinline__ void df_add2(f2p& h, f2p& l, f2p bh, f2p bl) {
+  const f2p s = add2(h, bh);
+  const f2p bb = sub2(s, h);
+  const f2p t = add2(sub2(h, sub2(s, bb)), sub2(bh, bb));
+  h = s;
+  l = add2(l, add2(t, bl));
+}
+// df_add of the negated operand on both lanes, with x + (-y) written x - y
+__device__ __forceinline__ void df_sub2(f2p& h, f2p& l, f2p bh, f2p bl) {
+  const f2p s = sub2(h, bh);
+  const f2p bb = sub2(s, h);
+  const f2p t = sub2(sub2(h, sub2(s, bb)), add2(bh, bb));
+  h = s;
+  l = add2(l, sub2(t, bl));
+}
+// df_fma on both lanes; nah = -ah, so q = -(ah bh) rounded is the negated
+// product and the error terms and TwoSum follow df_fma with p = -q
+__device__ __forceinline__ void df_fma2(f2p& h, f2p& l, f2p ah, f2p al, f2p nah, f2p bh, f2p bl) {
+  const f2p q = mul2(nah, bh);
+  f2p e = fma2(ah, bh, q);
+  e = fma2(ah, bl, e);
+  e = fma2(al, bh, e);
+  const f2p s = sub2(h, q);
+  const f2p bb = sub2(s, h);
+  const f2p t = sub2(sub2(h, sub2(s, bb)), add2(q, bb));
+  h = s;
+  l = add2(l, add2(t, e));
+}
+
 // ---- complex helpers used by the generic stencil code -------------------------------
 __device__ __forceinline__ dfc ldc(const df2s* p) {
   const float4 v = __ldg(&p->v);
@@ -92,14 +159,14 @@ __device__ __forceinline__ double2 to_d2(dfc a) {
   return make_double2((double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
 }
 __device__ __forceinline__ dfc cadd(dfc a, dfc b) {
-  df_add(a.h.x, a.l.x, b.h.x, b.l.x);
-  df_add(a.h.y, a.l.y, b.h.y, b.l.y);
-  return a;
+  f2p h = pk(a.h), l = pk(a.l);
+  df_add2(h, l, pk(b.h), pk(b.l));
+  return dfc{upk(h), upk(l)};
 }
 __device__ __forceinline__ dfc csub(dfc a, dfc b) {
-  df_add(a.h.x, a.l.x, -b.h.x, -b.l.x);
-  df_add(a.h.y, a.l.y, -b.h.y, -b.l.y);
-  return a;
+  f2p h = pk(a.h), l = pk(a.l);
+  df_sub2(h, l, pk(b.h), pk(b.l));
+  return dfc{upk(h), upk(l)};
 }
 // a + i b and a - i b
 __device__ __forceinline__ dfc caddi(dfc a, dfc b) {
@@ -112,32 +179,33 @@ __device__ __forceinline__ dfc csubi(dfc a, dfc b) {
   df_add(a.h.y, a.l.y, -b.h.x, -b.l.x);
   return a;
 }
-// acc += a b and acc += conj(a) b
+// acc += a b and acc += conj(a) b, as two double-float FMAs on (re, im) lane
+// pairs: re += a.re b.re then -/+ a.im b.im, im += a.re b.im then +/- a.im b.re
 __device__ __forceinline__ void cfma(dfc& acc, dfc a, dfc b) {
-  df_fma(acc.h.x, acc.l.x, a.h.x, a.l.x, b.h.x, b.l.x);
-  df_fma(acc.h.x, acc.l.x, -a.h.y, -a.l.y, b.h.y, b.l.y);
-  df_fma(acc.h.y, acc.l.y, a.h.x, a.l.x, b.h.y, b.l.y);
-  df_fma(acc.h.y, acc.l.y, a.h.y, a.l.y, b.h.x, b.l.x);
+  f2p h = pk(acc.h), l = pk(acc.l);
+  df_fma2(h, l, pk(a.h.x, a.h.x), pk(a.l.x, a.l.x), pk(-a.h.x, -a.h.x), pk(b.h), pk(b.l));
+  df_fma2(h, l, pk(-a.h.y, a.h.y), pk(-a.l.y, a.l.y), pk(a.h.y, -a.h.y), pk(b.h.y, b.h.x), pk(b.l.y, b.l.x));
+  acc = dfc{upk(h), upk(l)};
 }
 __device__ __forceinline__ void cfmac(dfc& acc, dfc a, dfc b) {
-  df_fma(acc.h.x, acc.l.x, a.h.x, a.l.x, b.h.x, b.l.x);
-  df_fma(acc.h.x, acc.l.x, a.h.y, a.l.y, b.h.y, b.l.y);
-  df_fma(acc.h.y, acc.l.y, a.h.x, a.l.x, b.h.y, b.l.y);
-  df_fma(acc.h.y, acc.l.y, -a.h.y, -a.l.y, b.h.x, b.l.x);
+  f2p h = pk(acc.h), l = pk(acc.l);
+  df_fma2(h, l, pk(a.h.x, a.h.x), pk(a.l.x, a.l.x), pk(-a.h.x, -a.h.x), pk(b.h), pk(b.l));
+  df_fma2(h, l, pk(a.h.y, -a.h.y), pk(a.l.y, -a.l.y), pk(-a.h.y, a.h.y), pk(b.h.y, b.h.x), pk(b.l.y, b.l.x));
+  acc = dfc{upk(h), upk(l)};
 }
 
 template <> struct ScalOf<dfc> { typedef float2 type; };
 template <> __device__ __forceinline__ float2 mkscal<dfc>(double x) { return split_d(x); }
 // a * s for a double-float real s
 __device__ __forceinline__ dfc scale(dfc a, float2 s) {
-  dfc r{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  df_fma(r.h.x, r.l.x, a.h.x, a.l.x, s.x, s.y);
-  df_fma(r.h.y, r.l.y, a.h.y, a.l.y, s.x, s.y);
-  return r;
+  f2p h = pk(0.f, 0.f), l = pk(0.f, 0.f);
+  df_fma2(h, l, pk(a.h), pk(a.l), pk(-a.h.x, -a.h.y), pk(s.x, s.x), pk(s.y, s.y));
+  return dfc{upk(h), upk(l)};
 }
 __device__ __forceinline__ void axpy(dfc& o, float2 s, dfc v) {
-  df_fma(o.h.x, o.l.x, v.h.x, v.l.x, s.x, s.y);
-  df_fma(o.h.y, o.l.y, v.h.y, v.l.y, s.x, s.y);
+  f2p h = pk(o.h), l = pk(o.l);
+  df_fma2(h, l, pk(v.h), pk(v.l), pk(-v.h.x, -v.h.y), pk(s.x, s.x), pk(s.y, s.y));
+  o = dfc{upk(h), upk(l)};
 }
 __device__ __forceinline__ float nrm2f(dfc a) { return fmaf(a.h.x, a.h.x, a.h.y * a.h.y); }
 
