@@ -337,17 +337,18 @@ __global__ void k_build_bundle(DomInst d, const S* __restrict__ lk, unsigned cha
   io[dir * LB_LANES + lane] = j;
   S zero;
   memset(&zero, 0, sizeof(S));
+  // pairs e = 0..3 (entries 2e, 2e + 1) two elements per lane, entry 8 one
+  S* dl = lo + (long long)dir * LB_DIR_S;
   for (int e = 0; e < 5; ++e) {
-    S* dst = lo + ((long long)(dir * 5 + e) * LB_LANES + lane) * 2;
+    S* dst = e < 4 ? dl + (e * LB_LANES + lane) * 2 : dl + 4 * LB_LANES * 2 + lane;
+    const int ne = e < 4 ? 2 : 1;
     if (j < 0) {
-      dst[0] = zero;
-      dst[1] = zero;
+      for (int h = 0; h < ne; ++h) dst[h] = zero;
       continue;
     }
     const S* src = dir < 4 ? lk + link_block(p, mu, n0, n_out) + ((long long)e * n_out + i) * 2
                            : lk + link_block(1 - p, mu, n0, n_in) + ((long long)e * n_in + j) * 2;
-    dst[0] = src[0];
-    dst[1] = src[1];
+    for (int h = 0; h < ne; ++h) dst[h] = src[h];
   }
 }
 

@@ -120,15 +120,18 @@ __device__ __host__ __forceinline__ long long link_block(int p, int mu, long lon
 // LB_QUARTERS quarters of LB_LANES sites.  A quarter's bundle holds, for its
 // 32 output sites, the 8 links the hop multiplies with (forward: U_mu(x);
 // backward: U_mu(x - mu), stored undaggered) and the 8 neighbour indices:
-//     links [dir 8][pair 5][lane 32] x (2 S)   then   index [dir 8][lane 32] int
-// so one bulk copy brings a quarter into shared memory, and lanes read
-// consecutive 16-byte (FP32) or 8-byte (BF16) words.  Missing neighbours have
-// index -1 and zero links; lanes past the end of the parity likewise.
+//     links [dir 8]{ [pair 4][lane 32] x (2 S), [lane 32] x S }   then   index [dir 8][lane 32] int
+// (entries 0..7 of a link in pairs, entry 8 alone: 9 complex per link, no
+// padding), so one bulk copy brings a quarter into shared memory, and lanes
+// read consecutive 16- and 8-byte (FP32) or 8- and 4-byte (BF16) words.
+// Missing neighbours have index -1 and zero links; lanes past the end of the
+// parity likewise.
 constexpr int LB_LANES = 32;
 constexpr int LB_QUARTERS = 4;
 constexpr int LB_CHUNK = LB_LANES * LB_QUARTERS;
+constexpr int LB_DIR_S = 9 * LB_LANES;     // storage elements of one direction's links
 template <class S>
-__device__ __host__ constexpr int lb_link_bytes() { return 8 * 5 * LB_LANES * 2 * (int)sizeof(S); }
+__device__ __host__ constexpr int lb_link_bytes() { return 8 * LB_DIR_S * (int)sizeof(S); }
 template <class S>
 __device__ __host__ constexpr int lb_quarter_bytes() { return lb_link_bytes<S>() + 8 * LB_LANES * 4; }
 // number of quarters of parity p of an instance with n[0], n[1] sites

@@ -725,7 +725,7 @@ template <class S, class C>
 __device__ __forceinline__ void lds_link(const S* dirblk, int lane, C (&U)[9]) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) lds_pair(dirblk + (e * LB_LANES + lane) * 2, U[2 * e], U[2 * e + 1]);
-  U[8] = lds_c(dirblk + (4 * LB_LANES + lane) * 2);
+  U[8] = lds_c(dirblk + 4 * LB_LANES * 2 + lane);
 }
 
 // one direction of the hop for the RR rhs of a thread: the link is read from
@@ -739,7 +739,7 @@ __device__ __forceinline__ void hop_lb_dir(C (&acc)[RR][12], const int* qi, cons
   const int j = qi[DIR * LB_LANES + lane];
   if (j < 0) return;
   C U[9];
-  lds_link(ql + DIR * 5 * LB_LANES * 2, lane, U);
+  lds_link(ql + DIR * LB_DIR_S, lane, U);
 #pragma unroll
   for (int k = 0; k < RR; ++k) {
     if (!actk[k]) continue;
