@@ -56,7 +56,8 @@ __device__ __forceinline__ void df_renorm(float& h, float& l) {
 // The f32x2 forms of add, sub, mul and fma (round to nearest on each lane) run
 // the real and imaginary parts of a complex double-float through one
 // instruction stream: every lane performs the same operations in the same
-// order as the scalar primitives above, so the results are theirs.
+// order as the scalar primitives above, so the values are theirs (an exact
+// zero may differ in sign where x + (-y) is written x - y).
 typedef unsigned long long f2p;
 __device__ __forceinline__ f2p pk(float x, float y) {
   f2p r;
